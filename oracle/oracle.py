@@ -1,0 +1,343 @@
+"""Python view of the plain CPU oracle (oracle/bfv_oracle.c).
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+CPU-baseline / reference leg of bench.py may import this module.  It shares no
+code with the CUDA path (paper_2503_09184_gb300) and never imports it.
+
+Layouts: a ciphertext is a uint64 array [2][L][N] in coefficient form with
+canonical residues in [0, q_i) (c0 first, then c1).
+
+The encodings follow Sec. 3.3.2 of the paper ("Exploiting Unstructured
+Sparsity in Fully Homomorphic Encrypted DNNs"):
+  * naive dense (Alg. 1): every k of the shared dimension;
+  * naive sparse: a plaintext mask B_ik = [A_ik == 0], products skipped where
+    the mask is set (B is dense here, so only the left mask matters);
+  * CSR: nonzeros of each row with a row-pointer array and a column array;
+  * ELLPACK: each row holds j = max nonzeros-per-row slots, the nonzeros first
+    and encrypted zero padding after, with a parallel column matrix.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build_oracle
+
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build_oracle.build()
+        L = ctypes.CDLL(path)
+        L.or_is_prime.argtypes = [ctypes.c_uint64]
+        L.or_is_prime.restype = ctypes.c_int
+        L.or_ntt_primes.argtypes = [ctypes.c_int, ctypes.c_int, _u64p]
+        L.or_psi.argtypes = [ctypes.c_uint64, ctypes.c_int]
+        L.or_psi.restype = ctypes.c_uint64
+        L.or_ntt_naive.argtypes = [ctypes.c_uint64, ctypes.c_int, _u64p, _u64p]
+        L.or_intt_naive.argtypes = [ctypes.c_uint64, ctypes.c_int, _u64p, _u64p]
+        L.or_negacyclic.argtypes = [ctypes.c_uint64, ctypes.c_int, _u64p, _u64p, _u64p]
+        L.or_prng_word.argtypes = [ctypes.c_uint64] * 6
+        L.or_prng_word.restype = ctypes.c_uint64
+        L.or_cdt.argtypes = [ctypes.c_double, _u64p]
+        L.or_ctx_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_double, ctypes.c_uint64]
+        L.or_ctx_create.restype = ctypes.c_void_p
+        L.or_ctx_free.argtypes = [ctypes.c_void_p]
+        L.or_ctx_info.argtypes = [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 4 + [_u64p] * 3
+        L.or_get_secret.argtypes = [ctypes.c_void_p, _i64p]
+        L.or_get_rlk.argtypes = [ctypes.c_void_p, _u64p]
+        L.or_get_cdt.argtypes = [ctypes.c_void_p, _u64p]
+        L.or_get_delta.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_int]
+        L.or_encrypt.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _u64p]
+        L.or_encrypt.restype = ctypes.c_int
+        L.or_decrypt.argtypes = [ctypes.c_void_p, _u64p, _i64p, ctypes.POINTER(ctypes.c_int)]
+        L.or_tensor_scale.argtypes = [ctypes.c_void_p, _u64p, _u64p, _u64p]
+        L.or_relin.argtypes = [ctypes.c_void_p, _u64p, _u64p]
+        L.or_mul_relin.argtypes = [ctypes.c_void_p, _u64p, _u64p, _u64p]
+        L.or_add.argtypes = [ctypes.c_void_p, _u64p, _u64p]
+        L.or_matmul_entries.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(_u64p), ctypes.POINTER(_u64p), _u64p, ctypes.c_int]
+        L.or_num_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    if a.dtype == np.uint64:
+        return a.ctypes.data_as(_u64p)
+    if a.dtype == np.int64:
+        return a.ctypes.data_as(_i64p)
+    raise TypeError(a.dtype)
+
+
+def is_prime(n: int) -> bool:
+    return bool(lib().or_is_prime(n))
+
+
+def ntt_primes(N: int, count: int) -> list[int]:
+    out = np.zeros(count, dtype=np.uint64)
+    if lib().or_ntt_primes(N, count, _p(out)) != 0:
+        raise ValueError("not enough primes")
+    return [int(x) for x in out]
+
+
+def psi(q: int, N: int) -> int:
+    return int(lib().or_psi(q, N))
+
+
+def ntt_naive(q: int, a: np.ndarray) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    out = np.zeros_like(a)
+    lib().or_ntt_naive(q, a.size, _p(a), _p(out))
+    return out
+
+
+def intt_naive(q: int, a: np.ndarray) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    out = np.zeros_like(a)
+    lib().or_intt_naive(q, a.size, _p(a), _p(out))
+    return out
+
+
+def negacyclic(m: int, a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    b = np.ascontiguousarray(b, dtype=np.uint64)
+    out = np.zeros_like(a)
+    lib().or_negacyclic(m, a.size, _p(a), _p(b), _p(out))
+    return out
+
+
+def prng_word(seed: int, domain: int, o0: int, o1: int, o2: int, idx: int) -> int:
+    return int(lib().or_prng_word(seed, domain, o0, o1, o2, idx))
+
+
+def cdt(sigma: float = 3.2) -> list[int]:
+    T = np.zeros(20, dtype=np.uint64)
+    lib().or_cdt(sigma, _p(T))
+    return [int(x) for x in T]
+
+
+def num_threads() -> int:
+    return int(lib().or_num_threads())
+
+
+class OracleCtx:
+    """Keys and per-ciphertext operations of the oracle (coefficient form)."""
+
+    def __init__(self, N: int, L: int, t: int = 65537, sigma: float = 3.2, seed: int = 0):
+        self._h = lib().or_ctx_create(N, L, t, sigma, seed)
+        if not self._h:
+            raise ValueError("oracle context creation failed")
+        n, l, nP, nA = (ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int())
+        q = np.zeros(16, dtype=np.uint64)
+        p = np.zeros(17, dtype=np.uint64)
+        aux = np.zeros(48, dtype=np.uint64)
+        lib().or_ctx_info(self._h, ctypes.byref(n), ctypes.byref(l), ctypes.byref(nP), ctypes.byref(nA),
+                          _p(q), _p(p), _p(aux))
+        self.N, self.L, self.t, self.seed, self.sigma = N, L, t, seed, sigma
+        self.q = [int(x) for x in q[:L]]
+        self.p = [int(x) for x in p[:nP.value]]
+        self.aux = [int(x) for x in aux[:nA.value]]
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().or_ctx_free(h)
+            self._h = None
+
+    @property
+    def ct_shape(self):
+        return (2, self.L, self.N)
+
+    def secret(self) -> np.ndarray:
+        s = np.zeros(self.N, dtype=np.int64)
+        lib().or_get_secret(self._h, _p(s))
+        return s
+
+    def rlk(self) -> np.ndarray:
+        """[L digit][2 (b, a)][L limb][N]"""
+        out = np.zeros((self.L, 2, self.L, self.N), dtype=np.uint64)
+        lib().or_get_rlk(self._h, _p(out))
+        return out
+
+    def cdt(self) -> list[int]:
+        T = np.zeros(20, dtype=np.uint64)
+        lib().or_get_cdt(self._h, _p(T))
+        return [int(x) for x in T]
+
+    def delta(self) -> int:
+        w = np.zeros(18, dtype=np.uint64)
+        lib().or_get_delta(self._h, _p(w), 18)
+        return sum(int(x) << (64 * i) for i, x in enumerate(w))
+
+    def encrypt(self, m: int, matrix_id: int, row: int, col: int) -> np.ndarray:
+        ct = np.zeros(self.ct_shape, dtype=np.uint64)
+        if lib().or_encrypt(self._h, int(m), matrix_id, row, col, _p(ct)) != 0:
+            raise RuntimeError("sampling failed")
+        return ct
+
+    def decrypt(self, ct: np.ndarray) -> tuple[int, int]:
+        ct = np.ascontiguousarray(ct, dtype=np.uint64)
+        m = ctypes.c_int64()
+        nb = ctypes.c_int()
+        lib().or_decrypt(self._h, _p(ct), ctypes.byref(m), ctypes.byref(nb))
+        return int(m.value), int(nb.value)
+
+    def tensor_scale(self, a: np.ndarray, b: np.ndarray) -> np.ndarray:
+        """(d0, d1, d2) after the exact scale-and-round, [3][L][N]."""
+        a = np.ascontiguousarray(a, dtype=np.uint64)
+        b = np.ascontiguousarray(b, dtype=np.uint64)
+        d = np.zeros((3, self.L, self.N), dtype=np.uint64)
+        lib().or_tensor_scale(self._h, _p(a), _p(b), _p(d))
+        return d
+
+    def relin(self, d: np.ndarray) -> np.ndarray:
+        d = np.ascontiguousarray(d, dtype=np.uint64)
+        out = np.zeros(self.ct_shape, dtype=np.uint64)
+        lib().or_relin(self._h, _p(d), _p(out))
+        return out
+
+    def mul_relin(self, a: np.ndarray, b: np.ndarray) -> np.ndarray:
+        a = np.ascontiguousarray(a, dtype=np.uint64)
+        b = np.ascontiguousarray(b, dtype=np.uint64)
+        out = np.zeros(self.ct_shape, dtype=np.uint64)
+        lib().or_mul_relin(self._h, _p(a), _p(b), _p(out))
+        return out
+
+    def add_(self, acc: np.ndarray, x: np.ndarray) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.uint64)
+        lib().or_add(self._h, _p(acc), _p(x))
+        return acc
+
+    def matmul_entries(self, entries, a_list, b_list, nthreads: int = 0) -> np.ndarray:
+        """Paper's multithreaded scheme (Sec. 3.4): entries = [(row, col, first, count)],
+        products first..first+count-1 of the flat lists a_list / b_list."""
+        ent = np.ascontiguousarray(np.asarray(entries, dtype=np.int32).reshape(-1, 4))
+        a_arr = (_u64p * len(a_list))(*[_p(a) for a in a_list])
+        b_arr = (_u64p * len(b_list))(*[_p(b) for b in b_list])
+        out = np.zeros((ent.shape[0],) + self.ct_shape, dtype=np.uint64)
+        lib().or_matmul_entries(self._h, ent.shape[0], ent.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                a_arr, b_arr, _p(out), nthreads)
+        return out
+
+
+# ---------------------------------------------------------------------------
+# sparse encodings (Sec. 3.3.2) and the product sets they list
+# ---------------------------------------------------------------------------
+DENSE, MASK, CSR, ELL = 0, 1, 2, 3
+ENCODINGS = {"dense": DENSE, "mask": MASK, "csr": CSR, "ell": ELL}
+
+
+@dataclass
+class Encoded:
+    """Plaintext structure of an encoded left operand and the (row, col)
+    coordinates of the element each stored ciphertext encrypts."""
+    encoding: int
+    rows: int
+    cols: int
+    values: list          # plaintext value of every stored ciphertext
+    coords: list          # (row, col) stream coordinates of every stored ciphertext
+    mask: np.ndarray | None = None       # naive sparse: 1 where A == 0
+    row_ptr: np.ndarray | None = None    # CSR
+    col_idx: np.ndarray | None = None    # CSR
+    ell_col: np.ndarray | None = None    # ELLPACK, -1 marks padding
+    width: int = 0                       # ELLPACK slots per row
+
+
+def encode(A: np.ndarray, encoding: int) -> Encoded:
+    A = np.asarray(A, dtype=np.int64)
+    M, K = A.shape
+    if encoding in (DENSE, MASK):
+        coords = [(i, k) for i in range(M) for k in range(K)]
+        vals = [int(A[i, k]) for i, k in coords]
+        mask = (A == 0).astype(np.uint8) if encoding == MASK else None
+        return Encoded(encoding, M, K, vals, coords, mask=mask)
+    if encoding == CSR:
+        row_ptr = [0]
+        col_idx, vals, coords = [], [], []
+        for i in range(M):
+            for k in range(K):
+                if A[i, k] != 0:
+                    col_idx.append(k)
+                    vals.append(int(A[i, k]))
+                    coords.append((i, k))
+            row_ptr.append(len(col_idx))
+        return Encoded(encoding, M, K, vals, coords, row_ptr=np.array(row_ptr, dtype=np.int32),
+                       col_idx=np.array(col_idx, dtype=np.int32))
+    if encoding == ELL:
+        width = max([int(np.count_nonzero(A[i])) for i in range(M)] + [0])
+        ell_col = -np.ones((M, width), dtype=np.int32)
+        vals, coords = [], []
+        for i in range(M):
+            nz = [k for k in range(K) if A[i, k] != 0]
+            for s in range(width):
+                if s < len(nz):
+                    ell_col[i, s] = nz[s]
+                    vals.append(int(A[i, nz[s]]))
+                    coords.append((i, nz[s]))
+                else:  # encrypted zero padding; its stream column is K + slot
+                    vals.append(0)
+                    coords.append((i, K + s))
+        return Encoded(encoding, M, K, vals, coords, ell_col=ell_col, width=width)
+    raise ValueError(encoding)
+
+
+def product_set(enc: Encoded, i: int) -> list[tuple[int, int]]:
+    """(stored ciphertext index, k) pairs Alg. 1's k-loop visits for row i."""
+    if enc.encoding == DENSE:
+        return [(i * enc.cols + k, k) for k in range(enc.cols)]
+    if enc.encoding == MASK:
+        return [(i * enc.cols + k, k) for k in range(enc.cols) if not enc.mask[i, k]]
+    if enc.encoding == CSR:
+        return [(t, int(enc.col_idx[t])) for t in range(enc.row_ptr[i], enc.row_ptr[i + 1])]
+    if enc.encoding == ELL:
+        return [(i * enc.width + s, int(enc.ell_col[i, s])) for s in range(enc.width) if enc.ell_col[i, s] >= 0]
+    raise ValueError(enc.encoding)
+
+
+class OracleMatmul:
+    """Encrypts plaintext operands and evaluates entries of C = A x B.
+
+    Ciphertexts are encrypted once per stream coordinate and reused, and each
+    product Relin(A[i][k] x B[k][j]) is computed once and shared by every
+    encoding that lists it (the encryption of an element depends only on its
+    coordinates, so all encodings multiply the same ciphertexts)."""
+
+    def __init__(self, ctx: OracleCtx, A: np.ndarray, B: np.ndarray, a_id: int, b_id: int):
+        self.ctx, self.A, self.B, self.a_id, self.b_id = ctx, np.asarray(A), np.asarray(B), a_id, b_id
+        self._ct = {}
+        self._prod = {}
+
+    def ct_a(self, row: int, col: int) -> np.ndarray:
+        key = ("a", row, col)
+        if key not in self._ct:
+            v = int(self.A[row, col]) if col < self.A.shape[1] else 0
+            self._ct[key] = self.ctx.encrypt(v, self.a_id, row, col)
+        return self._ct[key]
+
+    def ct_b(self, row: int, col: int) -> np.ndarray:
+        key = ("b", row, col)
+        if key not in self._ct:
+            self._ct[key] = self.ctx.encrypt(int(self.B[row, col]), self.b_id, row, col)
+        return self._ct[key]
+
+    def product(self, i: int, k: int, j: int) -> np.ndarray:
+        key = (i, k, j)
+        if key not in self._prod:
+            self._prod[key] = self.ctx.mul_relin(self.ct_a(i, k), self.ct_b(k, j))
+        return self._prod[key]
+
+    def entry(self, enc: Encoded, i: int, j: int) -> np.ndarray:
+        """C[i][j]: the trivial zero ciphertext plus every listed product."""
+        acc = np.zeros(self.ctx.ct_shape, dtype=np.uint64)
+        for _, k in product_set(enc, i):
+            self.ctx.add_(acc, self.product(i, k, j))
+        return acc
