@@ -1,0 +1,216 @@
+/*
+ * sfhe.h -- C ABI of the GB300 encrypted sparse matrix multiplication.
+ *
+ * The operation is the paper's encrypted matrix product (Ferguson et al.,
+ * "Exploiting Unstructured Sparsity in Fully Homomorphic Encrypted DNNs",
+ * Alg. 1 and Sec. 3.3): C[i][j] = sum over k of Relin(A[i][k] x B[k][j]),
+ * every matrix element encrypted in its own ciphertext (chunk size c = 1),
+ * with the k-loop running over every k (naive dense) or only over the
+ * nonzeros of A listed by one of the three sparse encodings (naive sparse
+ * mask, CSR, ELLPACK; Sec. 3.3.2).  The scheme is RNS BFV: ring
+ * Z[X]/(X^N + 1), ciphertext modulus Q = q_0 ... q_{L-1} (the L largest
+ * primes below 2^54 with q = 1 mod 2N), plaintext modulus t, ternary secret,
+ * rounded Gaussian errors, relinearisation key with one digit per prime.
+ * Each message is placed in the constant coefficient.
+ *
+ * Conventions for every entry point:
+ *  - Status codes only; no exception crosses the ABI.  sfhe_last_error()
+ *    returns a message for the calling thread's last failure.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on it unless stated; arguments are
+ *    validated on the host before anything is launched.
+ *  - "device" pointers are CUDA device memory owned by the caller (for
+ *    example torch tensors); "host" pointers are ordinary host memory owned
+ *    by the caller and only read during the call.  The library owns only
+ *    what an sfhe_ctx or sfhe_plan handle holds.
+ *  - Ciphertext layouts (uint64 words, canonical residues):
+ *      ciphertext  [2 (c0, c1)][L][N], NTT form (slot i = evaluation at
+ *                  psi^(2 bitrev(i) + 1), psi the smallest primitive 2N-th
+ *                  root of unity mod the limb's prime);
+ *      lifted      [2][L + Lp][N], NTT form over Q u P (Lp = L + 1
+ *                  extension primes, the next primes of the same rule);
+ *      coefficient [2][L][N] in coefficient form (sfhe_to_coeff).
+ */
+#ifndef SFHE_H
+#define SFHE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SFHE_OK = 0,
+    SFHE_EINVAL = 1,       /* malformed argument (null pointer, bad index array) */
+    SFHE_ESHAPE = 2,       /* operand shapes do not match */
+    SFHE_ENOMEM = 3,       /* device allocation failed or workspace too small */
+    SFHE_ECUDA = 4,        /* a CUDA runtime call failed */
+    SFHE_ETIMEOUT = 5,     /* reserved: a bounded device wait gave up */
+    SFHE_EBUDGET = 6,      /* reserved: request over a memory budget */
+    SFHE_EUNSUPPORTED = 7, /* parameters outside what the kernels implement */
+    SFHE_EDEVICE = 8       /* a kernel reported a failure through the status word */
+} sfhe_status;
+
+/* Sec. 3.3: naive dense (Alg. 1), naive sparse (plaintext zero mask), CSR, ELLPACK */
+typedef enum { SFHE_ENC_DENSE = 0, SFHE_ENC_MASK = 1, SFHE_ENC_CSR = 2, SFHE_ENC_ELL = 3 } sfhe_encoding;
+
+/* execution modes of a matmul */
+enum {
+    SFHE_EXEC_PLAIN = 1,      /* one short launch sequence per ciphertext product */
+    SFHE_EXEC_PERSISTENT = 2, /* all products of all matmuls in one persistent launch */
+    SFHE_EXEC_GRAPH = 4       /* with PERSISTENT: replay the launch as a CUDA graph */
+};
+
+typedef struct {
+    uint32_t N;    /* ring degree: 4096, 8192 or 16384 */
+    uint32_t L;    /* ciphertext primes: 2, 3, 4 or 8 */
+    uint64_t t;    /* plaintext modulus, 2 <= t < 2^32 */
+    double sigma;  /* error width; the rounded Gaussian is cut at 19 */
+} sfhe_params;
+
+typedef struct {
+    uint32_t N, L, Lp;
+    uint64_t t;
+    uint64_t q[8];          /* ciphertext primes, descending */
+    uint64_t p[9];          /* extension primes, descending */
+    uint64_t ct_words;      /* 2 L N */
+    uint64_t ext_words;     /* 2 (L + Lp) N */
+    int32_t num_sms;
+} sfhe_info;
+
+typedef struct sfhe_ctx sfhe_ctx;
+typedef struct sfhe_plan sfhe_plan;
+
+/*
+ * Encoded left or right operand (Sec. 3.3.2).  Plaintext structure arrays
+ * are host memory; ciphertext storage is device memory.
+ *   DENSE: nct = rows*cols, ciphertext r*cols + c encrypts element (r, c).
+ *   MASK:  as DENSE plus mask[rows*cols], 1 where the element is zero
+ *          (B_ik = [M_ik = 0]); products with a set mask are skipped.
+ *   CSR:   row_ptr[rows+1], col_idx[nct]; ciphertext t encrypts the t-th
+ *          nonzero in row-major order.
+ *   ELL:   ell_width slots per row, ell_col[rows*ell_width] (-1 = padding);
+ *          ciphertext r*ell_width + s encrypts slot s of row r (padding slots
+ *          hold encryptions of zero and are skipped).
+ * `ct` [nct][2][L][N] and `ext` [nct][2][L+Lp][N] are device buffers; the
+ * matmul reads `ext` of A and B (fill it with sfhe_lift) and writes `ct`
+ * of C (which must be DENSE, rows*cols ciphertexts).
+ */
+typedef struct {
+    int32_t rows, cols, encoding, nct, ell_width;
+    const uint8_t* mask;
+    const int32_t* row_ptr;
+    const int32_t* col_idx;
+    const int32_t* ell_col;
+    uint64_t* ct;
+    uint64_t* ext;
+} sfhe_matrix;
+
+/* ------------------------------------------------------------ context --- */
+/* Parameters and keys.  Selects the primes, builds the NTT and base
+ * conversion tables, and runs key generation on the current device from
+ * `seed` (secret and relinearisation key never leave the device unless
+ * exported).  Synchronous.  Errors: EINVAL (null), EUNSUPPORTED (N, L or t
+ * outside the list above), ECUDA / ENOMEM (device), EDEVICE (sampling). */
+sfhe_status sfhe_ctx_create(const sfhe_params* params, uint64_t seed, sfhe_ctx** out);
+void sfhe_ctx_destroy(sfhe_ctx* ctx);
+sfhe_status sfhe_ctx_info(const sfhe_ctx* ctx, sfhe_info* out);
+/* Synchronises `stream` and reads the context's device status word (set by
+ * encryption / key generation when a sampler exhausted its retries). */
+sfhe_status sfhe_ctx_check(sfhe_ctx* ctx, void* stream);
+const char* sfhe_last_error(void);
+
+/* Host-only helpers (no device needed).  Primes: the L largest primes below
+ * 2^54 that are 1 mod 2N, then the next L+1 (deterministic Miller-Rabin with
+ * the bases 2..37).  CDT: T[k] = floor(2^63 P(|e| <= k)) of the rounded
+ * Gaussian of width sigma, k < 19, T[19] = 2^63. */
+sfhe_status sfhe_select_primes(uint32_t N, uint32_t L, uint64_t* q, uint64_t* p);
+sfhe_status sfhe_cdt_table(double sigma, uint64_t* T20);
+
+/* ---------------------------------------------------------- operands --- */
+/* Structure of a plaintext matrix (host values[rows*cols], row-major) under
+ * an encoding: fills *nct and *ell_width. */
+sfhe_status sfhe_encode_count(const int64_t* values, int32_t rows, int32_t cols, int32_t encoding, int32_t* nct,
+                              int32_t* ell_width);
+/* Fills the structure arrays (each may be NULL when the encoding has none)
+ * and, per stored ciphertext, the value it encrypts (ct_values[nct]) and its
+ * stream coordinates (ct_coords[2*nct]: row, col; ELL padding slot s of row
+ * r has col = cols + s). */
+sfhe_status sfhe_encode_fill(const int64_t* values, int32_t rows, int32_t cols, int32_t encoding, uint8_t* mask,
+                             int32_t* row_ptr, int32_t* col_idx, int32_t* ell_col, int64_t* ct_values,
+                             int32_t* ct_coords);
+
+/* Secret-key encryption: ct[n] (device, [n][2][L][N], NTT form) encrypts
+ * values[n] (host) in the constant coefficient; the randomness of
+ * ciphertext n is drawn from the stream (matrix_id, coords[2n], coords[2n+1]). */
+sfhe_status sfhe_encrypt(sfhe_ctx* ctx, const int64_t* values, const int32_t* coords, int64_t n, uint64_t matrix_id,
+                         uint64_t* ct, void* stream);
+/* Exact centred extension to Q u P: ext[n] (device) from ct[n] (device).
+ * Needs sfhe_lift_workspace_size() bytes of device workspace. */
+sfhe_status sfhe_lift_workspace_size(const sfhe_ctx* ctx, int64_t n, size_t* bytes);
+sfhe_status sfhe_lift(sfhe_ctx* ctx, const uint64_t* ct, int64_t n, uint64_t* ext, void* work, size_t work_bytes,
+                      void* stream);
+/* Decryption of the constant coefficient of ct[n] (device) into out[n]
+ * (device int64), centred in (-t/2, t/2]. */
+sfhe_status sfhe_decrypt(sfhe_ctx* ctx, const uint64_t* ct, int64_t n, int64_t* out, void* stream);
+/* NTT form <-> coefficient form of npoly ciphertext polynomials laid out
+ * as [npoly][L][N] (a ciphertext is two of them: npoly = 2 n). */
+sfhe_status sfhe_to_coeff(sfhe_ctx* ctx, const uint64_t* in, int64_t npoly, uint64_t* out, void* stream);
+sfhe_status sfhe_from_coeff(sfhe_ctx* ctx, const uint64_t* in, int64_t npoly, uint64_t* out, void* stream);
+/* Keys in coefficient form: secret (host int8[N]); relinearisation key
+ * (device [L digit][2 (b, a)][L limb][N]). */
+sfhe_status sfhe_export_secret(sfhe_ctx* ctx, int8_t* s_host);
+sfhe_status sfhe_export_relin_key(sfhe_ctx* ctx, uint64_t* out, void* stream);
+
+/* ------------------------------------------------------------ matmul --- */
+/* Workspace (device bytes) for n matmuls A[m] x B[m] under `flags`. */
+sfhe_status sfhe_matmul_workspace_size(const sfhe_ctx* ctx, int32_t n, const sfhe_matrix* A, const sfhe_matrix* B,
+                                       uint32_t flags, size_t* bytes);
+/* C = A x B with the k-loop over every k (A must be DENSE-encoded). */
+sfhe_status sfhe_matmul_dense(sfhe_ctx* ctx, const sfhe_matrix* A, const sfhe_matrix* B, sfhe_matrix* C, uint32_t flags,
+                              void* work, size_t work_bytes, void* stream);
+/* C = A x B with the k-loop over the nonzeros of A as `encoding` lists them
+ * (A must carry that encoding; EINVAL otherwise). */
+sfhe_status sfhe_matmul_sparse(sfhe_ctx* ctx, const sfhe_matrix* A, const sfhe_matrix* B, int32_t encoding,
+                               sfhe_matrix* C, uint32_t flags, void* work, size_t work_bytes, void* stream);
+/* n independent matmuls C[m] = A[m] x B[m] (each A in its own encoding) in
+ * one execution. */
+sfhe_status sfhe_matmul_batch(sfhe_ctx* ctx, int32_t n, const sfhe_matrix* A, const sfhe_matrix* B, sfhe_matrix* C,
+                              uint32_t flags, void* work, size_t work_bytes, void* stream);
+
+/* Plans: the work list is built and uploaded once (into `work`), then
+ * sfhe_plan_execute only launches (with SFHE_EXEC_GRAPH, one graph launch),
+ * so it can be replayed and captured.  The plan keeps the pointers of A, B,
+ * C and `work`; they must stay valid until sfhe_plan_destroy. */
+sfhe_status sfhe_plan_create(sfhe_ctx* ctx, int32_t n, const sfhe_matrix* A, const sfhe_matrix* B, sfhe_matrix* C,
+                             uint32_t flags, void* work, size_t work_bytes, void* stream, sfhe_plan** out);
+sfhe_status sfhe_plan_execute(sfhe_plan* plan, void* stream);
+/* products performed, output entries, own kernel launches per execute, CTAs */
+sfhe_status sfhe_plan_stats(const sfhe_plan* plan, int64_t* products, int64_t* entries, int64_t* launches,
+                            int64_t* ctas);
+void sfhe_plan_destroy(sfhe_plan* plan);
+
+/* ------------------------------------------------- stage entry points --- */
+/* One product's tensor and exact scale-and-round: d[3][L][N] coefficient
+ * form from lifted a, b (device).  Workspace: 3 (L+Lp) N words. */
+sfhe_status sfhe_ct_tensor_scale(sfhe_ctx* ctx, const uint64_t* a_ext, const uint64_t* b_ext, uint64_t* d, void* work,
+                                 size_t work_bytes, void* stream);
+/* One product multiplied and relinearised, NTT form [2][L][N] (plain path).
+ * Workspace: (3 (L+Lp) + 3 L + (L+2) L) N words. */
+sfhe_status sfhe_ct_mul_relin(sfhe_ctx* ctx, const uint64_t* a_ext, const uint64_t* b_ext, uint64_t* out, void* work,
+                              size_t work_bytes, void* stream);
+/* Forward / inverse NTT of npoly polynomials (device, [npoly][N]) modulo
+ * prime `prime_index` (0..L-1: q_i, L..L+Lp-1: p_j). */
+sfhe_status sfhe_ntt(sfhe_ctx* ctx, int32_t prime_index, int32_t inverse, const uint64_t* in, int64_t npoly,
+                     uint64_t* out, void* stream);
+/* Words idx0 .. idx0+n-1 of the generator stream (seed, domain, o0, o1, o2)
+ * into out (device). */
+sfhe_status sfhe_prng_words(uint64_t seed, uint32_t domain, uint64_t o0, uint64_t o1, uint64_t o2, uint64_t idx0,
+                            int64_t n, uint64_t* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFHE_H */

@@ -1,0 +1,198 @@
+"""Convenience layer over the C ABI: contexts, encrypted matrices held in
+torch device tensors, matmul plans.  Argument marshalling only; all
+arithmetic runs in libsfhe.so's kernels."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import sfhe as S
+
+PLAIN, PERSISTENT, GRAPH = S.SFHE_EXEC_PLAIN, S.SFHE_EXEC_PERSISTENT, S.SFHE_EXEC_GRAPH
+
+
+def _dev_u64(shape) -> torch.Tensor:
+    """uint64 words in an int64 device tensor (same bits)."""
+    return torch.empty(shape, dtype=torch.int64, device="cuda")
+
+
+def to_numpy_u64(t: torch.Tensor) -> np.ndarray:
+    return t.detach().cpu().numpy().view(np.uint64)
+
+
+class Context:
+    def __init__(self, N: int, L: int, t: int = 65537, sigma: float = 3.2, seed: int = 0):
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.h = S.sfhe_ctx_create(N, L, t, sigma, seed)
+        info = S.sfhe_ctx_info(self.h)
+        self.N, self.L, self.Lp, self.t = info.N, info.L, info.Lp, info.t
+        self.q = [int(x) for x in info.q[: self.L]]
+        self.p = [int(x) for x in info.p[: self.Lp]]
+        self.ct_words, self.ext_words, self.num_sms = int(info.ct_words), int(info.ext_words), info.num_sms
+        self.seed = seed
+
+    def close(self):
+        if getattr(self, "h", None):
+            S.sfhe_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, stream=None):
+        S.sfhe_ctx_check(self.h, stream)
+
+
+class EncMatrix:
+    """An encoded, encrypted matrix: host structure arrays + device storage."""
+
+    def __init__(self, rows, cols, encoding, nct, ell_width=0, mask=None, row_ptr=None, col_idx=None, ell_col=None,
+                 ct=None, ext=None):
+        self.rows, self.cols, self.encoding, self.nct, self.ell_width = rows, cols, encoding, nct, ell_width
+        self.mask, self.row_ptr, self.col_idx, self.ell_col = mask, row_ptr, col_idx, ell_col
+        self.ct, self.ext = ct, ext
+
+    def desc(self) -> S.sfhe_matrix:
+        def p(a):
+            return None if a is None else S._ptr(a)
+        return S.sfhe_matrix(self.rows, self.cols, self.encoding, self.nct, self.ell_width, p(self.mask),
+                              p(self.row_ptr), p(self.col_idx), p(self.ell_col), p(self.ct), p(self.ext))
+
+    def bytes(self) -> int:
+        n = 0
+        for t in (self.ct, self.ext):
+            if t is not None:
+                n += t.numel() * 8
+        return n
+
+
+def encrypt_matrix(ctx: Context, values: np.ndarray, encoding: int | str, matrix_id: int, lift: bool = True,
+                   stream=None) -> EncMatrix:
+    if isinstance(encoding, str):
+        encoding = S.ENCODINGS[encoding]
+    values = np.ascontiguousarray(values, dtype=np.int64)
+    rows, cols = values.shape
+    f = S.sfhe_encode_fill(values, encoding)
+    nct = f["nct"]
+    M = EncMatrix(rows, cols, encoding, nct, f["ell_width"], f["mask"], f["row_ptr"], f["col_idx"], f["ell_col"])
+    M.ct = _dev_u64((max(nct, 1), 2, ctx.L, ctx.N))
+    S.sfhe_encrypt(ctx.h, f["ct_values"], f["ct_coords"], matrix_id, M.ct, stream)
+    if lift:
+        lift_matrix(ctx, M, stream)
+    return M
+
+
+def lift_matrix(ctx: Context, M: EncMatrix, stream=None):
+    M.ext = _dev_u64((max(M.nct, 1), 2, ctx.L + ctx.Lp, ctx.N))
+    if M.nct:
+        work = torch.empty(S.sfhe_lift_workspace_size(ctx.h, M.nct), dtype=torch.uint8, device="cuda")
+        S.sfhe_lift(ctx.h, M.ct, M.nct, M.ext, work, stream)
+        # keep the workspace alive until the stream has consumed it
+        (torch.cuda.current_stream() if stream is None else stream).synchronize()
+
+
+def result_matrix(ctx: Context, rows: int, cols: int) -> EncMatrix:
+    C = EncMatrix(rows, cols, S.SFHE_ENC_DENSE, rows * cols)
+    C.ct = _dev_u64((max(rows * cols, 1), 2, ctx.L, ctx.N))
+    return C
+
+
+def import_coeff(ctx: Context, coeff: np.ndarray, lift: bool = True, stream=None) -> EncMatrix:
+    """Ciphertexts given in coefficient form [n][2][L][N] as a 1 x n DENSE row."""
+    coeff = np.ascontiguousarray(coeff, dtype=np.uint64)
+    n = coeff.shape[0]
+    src = torch.from_numpy(coeff.view(np.int64)).cuda()
+    M = EncMatrix(1, n, S.SFHE_ENC_DENSE, n)
+    M.ct = _dev_u64(coeff.shape)
+    S.sfhe_from_coeff(ctx.h, src, 2 * n, M.ct, stream)
+    if lift:
+        lift_matrix(ctx, M, stream)
+    return M
+
+
+def to_coeff(ctx: Context, ct: torch.Tensor, n: int, stream=None) -> np.ndarray:
+    out = _dev_u64((n, 2, ctx.L, ctx.N))
+    S.sfhe_to_coeff(ctx.h, ct, 2 * n, out, stream)
+    return to_numpy_u64(out)
+
+
+def decrypt(ctx: Context, M: EncMatrix, stream=None) -> np.ndarray:
+    out = torch.empty(max(M.nct, 1), dtype=torch.int64, device="cuda")
+    S.sfhe_decrypt(ctx.h, M.ct, M.nct, out, stream)
+    vals = out.cpu().numpy()[: M.nct]
+    if M.encoding in (S.SFHE_ENC_DENSE, S.SFHE_ENC_MASK):
+        return vals.reshape(M.rows, M.cols)
+    return vals
+
+
+def _flags(mode: str, graph: bool = False) -> int:
+    f = PERSISTENT if mode == "persistent" else PLAIN
+    return f | (GRAPH if graph else 0)
+
+
+def workspace(ctx: Context, As, Bs, flags: int) -> torch.Tensor:
+    n = S.sfhe_matmul_workspace_size(ctx.h, [a.desc() for a in As], [b.desc() for b in Bs], flags)
+    return torch.empty(max(n, 256), dtype=torch.uint8, device="cuda")
+
+
+def matmul(ctx: Context, A: EncMatrix, B: EncMatrix, *, dense: bool = False, mode: str = "persistent",
+           stream=None, work: torch.Tensor | None = None) -> EncMatrix:
+    """C = A x B: the dense loop (Alg. 1) or the loop over A's nonzeros as
+    A's encoding lists them."""
+    C = result_matrix(ctx, A.rows, B.cols)
+    dense = dense or A.encoding == S.SFHE_ENC_DENSE
+    flags = _flags(mode)
+    if work is None:
+        work = workspace(ctx, [A], [B], flags)
+    Ad, Bd, Cd = A.desc(), B.desc(), C.desc()
+    if dense:
+        S.sfhe_matmul_dense(ctx.h, Ad, Bd, Cd, flags, work, stream)
+    else:
+        S.sfhe_matmul_sparse(ctx.h, Ad, Bd, A.encoding, Cd, flags, work, stream)
+    C._work = work
+    return C
+
+
+def matmul_batch(ctx: Context, As, Bs, *, mode: str = "persistent", stream=None) -> list[EncMatrix]:
+    Cs = [result_matrix(ctx, a.rows, b.cols) for a, b in zip(As, Bs)]
+    flags = _flags(mode)
+    work = workspace(ctx, As, Bs, flags)
+    S.sfhe_matmul_batch(ctx.h, [a.desc() for a in As], [b.desc() for b in Bs], [c.desc() for c in Cs], flags, work,
+                        stream)
+    for c in Cs:
+        c._work = work
+    return Cs
+
+
+class Plan:
+    """A matmul plan (work list uploaded once); execute() only launches."""
+
+    def __init__(self, ctx: Context, As, Bs, *, mode: str = "persistent", graph: bool = False, stream=None,
+                 Cs=None):
+        self.ctx = ctx
+        self.As, self.Bs = list(As), list(Bs)
+        self.Cs = Cs if Cs is not None else [result_matrix(ctx, a.rows, b.cols) for a, b in zip(As, Bs)]
+        flags = _flags(mode, graph)
+        self.work = workspace(ctx, self.As, self.Bs, flags)
+        self.h = S.sfhe_plan_create(ctx.h, [a.desc() for a in self.As], [b.desc() for b in self.Bs],
+                                    [c.desc() for c in self.Cs], flags, self.work, stream)
+        self.stats = S.sfhe_plan_stats(self.h)
+
+    def execute(self, stream=None):
+        S.sfhe_plan_execute(self.h, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            torch.cuda.synchronize()
+            S.sfhe_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

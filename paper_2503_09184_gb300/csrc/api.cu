@@ -1,0 +1,832 @@
+// api.cu -- the C ABI (include/sfhe.h): contexts, operands, matmul plans.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/sfhe.h"
+#include "host_math.h"
+#include "launch.h"
+
+using namespace sfhe;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+sfhe_status fail(sfhe_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+#define CUDA_TRY(expr)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess) return fail(SFHE_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+inline cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct sfhe_ctx {
+    sfhe_params params;
+    uint64_t seed;
+    int device;
+    int num_sms;
+    RnsConsts rc;
+    u64* d_tw;
+    u64* d_s;
+    signed char* d_s_coeff;
+    u64* d_rlk;
+    u64* d_rlk_sh;
+    int* d_err;
+};
+
+struct sfhe_plan {
+    sfhe_ctx* ctx;
+    uint32_t flags;
+    std::vector<MmDesc> mms;
+    std::vector<Entry> entries;
+    std::vector<int2> rowlist;
+    std::vector<size_t> c_words;  // per matmul: words of C
+    int64_t products;
+    // device regions inside the caller's workspace
+    unsigned* d_queue;
+    MmDesc* d_mms;
+    Entry* d_entries;
+    int2* d_rowlist;
+    u64* d_scratch;
+    size_t scratch_stride;
+    int grid;
+    u64 *d_T, *d_D, *d_U;
+    cudaGraph_t graph;
+    cudaGraphExec_t gexec;
+};
+
+extern "C" const char* sfhe_last_error(void) { return g_last_error.c_str(); }
+
+// ---------------------------------------------------------------- helpers ---
+extern "C" sfhe_status sfhe_select_primes(uint32_t N, uint32_t L, uint64_t* q, uint64_t* p)
+{
+    if (!q || !p) return fail(SFHE_EINVAL, "null output");
+    if (N < 2 || (N & (N - 1)) || L < 1 || L > SFHE_MAX_L) return fail(SFHE_EUNSUPPORTED, "N=%u L=%u", N, L);
+    std::vector<uint64_t> pr;
+    if (!ntt_primes(N, 2 * L + 1, pr)) return fail(SFHE_EUNSUPPORTED, "not enough primes");
+    for (uint32_t i = 0; i < L; i++) q[i] = pr[i];
+    for (uint32_t j = 0; j <= L; j++) p[j] = pr[L + j];
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_cdt_table(double sigma, uint64_t* T20)
+{
+    if (!T20) return fail(SFHE_EINVAL, "null output");
+    if (!(sigma > 0.0)) return fail(SFHE_EINVAL, "sigma must be positive");
+    cdt_table(sigma, T20);
+    return SFHE_OK;
+}
+
+// ---------------------------------------------------------------- context ---
+extern "C" void sfhe_ctx_destroy(sfhe_ctx* c)
+{
+    if (!c) return;
+    cudaFree(c->d_tw);
+    cudaFree(c->d_s);
+    cudaFree(c->d_s_coeff);
+    cudaFree(c->d_rlk);
+    cudaFree(c->d_rlk_sh);
+    cudaFree(c->d_err);
+    delete c;
+}
+
+extern "C" sfhe_status sfhe_ctx_create(const sfhe_params* params, uint64_t seed, sfhe_ctx** out)
+{
+    if (!params || !out) return fail(SFHE_EINVAL, "null argument");
+    *out = nullptr;
+    const uint32_t N = params->N, L = params->L;
+    int logN = 0;
+    while ((1u << logN) < N) logN++;
+    if ((1u << logN) != N || !supported_ring(logN, (int)L))
+        return fail(SFHE_EUNSUPPORTED, "ring N=%u L=%u not implemented (N in {4096, 8192, 16384}, L in {2,3,4,8})", N, L);
+    if (params->t < 2 || params->t >= (1ULL << 32)) return fail(SFHE_EUNSUPPORTED, "t out of range");
+    if (!(params->sigma > 0.0) || params->sigma > 8.0) return fail(SFHE_EUNSUPPORTED, "sigma out of range");
+
+    sfhe_ctx* c = new sfhe_ctx();
+    memset(&c->rc, 0, sizeof(c->rc));
+    c->params = *params;
+    c->seed = seed;
+    auto bail = [&](sfhe_status st) {
+        sfhe_ctx_destroy(c);
+        return st;
+    };
+    if (cudaGetDevice(&c->device) != cudaSuccess) return bail(fail(SFHE_ECUDA, "no CUDA device"));
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+
+    RnsConsts& rc = c->rc;
+    rc.N = (int)N;
+    rc.logN = logN;
+    rc.L = (int)L;
+    rc.Lp = (int)L + 1;
+    rc.t = params->t;
+    rc.seed = seed;
+    std::vector<uint64_t> pr;
+    if (!ntt_primes(N, 2 * L + 1, pr)) return bail(fail(SFHE_EUNSUPPORTED, "not enough primes"));
+    for (int k = 0; k < rc.L + rc.Lp; k++) rc.m[k].q = pr[k];
+    fill_constants(rc);
+    cdt_table(params->sigma, rc.cdt);
+
+    const int LQP = rc.L + rc.Lp;
+    std::vector<uint64_t> tw((size_t)LQP * 4 * N);
+    for (int k = 0; k < LQP; k++) twiddles(rc.m[k].q, N, tw.data() + (size_t)k * 4 * N, &rc.ninv[k], &rc.wlast[k]);
+
+    const size_t rlk_words = (size_t)L * 2 * L * N;
+    if (cudaMalloc(&c->d_tw, tw.size() * 8) != cudaSuccess || cudaMalloc(&c->d_s, (size_t)L * N * 8) != cudaSuccess ||
+        cudaMalloc(&c->d_s_coeff, N) != cudaSuccess || cudaMalloc(&c->d_rlk, rlk_words * 8) != cudaSuccess ||
+        cudaMalloc(&c->d_rlk_sh, rlk_words * 8) != cudaSuccess || cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess)
+        return bail(fail(SFHE_ENOMEM, "device allocation of the context failed"));
+    rc.tw = c->d_tw;
+    if (cudaMemcpy(c->d_tw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess)
+        return bail(fail(SFHE_ECUDA, "table upload failed"));
+    cudaError_t e = launch_keygen(rc, c->d_s, c->d_s_coeff, c->d_rlk, c->d_rlk_sh, c->d_err, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return bail(fail(SFHE_ECUDA, "key generation: %s", cudaGetErrorString(e)));
+    int err = 0;
+    cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (err) return bail(fail(SFHE_EDEVICE, "key generation sampler failed"));
+    *out = c;
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_ctx_info(const sfhe_ctx* c, sfhe_info* out)
+{
+    if (!c || !out) return fail(SFHE_EINVAL, "null argument");
+    memset(out, 0, sizeof(*out));
+    out->N = (uint32_t)c->rc.N;
+    out->L = (uint32_t)c->rc.L;
+    out->Lp = (uint32_t)c->rc.Lp;
+    out->t = c->rc.t;
+    for (int i = 0; i < c->rc.L; i++) out->q[i] = c->rc.m[i].q;
+    for (int j = 0; j < c->rc.Lp; j++) out->p[j] = c->rc.m[c->rc.L + j].q;
+    out->ct_words = (uint64_t)2 * c->rc.L * c->rc.N;
+    out->ext_words = (uint64_t)2 * (c->rc.L + c->rc.Lp) * c->rc.N;
+    out->num_sms = c->num_sms;
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_ctx_check(sfhe_ctx* c, void* stream)
+{
+    if (!c) return fail(SFHE_EINVAL, "null context");
+    CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
+    int err = 0;
+    CUDA_TRY(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) return fail(SFHE_EDEVICE, "a sampler exhausted its retries");
+    return SFHE_OK;
+}
+
+// --------------------------------------------------------------- operands ---
+static sfhe_status check_values(const int64_t* v, int32_t rows, int32_t cols, int32_t enc)
+{
+    if (!v && rows > 0 && cols > 0) return fail(SFHE_EINVAL, "null values");
+    if (rows < 0 || cols < 0) return fail(SFHE_ESHAPE, "negative shape");
+    if (enc < SFHE_ENC_DENSE || enc > SFHE_ENC_ELL) return fail(SFHE_EINVAL, "unknown encoding %d", enc);
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_encode_count(const int64_t* values, int32_t rows, int32_t cols, int32_t encoding,
+                                         int32_t* nct, int32_t* ell_width)
+{
+    sfhe_status st = check_values(values, rows, cols, encoding);
+    if (st != SFHE_OK) return st;
+    if (!nct || !ell_width) return fail(SFHE_EINVAL, "null output");
+    int64_t nnz = 0;
+    int32_t width = 0;
+    for (int32_t r = 0; r < rows; r++) {
+        int32_t row_nnz = 0;
+        for (int32_t c = 0; c < cols; c++) row_nnz += values[(int64_t)r * cols + c] != 0;
+        nnz += row_nnz;
+        width = std::max(width, row_nnz);
+    }
+    int64_t n = (int64_t)rows * cols;
+    if (encoding == SFHE_ENC_CSR) n = nnz;
+    if (encoding == SFHE_ENC_ELL) n = (int64_t)rows * width;
+    if (n > INT32_MAX) return fail(SFHE_EUNSUPPORTED, "too many ciphertexts");
+    *nct = (int32_t)n;
+    *ell_width = encoding == SFHE_ENC_ELL ? width : 0;
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_encode_fill(const int64_t* values, int32_t rows, int32_t cols, int32_t encoding,
+                                        uint8_t* mask, int32_t* row_ptr, int32_t* col_idx, int32_t* ell_col,
+                                        int64_t* ct_values, int32_t* ct_coords)
+{
+    int32_t nct = 0, width = 0;
+    sfhe_status st = sfhe_encode_count(values, rows, cols, encoding, &nct, &width);
+    if (st != SFHE_OK) return st;
+    if (!ct_values || !ct_coords) return fail(SFHE_EINVAL, "null output");
+    int64_t t = 0;
+    switch (encoding) {
+    case SFHE_ENC_DENSE:
+    case SFHE_ENC_MASK:
+        if (encoding == SFHE_ENC_MASK && !mask) return fail(SFHE_EINVAL, "null mask");
+        for (int32_t r = 0; r < rows; r++)
+            for (int32_t c = 0; c < cols; c++, t++) {
+                const int64_t v = values[(int64_t)r * cols + c];
+                if (encoding == SFHE_ENC_MASK) mask[t] = v == 0;
+                ct_values[t] = v;
+                ct_coords[2 * t] = r;
+                ct_coords[2 * t + 1] = c;
+            }
+        break;
+    case SFHE_ENC_CSR:
+        if (!row_ptr || (!col_idx && nct > 0)) return fail(SFHE_EINVAL, "null CSR arrays");
+        row_ptr[0] = 0;
+        for (int32_t r = 0; r < rows; r++) {
+            for (int32_t c = 0; c < cols; c++) {
+                const int64_t v = values[(int64_t)r * cols + c];
+                if (!v) continue;
+                col_idx[t] = c;
+                ct_values[t] = v;
+                ct_coords[2 * t] = r;
+                ct_coords[2 * t + 1] = c;
+                t++;
+            }
+            row_ptr[r + 1] = (int32_t)t;
+        }
+        break;
+    case SFHE_ENC_ELL:
+        if (!ell_col && nct > 0) return fail(SFHE_EINVAL, "null ELL column array");
+        for (int32_t r = 0; r < rows; r++) {
+            int32_t s = 0;
+            for (int32_t c = 0; c < cols; c++) {
+                const int64_t v = values[(int64_t)r * cols + c];
+                if (!v) continue;
+                t = (int64_t)r * width + s;
+                ell_col[t] = c;
+                ct_values[t] = v;
+                ct_coords[2 * t] = r;
+                ct_coords[2 * t + 1] = c;
+                s++;
+            }
+            for (; s < width; s++) {  // encrypted zero padding
+                t = (int64_t)r * width + s;
+                ell_col[t] = -1;
+                ct_values[t] = 0;
+                ct_coords[2 * t] = r;
+                ct_coords[2 * t + 1] = cols + s;
+            }
+        }
+        break;
+    }
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_encrypt(sfhe_ctx* c, const int64_t* values, const int32_t* coords, int64_t n,
+                                    uint64_t matrix_id, uint64_t* ct, void* stream)
+{
+    if (!c) return fail(SFHE_EINVAL, "null context");
+    if (n < 0) return fail(SFHE_ESHAPE, "negative count");
+    if (n == 0) return SFHE_OK;
+    if (!values || !coords || !ct) return fail(SFHE_EINVAL, "null argument");
+    cudaStream_t s = as_stream(stream);
+    long long* d_vals = nullptr;
+    int* d_coords = nullptr;
+    CUDA_TRY(cudaMallocAsync((void**)&d_vals, n * sizeof(long long), s));
+    CUDA_TRY(cudaMallocAsync((void**)&d_coords, n * 2 * sizeof(int), s));
+    CUDA_TRY(cudaMemcpyAsync(d_vals, values, n * sizeof(long long), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(d_coords, coords, n * 2 * sizeof(int), cudaMemcpyHostToDevice, s));
+    cudaError_t e = launch_encrypt(c->rc, c->d_s, d_vals, d_coords, n, matrix_id, ct, c->d_err, s);
+    cudaFreeAsync(d_vals, s);
+    cudaFreeAsync(d_coords, s);
+    if (e != cudaSuccess) return fail(SFHE_ECUDA, "encrypt: %s", cudaGetErrorString(e));
+    return SFHE_OK;
+}
+
+static const int64_t kLiftChunk = 256;
+
+extern "C" sfhe_status sfhe_lift_workspace_size(const sfhe_ctx* c, int64_t n, size_t* bytes)
+{
+    if (!c || !bytes) return fail(SFHE_EINVAL, "null argument");
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n, kLiftChunk));
+    *bytes = (size_t)chunk * 2 * (c->rc.L + c->rc.Lp) * c->rc.N * 8;
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_lift(sfhe_ctx* c, const uint64_t* ct, int64_t n, uint64_t* ext, void* work,
+                                 size_t work_bytes, void* stream)
+{
+    if (!c) return fail(SFHE_EINVAL, "null context");
+    if (n < 0) return fail(SFHE_ESHAPE, "negative count");
+    if (n == 0) return SFHE_OK;
+    if (!ct || !ext || !work) return fail(SFHE_EINVAL, "null argument");
+    const RnsConsts& rc = c->rc;
+    const size_t N = rc.N, L = rc.L, Lp = rc.Lp;
+    const size_t per_ct = 2 * (L + Lp) * N * 8;
+    const int64_t chunk = (int64_t)(work_bytes / per_ct);
+    if (chunk < 1) return fail(SFHE_ENOMEM, "lift workspace too small");
+    cudaStream_t s = as_stream(stream);
+    u64* wq = (u64*)work;                    // [2c][L][N]
+    const size_t ctw = 2 * L * N, extw = 2 * (L + Lp) * N;
+    for (int64_t n0 = 0; n0 < n; n0 += chunk) {
+        const int64_t cnt = std::min(chunk, n - n0);
+        u64* wp = wq + (size_t)cnt * 2 * L * N;  // [2c][Lp][N]
+        const u64* src = ct + n0 * ctw;
+        u64* dst = ext + n0 * extw;
+        cudaError_t e = launch_ntt(rc, true, src, L * N, 0, wq, L * N, 0, 0, (int)L, 2 * cnt, s);
+        if (e == cudaSuccess) e = launch_lift_extend(rc, wq, wp, 2 * cnt, s);
+        if (e == cudaSuccess) e = launch_ntt(rc, false, wp, Lp * N, 0, dst, (L + Lp) * N, (int)L, (int)L, (int)Lp, 2 * cnt, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(dst, (L + Lp) * N * 8, src, L * N * 8, L * N * 8, 2 * cnt, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return fail(SFHE_ECUDA, "lift: %s", cudaGetErrorString(e));
+    }
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_decrypt(sfhe_ctx* c, const uint64_t* ct, int64_t n, int64_t* out, void* stream)
+{
+    if (!c) return fail(SFHE_EINVAL, "null context");
+    if (n < 0) return fail(SFHE_ESHAPE, "negative count");
+    if (n == 0) return SFHE_OK;
+    if (!ct || !out) return fail(SFHE_EINVAL, "null argument");
+    cudaError_t e = launch_decrypt(c->rc, c->d_s, ct, n, (long long*)out, as_stream(stream));
+    if (e != cudaSuccess) return fail(SFHE_ECUDA, "decrypt: %s", cudaGetErrorString(e));
+    return SFHE_OK;
+}
+
+static sfhe_status convert(sfhe_ctx* c, const uint64_t* in, int64_t npoly, uint64_t* out, void* stream, bool inverse)
+{
+    if (!c) return fail(SFHE_EINVAL, "null context");
+    if (npoly < 0) return fail(SFHE_ESHAPE, "negative count");
+    if (npoly == 0) return SFHE_OK;
+    if (!in || !out) return fail(SFHE_EINVAL, "null argument");
+    const size_t LN = (size_t)c->rc.L * c->rc.N;
+    cudaError_t e = launch_ntt(c->rc, inverse, in, LN, 0, out, LN, 0, 0, c->rc.L, npoly, as_stream(stream));
+    if (e != cudaSuccess) return fail(SFHE_ECUDA, "ntt: %s", cudaGetErrorString(e));
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_to_coeff(sfhe_ctx* c, const uint64_t* in, int64_t npoly, uint64_t* out, void* stream)
+{
+    return convert(c, in, npoly, out, stream, true);
+}
+
+extern "C" sfhe_status sfhe_from_coeff(sfhe_ctx* c, const uint64_t* in, int64_t npoly, uint64_t* out, void* stream)
+{
+    return convert(c, in, npoly, out, stream, false);
+}
+
+extern "C" sfhe_status sfhe_export_secret(sfhe_ctx* c, int8_t* s_host)
+{
+    if (!c || !s_host) return fail(SFHE_EINVAL, "null argument");
+    CUDA_TRY(cudaMemcpy(s_host, c->d_s_coeff, c->rc.N, cudaMemcpyDeviceToHost));
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_export_relin_key(sfhe_ctx* c, uint64_t* out, void* stream)
+{
+    if (!c || !out) return fail(SFHE_EINVAL, "null argument");
+    return convert(c, c->d_rlk, 2 * c->rc.L, out, stream, true);
+}
+
+// ------------------------------------------------------------- work lists ---
+namespace {
+
+struct Layout {
+    size_t queue, mms, entries, rowlist, scratch, T, D, U, total;
+};
+
+sfhe_status validate_matrix(const sfhe_matrix& m, const char* name)
+{
+    if (m.rows < 0 || m.cols < 0) return fail(SFHE_ESHAPE, "%s: negative shape", name);
+    if (m.encoding < SFHE_ENC_DENSE || m.encoding > SFHE_ENC_ELL) return fail(SFHE_EINVAL, "%s: bad encoding", name);
+    const int64_t dense = (int64_t)m.rows * m.cols;
+    switch (m.encoding) {
+    case SFHE_ENC_DENSE:
+        if (m.nct != dense) return fail(SFHE_ESHAPE, "%s: DENSE needs rows*cols ciphertexts", name);
+        break;
+    case SFHE_ENC_MASK:
+        if (m.nct != dense) return fail(SFHE_ESHAPE, "%s: MASK needs rows*cols ciphertexts", name);
+        if (!m.mask && dense > 0) return fail(SFHE_EINVAL, "%s: null mask", name);
+        break;
+    case SFHE_ENC_CSR: {
+        if (!m.row_ptr) return fail(SFHE_EINVAL, "%s: null row_ptr", name);
+        if (m.row_ptr[0] != 0) return fail(SFHE_EINVAL, "%s: row_ptr[0] != 0", name);
+        for (int32_t r = 0; r < m.rows; r++)
+            if (m.row_ptr[r + 1] < m.row_ptr[r]) return fail(SFHE_EINVAL, "%s: row_ptr not monotone at %d", name, r);
+        if (m.row_ptr[m.rows] != m.nct) return fail(SFHE_ESHAPE, "%s: row_ptr[rows] != nct", name);
+        if (m.nct > 0 && !m.col_idx) return fail(SFHE_EINVAL, "%s: null col_idx", name);
+        for (int32_t t = 0; t < m.nct; t++)
+            if (m.col_idx[t] < 0 || m.col_idx[t] >= m.cols) return fail(SFHE_EINVAL, "%s: col_idx[%d] out of range", name, t);
+        break;
+    }
+    case SFHE_ENC_ELL:
+        if (m.ell_width < 0 || (int64_t)m.rows * m.ell_width != m.nct)
+            return fail(SFHE_ESHAPE, "%s: ELL needs rows*ell_width ciphertexts", name);
+        if (m.nct > 0 && !m.ell_col) return fail(SFHE_EINVAL, "%s: null ell_col", name);
+        for (int32_t t = 0; t < m.nct; t++)
+            if (m.ell_col[t] < -1 || m.ell_col[t] >= m.cols) return fail(SFHE_EINVAL, "%s: ell_col[%d] out of range", name, t);
+        break;
+    }
+    return SFHE_OK;
+}
+
+// rows of (A ciphertext index, k) pairs listed by A's encoding
+void row_pairs(const sfhe_matrix& A, int32_t i, bool dense_loop, std::vector<int2>& out)
+{
+    const int32_t K = A.cols;
+    if (dense_loop) {
+        for (int32_t k = 0; k < K; k++) out.push_back(make_int2(i * K + k, k));
+        return;
+    }
+    switch (A.encoding) {
+    case SFHE_ENC_DENSE:
+        for (int32_t k = 0; k < K; k++) out.push_back(make_int2(i * K + k, k));
+        break;
+    case SFHE_ENC_MASK:
+        for (int32_t k = 0; k < K; k++)
+            if (!A.mask[(int64_t)i * K + k]) out.push_back(make_int2(i * K + k, k));
+        break;
+    case SFHE_ENC_CSR:
+        for (int32_t t = A.row_ptr[i]; t < A.row_ptr[i + 1]; t++) out.push_back(make_int2(t, A.col_idx[t]));
+        break;
+    case SFHE_ENC_ELL:
+        for (int32_t s = 0; s < A.ell_width; s++) {
+            const int32_t k = A.ell_col[(int64_t)i * A.ell_width + s];
+            if (k >= 0) out.push_back(make_int2(i * A.ell_width + s, k));
+        }
+        break;
+    }
+}
+
+sfhe_status build(const sfhe_ctx* c, int32_t n, const sfhe_matrix* A, const sfhe_matrix* B, const sfhe_matrix* C,
+                  const bool* dense_loop, sfhe_plan& P)
+{
+    if (n < 0) return fail(SFHE_ESHAPE, "negative matmul count");
+    if (n > 0 && (!A || !B)) return fail(SFHE_EINVAL, "null operands");
+    P.mms.clear();
+    P.entries.clear();
+    P.rowlist.clear();
+    P.c_words.clear();
+    P.products = 0;
+    const size_t ctw = (size_t)2 * c->rc.L * c->rc.N;
+    for (int32_t m = 0; m < n; m++) {
+        sfhe_status st = validate_matrix(A[m], "A");
+        if (st == SFHE_OK) st = validate_matrix(B[m], "B");
+        if (st != SFHE_OK) return st;
+        if (B[m].encoding != SFHE_ENC_DENSE) return fail(SFHE_EINVAL, "B must be DENSE-encoded");
+        if (A[m].cols != B[m].rows) return fail(SFHE_ESHAPE, "A is %dx%d, B is %dx%d", A[m].rows, A[m].cols, B[m].rows, B[m].cols);
+        if (C) {
+            if (C[m].rows != A[m].rows || C[m].cols != B[m].cols) return fail(SFHE_ESHAPE, "C shape mismatch");
+            if (C[m].encoding != SFHE_ENC_DENSE || C[m].nct != C[m].rows * C[m].cols)
+                return fail(SFHE_EINVAL, "C must be DENSE with rows*cols ciphertexts");
+            if (!C[m].ct && C[m].nct > 0) return fail(SFHE_EINVAL, "null C storage");
+        }
+        if ((A[m].nct > 0 && !A[m].ext) || (B[m].nct > 0 && !B[m].ext))
+            return fail(SFHE_EINVAL, "operands need lifted storage (sfhe_lift)");
+        MmDesc d;
+        d.A_ext = A[m].ext;
+        d.B_ext = B[m].ext;
+        d.C = C ? C[m].ct : nullptr;
+        d.Nc = B[m].cols;
+        d.pad = 0;
+        P.mms.push_back(d);
+        P.c_words.push_back((size_t)A[m].rows * B[m].cols * ctw);
+        for (int32_t i = 0; i < A[m].rows; i++) {
+            const int first = (int)P.rowlist.size();
+            row_pairs(A[m], i, dense_loop[m], P.rowlist);
+            const int count = (int)P.rowlist.size() - first;
+            if (count > 1024) return fail(SFHE_EUNSUPPORTED, "more than 1024 products per output entry");
+            for (int32_t j = 0; j < B[m].cols; j++) {
+                Entry en;
+                memset(&en, 0, sizeof(en));
+                en.mm = m;
+                en.row = i;
+                en.col = j;
+                en.count = count;
+                en.first = first;
+                P.entries.push_back(en);
+                P.products += count;
+            }
+        }
+    }
+    // longest entries first: the persistent queue then approximates LPT
+    std::stable_sort(P.entries.begin(), P.entries.end(), [](const Entry& a, const Entry& b) { return a.count > b.count; });
+    return SFHE_OK;
+}
+
+Layout layout_of(const sfhe_ctx* c, const sfhe_plan& P, uint32_t flags, int* grid_out, size_t* stride_out)
+{
+    Layout Lo;
+    memset(&Lo, 0, sizeof(Lo));
+    size_t off = 0;
+    Lo.queue = off;
+    off += 256;
+    Lo.mms = off;
+    off += align256(P.mms.size() * sizeof(MmDesc));
+    Lo.entries = off;
+    off += align256(P.entries.size() * sizeof(Entry));
+    Lo.rowlist = off;
+    off += align256(P.rowlist.size() * sizeof(int2));
+    const size_t N = c->rc.N, L = c->rc.L, LQP = c->rc.L + c->rc.Lp;
+    *grid_out = 0;
+    *stride_out = 0;
+    if (flags & SFHE_EXEC_PERSISTENT) {
+        const int per_sm = persistent_ctas_per_sm(c->rc);
+        int grid = per_sm * c->num_sms;
+        grid = (int)std::min<size_t>((size_t)grid, std::max<size_t>(1, P.entries.size()));
+        const size_t stride = persistent_scratch_words(c->rc);
+        Lo.scratch = off;
+        off += align256((size_t)grid * stride * 8);
+        *grid_out = grid;
+        *stride_out = stride;
+    }
+    if (flags & SFHE_EXEC_PLAIN) {
+        Lo.T = off;
+        off += align256(3 * LQP * N * 8);
+        Lo.D = off;
+        off += align256(3 * L * N * 8);
+        Lo.U = off;
+        off += align256((L + 2) * L * N * 8);
+    }
+    Lo.total = off;
+    return Lo;
+}
+
+sfhe_status check_flags(uint32_t flags)
+{
+    const bool plain = flags & SFHE_EXEC_PLAIN, pers = flags & SFHE_EXEC_PERSISTENT;
+    if (plain == pers) return fail(SFHE_EINVAL, "exactly one of PLAIN and PERSISTENT");
+    if ((flags & SFHE_EXEC_GRAPH) && !pers) return fail(SFHE_EINVAL, "GRAPH needs PERSISTENT");
+    if (flags & ~(uint32_t)(SFHE_EXEC_PLAIN | SFHE_EXEC_PERSISTENT | SFHE_EXEC_GRAPH)) return fail(SFHE_EINVAL, "unknown flags");
+    return SFHE_OK;
+}
+
+sfhe_status launch_plan(sfhe_plan* P, cudaStream_t s)
+{
+    const sfhe_ctx* c = P->ctx;
+    const RnsConsts& rc = c->rc;
+    if (P->flags & SFHE_EXEC_PERSISTENT) {
+        if (P->gexec) {
+            CUDA_TRY(cudaGraphLaunch(P->gexec, s));
+            return SFHE_OK;
+        }
+        CUDA_TRY(cudaMemsetAsync(P->d_queue, 0, sizeof(unsigned), s));
+        if (P->entries.empty()) return SFHE_OK;
+        CUDA_TRY(launch_persistent(rc, P->d_mms, P->d_entries, (int)P->entries.size(), P->d_rowlist, c->d_rlk, c->d_rlk_sh,
+                                   P->d_scratch, P->scratch_stride, P->d_queue, P->grid, s));
+        return SFHE_OK;
+    }
+    // plain: C = 0, then one launch sequence per product
+    for (size_t m = 0; m < P->mms.size(); m++)
+        if (P->c_words[m]) CUDA_TRY(cudaMemsetAsync(P->mms[m].C, 0, P->c_words[m] * 8, s));
+    const size_t N = rc.N, L = rc.L, LQP = rc.L + rc.Lp;
+    const size_t ctw = 2 * L * N, extw = 2 * LQP * N;
+    for (const Entry& en : P->entries) {
+        const MmDesc& mm = P->mms[en.mm];
+        u64* Cout = mm.C + ((size_t)en.row * mm.Nc + en.col) * ctw;
+        for (int p = 0; p < en.count; p++) {
+            const int2 it = P->rowlist[en.first + p];
+            const u64* a = mm.A_ext + (size_t)it.x * extw;
+            const u64* b = mm.B_ext + ((size_t)it.y * mm.Nc + en.col) * extw;
+            CUDA_TRY(launch_tensor_intt(rc, a, b, P->d_T, s));
+            CUDA_TRY(launch_scale_round(rc, P->d_T, P->d_D, s));
+            CUDA_TRY(launch_relin_ntt(rc, P->d_D, P->d_U, s));
+            CUDA_TRY(launch_relin_accum(rc, P->d_U, c->d_rlk, c->d_rlk_sh, Cout, s));
+        }
+    }
+    return SFHE_OK;
+}
+
+}  // namespace
+
+extern "C" void sfhe_plan_destroy(sfhe_plan* P)
+{
+    if (!P) return;
+    if (P->gexec) cudaGraphExecDestroy(P->gexec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    delete P;
+}
+
+static sfhe_status plan_create_impl(sfhe_ctx* c, int32_t n, const sfhe_matrix* A, const sfhe_matrix* B,
+                                    sfhe_matrix* C, const bool* dense_loop, uint32_t flags, void* work,
+                                    size_t work_bytes, void* stream, sfhe_plan** out)
+{
+    if (!c || !out) return fail(SFHE_EINVAL, "null argument");
+    *out = nullptr;
+    sfhe_status st = check_flags(flags);
+    if (st != SFHE_OK) return st;
+    if (n > 0 && !C) return fail(SFHE_EINVAL, "null C");
+    sfhe_plan* P = new sfhe_plan();
+    P->ctx = c;
+    P->flags = flags;
+    P->graph = nullptr;
+    P->gexec = nullptr;
+    st = build(c, n, A, B, C, dense_loop, *P);
+    if (st != SFHE_OK) {
+        delete P;
+        return st;
+    }
+    Layout Lo = layout_of(c, *P, flags, &P->grid, &P->scratch_stride);
+    if ((flags & SFHE_EXEC_PERSISTENT) && P->grid <= 0) {
+        delete P;
+        return fail(SFHE_ECUDA, "persistent kernel cannot be resident on this device");
+    }
+    if (!work || work_bytes < Lo.total) {
+        delete P;
+        return fail(SFHE_ENOMEM, "workspace of %zu bytes needed, %zu given", Lo.total, work_bytes);
+    }
+    char* w = (char*)work;
+    P->d_queue = (unsigned*)(w + Lo.queue);
+    P->d_mms = (MmDesc*)(w + Lo.mms);
+    P->d_entries = (Entry*)(w + Lo.entries);
+    P->d_rowlist = (int2*)(w + Lo.rowlist);
+    P->d_scratch = (u64*)(w + Lo.scratch);
+    P->d_T = (u64*)(w + Lo.T);
+    P->d_D = (u64*)(w + Lo.D);
+    P->d_U = (u64*)(w + Lo.U);
+    cudaStream_t s = as_stream(stream);
+    auto up = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+        return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+    };
+    cudaError_t e = up(P->d_mms, P->mms.data(), P->mms.size() * sizeof(MmDesc));
+    if (e == cudaSuccess) e = up(P->d_entries, P->entries.data(), P->entries.size() * sizeof(Entry));
+    if (e == cudaSuccess) e = up(P->d_rowlist, P->rowlist.data(), P->rowlist.size() * sizeof(int2));
+    if (e != cudaSuccess) {
+        delete P;
+        return fail(SFHE_ECUDA, "work list upload: %s", cudaGetErrorString(e));
+    }
+    if (flags & SFHE_EXEC_GRAPH) {
+        cudaStream_t cap;
+        e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            sfhe_status ls = SFHE_OK;
+            if (cudaMemsetAsync(P->d_queue, 0, sizeof(unsigned), cap) != cudaSuccess) ls = SFHE_ECUDA;
+            if (ls == SFHE_OK && !P->entries.empty())
+                if (launch_persistent(c->rc, P->d_mms, P->d_entries, (int)P->entries.size(), P->d_rowlist, c->d_rlk,
+                                      c->d_rlk_sh, P->d_scratch, P->scratch_stride, P->d_queue, P->grid, cap) != cudaSuccess)
+                    ls = SFHE_ECUDA;
+            cudaError_t e2 = cudaStreamEndCapture(cap, &P->graph);
+            if (ls != SFHE_OK || e2 != cudaSuccess) e = cudaErrorUnknown;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&P->gexec, P->graph, 0);
+        cudaStreamDestroy(cap);
+        if (e != cudaSuccess) {
+            sfhe_plan_destroy(P);
+            return fail(SFHE_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        }
+    }
+    *out = P;
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_plan_create(sfhe_ctx* c, int32_t n, const sfhe_matrix* A, const sfhe_matrix* B,
+                                        sfhe_matrix* C, uint32_t flags, void* work, size_t work_bytes, void* stream,
+                                        sfhe_plan** out)
+{
+    std::vector<char> dl(std::max(n, 0), 0);
+    return plan_create_impl(c, n, A, B, C, (const bool*)dl.data(), flags, work, work_bytes, stream, out);
+}
+
+extern "C" sfhe_status sfhe_plan_execute(sfhe_plan* P, void* stream)
+{
+    if (!P) return fail(SFHE_EINVAL, "null plan");
+    return launch_plan(P, as_stream(stream));
+}
+
+extern "C" sfhe_status sfhe_plan_stats(const sfhe_plan* P, int64_t* products, int64_t* entries, int64_t* launches,
+                                       int64_t* ctas)
+{
+    if (!P) return fail(SFHE_EINVAL, "null plan");
+    if (products) *products = P->products;
+    if (entries) *entries = (int64_t)P->entries.size();
+    if (launches) *launches = (P->flags & SFHE_EXEC_PERSISTENT) ? (P->entries.empty() ? 0 : 1) : 4 * P->products;
+    if (ctas) *ctas = P->grid;
+    return SFHE_OK;
+}
+
+static sfhe_status size_impl(const sfhe_ctx* c, int32_t n, const sfhe_matrix* A, const sfhe_matrix* B,
+                             const bool* dense_loop, uint32_t flags, size_t* bytes)
+{
+    if (!c || !bytes) return fail(SFHE_EINVAL, "null argument");
+    sfhe_status st = check_flags(flags);
+    if (st != SFHE_OK) return st;
+    sfhe_plan P;
+    P.ctx = const_cast<sfhe_ctx*>(c);
+    st = build(c, n, A, B, nullptr, dense_loop, P);
+    if (st != SFHE_OK) return st;
+    int grid;
+    size_t stride;
+    *bytes = layout_of(c, P, flags, &grid, &stride).total;
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_matmul_workspace_size(const sfhe_ctx* c, int32_t n, const sfhe_matrix* A,
+                                                  const sfhe_matrix* B, uint32_t flags, size_t* bytes)
+{
+    std::vector<char> dl(std::max(n, 0), 0);
+    return size_impl(c, n, A, B, (const bool*)dl.data(), flags, bytes);
+}
+
+static sfhe_status one_shot(sfhe_ctx* c, int32_t n, const sfhe_matrix* A, const sfhe_matrix* B, sfhe_matrix* C,
+                            const bool* dense_loop, uint32_t flags, void* work, size_t work_bytes, void* stream)
+{
+    sfhe_plan* P = nullptr;
+    // a one-shot call launches directly; graphs are for replayed plans
+    sfhe_status st = plan_create_impl(c, n, A, B, C, dense_loop, flags & ~(uint32_t)SFHE_EXEC_GRAPH, work, work_bytes,
+                                      stream, &P);
+    if (st != SFHE_OK) return st;
+    st = launch_plan(P, as_stream(stream));
+    sfhe_plan_destroy(P);
+    return st;
+}
+
+extern "C" sfhe_status sfhe_matmul_dense(sfhe_ctx* c, const sfhe_matrix* A, const sfhe_matrix* B, sfhe_matrix* C,
+                                         uint32_t flags, void* work, size_t work_bytes, void* stream)
+{
+    if (!A) return fail(SFHE_EINVAL, "null A");
+    if (A->encoding != SFHE_ENC_DENSE && A->encoding != SFHE_ENC_MASK)
+        return fail(SFHE_EINVAL, "the dense loop needs every element of A stored (DENSE or MASK)");
+    const bool dl = true;
+    return one_shot(c, 1, A, B, C, &dl, flags, work, work_bytes, stream);
+}
+
+extern "C" sfhe_status sfhe_matmul_sparse(sfhe_ctx* c, const sfhe_matrix* A, const sfhe_matrix* B, int32_t encoding,
+                                          sfhe_matrix* C, uint32_t flags, void* work, size_t work_bytes, void* stream)
+{
+    if (!A) return fail(SFHE_EINVAL, "null A");
+    if (encoding != SFHE_ENC_MASK && encoding != SFHE_ENC_CSR && encoding != SFHE_ENC_ELL)
+        return fail(SFHE_EINVAL, "sparse encoding must be MASK, CSR or ELL");
+    if (A->encoding != encoding) return fail(SFHE_EINVAL, "A is encoded as %d, not %d", A->encoding, encoding);
+    const bool dl = false;
+    return one_shot(c, 1, A, B, C, &dl, flags, work, work_bytes, stream);
+}
+
+extern "C" sfhe_status sfhe_matmul_batch(sfhe_ctx* c, int32_t n, const sfhe_matrix* A, const sfhe_matrix* B,
+                                         sfhe_matrix* C, uint32_t flags, void* work, size_t work_bytes, void* stream)
+{
+    std::vector<char> dl(std::max(n, 0), 0);
+    return one_shot(c, n, A, B, C, (const bool*)dl.data(), flags, work, work_bytes, stream);
+}
+
+// ------------------------------------------------------ stage entry points ---
+extern "C" sfhe_status sfhe_ct_tensor_scale(sfhe_ctx* c, const uint64_t* a_ext, const uint64_t* b_ext, uint64_t* d,
+                                            void* work, size_t work_bytes, void* stream)
+{
+    if (!c || !a_ext || !b_ext || !d || !work) return fail(SFHE_EINVAL, "null argument");
+    const size_t need = (size_t)3 * (c->rc.L + c->rc.Lp) * c->rc.N * 8;
+    if (work_bytes < need) return fail(SFHE_ENOMEM, "workspace of %zu bytes needed", need);
+    cudaStream_t s = as_stream(stream);
+    CUDA_TRY(launch_tensor_intt(c->rc, a_ext, b_ext, (u64*)work, s));
+    CUDA_TRY(launch_scale_round(c->rc, (u64*)work, d, s));
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_ct_mul_relin(sfhe_ctx* c, const uint64_t* a_ext, const uint64_t* b_ext, uint64_t* out,
+                                         void* work, size_t work_bytes, void* stream)
+{
+    if (!c || !a_ext || !b_ext || !out || !work) return fail(SFHE_EINVAL, "null argument");
+    const size_t N = c->rc.N, L = c->rc.L, LQP = c->rc.L + c->rc.Lp;
+    const size_t need = (3 * LQP + 3 * L + (L + 2) * L) * N * 8;
+    if (work_bytes < need) return fail(SFHE_ENOMEM, "workspace of %zu bytes needed", need);
+    cudaStream_t s = as_stream(stream);
+    u64* T = (u64*)work;
+    u64* D = T + 3 * LQP * N;
+    u64* U = D + 3 * L * N;
+    CUDA_TRY(cudaMemsetAsync(out, 0, 2 * L * N * 8, s));
+    CUDA_TRY(launch_tensor_intt(c->rc, a_ext, b_ext, T, s));
+    CUDA_TRY(launch_scale_round(c->rc, T, D, s));
+    CUDA_TRY(launch_relin_ntt(c->rc, D, U, s));
+    CUDA_TRY(launch_relin_accum(c->rc, U, c->d_rlk, c->d_rlk_sh, out, s));
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_ntt(sfhe_ctx* c, int32_t prime_index, int32_t inverse, const uint64_t* in, int64_t npoly,
+                                uint64_t* out, void* stream)
+{
+    if (!c || !in || !out) return fail(SFHE_EINVAL, "null argument");
+    if (prime_index < 0 || prime_index >= c->rc.L + c->rc.Lp) return fail(SFHE_EINVAL, "prime index out of range");
+    if (npoly < 0) return fail(SFHE_ESHAPE, "negative count");
+    cudaError_t e = launch_ntt(c->rc, inverse != 0, in, c->rc.N, 0, out, c->rc.N, 0, prime_index, 1, npoly, as_stream(stream));
+    if (e != cudaSuccess) return fail(SFHE_ECUDA, "ntt: %s", cudaGetErrorString(e));
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_prng_words(uint64_t seed, uint32_t domain, uint64_t o0, uint64_t o1, uint64_t o2,
+                                       uint64_t idx0, int64_t n, uint64_t* out, void* stream)
+{
+    if (n < 0) return fail(SFHE_ESHAPE, "negative count");
+    if (n > 0 && !out) return fail(SFHE_EINVAL, "null output");
+    CUDA_TRY(launch_prng(seed, domain, o0, o1, o2, idx0, n, out, as_stream(stream)));
+    return SFHE_OK;
+}

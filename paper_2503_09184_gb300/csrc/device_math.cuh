@@ -1,0 +1,219 @@
+// device_math.cuh -- 64-bit modular arithmetic for 54-bit primes, the exact
+// CRT rounding used by every base conversion, and the counter-based
+// generator.  All moduli satisfy 2^53 < q < 2^54.
+#pragma once
+#include <stdint.h>
+#include "rns.h"
+
+#define SFHE_DEV __device__ __forceinline__
+
+// ---------------------------------------------------------------- scalar ---
+SFHE_DEV u64 mulhi(u64 a, u64 b) { return __umul64hi(a, b); }
+
+// a + b mod q for a, b < q
+SFHE_DEV u64 add_mod(u64 a, u64 b, u64 q)
+{
+    u64 s = a + b;
+    return s >= q ? s - q : s;
+}
+// a - b mod q for a, b < q
+SFHE_DEV u64 sub_mod(u64 a, u64 b, u64 q)
+{
+    return a >= b ? a - b : a + q - b;
+}
+SFHE_DEV u64 csub(u64 a, u64 q) { return a >= q ? a - q : a; }
+
+// Shoup: a * w mod q in [0, 2q) for any a < 2^64 (Harvey's lazy form).
+SFHE_DEV u64 shoup_lazy(u64 a, u64 w, u64 ws, u64 q)
+{
+    return a * w - mulhi(a, ws) * q;
+}
+SFHE_DEV u64 shoup_lazy(u64 a, ShoupC c, u64 q) { return shoup_lazy(a, c.w, c.ws, q); }
+SFHE_DEV u64 shoup(u64 a, ShoupC c, u64 q) { return csub(shoup_lazy(a, c.w, c.ws, q), q); }
+
+// Shoup with the exact quotient: a * w = quo * q + rem, rem in [0, q),
+// for a < q.
+SFHE_DEV u64 shoup_quot(u64 a, ShoupC c, u64 q, u64& quo)
+{
+    u64 qh = mulhi(a, c.ws);
+    u64 r = a * c.w - qh * q;
+    if (r >= q) {
+        r -= q;
+        qh += 1;
+    }
+    quo = qh;
+    return r;
+}
+
+// Barrett reduction of x = hi:lo < 2^114 with mu = floor(2^114 / q):
+// qhat = floor(floor(x / 2^50) * mu / 2^64) is at most 2 below floor(x/q),
+// so x - qhat q < 3q and two conditional subtractions finish it.
+SFHE_DEV u64 barrett(u64 hi, u64 lo, Mod m)
+{
+    u64 xs = (hi << 14) | (lo >> 50);
+    u64 qh = mulhi(xs, m.mu);
+    u64 r = lo - qh * m.q;
+    r = csub(r, m.q);
+    return csub(r, m.q);
+}
+SFHE_DEV u64 barrett64(u64 x, Mod m) { return barrett(0, x, m); }
+
+// (hi:lo) += a * b
+SFHE_DEV void mac(u64& hi, u64& lo, u64 a, u64 b)
+{
+    u64 l = a * b;
+    u64 h = mulhi(a, b);
+    lo += l;
+    hi += h + (lo < l ? 1 : 0);
+}
+SFHE_DEV void add128(u64& hi, u64& lo, u64 a)
+{
+    lo += a;
+    hi += (lo < a ? 1 : 0);
+}
+
+// a * b mod q for variable a, b < 2^54
+SFHE_DEV u64 mul_mod(u64 a, u64 b, Mod m)
+{
+    return barrett(mulhi(a, b), a * b, m);
+}
+
+// ------------------------------------------------------ exact CRT rounding ---
+// round(sum_{i<L} y_i / q_i) for residues y_i in [0, q_i), exactly.
+//
+// Estimate: e_i = floor((y_i 2^10) mu_i / 2^64) with mu_i = floor(2^114/q_i)
+// lies in (y_i 2^60 / q_i - 2, y_i 2^60 / q_i], so with E = sum e_i the true
+// value V satisfies V 2^60 in [E, E + 2L).  floor((E + 2^59) / 2^60) is
+// exact unless (E + 2^59) mod 2^60 >= 2^60 - 2L; in that band the decision
+// V >= k0 + 1/2 is taken exactly as 2 S >= (2 k0 + 1) Q with the multiword
+// S = sum_i y_i (Q/q_i)  (V = S / Q; Q is odd, so there are no ties).
+SFHE_DEV bool crt_round_fallback(const u64* y, const RnsConsts& c, u64 k0)
+{
+    const int W = c.Qwords + 1;
+    u64 S[SFHE_MAX_L + 2];
+    u64 R[SFHE_MAX_L + 2];
+    for (int w = 0; w <= W; w++) { S[w] = 0; R[w] = 0; }
+    for (int i = 0; i < c.L; i++) {
+        u64 carry = 0;
+        for (int w = 0; w < W; w++) {
+            u64 lo = y[i] * c.Qhat_w[i][w];
+            u64 hi = mulhi(y[i], c.Qhat_w[i][w]);
+            lo += carry;
+            hi += (lo < carry ? 1 : 0);
+            u64 s = S[w] + lo;
+            hi += (s < lo ? 1 : 0);
+            S[w] = s;
+            carry = hi;
+        }
+        S[W] += carry;
+    }
+    // 2S
+    for (int w = W; w > 0; w--) S[w] = (S[w] << 1) | (S[w - 1] >> 63);
+    S[0] <<= 1;
+    // (2 k0 + 1) Q
+    u64 f = 2 * k0 + 1, carry = 0;
+    for (int w = 0; w < W; w++) {
+        u64 qw = w < c.Qwords ? c.Qw[w] : 0;
+        u64 lo = qw * f + carry;
+        u64 hi = mulhi(qw, f) + (lo < carry ? 1 : 0);
+        R[w] = lo;
+        carry = hi;
+    }
+    R[W] = carry;
+    for (int w = W; w >= 0; w--) {
+        if (S[w] != R[w]) return S[w] > R[w];
+    }
+    return true;  // unreachable: 2S is even, (2k0+1)Q is odd
+}
+
+template <int L_STATIC>
+SFHE_DEV u64 crt_round(const u64* y, const RnsConsts& c, int L)
+{
+    u64 E = 0;
+    const int n = L_STATIC > 0 ? L_STATIC : L;
+#pragma unroll
+    for (int i = 0; i < (L_STATIC > 0 ? L_STATIC : SFHE_MAX_L); i++) {
+        if (i < n) E += mulhi(y[i] << 10, c.m[i].mu);
+    }
+    u64 Eh = E + (1ULL << 59);
+    u64 k0 = Eh >> 60;
+    u64 fr = Eh & ((1ULL << 60) - 1);
+    if (fr >= (1ULL << 60) - 2 * (u64)n) {
+        if (crt_round_fallback(y, c, k0)) k0 += 1;
+    }
+    return k0;
+}
+
+// round(sum_j y_j / p_j) over the P base when the value is known to lie within
+// 2^-24 of an integer (base P -> Q conversion of a scaled product); the
+// 2^-55 error of the estimate cannot cross a half-integer there.
+SFHE_DEV u64 crt_round_p_nearint(const u64* y, const RnsConsts& c)
+{
+    u64 E = 0;
+    for (int j = 0; j < c.Lp; j++) E += mulhi(y[j] << 10, c.m[c.L + j].mu);
+    return (E + (1ULL << 59)) >> 60;
+}
+
+// ---------------------------------------------------------- generator ------
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) used counter-style:
+//   key  = absorb(absorb(absorb(absorb(mix(seed + G), domain), o0), o1), o2)
+//   word = mix(key + (idx + 1) G),  absorb(h, x) = mix(h ^ mix(x + G)).
+#define SFHE_GAMMA 0x9E3779B97F4A7C15ULL
+SFHE_DEV u64 sm_mix(u64 z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+SFHE_DEV u64 sm_absorb(u64 h, u64 x) { return sm_mix(h ^ sm_mix(x + SFHE_GAMMA)); }
+SFHE_DEV u64 sm_key(u64 seed, u64 dom, u64 o0, u64 o1, u64 o2)
+{
+    u64 h = sm_mix(seed + SFHE_GAMMA);
+    h = sm_absorb(h, dom);
+    h = sm_absorb(h, o0);
+    h = sm_absorb(h, o1);
+    return sm_absorb(h, o2);
+}
+SFHE_DEV u64 sm_word(u64 key, u64 idx) { return sm_mix(key + (idx + 1) * SFHE_GAMMA); }
+
+// uniform residue for slot: first of words slot*16+r (r < 16) below
+// floor(2^64/q) q, reduced mod q; sets *fail when all 16 are rejected.
+SFHE_DEV u64 sample_uniform(u64 key, u64 slot, u64 q, int* fail)
+{
+    u64 lim = (~0ULL / q) * q;
+    for (u64 r = 0; r < 16; r++) {
+        u64 w = sm_word(key, slot * 16 + r);
+        if (w < lim) return w % q;
+    }
+    *fail = 1;
+    return 0;
+}
+SFHE_DEV int sample_ternary(u64 key, u64 slot, int* fail)
+{
+    u64 lim = (~0ULL / 3) * 3;
+    for (u64 r = 0; r < 16; r++) {
+        u64 w = sm_word(key, slot * 16 + r);
+        if (w < lim) {
+            u64 v = w % 3;
+            return v == 0 ? 0 : (v == 1 ? 1 : -1);
+        }
+    }
+    *fail = 1;
+    return 0;
+}
+SFHE_DEV int sample_gauss(u64 key, u64 slot, const u64* cdt)
+{
+    u64 w = sm_word(key, slot * 16);
+    u64 u = w >> 1;
+    int k = 0;
+    while (k < 19 && u >= cdt[k]) k++;
+    if (k == 0) return 0;
+    return (w & 1) ? -k : k;
+}
+// signed small integer to its residue mod q
+SFHE_DEV u64 to_residue(long long v, u64 q)
+{
+    if (v >= 0) return (u64)v % q;
+    u64 r = (u64)(-v) % q;
+    return r ? q - r : 0;
+}

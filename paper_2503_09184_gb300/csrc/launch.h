@@ -1,0 +1,44 @@
+// launch.h -- host launchers of the kernels (kernels.cu); every launcher
+// dispatches on the ring degree (and, where it matters, on L) and returns
+// the launch's cudaError_t.
+#pragma once
+#include <cuda_runtime.h>
+#include "rns.h"
+#include "worklist.h"
+
+namespace sfhe {
+
+bool supported_ring(int logN, int L);
+int ntt_threads(int logN);
+size_t ntt_smem_bytes(int logN);
+
+cudaError_t launch_ntt(const RnsConsts& rc, bool inverse, const u64* in, size_t in_gstride, int in_l0, u64* out,
+                       size_t out_gstride, int out_l0, int prime0, int nlimbs, long long ngroups, cudaStream_t s);
+cudaError_t launch_keygen(const RnsConsts& rc, u64* s_ntt, signed char* s_coeff, u64* rlk, u64* rlk_sh, int* err,
+                          cudaStream_t s);
+cudaError_t launch_encrypt(const RnsConsts& rc, const u64* s_ntt, const long long* vals, const int* coords, long long n,
+                           u64 matrix_id, u64* ct, int* err, cudaStream_t s);
+cudaError_t launch_decrypt(const RnsConsts& rc, const u64* s_ntt, const u64* ct, long long n, long long* out,
+                           cudaStream_t s);
+cudaError_t launch_lift_extend(const RnsConsts& rc, const u64* in, u64* out, long long ngroups, cudaStream_t s);
+// plain per-product path
+cudaError_t launch_tensor_intt(const RnsConsts& rc, const u64* a, const u64* b, u64* T, cudaStream_t s);
+cudaError_t launch_scale_round(const RnsConsts& rc, const u64* T, u64* D, cudaStream_t s);
+cudaError_t launch_relin_ntt(const RnsConsts& rc, const u64* D, u64* U, cudaStream_t s);
+cudaError_t launch_relin_accum(const RnsConsts& rc, const u64* U, const u64* rlk, const u64* rlk_sh, u64* C,
+                               cudaStream_t s);
+// fused persistent path (persistent_<logN>.cu)
+template <int LOGN>
+int persistent_occupancy(int L);
+template <int LOGN>
+cudaError_t persistent_launch(const RnsConsts& rc, const MmDesc* mms, const Entry* entries, int n_entries,
+                              const int2* rowlist, const u64* rlk, const u64* rlk_sh, u64* scratch,
+                              size_t scratch_stride, unsigned* queue, int grid, cudaStream_t s);
+size_t persistent_scratch_words(const RnsConsts& rc);
+int persistent_ctas_per_sm(const RnsConsts& rc);
+cudaError_t launch_persistent(const RnsConsts& rc, const MmDesc* mms, const Entry* entries, int n_entries,
+                              const int2* rowlist, const u64* rlk, const u64* rlk_sh, u64* scratch,
+                              size_t scratch_stride, unsigned* queue, int grid, cudaStream_t s);
+cudaError_t launch_prng(u64 seed, u64 dom, u64 o0, u64 o1, u64 o2, u64 idx0, long long n, u64* out, cudaStream_t s);
+
+}  // namespace sfhe

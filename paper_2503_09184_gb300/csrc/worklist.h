@@ -1,0 +1,20 @@
+// worklist.h -- device work list of the matmul kernels (filled on the host).
+#pragma once
+#include "rns.h"
+
+struct MmDesc {
+    const u64* A_ext;  // [nct_A][2][L+Lp][N]
+    const u64* B_ext;  // [K*Nc][2][L+Lp][N]
+    u64* C;            // [M*Nc][2][L][N]
+    int Nc;
+    int pad;
+};
+
+struct Entry {
+    int mm;     // matmul index
+    int row;    // i
+    int col;    // j
+    int count;  // products
+    int first;  // first (a_idx, k) pair in the row list
+    int pad[3];
+};

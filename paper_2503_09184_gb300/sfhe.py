@@ -1,0 +1,303 @@
+"""Thin Python binding of the C ABI in include/sfhe.h (libsfhe.so).
+
+Functions keep the C names and only marshal arguments: every step of the
+computation runs in the library's CUDA kernels.  Device buffers are torch
+tensors (int64 storage holding the uint64 words); streams are torch CUDA
+streams.  Loading fails loudly when the compiled library is missing: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsfhe.so")
+
+SFHE_OK, SFHE_EINVAL, SFHE_ESHAPE, SFHE_ENOMEM, SFHE_ECUDA = 0, 1, 2, 3, 4
+SFHE_ETIMEOUT, SFHE_EBUDGET, SFHE_EUNSUPPORTED, SFHE_EDEVICE = 5, 6, 7, 8
+SFHE_ENC_DENSE, SFHE_ENC_MASK, SFHE_ENC_CSR, SFHE_ENC_ELL = 0, 1, 2, 3
+SFHE_EXEC_PLAIN, SFHE_EXEC_PERSISTENT, SFHE_EXEC_GRAPH = 1, 2, 4
+ENCODINGS = {"dense": SFHE_ENC_DENSE, "mask": SFHE_ENC_MASK, "csr": SFHE_ENC_CSR, "ell": SFHE_ENC_ELL}
+
+
+class SfheError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"sfhe status {status}: {message}")
+        self.status = status
+
+
+class sfhe_params(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_uint32), ("L", ctypes.c_uint32), ("t", ctypes.c_uint64), ("sigma", ctypes.c_double)]
+
+
+class sfhe_info(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_uint32), ("L", ctypes.c_uint32), ("Lp", ctypes.c_uint32), ("t", ctypes.c_uint64),
+                ("q", ctypes.c_uint64 * 8), ("p", ctypes.c_uint64 * 9), ("ct_words", ctypes.c_uint64),
+                ("ext_words", ctypes.c_uint64), ("num_sms", ctypes.c_int32)]
+
+
+class sfhe_matrix(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int32), ("cols", ctypes.c_int32), ("encoding", ctypes.c_int32),
+                ("nct", ctypes.c_int32), ("ell_width", ctypes.c_int32),
+                ("mask", ctypes.c_void_p), ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p),
+                ("ell_col", ctypes.c_void_p), ("ct", ctypes.c_void_p), ("ext", ctypes.c_void_p)]
+
+
+_vp, _u32, _u64, _i32, _i64, _sz = (ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32,
+                                     ctypes.c_int64, ctypes.c_size_t)
+_P = ctypes.POINTER
+
+# name -> (argtypes, restype)
+_SIGS = {
+    "sfhe_ctx_create": ([_P(sfhe_params), _u64, _P(_vp)], ctypes.c_int),
+    "sfhe_ctx_destroy": ([_vp], None),
+    "sfhe_ctx_info": ([_vp, _P(sfhe_info)], ctypes.c_int),
+    "sfhe_ctx_check": ([_vp, _vp], ctypes.c_int),
+    "sfhe_last_error": ([], ctypes.c_char_p),
+    "sfhe_select_primes": ([_u32, _u32, _vp, _vp], ctypes.c_int),
+    "sfhe_cdt_table": ([ctypes.c_double, _vp], ctypes.c_int),
+    "sfhe_encode_count": ([_vp, _i32, _i32, _i32, _P(_i32), _P(_i32)], ctypes.c_int),
+    "sfhe_encode_fill": ([_vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "sfhe_encrypt": ([_vp, _vp, _vp, _i64, _u64, _vp, _vp], ctypes.c_int),
+    "sfhe_lift_workspace_size": ([_vp, _i64, _P(_sz)], ctypes.c_int),
+    "sfhe_lift": ([_vp, _vp, _i64, _vp, _vp, _sz, _vp], ctypes.c_int),
+    "sfhe_decrypt": ([_vp, _vp, _i64, _vp, _vp], ctypes.c_int),
+    "sfhe_to_coeff": ([_vp, _vp, _i64, _vp, _vp], ctypes.c_int),
+    "sfhe_from_coeff": ([_vp, _vp, _i64, _vp, _vp], ctypes.c_int),
+    "sfhe_export_secret": ([_vp, _vp], ctypes.c_int),
+    "sfhe_export_relin_key": ([_vp, _vp, _vp], ctypes.c_int),
+    "sfhe_matmul_workspace_size": ([_vp, _i32, _P(sfhe_matrix), _P(sfhe_matrix), _u32, _P(_sz)], ctypes.c_int),
+    "sfhe_matmul_dense": ([_vp, _P(sfhe_matrix), _P(sfhe_matrix), _P(sfhe_matrix), _u32, _vp, _sz, _vp], ctypes.c_int),
+    "sfhe_matmul_sparse": ([_vp, _P(sfhe_matrix), _P(sfhe_matrix), _i32, _P(sfhe_matrix), _u32, _vp, _sz, _vp],
+                           ctypes.c_int),
+    "sfhe_matmul_batch": ([_vp, _i32, _P(sfhe_matrix), _P(sfhe_matrix), _P(sfhe_matrix), _u32, _vp, _sz, _vp],
+                          ctypes.c_int),
+    "sfhe_plan_create": ([_vp, _i32, _P(sfhe_matrix), _P(sfhe_matrix), _P(sfhe_matrix), _u32, _vp, _sz, _vp, _P(_vp)],
+                         ctypes.c_int),
+    "sfhe_plan_execute": ([_vp, _vp], ctypes.c_int),
+    "sfhe_plan_stats": ([_vp, _P(_i64), _P(_i64), _P(_i64), _P(_i64)], ctypes.c_int),
+    "sfhe_plan_destroy": ([_vp], None),
+    "sfhe_ct_tensor_scale": ([_vp, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
+    "sfhe_ct_mul_relin": ([_vp, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
+    "sfhe_ntt": ([_vp, _i32, _i32, _vp, _i64, _vp, _vp], ctypes.c_int),
+    "sfhe_prng_words": ([_u64, _u32, _u64, _u64, _u64, _u64, _i64, _vp, _vp], ctypes.c_int),
+}
+
+_lib = None
+
+
+def lib(path: str = LIB_PATH):
+    """The loaded libsfhe.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                               "(the CUDA library is required; there is no CPU path)")
+        L = ctypes.CDLL(path)
+        for name, (argt, rest) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = argt
+            f.restype = rest
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def _check(status: int):
+    if status != SFHE_OK:
+        msg = lib().sfhe_last_error()
+        raise SfheError(status, msg.decode() if msg else "")
+
+
+def _ptr(t) -> int | None:
+    """device/host address of a torch tensor or numpy array (None for None)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"]
+        return t.ctypes.data
+    assert t.is_contiguous()
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+
+
+# ---------------------------------------------------------------- context ---
+def sfhe_ctx_create(N: int, L: int, t: int = 65537, sigma: float = 3.2, seed: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().sfhe_ctx_create(ctypes.byref(sfhe_params(N, L, t, sigma)), seed, ctypes.byref(h)))
+    return h.value
+
+
+def sfhe_ctx_destroy(ctx: int) -> None:
+    lib().sfhe_ctx_destroy(ctx)
+
+
+def sfhe_ctx_info(ctx: int) -> sfhe_info:
+    info = sfhe_info()
+    _check(lib().sfhe_ctx_info(ctx, ctypes.byref(info)))
+    return info
+
+
+def sfhe_ctx_check(ctx: int, stream=None) -> None:
+    _check(lib().sfhe_ctx_check(ctx, _stream(stream)))
+
+
+def sfhe_select_primes(N: int, L: int) -> tuple[list[int], list[int]]:
+    q = np.zeros(8, dtype=np.uint64)
+    p = np.zeros(9, dtype=np.uint64)
+    _check(lib().sfhe_select_primes(N, L, _ptr(q), _ptr(p)))
+    return [int(x) for x in q[:L]], [int(x) for x in p[:L + 1]]
+
+
+def sfhe_cdt_table(sigma: float = 3.2) -> list[int]:
+    T = np.zeros(20, dtype=np.uint64)
+    _check(lib().sfhe_cdt_table(sigma, _ptr(T)))
+    return [int(x) for x in T]
+
+
+# --------------------------------------------------------------- operands ---
+def sfhe_encode_count(values: np.ndarray, encoding: int) -> tuple[int, int]:
+    v = np.ascontiguousarray(values, dtype=np.int64)
+    nct, w = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().sfhe_encode_count(_ptr(v), v.shape[0], v.shape[1], encoding, ctypes.byref(nct), ctypes.byref(w)))
+    return nct.value, w.value
+
+
+def sfhe_encode_fill(values: np.ndarray, encoding: int) -> dict:
+    v = np.ascontiguousarray(values, dtype=np.int64)
+    rows, cols = v.shape
+    nct, width = sfhe_encode_count(v, encoding)
+    out = {"nct": nct, "ell_width": width, "mask": None, "row_ptr": None, "col_idx": None, "ell_col": None,
+           "ct_values": np.zeros(nct, dtype=np.int64), "ct_coords": np.zeros(2 * max(nct, 1), dtype=np.int32)}
+    if encoding == SFHE_ENC_MASK:
+        out["mask"] = np.zeros(rows * cols, dtype=np.uint8)
+    if encoding == SFHE_ENC_CSR:
+        out["row_ptr"] = np.zeros(rows + 1, dtype=np.int32)
+        out["col_idx"] = np.zeros(max(nct, 1), dtype=np.int32)
+    if encoding == SFHE_ENC_ELL:
+        out["ell_col"] = np.zeros(max(rows * width, 1), dtype=np.int32)
+    _check(lib().sfhe_encode_fill(_ptr(v), rows, cols, encoding, _ptr(out["mask"]), _ptr(out["row_ptr"]),
+                                  _ptr(out["col_idx"]), _ptr(out["ell_col"]), _ptr(out["ct_values"]),
+                                  _ptr(out["ct_coords"])))
+    return out
+
+
+def sfhe_encrypt(ctx: int, values: np.ndarray, coords: np.ndarray, matrix_id: int, ct, stream=None) -> None:
+    values = np.ascontiguousarray(values, dtype=np.int64)
+    coords = np.ascontiguousarray(coords, dtype=np.int32)
+    _check(lib().sfhe_encrypt(ctx, _ptr(values), _ptr(coords), values.size, matrix_id, _ptr(ct), _stream(stream)))
+
+
+def sfhe_lift_workspace_size(ctx: int, n: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().sfhe_lift_workspace_size(ctx, n, ctypes.byref(b)))
+    return b.value
+
+
+def sfhe_lift(ctx: int, ct, n: int, ext, work, stream=None) -> None:
+    _check(lib().sfhe_lift(ctx, _ptr(ct), n, _ptr(ext), _ptr(work), work.numel() * work.element_size(),
+                           _stream(stream)))
+
+
+def sfhe_decrypt(ctx: int, ct, n: int, out, stream=None) -> None:
+    _check(lib().sfhe_decrypt(ctx, _ptr(ct), n, _ptr(out), _stream(stream)))
+
+
+def sfhe_to_coeff(ctx: int, inp, npoly: int, out, stream=None) -> None:
+    _check(lib().sfhe_to_coeff(ctx, _ptr(inp), npoly, _ptr(out), _stream(stream)))
+
+
+def sfhe_from_coeff(ctx: int, inp, npoly: int, out, stream=None) -> None:
+    _check(lib().sfhe_from_coeff(ctx, _ptr(inp), npoly, _ptr(out), _stream(stream)))
+
+
+def sfhe_export_secret(ctx: int) -> np.ndarray:
+    info = sfhe_ctx_info(ctx)
+    s = np.zeros(info.N, dtype=np.int8)
+    _check(lib().sfhe_export_secret(ctx, _ptr(s)))
+    return s
+
+
+def sfhe_export_relin_key(ctx: int, out, stream=None) -> None:
+    _check(lib().sfhe_export_relin_key(ctx, _ptr(out), _stream(stream)))
+
+
+# ----------------------------------------------------------------- matmul ---
+def _mats(ms) -> ctypes.Array:
+    arr = (sfhe_matrix * len(ms))()
+    for k, m in enumerate(ms):
+        arr[k] = m
+    return arr
+
+
+def sfhe_matmul_workspace_size(ctx: int, A: list, B: list, flags: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().sfhe_matmul_workspace_size(ctx, len(A), _mats(A), _mats(B), flags, ctypes.byref(b)))
+    return b.value
+
+
+def sfhe_matmul_dense(ctx: int, A, B, C, flags: int, work, stream=None) -> None:
+    _check(lib().sfhe_matmul_dense(ctx, ctypes.byref(A), ctypes.byref(B), ctypes.byref(C), flags, _ptr(work),
+                                   work.numel() * work.element_size(), _stream(stream)))
+
+
+def sfhe_matmul_sparse(ctx: int, A, B, encoding: int, C, flags: int, work, stream=None) -> None:
+    _check(lib().sfhe_matmul_sparse(ctx, ctypes.byref(A), ctypes.byref(B), encoding, ctypes.byref(C), flags,
+                                    _ptr(work), work.numel() * work.element_size(), _stream(stream)))
+
+
+def sfhe_matmul_batch(ctx: int, A: list, B: list, C: list, flags: int, work, stream=None) -> None:
+    _check(lib().sfhe_matmul_batch(ctx, len(A), _mats(A), _mats(B), _mats(C), flags, _ptr(work),
+                                   work.numel() * work.element_size(), _stream(stream)))
+
+
+def sfhe_plan_create(ctx: int, A: list, B: list, C: list, flags: int, work, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().sfhe_plan_create(ctx, len(A), _mats(A), _mats(B), _mats(C), flags, _ptr(work),
+                                  work.numel() * work.element_size(), _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def sfhe_plan_execute(plan: int, stream=None) -> None:
+    _check(lib().sfhe_plan_execute(plan, _stream(stream)))
+
+
+def sfhe_plan_stats(plan: int) -> dict:
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(lib().sfhe_plan_stats(plan, *[ctypes.byref(x) for x in v]))
+    return dict(zip(("products", "entries", "launches", "ctas"), (x.value for x in v)))
+
+
+def sfhe_plan_destroy(plan: int) -> None:
+    lib().sfhe_plan_destroy(plan)
+
+
+# ------------------------------------------------------------ stage calls ---
+def sfhe_ct_tensor_scale(ctx: int, a_ext, b_ext, d, work, stream=None) -> None:
+    _check(lib().sfhe_ct_tensor_scale(ctx, _ptr(a_ext), _ptr(b_ext), _ptr(d), _ptr(work),
+                                      work.numel() * work.element_size(), _stream(stream)))
+
+
+def sfhe_ct_mul_relin(ctx: int, a_ext, b_ext, out, work, stream=None) -> None:
+    _check(lib().sfhe_ct_mul_relin(ctx, _ptr(a_ext), _ptr(b_ext), _ptr(out), _ptr(work),
+                                   work.numel() * work.element_size(), _stream(stream)))
+
+
+def sfhe_ntt(ctx: int, prime_index: int, inverse: bool, inp, npoly: int, out, stream=None) -> None:
+    _check(lib().sfhe_ntt(ctx, prime_index, int(inverse), _ptr(inp), npoly, _ptr(out), _stream(stream)))
+
+
+def sfhe_prng_words(seed: int, domain: int, o0: int, o1: int, o2: int, idx0: int, n: int, out, stream=None) -> None:
+    _check(lib().sfhe_prng_words(seed, domain, o0, o1, o2, idx0, n, _ptr(out), _stream(stream)))

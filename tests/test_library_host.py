@@ -1,0 +1,82 @@
+"""CPU checks of the C ABI library: it loads, exports every entry point the
+header declares, and its host-only helpers (prime selection, error table,
+sparse encoders) agree with the oracle.  No GPU is touched."""
+from __future__ import annotations
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2503_09184_gb300 import _build, sfhe
+    _build.build()
+    return sfhe
+
+
+def _declared_functions():
+    hdr = open(os.path.join(ROOT, "include", "sfhe.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    return sorted(set(re.findall(r"\b(sfhe_[a-z_0-9]+)\s*\(", hdr)))
+
+
+def test_header_symbols_exported(S):
+    import ctypes
+    lib = ctypes.CDLL(S.LIB_PATH)
+    declared = _declared_functions()
+    assert len(declared) >= 29
+    for name in declared:
+        assert hasattr(lib, name), name
+    # the binding wraps exactly the declared entry points
+    assert sorted(S.exported_symbols()) == declared
+
+
+@pytest.mark.parametrize("N,L", [(4096, 2), (8192, 4), (16384, 8), (4096, 3)])
+def test_primes_match_oracle(S, N, L):
+    from oracle import oracle as O
+    q, p = S.sfhe_select_primes(N, L)
+    ref = O.ntt_primes(N, 2 * L + 1)
+    assert q == ref[:L] and p == ref[L:]
+
+
+def test_cdt_matches_oracle_and_golden(S):
+    from oracle import oracle as O
+    path = os.path.join(ROOT, "tests", "golden", "cdt_sigma3.2.txt")
+    golden = [int(l.split()[1]) for l in open(path) if l.strip() and not l.startswith("#")]
+    assert S.sfhe_cdt_table(3.2) == O.cdt(3.2) == golden
+
+
+@pytest.mark.parametrize("enc", ["dense", "mask", "csr", "ell"])
+def test_encoders_match_oracle(S, enc):
+    from oracle import oracle as O
+    from workloads import sparse_int_matrix
+    A = sparse_int_matrix(7, 9, 0.6, -16, 16, 3)
+    A[2, :] = 0
+    f = S.sfhe_encode_fill(A, S.ENCODINGS[enc])
+    ref = O.encode(A, O.ENCODINGS[enc])
+    assert f["nct"] == len(ref.values)
+    assert list(f["ct_values"]) == ref.values
+    assert [tuple(x) for x in f["ct_coords"][: 2 * f["nct"]].reshape(-1, 2)] == ref.coords
+    if enc == "mask":
+        assert (f["mask"].reshape(A.shape) == ref.mask).all()
+    if enc == "csr":
+        assert list(f["row_ptr"]) == list(ref.row_ptr) and list(f["col_idx"][: f["nct"]]) == list(ref.col_idx)
+    if enc == "ell":
+        assert f["ell_width"] == ref.width
+        assert (f["ell_col"][: f["nct"]].reshape(7, ref.width) == ref.ell_col).all()
+
+
+def test_encoder_edge_cases(S):
+    # all-zero matrix: CSR and ELL store nothing
+    Z = np.zeros((3, 4), dtype=np.int64)
+    assert S.sfhe_encode_count(Z, S.SFHE_ENC_CSR) == (0, 0)
+    assert S.sfhe_encode_count(Z, S.SFHE_ENC_ELL) == (0, 0)
+    assert S.sfhe_encode_count(Z, S.SFHE_ENC_DENSE) == (12, 0)
+    with pytest.raises(S.SfheError) as e:
+        S.sfhe_encode_count(Z, 9)
+    assert e.value.status == S.SFHE_EINVAL
