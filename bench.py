@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--plain-rows", type=int, default=2, help="rows of A timed through the plain path")
     ap.add_argument("--cpu-products", type=int, default=12, help="oracle products in the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shape", default=None, help="M,K,Nc override (small profiling cases)")
     return ap.parse_args()
 
 
@@ -129,7 +130,7 @@ class ClockSampler:
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k]})
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
         power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows), "power_w_max": max(power) if power else None}
@@ -210,6 +211,11 @@ def main():
 
     ring = W.SWEEP_RING
     shape = W.sweep(SPARSITY)
+    workload = "sweep-64x64x64-s0.5"
+    if args.shape:
+        M, K, Nc = (int(x) for x in args.shape.split(","))
+        shape = W.MatmulShape(M, K, Nc, shape.sparsity, shape.lo, shape.hi, shape.seed)
+        workload = f"sweep-{M}x{K}x{Nc}-s0.5"
     A_vals, B_vals = W.operands(shape)
     ctx = api.Context(ring.N, ring.L, seed=0)
     stream = torch.cuda.current_stream()
@@ -331,7 +337,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": "sweep-64x64x64-s0.5", "M": shape.M, "K": shape.K, "Nc": shape.Nc,
+        "config": {"workload": workload, "M": shape.M, "K": shape.K, "Nc": shape.Nc,
                    "sparsity": SPARSITY, "encoding": ENCODING, "N": ring.N, "L": ring.L, "t": W.T_PLAIN,
                    "products_per_step": products, "dense_products": shape.M * shape.K * shape.Nc,
                    "l2": f"inputs larger than L2 (lifted A and B: {(A.ext.numel() + B.ext.numel()) * 8 / 1e9:.1f} GB)",
