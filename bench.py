@@ -38,12 +38,13 @@ METRIC = "ct-mults/s and encrypted matmul ms at 50% sparsity, batched vs plain, 
 UNIT = "ct-mults/s"
 SPARSITY = 0.5
 ENCODING = "csr"
-# nominal integer multiply-add rate of a Blackwell SM (32-bit IMAD, results
-# per clock) and the 32-bit multiply-adds one 64-bit Shoup modular multiply
-# needs (mul.hi.u64: 4 partial products, two mul.lo.u64: 3 each, counted as
-# 10 multiply-add issues); see DESIGN.md "Roofline".
+# The path is bound by the integer multiply pipe.  Work is counted in 32x32-bit
+# multiplies (partial products) that the algorithm's modular arithmetic needs:
+# a 30-bit Shoup or Barrett multiply 3, a 64-bit Shoup multiply 10 (mul.hi.u64
+# 4 + two mul.lo.u64 3 each), a 64-bit Barrett reduction 7, a 30x54-bit split
+# product 2.  Peak: 64 integer multiply-adds per clock per SM (Blackwell's
+# integer multiply rate) x 152 SMs x the maximum SM clock.
 IMAD_PER_CLK_PER_SM = 64
-IMAD_PER_MULMOD = 10
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 
@@ -62,32 +63,38 @@ def parse():
 
 
 # --------------------------------------------------------- algorithmic work ---
-def mul64_per_product(N: int, L: int) -> int:
-    """64-bit multiply instructions (mul.lo / mul.hi) one product needs:
-    tensor (14 per coefficient and limb of Q u P), 3 (L+Lp) inverse NTTs
-    (3 per butterfly), exact scale-and-round (10L + 4 L Lp + 9 Lp per
-    coefficient of each of the 3 polynomials)."""
-    Lp = L + 1
-    LQP = L + Lp
+def tensor_base_size(logN: int, L: int) -> int:
+    """tensor-base primes K (as the library chooses them)."""
+    return (10 * (logN + 108 * L + 27) + 298) // 299
+
+
+def mults_per_product(N: int, L: int) -> int:
+    """32-bit multiplies of one product: tensor over the K tensor-base primes
+    (10 per coefficient and prime), 3K inverse NTTs (3 per butterfly), exact
+    scale-and-round of the 3 polynomials (6K + 2KL + 9L per coefficient: the
+    CRT digits, the overflow count, the fixed-point fraction, and the
+    reconstruction mod every q_i)."""
     logN = int(math.log2(N))
-    tensor = 14 * LQP * N
-    intt = 3 * LQP * (N // 2) * logN * 3
-    scale = 3 * N * (10 * L + 4 * L * Lp + 9 * Lp)
+    K = tensor_base_size(logN, L)
+    tensor = 10 * K * N
+    intt = 3 * K * (N // 2) * logN * 3
+    scale = 3 * N * (6 * K + 2 * K * L + 9 * L)
     return tensor + intt + scale
 
 
-def mul64_per_entry(N: int, L: int) -> int:
-    """per output entry with at least one product: L (L + 2) forward NTTs of
-    the accumulated sums (with their Barrett reduction) and the key products."""
+def mults_per_entry(N: int, L: int) -> int:
+    """per output entry with at least one product: L (L + 2) forward 64-bit
+    NTTs of the accumulated sums (10 per butterfly, Barrett-reduced inputs),
+    the key products (10 each) and the final reductions."""
     logN = int(math.log2(N))
-    ntts = L * (L + 2) * ((N // 2) * logN * 3 + 2 * N)
-    keyprod = 2 * L * L * N * 3
-    final = 2 * L * N * 2
+    ntts = L * (L + 2) * ((N // 2) * logN * 10 + 7 * N)
+    keyprod = 2 * L * L * N * 10
+    final = 2 * L * N * 7
     return ntts + keyprod + final
 
 
-def mulmods(products: int, entries: int, N: int, L: int) -> float:
-    return (products * mul64_per_product(N, L) + entries * mul64_per_entry(N, L)) / 3.0
+def mults(products: int, entries: int, N: int, L: int) -> float:
+    return products * mults_per_product(N, L) + entries * mults_per_entry(N, L)
 
 
 # ------------------------------------------------------------------- clocks ---
@@ -223,8 +230,8 @@ def main():
     # setup (untimed): encryption of the operands
     A = api.encrypt_matrix(ctx, A_vals, ENCODING, 1, lift=False)
     B = api.encrypt_matrix(ctx, B_vals, "dense", 2, lift=False)
-    A.ext = api._dev_u64((A.nct, 2, ctx.L + ctx.Lp, ctx.N))
-    B.ext = api._dev_u64((B.nct, 2, ctx.L + ctx.Lp, ctx.N))
+    A.ext = api._dev_u32((A.nct, 2, ctx.K, ctx.N))
+    B.ext = api._dev_u32((B.nct, 2, ctx.K, ctx.N))
     C = api.result_matrix(ctx, shape.M, shape.Nc)
     lift_ws = torch.empty(S.sfhe_lift_workspace_size(ctx.h, max(A.nct, B.nct)), dtype=torch.uint8, device="cuda")
     flags = api.PERSISTENT
@@ -329,10 +336,10 @@ def main():
     plain_equal = bool((pers_rows == plain_rows).all())
 
     value = products * world / (ms / 1e3)
-    work = mulmods(products, nonempty_entries, ring.N, ring.L)
+    work = mults(products, nonempty_entries, ring.N, ring.L)
     achieved = work / (kms / 1e3) / 1e12
     sm_clock = clk.get("sm_mhz") or SM_MAX_MHZ
-    peak = SM_COUNT * IMAD_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / IMAD_PER_MULMOD / 1e12
+    peak = SM_COUNT * IMAD_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -340,7 +347,7 @@ def main():
         "config": {"workload": workload, "M": shape.M, "K": shape.K, "Nc": shape.Nc,
                    "sparsity": SPARSITY, "encoding": ENCODING, "N": ring.N, "L": ring.L, "t": W.T_PLAIN,
                    "products_per_step": products, "dense_products": shape.M * shape.K * shape.Nc,
-                   "l2": f"inputs larger than L2 (lifted A and B: {(A.ext.numel() + B.ext.numel()) * 8 / 1e9:.1f} GB)",
+                   "l2": f"inputs larger than L2 (lifted A and B: {(A.ext.numel() + B.ext.numel()) * A.ext.element_size() / 1e9:.1f} GB)",
                    "step": "lift A and B + work list + persistent matmul", "parallelism": f"replicas x{world}"},
         "matmul_ms": ms,
         "kernel_ms": kms,
@@ -351,10 +358,11 @@ def main():
         "speedup_batched_vs_plain": value / world / plain_rate,
         "e2e": {"value": products * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tmulmod/s",
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T int32-mul/s",
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "k_matmul_persistent<13,4>",
-                     "peak_note": "152 SM x 64 IMAD/clk x 2070 MHz / 10 IMAD per 64-bit Shoup mulmod (derived)",
+                     "work_per_launch": work,
+                     "peak_note": "152 SM x 64 int32 multiplies/clk x 2070 MHz (derived from unit counts and clock)",
                      "frac_at_measured_clock": achieved / (peak * sm_clock / SM_MAX_MHZ)},
         "gpu_launches": (lift_launches + 1) * args.steps,
         "clocks": clk,

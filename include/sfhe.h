@@ -27,8 +27,10 @@
  *      ciphertext  [2 (c0, c1)][L][N], NTT form (slot i = evaluation at
  *                  psi^(2 bitrev(i) + 1), psi the smallest primitive 2N-th
  *                  root of unity mod the limb's prime);
- *      lifted      [2][L + Lp][N], NTT form over Q u P (Lp = L + 1
- *                  extension primes, the next primes of the same rule);
+ *      lifted      [2][K][N] uint32, NTT form over the tensor base
+ *                  B = b_0 .. b_{K-1}: the K largest primes below 2^30 with
+ *                  b = 1 mod 2N, enough that B > N Q^2 2^27 (the exact
+ *                  integer tensor of two ciphertexts fits with margin);
  *      coefficient [2][L][N] in coefficient form (sfhe_to_coeff).
  */
 #ifndef SFHE_H
@@ -71,12 +73,13 @@ typedef struct {
 } sfhe_params;
 
 typedef struct {
-    uint32_t N, L, Lp;
+    uint32_t N, L;
+    uint32_t K;             /* tensor-base primes */
     uint64_t t;
     uint64_t q[8];          /* ciphertext primes, descending */
-    uint64_t p[9];          /* extension primes, descending */
-    uint64_t ct_words;      /* 2 L N */
-    uint64_t ext_words;     /* 2 (L + Lp) N */
+    uint32_t b[32];         /* tensor-base primes, descending */
+    uint64_t ct_words;      /* 2 L N (uint64 words) */
+    uint64_t ext_words;     /* 2 K N (uint32 words) */
     int32_t num_sms;
 } sfhe_info;
 
@@ -94,9 +97,9 @@ typedef struct sfhe_plan sfhe_plan;
  *   ELL:   ell_width slots per row, ell_col[rows*ell_width] (-1 = padding);
  *          ciphertext r*ell_width + s encrypts slot s of row r (padding slots
  *          hold encryptions of zero and are skipped).
- * `ct` [nct][2][L][N] and `ext` [nct][2][L+Lp][N] are device buffers; the
- * matmul reads `ext` of A and B (fill it with sfhe_lift) and writes `ct`
- * of C (which must be DENSE, rows*cols ciphertexts).
+ * `ct` [nct][2][L][N] (uint64) and `ext` [nct][2][K][N] (uint32) are device
+ * buffers; the matmul reads `ext` of A and B (fill it with sfhe_lift) and
+ * writes `ct` of C (which must be DENSE, rows*cols ciphertexts).
  */
 typedef struct {
     int32_t rows, cols, encoding, nct, ell_width;
@@ -105,7 +108,7 @@ typedef struct {
     const int32_t* col_idx;
     const int32_t* ell_col;
     uint64_t* ct;
-    uint64_t* ext;
+    uint32_t* ext;
 } sfhe_matrix;
 
 /* ------------------------------------------------------------ context --- */
@@ -122,11 +125,12 @@ sfhe_status sfhe_ctx_info(const sfhe_ctx* ctx, sfhe_info* out);
 sfhe_status sfhe_ctx_check(sfhe_ctx* ctx, void* stream);
 const char* sfhe_last_error(void);
 
-/* Host-only helpers (no device needed).  Primes: the L largest primes below
- * 2^54 that are 1 mod 2N, then the next L+1 (deterministic Miller-Rabin with
- * the bases 2..37).  CDT: T[k] = floor(2^63 P(|e| <= k)) of the rounded
- * Gaussian of width sigma, k < 19, T[19] = 2^63. */
-sfhe_status sfhe_select_primes(uint32_t N, uint32_t L, uint64_t* q, uint64_t* p);
+/* Host-only helpers (no device needed).  Primes: q[L] the L largest primes
+ * below 2^54 that are 1 mod 2N; b[*K] the *K largest below 2^30 of the same
+ * form (the tensor base); primality by deterministic Miller-Rabin with the
+ * bases 2..37.  CDT: T[k] = floor(2^63 P(|e| <= k)) of the rounded Gaussian
+ * of width sigma, k < 19, T[19] = 2^63. */
+sfhe_status sfhe_select_primes(uint32_t N, uint32_t L, uint64_t* q, uint32_t* b, int32_t* K);
 sfhe_status sfhe_cdt_table(double sigma, uint64_t* T20);
 
 /* ---------------------------------------------------------- operands --- */
@@ -147,10 +151,12 @@ sfhe_status sfhe_encode_fill(const int64_t* values, int32_t rows, int32_t cols, 
  * ciphertext n is drawn from the stream (matrix_id, coords[2n], coords[2n+1]). */
 sfhe_status sfhe_encrypt(sfhe_ctx* ctx, const int64_t* values, const int32_t* coords, int64_t n, uint64_t matrix_id,
                          uint64_t* ct, void* stream);
-/* Exact centred extension to Q u P: ext[n] (device) from ct[n] (device).
- * Needs sfhe_lift_workspace_size() bytes of device workspace. */
+/* Exact centred lift to the tensor base: ext[n] (device, uint32) from ct[n]
+ * (device): every coefficient's representative in (-Q/2, Q/2) reduced mod
+ * each b_k, NTT form.  Needs sfhe_lift_workspace_size() bytes of device
+ * workspace (a smaller workspace processes the ciphertexts in chunks). */
 sfhe_status sfhe_lift_workspace_size(const sfhe_ctx* ctx, int64_t n, size_t* bytes);
-sfhe_status sfhe_lift(sfhe_ctx* ctx, const uint64_t* ct, int64_t n, uint64_t* ext, void* work, size_t work_bytes,
+sfhe_status sfhe_lift(sfhe_ctx* ctx, const uint64_t* ct, int64_t n, uint32_t* ext, void* work, size_t work_bytes,
                       void* stream);
 /* Decryption of the constant coefficient of ct[n] (device) into out[n]
  * (device int64), centred in (-t/2, t/2]. */
@@ -193,18 +199,21 @@ sfhe_status sfhe_plan_stats(const sfhe_plan* plan, int64_t* products, int64_t* e
 void sfhe_plan_destroy(sfhe_plan* plan);
 
 /* ------------------------------------------------- stage entry points --- */
-/* One product's tensor and exact scale-and-round: d[3][L][N] coefficient
- * form from lifted a, b (device).  Workspace: 3 (L+Lp) N words. */
-sfhe_status sfhe_ct_tensor_scale(sfhe_ctx* ctx, const uint64_t* a_ext, const uint64_t* b_ext, uint64_t* d, void* work,
+/* One product's tensor and exact scale-and-round (Alg. 1 "a <- a x b"):
+ * d[3][L][N] (uint64, coefficient form) from lifted a, b (device).
+ * Workspace: 3 K N uint32 words. */
+sfhe_status sfhe_ct_tensor_scale(sfhe_ctx* ctx, const uint32_t* a_ext, const uint32_t* b_ext, uint64_t* d, void* work,
                                  size_t work_bytes, void* stream);
-/* One product multiplied and relinearised, NTT form [2][L][N] (plain path).
- * Workspace: (3 (L+Lp) + 3 L + (L+2) L) N words. */
-sfhe_status sfhe_ct_mul_relin(sfhe_ctx* ctx, const uint64_t* a_ext, const uint64_t* b_ext, uint64_t* out, void* work,
+/* One product multiplied and relinearised (Alg. 1 "a <- a x b; fhe_relin"),
+ * NTT form [2][L][N] (plain path).  Workspace: 3 K N uint32 words (rounded up
+ * to 256 bytes) + (3 L + (L+2) L) N uint64 words. */
+sfhe_status sfhe_ct_mul_relin(sfhe_ctx* ctx, const uint32_t* a_ext, const uint32_t* b_ext, uint64_t* out, void* work,
                               size_t work_bytes, void* stream);
 /* Forward / inverse NTT of npoly polynomials (device, [npoly][N]) modulo
- * prime `prime_index` (0..L-1: q_i, L..L+Lp-1: p_j). */
-sfhe_status sfhe_ntt(sfhe_ctx* ctx, int32_t prime_index, int32_t inverse, const uint64_t* in, int64_t npoly,
-                     uint64_t* out, void* stream);
+ * prime `prime_index`: 0..L-1 the q_i (uint64 words), L..L+K-1 the b_k
+ * (uint32 words). */
+sfhe_status sfhe_ntt(sfhe_ctx* ctx, int32_t prime_index, int32_t inverse, const void* in, int64_t npoly, void* out,
+                     void* stream);
 /* Words idx0 .. idx0+n-1 of the generator stream (seed, domain, o0, o1, o2)
  * into out (device). */
 sfhe_status sfhe_prng_words(uint64_t seed, uint32_t domain, uint64_t o0, uint64_t o1, uint64_t o2, uint64_t idx0,

@@ -16,8 +16,17 @@ def _dev_u64(shape) -> torch.Tensor:
     return torch.empty(shape, dtype=torch.int64, device="cuda")
 
 
+def _dev_u32(shape) -> torch.Tensor:
+    """uint32 words in an int32 device tensor (same bits)."""
+    return torch.empty(shape, dtype=torch.int32, device="cuda")
+
+
 def to_numpy_u64(t: torch.Tensor) -> np.ndarray:
     return t.detach().cpu().numpy().view(np.uint64)
+
+
+def to_numpy_u32(t: torch.Tensor) -> np.ndarray:
+    return t.detach().cpu().numpy().view(np.uint32)
 
 
 class Context:
@@ -26,9 +35,9 @@ class Context:
             raise RuntimeError("a CUDA device is required")
         self.h = S.sfhe_ctx_create(N, L, t, sigma, seed)
         info = S.sfhe_ctx_info(self.h)
-        self.N, self.L, self.Lp, self.t = info.N, info.L, info.Lp, info.t
+        self.N, self.L, self.K, self.t = info.N, info.L, info.K, info.t
         self.q = [int(x) for x in info.q[: self.L]]
-        self.p = [int(x) for x in info.p[: self.Lp]]
+        self.b = [int(x) for x in info.b[: self.K]]
         self.ct_words, self.ext_words, self.num_sms = int(info.ct_words), int(info.ext_words), info.num_sms
         self.seed = seed
 
@@ -87,7 +96,7 @@ def encrypt_matrix(ctx: Context, values: np.ndarray, encoding: int | str, matrix
 
 
 def lift_matrix(ctx: Context, M: EncMatrix, stream=None):
-    M.ext = _dev_u64((max(M.nct, 1), 2, ctx.L + ctx.Lp, ctx.N))
+    M.ext = _dev_u32((max(M.nct, 1), 2, ctx.K, ctx.N))
     if M.nct:
         work = torch.empty(S.sfhe_lift_workspace_size(ctx.h, M.nct), dtype=torch.uint8, device="cuda")
         S.sfhe_lift(ctx.h, M.ct, M.nct, M.ext, work, stream)
@@ -112,6 +121,18 @@ def import_coeff(ctx: Context, coeff: np.ndarray, lift: bool = True, stream=None
     if lift:
         lift_matrix(ctx, M, stream)
     return M
+
+
+def ext_to_coeff(ctx: Context, ext: torch.Tensor) -> np.ndarray:
+    """coefficient form of lifted ciphertexts: [n][2][K][N] uint32 residues mod b_k."""
+    n = ext.shape[0]
+    out = np.zeros((n, 2, ctx.K, ctx.N), dtype=np.uint32)
+    for k in range(ctx.K):
+        src = ext[:, :, k].contiguous()
+        dst = torch.empty_like(src)
+        S.sfhe_ntt(ctx.h, ctx.L + k, True, src, 2 * n, dst)
+        out[:, :, k] = to_numpy_u32(dst)
+    return out
 
 
 def to_coeff(ctx: Context, ct: torch.Tensor, n: int, stream=None) -> np.ndarray:

@@ -46,6 +46,7 @@ struct sfhe_ctx {
     int num_sms;
     RnsConsts rc;
     u64* d_tw;
+    u32* d_twb;
     u64* d_s;
     signed char* d_s_coeff;
     u64* d_rlk;
@@ -69,7 +70,8 @@ struct sfhe_plan {
     u64* d_scratch;
     size_t scratch_stride;
     int grid;
-    u64 *d_T, *d_D, *d_U;
+    u32* d_T;
+    u64 *d_D, *d_U;
     cudaGraph_t graph;
     cudaGraphExec_t gexec;
 };
@@ -77,14 +79,19 @@ struct sfhe_plan {
 extern "C" const char* sfhe_last_error(void) { return g_last_error.c_str(); }
 
 // ---------------------------------------------------------------- helpers ---
-extern "C" sfhe_status sfhe_select_primes(uint32_t N, uint32_t L, uint64_t* q, uint64_t* p)
+extern "C" sfhe_status sfhe_select_primes(uint32_t N, uint32_t L, uint64_t* q, uint32_t* b, int32_t* K)
 {
-    if (!q || !p) return fail(SFHE_EINVAL, "null output");
-    if (N < 2 || (N & (N - 1)) || L < 1 || L > SFHE_MAX_L) return fail(SFHE_EUNSUPPORTED, "N=%u L=%u", N, L);
-    std::vector<uint64_t> pr;
-    if (!ntt_primes(N, 2 * L + 1, pr)) return fail(SFHE_EUNSUPPORTED, "not enough primes");
-    for (uint32_t i = 0; i < L; i++) q[i] = pr[i];
-    for (uint32_t j = 0; j <= L; j++) p[j] = pr[L + j];
+    if (!q || !b || !K) return fail(SFHE_EINVAL, "null output");
+    int logN = 0;
+    while ((1u << logN) < N) logN++;
+    if ((1u << logN) != N || logN < 1 || logN > 15 || L < 1 || L > SFHE_MAX_L)
+        return fail(SFHE_EUNSUPPORTED, "N=%u L=%u", N, L);
+    *K = tensor_base_size(logN, (int)L);
+    if (*K > SFHE_MAX_K) return fail(SFHE_EUNSUPPORTED, "tensor base larger than %d primes", SFHE_MAX_K);
+    std::vector<uint64_t> pq, pb;
+    if (!ntt_primes(N, (int)L, pq, 54) || !ntt_primes(N, *K, pb, 30)) return fail(SFHE_EUNSUPPORTED, "not enough primes");
+    for (uint32_t i = 0; i < L; i++) q[i] = pq[i];
+    for (int k = 0; k < *K; k++) b[k] = (uint32_t)pb[k];
     return SFHE_OK;
 }
 
@@ -101,6 +108,7 @@ extern "C" void sfhe_ctx_destroy(sfhe_ctx* c)
 {
     if (!c) return;
     cudaFree(c->d_tw);
+    cudaFree(c->d_twb);
     cudaFree(c->d_s);
     cudaFree(c->d_s_coeff);
     cudaFree(c->d_rlk);
@@ -136,26 +144,33 @@ extern "C" sfhe_status sfhe_ctx_create(const sfhe_params* params, uint64_t seed,
     rc.N = (int)N;
     rc.logN = logN;
     rc.L = (int)L;
-    rc.Lp = (int)L + 1;
+    rc.K = tensor_base_size(logN, (int)L);
     rc.t = params->t;
     rc.seed = seed;
-    std::vector<uint64_t> pr;
-    if (!ntt_primes(N, 2 * L + 1, pr)) return bail(fail(SFHE_EUNSUPPORTED, "not enough primes"));
-    for (int k = 0; k < rc.L + rc.Lp; k++) rc.m[k].q = pr[k];
-    fill_constants(rc);
+    std::vector<uint64_t> pq, pb;
+    if (!ntt_primes(N, rc.L, pq, 54) || !ntt_primes(N, rc.K, pb, 30))
+        return bail(fail(SFHE_EUNSUPPORTED, "not enough primes"));
+    for (int i = 0; i < rc.L; i++) rc.m[i].q = pq[i];
+    for (int k = 0; k < rc.K; k++) rc.mb[k].b = (u32)pb[k];
+    if (!fill_constants(rc)) return bail(fail(SFHE_EUNSUPPORTED, "tensor base too small for these parameters"));
     cdt_table(params->sigma, rc.cdt);
 
-    const int LQP = rc.L + rc.Lp;
-    std::vector<uint64_t> tw((size_t)LQP * 4 * N);
-    for (int k = 0; k < LQP; k++) twiddles(rc.m[k].q, N, tw.data() + (size_t)k * 4 * N, &rc.ninv[k], &rc.wlast[k]);
+    std::vector<uint64_t> tw((size_t)rc.L * 4 * N);
+    for (int i = 0; i < rc.L; i++) twiddles(rc.m[i].q, N, tw.data() + (size_t)i * 4 * N, &rc.ninv[i], &rc.wlast[i]);
+    std::vector<uint32_t> twb((size_t)rc.K * 4 * N);
+    for (int k = 0; k < rc.K; k++)
+        twiddles32(rc.mb[k].b, N, twb.data() + (size_t)k * 4 * N, &rc.ninv_b[k], &rc.wlast_b[k]);
 
     const size_t rlk_words = (size_t)L * 2 * L * N;
-    if (cudaMalloc(&c->d_tw, tw.size() * 8) != cudaSuccess || cudaMalloc(&c->d_s, (size_t)L * N * 8) != cudaSuccess ||
+    if (cudaMalloc(&c->d_tw, tw.size() * 8) != cudaSuccess || cudaMalloc(&c->d_twb, twb.size() * 4) != cudaSuccess ||
+        cudaMalloc(&c->d_s, (size_t)L * N * 8) != cudaSuccess ||
         cudaMalloc(&c->d_s_coeff, N) != cudaSuccess || cudaMalloc(&c->d_rlk, rlk_words * 8) != cudaSuccess ||
         cudaMalloc(&c->d_rlk_sh, rlk_words * 8) != cudaSuccess || cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess)
         return bail(fail(SFHE_ENOMEM, "device allocation of the context failed"));
     rc.tw = c->d_tw;
+    rc.twb = c->d_twb;
     if (cudaMemcpy(c->d_tw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_twb, twb.data(), twb.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess)
         return bail(fail(SFHE_ECUDA, "table upload failed"));
     cudaError_t e = launch_keygen(rc, c->d_s, c->d_s_coeff, c->d_rlk, c->d_rlk_sh, c->d_err, 0);
@@ -174,12 +189,12 @@ extern "C" sfhe_status sfhe_ctx_info(const sfhe_ctx* c, sfhe_info* out)
     memset(out, 0, sizeof(*out));
     out->N = (uint32_t)c->rc.N;
     out->L = (uint32_t)c->rc.L;
-    out->Lp = (uint32_t)c->rc.Lp;
+    out->K = (uint32_t)c->rc.K;
     out->t = c->rc.t;
     for (int i = 0; i < c->rc.L; i++) out->q[i] = c->rc.m[i].q;
-    for (int j = 0; j < c->rc.Lp; j++) out->p[j] = c->rc.m[c->rc.L + j].q;
+    for (int k = 0; k < c->rc.K; k++) out->b[k] = c->rc.mb[k].b;
     out->ct_words = (uint64_t)2 * c->rc.L * c->rc.N;
-    out->ext_words = (uint64_t)2 * (c->rc.L + c->rc.Lp) * c->rc.N;
+    out->ext_words = (uint64_t)2 * c->rc.K * c->rc.N;
     out->num_sms = c->num_sms;
     return SFHE_OK;
 }
@@ -318,11 +333,11 @@ extern "C" sfhe_status sfhe_lift_workspace_size(const sfhe_ctx* c, int64_t n, si
 {
     if (!c || !bytes) return fail(SFHE_EINVAL, "null argument");
     const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n, kLiftChunk));
-    *bytes = (size_t)chunk * 2 * (c->rc.L + c->rc.Lp) * c->rc.N * 8;
+    *bytes = (size_t)chunk * 2 * c->rc.N * (c->rc.L * 8 + c->rc.K * 4);
     return SFHE_OK;
 }
 
-extern "C" sfhe_status sfhe_lift(sfhe_ctx* c, const uint64_t* ct, int64_t n, uint64_t* ext, void* work,
+extern "C" sfhe_status sfhe_lift(sfhe_ctx* c, const uint64_t* ct, int64_t n, uint32_t* ext, void* work,
                                  size_t work_bytes, void* stream)
 {
     if (!c) return fail(SFHE_EINVAL, "null context");
@@ -330,23 +345,21 @@ extern "C" sfhe_status sfhe_lift(sfhe_ctx* c, const uint64_t* ct, int64_t n, uin
     if (n == 0) return SFHE_OK;
     if (!ct || !ext || !work) return fail(SFHE_EINVAL, "null argument");
     const RnsConsts& rc = c->rc;
-    const size_t N = rc.N, L = rc.L, Lp = rc.Lp;
-    const size_t per_ct = 2 * (L + Lp) * N * 8;
+    const size_t N = rc.N, L = rc.L, K = rc.K;
+    const size_t per_ct = 2 * N * (L * 8 + K * 4);
     const int64_t chunk = (int64_t)(work_bytes / per_ct);
     if (chunk < 1) return fail(SFHE_ENOMEM, "lift workspace too small");
     cudaStream_t s = as_stream(stream);
-    u64* wq = (u64*)work;                    // [2c][L][N]
-    const size_t ctw = 2 * L * N, extw = 2 * (L + Lp) * N;
+    u64* wq = (u64*)work;  // [2c][L][N] coefficient form over Q
+    const size_t ctw = 2 * L * N, extw = 2 * K * N;
     for (int64_t n0 = 0; n0 < n; n0 += chunk) {
         const int64_t cnt = std::min(chunk, n - n0);
-        u64* wp = wq + (size_t)cnt * 2 * L * N;  // [2c][Lp][N]
+        u32* wb = (u32*)(wq + (size_t)cnt * 2 * L * N);  // [2c][K][N] coefficient form over B
         const u64* src = ct + n0 * ctw;
-        u64* dst = ext + n0 * extw;
+        u32* dst = ext + n0 * extw;
         cudaError_t e = launch_ntt(rc, true, src, L * N, 0, wq, L * N, 0, 0, (int)L, 2 * cnt, s);
-        if (e == cudaSuccess) e = launch_lift_extend(rc, wq, wp, 2 * cnt, s);
-        if (e == cudaSuccess) e = launch_ntt(rc, false, wp, Lp * N, 0, dst, (L + Lp) * N, (int)L, (int)L, (int)Lp, 2 * cnt, s);
-        if (e == cudaSuccess)
-            e = cudaMemcpy2DAsync(dst, (L + Lp) * N * 8, src, L * N * 8, L * N * 8, 2 * cnt, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = launch_lift_extend(rc, wq, wb, 2 * cnt, s);
+        if (e == cudaSuccess) e = launch_ntt32(rc, false, wb, K * N, 0, dst, K * N, 0, 0, (int)K, 2 * cnt, s);
         if (e != cudaSuccess) return fail(SFHE_ECUDA, "lift: %s", cudaGetErrorString(e));
     }
     return SFHE_OK;
@@ -537,7 +550,7 @@ Layout layout_of(const sfhe_ctx* c, const sfhe_plan& P, uint32_t flags, int* gri
     off += align256(P.entries.size() * sizeof(Entry));
     Lo.rowlist = off;
     off += align256(P.rowlist.size() * sizeof(int2));
-    const size_t N = c->rc.N, L = c->rc.L, LQP = c->rc.L + c->rc.Lp;
+    const size_t N = c->rc.N, L = c->rc.L, K = c->rc.K;
     *grid_out = 0;
     *stride_out = 0;
     if (flags & SFHE_EXEC_PERSISTENT) {
@@ -552,7 +565,7 @@ Layout layout_of(const sfhe_ctx* c, const sfhe_plan& P, uint32_t flags, int* gri
     }
     if (flags & SFHE_EXEC_PLAIN) {
         Lo.T = off;
-        off += align256(3 * LQP * N * 8);
+        off += align256(3 * K * N * 4);
         Lo.D = off;
         off += align256(3 * L * N * 8);
         Lo.U = off;
@@ -589,15 +602,15 @@ sfhe_status launch_plan(sfhe_plan* P, cudaStream_t s)
     // plain: C = 0, then one launch sequence per product
     for (size_t m = 0; m < P->mms.size(); m++)
         if (P->c_words[m]) CUDA_TRY(cudaMemsetAsync(P->mms[m].C, 0, P->c_words[m] * 8, s));
-    const size_t N = rc.N, L = rc.L, LQP = rc.L + rc.Lp;
-    const size_t ctw = 2 * L * N, extw = 2 * LQP * N;
+    const size_t N = rc.N, L = rc.L, K = rc.K;
+    const size_t ctw = 2 * L * N, extw = 2 * K * N;
     for (const Entry& en : P->entries) {
         const MmDesc& mm = P->mms[en.mm];
         u64* Cout = mm.C + ((size_t)en.row * mm.Nc + en.col) * ctw;
         for (int p = 0; p < en.count; p++) {
             const int2 it = P->rowlist[en.first + p];
-            const u64* a = mm.A_ext + (size_t)it.x * extw;
-            const u64* b = mm.B_ext + ((size_t)it.y * mm.Nc + en.col) * extw;
+            const u32* a = mm.A_ext + (size_t)it.x * extw;
+            const u32* b = mm.B_ext + ((size_t)it.y * mm.Nc + en.col) * extw;
             CUDA_TRY(launch_tensor_intt(rc, a, b, P->d_T, s));
             CUDA_TRY(launch_scale_round(rc, P->d_T, P->d_D, s));
             CUDA_TRY(launch_relin_ntt(rc, P->d_D, P->d_U, s));
@@ -651,7 +664,7 @@ static sfhe_status plan_create_impl(sfhe_ctx* c, int32_t n, const sfhe_matrix* A
     P->d_entries = (Entry*)(w + Lo.entries);
     P->d_rowlist = (int2*)(w + Lo.rowlist);
     P->d_scratch = (u64*)(w + Lo.scratch);
-    P->d_T = (u64*)(w + Lo.T);
+    P->d_T = (u32*)(w + Lo.T);
     P->d_D = (u64*)(w + Lo.D);
     P->d_U = (u64*)(w + Lo.U);
     cudaStream_t s = as_stream(stream);
@@ -780,28 +793,29 @@ extern "C" sfhe_status sfhe_matmul_batch(sfhe_ctx* c, int32_t n, const sfhe_matr
 }
 
 // ------------------------------------------------------ stage entry points ---
-extern "C" sfhe_status sfhe_ct_tensor_scale(sfhe_ctx* c, const uint64_t* a_ext, const uint64_t* b_ext, uint64_t* d,
+extern "C" sfhe_status sfhe_ct_tensor_scale(sfhe_ctx* c, const uint32_t* a_ext, const uint32_t* b_ext, uint64_t* d,
                                             void* work, size_t work_bytes, void* stream)
 {
     if (!c || !a_ext || !b_ext || !d || !work) return fail(SFHE_EINVAL, "null argument");
-    const size_t need = (size_t)3 * (c->rc.L + c->rc.Lp) * c->rc.N * 8;
+    const size_t need = (size_t)3 * c->rc.K * c->rc.N * 4;
     if (work_bytes < need) return fail(SFHE_ENOMEM, "workspace of %zu bytes needed", need);
     cudaStream_t s = as_stream(stream);
-    CUDA_TRY(launch_tensor_intt(c->rc, a_ext, b_ext, (u64*)work, s));
-    CUDA_TRY(launch_scale_round(c->rc, (u64*)work, d, s));
+    CUDA_TRY(launch_tensor_intt(c->rc, a_ext, b_ext, (u32*)work, s));
+    CUDA_TRY(launch_scale_round(c->rc, (const u32*)work, d, s));
     return SFHE_OK;
 }
 
-extern "C" sfhe_status sfhe_ct_mul_relin(sfhe_ctx* c, const uint64_t* a_ext, const uint64_t* b_ext, uint64_t* out,
+extern "C" sfhe_status sfhe_ct_mul_relin(sfhe_ctx* c, const uint32_t* a_ext, const uint32_t* b_ext, uint64_t* out,
                                          void* work, size_t work_bytes, void* stream)
 {
     if (!c || !a_ext || !b_ext || !out || !work) return fail(SFHE_EINVAL, "null argument");
-    const size_t N = c->rc.N, L = c->rc.L, LQP = c->rc.L + c->rc.Lp;
-    const size_t need = (3 * LQP + 3 * L + (L + 2) * L) * N * 8;
+    const size_t N = c->rc.N, L = c->rc.L, K = c->rc.K;
+    const size_t tw = align256(3 * K * N * 4);
+    const size_t need = tw + (3 * L + (L + 2) * L) * N * 8;
     if (work_bytes < need) return fail(SFHE_ENOMEM, "workspace of %zu bytes needed", need);
     cudaStream_t s = as_stream(stream);
-    u64* T = (u64*)work;
-    u64* D = T + 3 * LQP * N;
+    u32* T = (u32*)work;
+    u64* D = (u64*)((char*)work + tw);
     u64* U = D + 3 * L * N;
     CUDA_TRY(cudaMemsetAsync(out, 0, 2 * L * N * 8, s));
     CUDA_TRY(launch_tensor_intt(c->rc, a_ext, b_ext, T, s));
@@ -811,13 +825,18 @@ extern "C" sfhe_status sfhe_ct_mul_relin(sfhe_ctx* c, const uint64_t* a_ext, con
     return SFHE_OK;
 }
 
-extern "C" sfhe_status sfhe_ntt(sfhe_ctx* c, int32_t prime_index, int32_t inverse, const uint64_t* in, int64_t npoly,
-                                uint64_t* out, void* stream)
+extern "C" sfhe_status sfhe_ntt(sfhe_ctx* c, int32_t prime_index, int32_t inverse, const void* in, int64_t npoly,
+                                void* out, void* stream)
 {
     if (!c || !in || !out) return fail(SFHE_EINVAL, "null argument");
-    if (prime_index < 0 || prime_index >= c->rc.L + c->rc.Lp) return fail(SFHE_EINVAL, "prime index out of range");
+    if (prime_index < 0 || prime_index >= c->rc.L + c->rc.K) return fail(SFHE_EINVAL, "prime index out of range");
     if (npoly < 0) return fail(SFHE_ESHAPE, "negative count");
-    cudaError_t e = launch_ntt(c->rc, inverse != 0, in, c->rc.N, 0, out, c->rc.N, 0, prime_index, 1, npoly, as_stream(stream));
+    const size_t N = c->rc.N;
+    cudaError_t e = prime_index < c->rc.L
+                        ? launch_ntt(c->rc, inverse != 0, (const u64*)in, N, 0, (u64*)out, N, 0, prime_index, 1, npoly,
+                                     as_stream(stream))
+                        : launch_ntt32(c->rc, inverse != 0, (const u32*)in, N, 0, (u32*)out, N, 0,
+                                       prime_index - c->rc.L, 1, npoly, as_stream(stream));
     if (e != cudaSuccess) return fail(SFHE_ECUDA, "ntt: %s", cudaGetErrorString(e));
     return SFHE_OK;
 }

@@ -144,14 +144,41 @@ SFHE_DEV u64 crt_round(const u64* y, const RnsConsts& c, int L)
     return k0;
 }
 
-// round(sum_j y_j / p_j) over the P base when the value is known to lie within
-// 2^-24 of an integer (base P -> Q conversion of a scaled product); the
-// 2^-55 error of the estimate cannot cross a half-integer there.
-SFHE_DEV u64 crt_round_p_nearint(const u64* y, const RnsConsts& c)
+// ------------------------------------------------- 30-bit tensor base -------
+SFHE_DEV u32 csub32(u32 a, u32 b) { return a >= b ? a - b : a; }
+
+// Shoup for b < 2^30: a * w mod b in [0, 2b) for any a < 2^32.
+SFHE_DEV u32 shoup32_lazy(u32 a, u32 w, u32 ws, u32 b) { return a * w - __umulhi(a, ws) * b; }
+SFHE_DEV u32 shoup32(u32 a, Shoup32 c, u32 b) { return csub32(shoup32_lazy(a, c.w, c.ws, b), b); }
+
+// x mod b for x < 2^61 with mu61 = floor(2^61 / b): the estimate
+// floor(floor(x / 2^29) mu61 / 2^32) is at most 2 below floor(x / b), so the
+// remainder is below 3b < 2^32 and two conditional subtractions finish it.
+SFHE_DEV u32 reduce61(u64 x, Mod32 m)
+{
+    const u32 qh = __umulhi((u32)(x >> 29), m.mu61);
+    u32 r = (u32)x - qh * m.b;
+    r = csub32(r, m.b);
+    return csub32(r, m.b);
+}
+
+// x mod b for any 64-bit x with mu64 = floor(2^64 / b) (estimate at most 1 low).
+SFHE_DEV u32 reduce64b(u64 x, Mod32 m)
+{
+    const u64 qh = mulhi(x, m.mu64);
+    return csub32((u32)(x - qh * m.b), m.b);
+}
+
+// round(sum_{k<n} y_k / b_k) for y_k in [0, b_k) when the sum is known to lie
+// within 2^-27 of an integer: with bfrac_k = floor(2^58 / b_k) the estimate
+// is at most n 2^-28 below the sum, which cannot cross a half-integer.
+template <int n>
+SFHE_DEV u32 round_b(const u32* y, const RnsConsts& c)
 {
     u64 E = 0;
-    for (int j = 0; j < c.Lp; j++) E += mulhi(y[j] << 10, c.m[c.L + j].mu);
-    return (E + (1ULL << 59)) >> 60;
+#pragma unroll
+    for (int k = 0; k < n; k++) E += (u64)y[k] * c.bfrac[k];
+    return (u32)((E + (1ULL << 57)) >> 58);
 }
 
 // ---------------------------------------------------------- generator ------

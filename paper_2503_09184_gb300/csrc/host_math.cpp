@@ -31,6 +31,14 @@ static ShoupC shoup_of(uint64_t w, uint64_t q)
     return c;
 }
 
+static Shoup32 shoup32_of(uint64_t w, uint64_t b)
+{
+    Shoup32 c;
+    c.w = (uint32_t)w;
+    c.ws = (uint32_t)((w << 32) / b);
+    return c;
+}
+
 bool is_prime_u64(uint64_t n)
 {
     static const uint64_t witnesses[] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
@@ -57,13 +65,13 @@ bool is_prime_u64(uint64_t n)
     return true;
 }
 
-bool ntt_primes(uint32_t N, int count, std::vector<uint64_t>& out)
+bool ntt_primes(uint32_t N, int count, std::vector<uint64_t>& out, int bits)
 {
     out.clear();
     const uint64_t step = 2ULL * N;
-    // largest candidate of the form k 2N + 1 below 2^54
-    uint64_t cand = (((1ULL << 54) - 1) / step) * step + 1;
-    if (cand >= (1ULL << 54)) cand -= step;
+    // largest candidate of the form k 2N + 1 below 2^bits
+    uint64_t cand = (((1ULL << bits) - 1) / step) * step + 1;
+    if (cand >= (1ULL << bits)) cand -= step;
     while ((int)out.size() < count && cand > step) {
         if (is_prime_u64(cand)) out.push_back(cand);
         cand -= step;
@@ -113,7 +121,8 @@ static uint32_t bit_reverse(uint32_t x, int bits)
     return r;
 }
 
-void twiddles(uint64_t q, uint32_t N, uint64_t* out, ShoupC* ninv, ShoupC* wlast)
+// psi^(+-bitrev(k)) for k < N
+static void root_tables(uint64_t q, uint32_t N, std::vector<uint64_t>& fwd, std::vector<uint64_t>& inv)
 {
     int logn = 0;
     while ((1u << logn) < N) ++logn;
@@ -125,63 +134,173 @@ void twiddles(uint64_t q, uint32_t N, uint64_t* out, ShoupC* ninv, ShoupC* wlast
         pw[k] = mulm(pw[k - 1], psi, q);
         ipw[k] = mulm(ipw[k - 1], ipsi, q);
     }
+    fwd.resize(N);
+    inv.resize(N);
     for (uint32_t k = 0; k < N; ++k) {
         const uint32_t r = bit_reverse(k, logn);
-        const ShoupC f = shoup_of(pw[r], q), g = shoup_of(ipw[r], q);
-        out[k] = f.w;
-        out[N + k] = f.ws;
-        out[2 * N + k] = g.w;
-        out[3 * N + k] = g.ws;
+        fwd[k] = pw[r];
+        inv[k] = ipw[r];
+    }
+}
+
+void twiddles(uint64_t q, uint32_t N, uint64_t* out, ShoupC* ninv, ShoupC* wlast)
+{
+    std::vector<uint64_t> f, g;
+    root_tables(q, N, f, g);
+    for (uint32_t k = 0; k < N; ++k) {
+        const ShoupC a = shoup_of(f[k], q), b = shoup_of(g[k], q);
+        out[k] = a.w;
+        out[N + k] = a.ws;
+        out[2 * N + k] = b.w;
+        out[3 * N + k] = b.ws;
     }
     const uint64_t ni = invm(N, q);
     *ninv = shoup_of(ni, q);
-    *wlast = shoup_of(mulm(out[2 * N + 1], ni, q), q);
+    *wlast = shoup_of(mulm(g[1], ni, q), q);
 }
 
-// product of the moduli in [lo, hi) except `skip`, mod m
-static uint64_t prod_mod(const RnsConsts& rc, int lo, int hi, int skip, uint64_t m)
+void twiddles32(uint32_t b, uint32_t N, uint32_t* out, Shoup32* ninv, Shoup32* wlast)
+{
+    std::vector<uint64_t> f, g;
+    root_tables(b, N, f, g);
+    for (uint32_t k = 0; k < N; ++k) {
+        const Shoup32 x = shoup32_of(f[k], b), y = shoup32_of(g[k], b);
+        out[k] = x.w;
+        out[N + k] = x.ws;
+        out[2 * N + k] = y.w;
+        out[3 * N + k] = y.ws;
+    }
+    const uint64_t ni = invm(N, b);
+    *ninv = shoup32_of(ni, b);
+    *wlast = shoup32_of(mulm(g[1], ni, b), b);
+}
+
+// --------------------------------------------------------- multiword ---
+namespace {
+const int MWW = 20;  // 1280 bits
+struct Big {
+    uint64_t w[MWW];
+};
+Big big(uint64_t v)
+{
+    Big r;
+    memset(&r, 0, sizeof(r));
+    r.w[0] = v;
+    return r;
+}
+void mul_small(Big& a, uint64_t f)
+{
+    u128 carry = 0;
+    for (int k = 0; k < MWW; ++k) {
+        u128 p = (u128)a.w[k] * f + carry;
+        a.w[k] = (uint64_t)p;
+        carry = p >> 64;
+    }
+}
+void shl(Big& a, int bits)
+{
+    for (; bits > 0; --bits) {
+        for (int k = MWW - 1; k > 0; --k) a.w[k] = (a.w[k] << 1) | (a.w[k - 1] >> 63);
+        a.w[0] <<= 1;
+    }
+}
+bool greater(const Big& a, const Big& b)
+{
+    for (int k = MWW - 1; k >= 0; --k)
+        if (a.w[k] != b.w[k]) return a.w[k] > b.w[k];
+    return false;
+}
+void sub(Big& a, const Big& b)  // a -= b, a >= b
+{
+    uint64_t borrow = 0;
+    for (int k = 0; k < MWW; ++k) {
+        const uint64_t ak = a.w[k], bk = b.w[k];
+        a.w[k] = ak - bk - borrow;
+        borrow = (ak < bk) || (ak - bk < borrow);
+    }
+}
+// bitwise long division: a = quo * b + rem
+void divmod(const Big& a, const Big& b, Big& quo, Big& rem)
+{
+    quo = big(0);
+    rem = big(0);
+    for (int bit = MWW * 64 - 1; bit >= 0; --bit) {
+        shl(rem, 1);
+        rem.w[0] |= (a.w[bit / 64] >> (bit % 64)) & 1;
+        if (!greater(b, rem)) {
+            sub(rem, b);
+            quo.w[bit / 64] |= 1ULL << (bit % 64);
+        }
+    }
+}
+uint64_t mod_small(const Big& a, uint64_t m)
+{
+    uint64_t r = 0;
+    for (int k = MWW - 1; k >= 0; --k) r = (uint64_t)((((u128)r << 64) | a.w[k]) % m);
+    return r;
+}
+}  // namespace
+
+// product of the chosen moduli (mod m), skipping index `skip`
+static uint64_t prod_q(const RnsConsts& rc, int skip, uint64_t m)
 {
     uint64_t acc = 1 % m;
-    for (int k = lo; k < hi; ++k)
-        if (k != skip) acc = mulm(acc, rc.m[k].q % m, m);
+    for (int i = 0; i < rc.L; ++i)
+        if (i != skip) acc = mulm(acc, rc.m[i].q % m, m);
+    return acc;
+}
+static uint64_t prod_b(const RnsConsts& rc, int count, int skip, uint64_t m)
+{
+    uint64_t acc = 1 % m;
+    for (int k = 0; k < count; ++k)
+        if (k != skip) acc = mulm(acc, rc.mb[k].b % m, m);
     return acc;
 }
 
-void fill_constants(RnsConsts& rc)
+bool fill_constants(RnsConsts& rc)
 {
-    const int L = rc.L, Lp = rc.Lp;
+    const int L = rc.L, K = rc.K;
     const uint64_t t = rc.t;
-    for (int k = 0; k < L + Lp; ++k) rc.m[k].mu = (uint64_t)(((u128)1 << 114) / rc.m[k].q);
+    // exact size margin: B > N Q^2 2^27 (the centred tensor |x| < N Q^2 / 2)
+    Big Qbig = big(1), Bbig = big(1);
+    for (int i = 0; i < L; ++i) mul_small(Qbig, rc.m[i].q);
+    for (int k = 0; k < K; ++k) mul_small(Bbig, rc.mb[k].b);
+    {
+        Big need_b = big(rc.N);
+        for (int i = 0; i < L; ++i) {
+            mul_small(need_b, rc.m[i].q);
+            mul_small(need_b, rc.m[i].q);
+        }
+        shl(need_b, 27);
+        if (!greater(Bbig, need_b)) return false;
+    }
+    for (int i = 0; i < L; ++i) rc.m[i].mu = (uint64_t)(((u128)1 << 114) / rc.m[i].q);
+    for (int k = 0; k < K; ++k) {
+        const uint64_t b = rc.mb[k].b;
+        rc.mb[k].mu61 = (uint32_t)((1ULL << 61) / b);
+        rc.mb[k].mu64 = (uint64_t)(((u128)1 << 64) / b);
+    }
 
+    // ---- Q side, lift Q -> B and the exact-rounding words
     for (int i = 0; i < L; ++i) {
         const uint64_t qi = rc.m[i].q;
-        // (Q/q_i)^-1, (QP/q_i)^-1 mod q_i
-        const uint64_t qhat = prod_mod(rc, 0, L, i, qi);
+        const uint64_t qhat = prod_q(rc, i, qi);
         rc.qhat_inv[i] = shoup_of(invm(qhat, qi), qi);
-        const uint64_t P_mod = prod_mod(rc, L, L + Lp, -1, qi);
-        rc.qphat_inv[i] = shoup_of(invm(mulm(qhat, P_mod, qi), qi), qi);
-        rc.tP_q[i] = shoup_of(mulm(t % qi, P_mod, qi), qi);
-        rc.negP_mod_q[i] = (qi - P_mod) % qi;
         rc.t_q[i] = shoup_of(t % qi, qi);
-        for (int j = 0; j < Lp; ++j) {
-            const uint64_t pj = rc.m[L + j].q;
-            // [Q/q_i]_{p_j}
-            rc.qhat_mod_p[i][j] = prod_mod(rc, 0, L, i, pj);
-            // floor(tP/q_i) = (tP - [tP]_{q_i}) / q_i, and tP = 0 mod p_j
-            const uint64_t c = rc.tP_q[i].w % pj;
-            rc.omega[i][j] = mulm((pj - c) % pj, invm(qi % pj, pj), pj);
+        for (int k = 0; k < K; ++k) {
+            const uint64_t b = rc.mb[k].b;
+            const uint64_t c = prod_q(rc, i, b);
+            rc.qhat_b[i][k] = (uint32_t)c;
+            rc.qhat_b27[i][k] = (uint32_t)mulm(c, (1ULL << 27) % b, b);
         }
     }
-    for (int j = 0; j < Lp; ++j) {
-        const uint64_t pj = rc.m[L + j].q;
-        const uint64_t Q_mod = prod_mod(rc, 0, L, -1, pj);
-        rc.negQ_mod_p[j] = (pj - Q_mod) % pj;
-        rc.tQinv_p[j] = shoup_of(mulm(t % pj, invm(Q_mod, pj), pj), pj);
-        const uint64_t phat_p = prod_mod(rc, L, L + Lp, L + j, pj);
-        rc.phat_inv[j] = shoup_of(invm(phat_p, pj), pj);
-        for (int i = 0; i < L; ++i) rc.phat_mod_q[j][i] = prod_mod(rc, L, L + Lp, L + j, rc.m[i].q);
+    for (int k = 0; k < K; ++k) {
+        const uint64_t b = rc.mb[k].b;
+        rc.negQ_b[k] = (uint32_t)((b - prod_q(rc, -1, b)) % b);
     }
-    // Q and Q/q_i as little-endian words
+    const int W = SFHE_MAX_L + 1;
+    memset(rc.Qw, 0, sizeof(rc.Qw));
+    rc.Qw[0] = 1;
     auto mul_words = [](uint64_t* w, int n, uint64_t f) {
         u128 carry = 0;
         for (int k = 0; k < n; ++k) {
@@ -190,9 +309,6 @@ void fill_constants(RnsConsts& rc)
             carry = p >> 64;
         }
     };
-    const int W = SFHE_MAX_L + 1;
-    memset(rc.Qw, 0, sizeof(rc.Qw));
-    rc.Qw[0] = 1;
     for (int i = 0; i < L; ++i) mul_words(rc.Qw, W, rc.m[i].q);
     int words = W;
     while (words > 1 && rc.Qw[words - 1] == 0) --words;
@@ -203,16 +319,70 @@ void fill_constants(RnsConsts& rc)
         for (int k = 0; k < L; ++k)
             if (k != i) mul_words(rc.Qhat_w[i], W, rc.m[k].q);
     }
-    // Delta = floor(Q/t) = (Q - [Q]_t) / t, and Q = 0 mod q_i
-    const uint64_t Q_mod_t = [&] {
-        uint64_t a = 1 % t;
-        for (int i = 0; i < L; ++i) a = mulm(a, rc.m[i].q % t, t);
-        return a;
-    }();
+
+    // ---- tensor from B to Q
+    for (int k = 0; k < K; ++k) {
+        const uint64_t b = rc.mb[k].b;
+        rc.bhat_inv[k] = shoup32_of(invm(prod_b(rc, K, k, b), b), b);
+        rc.bfrac[k] = (uint32_t)((1ULL << 58) / b);
+        for (int i = 0; i < L; ++i) {
+            const uint64_t c = prod_b(rc, K, k, rc.m[i].q);
+            rc.bhat_q_lo[k][i] = (uint32_t)(c & ((1ULL << 27) - 1));
+            rc.bhat_q_hi[k][i] = (uint32_t)(c >> 27);
+        }
+    }
+    for (int i = 0; i < L; ++i) {
+        const uint64_t qi = rc.m[i].q;
+        rc.negB_q[i] = (qi - prod_b(rc, K, -1, qi)) % qi;
+    }
+
+    // ---- scale and round directly from B: t (B/b_k) = alpha_k Q + r_k, t B = alpha_B Q + r_B
+    auto split_const = [&](const Big& c, Big& alpha, Big& rem, uint64_t& rho) {
+        divmod(c, Qbig, alpha, rem);
+        Big shifted = rem, quo, r2;
+        shl(shifted, 64);
+        divmod(shifted, Qbig, quo, r2);  // floor(rem 2^64 / Q) < 2^64
+        rho = quo.w[0];
+    };
+    for (int k = 0; k < K; ++k) {
+        Big ck = big(t);
+        for (int j = 0; j < K; ++j)
+            if (j != k) mul_small(ck, rc.mb[j].b);
+        Big alpha, rem;
+        uint64_t rho;
+        split_const(ck, alpha, rem, rho);
+        rc.rho_lo[k] = (uint32_t)rho;
+        rc.rho_hi[k] = (uint32_t)(rho >> 32);
+        for (int i = 0; i < L; ++i) {
+            const uint64_t a = mod_small(alpha, rc.m[i].q);
+            rc.alpha_q_lo[k][i] = (uint32_t)(a & ((1ULL << 27) - 1));
+            rc.alpha_q_hi[k][i] = (uint32_t)(a >> 27);
+        }
+        for (int w = 0; w < SFHE_MAX_L + 1; ++w) rc.r_w[k][w] = rem.w[w];
+    }
+    {
+        Big cB = Bbig;
+        mul_small(cB, t);
+        Big alpha, rem;
+        uint64_t rho;
+        split_const(cB, alpha, rem, rho);
+        rc.rhoB_lo = (uint32_t)rho;
+        rc.rhoB_hi = (uint32_t)(rho >> 32);
+        for (int i = 0; i < L; ++i) {
+            const uint64_t qi = rc.m[i].q;
+            rc.negalphaB_q[i] = (qi - mod_small(alpha, qi)) % qi;
+            rc.negK_q[i] = qi - (uint64_t)K;
+        }
+        for (int w = 0; w < SFHE_MAX_L + 1; ++w) rc.rB_w[w] = rem.w[w];
+    }
+
+    // ---- encryption: Delta = floor(Q/t) = (Q - [Q]_t) / t, and Q = 0 mod q_i
+    const uint64_t Q_mod_t = prod_q(rc, -1, t);
     for (int i = 0; i < L; ++i) {
         const uint64_t qi = rc.m[i].q;
         rc.delta_q[i] = mulm((qi - Q_mod_t % qi) % qi, invm(t % qi, qi), qi);
     }
+    return true;
 }
 
 }  // namespace sfhe

@@ -8,17 +8,21 @@
 namespace sfhe {
 
 bool is_prime_u64(uint64_t n);
-// The `count` largest primes below 2^54 that are 1 mod 2N, descending.
-bool ntt_primes(uint32_t N, int count, std::vector<uint64_t>& out);
+// The `count` largest primes below 2^bits that are 1 mod 2N, descending.
+bool ntt_primes(uint32_t N, int count, std::vector<uint64_t>& out, int bits = 54);
 // Smallest primitive 2N-th root of unity mod q.
 uint64_t min_primitive_2n_root(uint64_t q, uint32_t N);
 // Rounded-Gaussian |e| table (20 entries) for width sigma.
 void cdt_table(double sigma, uint64_t* T);
 // Twiddle tables of one prime: [4][N] = psi_rev, psi_rev_shoup, ipsi_rev,
-// ipsi_rev_shoup; also N^-1 and the merged last-stage multiplier.
+// ipsi_rev_shoup; also N^-1 and the merged last-stage multiplier.  The
+// 64-bit version is for the 54-bit primes (Shoup companions over 2^64), the
+// 32-bit one for the 30-bit primes (companions over 2^32).
 void twiddles(uint64_t q, uint32_t N, uint64_t* out4N, ShoupC* ninv, ShoupC* wlast);
+void twiddles32(uint32_t b, uint32_t N, uint32_t* out4N, Shoup32* ninv, Shoup32* wlast);
 // Fills every base-conversion constant of rc from its primes (rc.m[].q,
-// rc.L, rc.Lp, rc.t, rc.N already set).
-void fill_constants(RnsConsts& rc);
+// rc.mb[].b, rc.L, rc.K, rc.t, rc.N set).  Returns false if a size
+// margin does not hold.
+bool fill_constants(RnsConsts& rc);
 
 }  // namespace sfhe

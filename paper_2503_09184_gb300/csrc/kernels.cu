@@ -26,6 +26,11 @@ namespace {
 
 const long long kMaxGridY = 65535;
 
+template <int LOGN>
+constexpr size_t smem32_of() { return (size_t)NttGeom<LOGN>::T32::SMEM_WORDS * sizeof(u32); }
+template <int LOGN>
+constexpr int nt32_of() { return NttGeom<LOGN>::T32::NT; }
+
 }  // namespace
 
 bool supported_ring(int logN, int L)
@@ -84,6 +89,38 @@ cudaError_t launch_ntt(const RnsConsts& rc, bool inverse, const u64* in, size_t 
 }
 
 template <int LOGN>
+static cudaError_t ntt32_impl(const RnsConsts& rc, bool inverse, const u32* in, size_t in_gstride, int in_l0, u32* out,
+                              size_t out_gstride, int out_l0, int prime0, int nlimbs, long long ngroups, cudaStream_t s)
+{
+    const size_t smem = smem32_of<LOGN>();
+    cudaError_t e = inverse ? allow_smem(k_ntt32_inv<LOGN>, smem) : allow_smem(k_ntt32_fwd<LOGN>, smem);
+    if (e != cudaSuccess) return e;
+    for (long long g0 = 0; g0 < ngroups; g0 += kMaxGridY) {
+        const long long ng = ngroups - g0 < kMaxGridY ? ngroups - g0 : kMaxGridY;
+        dim3 grid(nlimbs, (unsigned)ng);
+        const u32* src = in + g0 * in_gstride;
+        u32* dst = out + g0 * out_gstride;
+        if (inverse)
+            k_ntt32_inv<LOGN><<<grid, nt32_of<LOGN>(), smem, s>>>(rc, src, in_gstride, in_l0, dst, out_gstride, out_l0,
+                                                                  prime0);
+        else
+            k_ntt32_fwd<LOGN><<<grid, nt32_of<LOGN>(), smem, s>>>(rc, src, in_gstride, in_l0, dst, out_gstride, out_l0,
+                                                                  prime0);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_ntt32(const RnsConsts& rc, bool inverse, const u32* in, size_t in_gstride, int in_l0, u32* out,
+                         size_t out_gstride, int out_l0, int prime0, int nlimbs, long long ngroups, cudaStream_t s)
+{
+    if (ngroups <= 0 || nlimbs <= 0) return cudaSuccess;
+    SFHE_DISPATCH_LOGN(rc.logN, return ntt32_impl<LG>(rc, inverse, in, in_gstride, in_l0, out, out_gstride, out_l0,
+                                                      prime0, nlimbs, ngroups, s));
+}
+
+template <int LOGN>
 static cudaError_t keygen_impl(const RnsConsts& rc, u64* s_ntt, signed char* s_coeff, u64* rlk, u64* rlk_sh, int* err,
                                cudaStream_t s)
 {
@@ -134,29 +171,34 @@ cudaError_t launch_decrypt(const RnsConsts& rc, const u64* s_ntt, const u64* ct,
     SFHE_DISPATCH_LOGN(rc.logN, k_decrypt<LG><<<(unsigned)n, 256, 0, s>>>(rc, s_ntt, ct, out); return cudaGetLastError());
 }
 
-cudaError_t launch_lift_extend(const RnsConsts& rc, const u64* in, u64* out, long long ngroups, cudaStream_t s)
+cudaError_t launch_lift_extend(const RnsConsts& rc, const u64* in, u32* out, long long ngroups, cudaStream_t s)
 {
     const long long total = ngroups * rc.N;
     if (total <= 0) return cudaSuccess;
-    const long long blocks = (total + 255) / 256;
-    k_lift_extend<<<(unsigned)blocks, 256, 0, s>>>(rc, in, out, (int)ngroups);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_tensor_intt(const RnsConsts& rc, const u64* a, const u64* b, u64* T, cudaStream_t s)
-{
-    SFHE_DISPATCH_LOGN(rc.logN, {
-        cudaError_t e = allow_smem(k_tensor_intt<LG>, smem_of<LG>());
-        if (e != cudaSuccess) return e;
-        k_tensor_intt<LG><<<dim3(rc.L + rc.Lp, 3), nt_of<LG>(), smem_of<LG>(), s>>>(rc, a, b, T);
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    SFHE_DISPATCH_LOGN(rc.logN, SFHE_DISPATCH_L(rc.L, {
+        k_lift_extend<LL, Cfg<LG, LL>::K><<<blocks, 256, 0, s>>>(rc, in, out, (int)ngroups);
         return cudaGetLastError();
-    });
+    }));
 }
 
-cudaError_t launch_scale_round(const RnsConsts& rc, const u64* T, u64* D, cudaStream_t s)
+cudaError_t launch_tensor_intt(const RnsConsts& rc, const u32* a, const u32* b, u32* T, cudaStream_t s)
+{
+    SFHE_DISPATCH_LOGN(rc.logN, SFHE_DISPATCH_L(rc.L, {
+        cudaError_t e = allow_smem(k_tensor_intt<LG, LL>, smem32_of<LG>());
+        if (e != cudaSuccess) return e;
+        k_tensor_intt<LG, LL><<<dim3(rc.K, 3), nt32_of<LG>(), smem32_of<LG>(), s>>>(rc, a, b, T);
+        return cudaGetLastError();
+    }));
+}
+
+cudaError_t launch_scale_round(const RnsConsts& rc, const u32* T, u64* D, cudaStream_t s)
 {
     dim3 grid((rc.N + 127) / 128, 3);
-    SFHE_DISPATCH_L(rc.L, k_scale_round<LL><<<grid, 128, 0, s>>>(rc, T, D); return cudaGetLastError());
+    SFHE_DISPATCH_LOGN(rc.logN, SFHE_DISPATCH_L(rc.L, {
+        k_scale_round<LG, LL><<<grid, 128, 0, s>>>(rc, T, D);
+        return cudaGetLastError();
+    }));
 }
 
 cudaError_t launch_relin_ntt(const RnsConsts& rc, const u64* D, u64* U, cudaStream_t s)
@@ -178,8 +220,8 @@ cudaError_t launch_relin_accum(const RnsConsts& rc, const u64* U, const u64* rlk
 
 size_t persistent_scratch_words(const RnsConsts& rc)
 {
-    const size_t N = rc.N, L = rc.L, LQP = rc.L + rc.Lp;
-    size_t w = 3 * LQP * N + 3 * L * N + 2 * N;
+    const size_t N = rc.N, L = rc.L, K = rc.K;
+    const size_t w = 3 * L * N + 2 * N + (3 * K * N + 1) / 2;
     return (w + 31) & ~(size_t)31;  // 256-byte aligned slots
 }
 

@@ -1,76 +1,165 @@
 // kernels.cuh -- device code of the encrypted sparse matmul.
 //
-// Storage (all uint64, canonical residues):
-//   ciphertext, base Q, NTT form:      [2 (c0, c1)][L][N]
-//   lifted ciphertext, base Q u P, NTT: [2][L + Lp][N]  (Q limbs first)
-//   relinearisation key, NTT form:      [L digit j][2 (b, a)][L limb i][N] (+ Shoup companions)
-// Per product (Alg. 1, "a <- a x b; fhe_relin; fhe_add"):
-//   tensor d0 = a0 b0, d1 = a0 b1 + a1 b0, d2 = a1 b1 over Q u P (NTT form),
-//   inverse NTT, exact scale-and-round by t/Q (result in base Q), digits
-//   D_j = [d2]_{q_j}, relinearise with the key, add into C.
+// Storage (canonical residues):
+//   ciphertext, base Q, NTT form:          [2 (c0, c1)][L][N]  uint64
+//   lifted ciphertext, base B, NTT form:   [2][K][N]           uint32
+//   relinearisation key, base Q, NTT form: [L digit j][2 (b, a)][L limb i][N] uint64 (+ Shoup companions)
+// Per product (Alg. 1: "a <- a x b; fhe_relin; fhe_add"):
+//   tensor d0 = a0 b0, d1 = a0 b1 + a1 b0, d2 = a1 b1 over B (NTT form, 30-bit
+//   arithmetic), inverse NTT: the exact integer tensor x in B (|x| < B 2^-28);
+//   exact scale-and-round by t/Q straight from B (the result in Q);
+//   digits D_j = [d2]_{q_j}; relinearise with the key; add into C.
 #pragma once
 #include "ntt.cuh"
 #include "worklist.h"
 
+template <int LOGN, int L>
+struct Cfg {
+    static constexpr int K = tensor_base_size(LOGN, L);
+    using NQ = typename NttGeom<LOGN>::T;     // 64-bit transforms (ciphertext primes)
+    using NB = typename NttGeom<LOGN>::T32;   // 32-bit transforms (tensor base)
+};
+
 // ------------------------------------------------------------------------
 // elementwise pieces
 // ------------------------------------------------------------------------
-// one coefficient of tensor polynomial `poly` (0: a0 b0, 1: a0 b1 + a1 b0,
-// 2: a1 b1) in limb l; a, b point at [2][L+Lp][N] lifted ciphertexts
-SFHE_DEV u64 tensor_coeff(int poly, const u64* __restrict__ a, const u64* __restrict__ b, size_t off1, size_t e,
-                          Mod m)
+// coefficient e of tensor polynomial `poly` (0: a0 b0, 1: a0 b1 + a1 b0,
+// 2: a1 b1) mod b; a, b point at limb k of c0 of lifted ciphertexts, off1
+// is the distance to the same limb of c1.
+SFHE_DEV u32 tensor_coeff32(int poly, const u32* __restrict__ a, const u32* __restrict__ b, size_t off1, int e,
+                            Mod32 m)
 {
-    // off1: distance between c0 and c1 of a lifted ciphertext
-    if (poly == 0) return mul_mod(__ldg(a + e), __ldg(b + e), m);
-    if (poly == 2) return mul_mod(__ldg(a + off1 + e), __ldg(b + off1 + e), m);
-    u64 a0 = __ldg(a + e), a1 = __ldg(a + off1 + e), b0 = __ldg(b + e), b1 = __ldg(b + off1 + e);
-    u64 hi = mulhi(a0, b1), lo = a0 * b1;
-    mac(hi, lo, a1, b0);
-    return barrett(hi, lo, m);
+    if (poly == 0) return reduce61((u64)__ldg(a + e) * __ldg(b + e), m);
+    if (poly == 2) return reduce61((u64)__ldg(a + off1 + e) * __ldg(b + off1 + e), m);
+    return reduce61((u64)__ldg(a + e) * __ldg(b + off1 + e) + (u64)__ldg(a + off1 + e) * __ldg(b + e), m);
 }
 
-// Exact round(t x / Q) for a tensor coefficient x given over Q u P
-// (x: L residues mod q_i, xp: Lp residues mod p_j, canonical); writes the
-// result's residues mod q_i.  Step 1 gives the result in base P:
-//   x~_i = [x_i (QP/q_i)^-1]_{q_i},  x~_i [tP]_{q_i} = u_i q_i + y_i,
-//   r = sum u_i + round(sum y_i / q_i),
-//   d_j = [x_j [tQ^-1]_{p_j} + sum_i x~_i [floor(tP/q_i)]_{p_j} + r]_{p_j};
-// step 2 converts the centred d from P to Q (|d| < P 2^-24, so the rounding
-// of sum d~_j / p_j is never near a half-integer).
-template <int L>
-SFHE_DEV void scale_round(const u64* x, const u64* xp, const RnsConsts& c, u64* d)
+// Exact decision of round(F) + K near a half-integer: with the words of
+// Z = sum_k x~_k r_k - v r_B + K Q  (Z = (F + K) Q >= 0), the result is the
+// candidate m-1, m or m+1 for which (2c - 1) Q <= 2 Z < (2c + 1) Q.
+template <int K>
+__device__ __noinline__ u64 scale_round_fallback(const u32* xt, u32 v, u64 m, const RnsConsts& c)
 {
-    constexpr int LP = L + 1;
-    u64 xt[L], y[L];
-    u64 usum = 0;
+    const int W = c.Qwords + 1;
+    u64 Z[SFHE_MAX_L + 2], R[SFHE_MAX_L + 2];
+    // Z = K Q
+    u64 carry = 0;
+    for (int w = 0; w <= W; w++) {
+        const u64 qw = w < c.Qwords ? c.Qw[w] : 0;
+        const u64 lo = qw * (u64)K + carry;
+        carry = mulhi(qw, (u64)K) + (lo < carry ? 1 : 0);
+        Z[w] = lo;
+    }
+    // + sum_k x~_k r_k
+    for (int k = 0; k < K; k++) {
+        u64 cy = 0;
+        for (int w = 0; w <= W; w++) {
+            const u64 rw = w <= SFHE_MAX_L ? c.r_w[k][w] : 0;
+            u64 lo = rw * xt[k], hi = mulhi(rw, (u64)xt[k]);
+            lo += cy;
+            hi += lo < cy ? 1 : 0;
+            const u64 s = Z[w] + lo;
+            hi += s < lo ? 1 : 0;
+            Z[w] = s;
+            cy = hi;
+        }
+    }
+    // - v r_B
+    {
+        u64 cy = 0, borrow = 0;
+        for (int w = 0; w <= W; w++) {
+            const u64 rw = w <= SFHE_MAX_L ? c.rB_w[w] : 0;
+            u64 lo = rw * v, hi = mulhi(rw, (u64)v);
+            lo += cy;
+            hi += lo < cy ? 1 : 0;
+            cy = hi;
+            const u64 z = Z[w];
+            const u64 d = z - lo - borrow;
+            borrow = (z < lo) || (z - lo < borrow) ? 1 : 0;
+            Z[w] = d;
+        }
+    }
+    // 2Z
+    for (int w = W; w > 0; w--) Z[w] = (Z[w] << 1) | (Z[w - 1] >> 63);
+    Z[0] <<= 1;
+    // count how many of (2m - 1) Q and (2m + 1) Q are <= 2Z
+    u64 res = m - 1;
+    for (int s = 0; s < 2; s++) {
+        const long long f = 2 * (long long)m - 1 + 2 * s;
+        if (f < 0) {
+            res += 1;
+            continue;
+        }
+        u64 cyf = 0;
+        for (int w = 0; w <= W; w++) {
+            const u64 qw = w < c.Qwords ? c.Qw[w] : 0;
+            const u64 lo = qw * (u64)f + cyf;
+            cyf = mulhi(qw, (u64)f) + (lo < cyf ? 1 : 0);
+            R[w] = lo;
+        }
+        bool ge = true;
+        for (int w = W; w >= 0; w--) {
+            if (Z[w] != R[w]) {
+                ge = Z[w] > R[w];
+                break;
+            }
+        }
+        res += ge ? 1 : 0;
+    }
+    return res;
+}
+
+// Exact round(t x / Q) mod q_i for one tensor coefficient x given by its
+// residues x32[k] mod b_k (canonical, k < K):
+//   x = sum_k x~_k (B/b_k) - v B,  x~_k = [x_k (B/b_k)^-1]_{b_k},
+//   v = round(sum_k x~_k / b_k)  (|x| < B 2^-28: never near a half-integer);
+//   with t (B/b_k) = alpha_k Q + r_k and t B = alpha_B Q + r_B,
+//   t x / Q = sum_k x~_k alpha_k - v alpha_B + F,  F = (sum_k x~_k r_k - v r_B) / Q,
+// so round(t x / Q) = sum_k x~_k alpha_k - v alpha_B + round(F).  F + K > 0
+// is estimated as G / 2^64 with G = sum_k x~_k rho_k - v rho_B + K 2^64,
+// rho = floor(r 2^64 / Q); the true value lies in (G - K, G + K 2^30) / 2^64,
+// so round(F) + K = floor((G + 2^63) / 2^64) unless that interval crosses
+// the rounding point, where the decision is taken exactly (Q is odd: no ties).
+// 54-bit constants [alpha_k]_{q_i} are split at bit 27 so that every partial
+// product is one 32x32-bit multiply.
+template <int L, int K>
+SFHE_DEV void scale_round_b(const u32* x32, const RnsConsts& c, u64* d)
+{
+    u32 xt[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) xt[k] = shoup32(x32[k], c.bhat_inv[k], c.mb[k].b);
+    const u32 v = round_b<K>(xt, c);
+    // G = sum_k x~_k rho_k - v rho_B + K 2^64 + 2^63, as hi:lo
+    u64 ghi = (u64)K, glo = 1ULL << 63;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        const u64 p0 = (u64)xt[k] * c.rho_lo[k], p1 = (u64)xt[k] * c.rho_hi[k];
+        add128(ghi, glo, p0);
+        add128(ghi, glo, p1 << 32);
+        ghi += p1 >> 32;
+    }
+    {
+        const u64 p0 = (u64)v * c.rhoB_lo, p1 = (u64)v * c.rhoB_hi;
+        const u64 sub = p0 + (p1 << 32);
+        const u64 subhi = (p1 >> 32) + (sub < p0 ? 1 : 0);
+        ghi -= subhi + (glo < sub ? 1 : 0);
+        glo -= sub;
+    }
+    u64 mK = ghi;  // round(F) + K, unless glo sits in the uncertainty band
+    if (glo < (u64)K || glo >= 0ULL - ((u64)K << 30)) mK = scale_round_fallback<K>(xt, v, mK, c);
 #pragma unroll
     for (int i = 0; i < L; i++) {
-        const u64 qi = c.m[i].q;
-        xt[i] = shoup(x[i], c.qphat_inv[i], qi);
-        u64 quo;
-        y[i] = shoup_quot(xt[i], c.tP_q[i], qi, quo);
-        usum += quo;
-    }
-    const u64 r = usum + crt_round<L>(y, c, L);
-    u64 dt[LP];
+        u64 slo = 0, shi = 0;
 #pragma unroll
-    for (int j = 0; j < LP; j++) {
-        const Mod pm = c.m[L + j];
-        u64 hi = 0, lo = 0;
-#pragma unroll
-        for (int i = 0; i < L; i++) mac(hi, lo, xt[i], c.omega[i][j]);
-        add128(hi, lo, shoup_lazy(xp[j], c.tQinv_p[j], pm.q));
-        add128(hi, lo, r);
-        const u64 dj = barrett(hi, lo, pm);
-        dt[j] = shoup(dj, c.phat_inv[j], pm.q);
-    }
-    const u64 v = crt_round_p_nearint(dt, c);
-#pragma unroll
-    for (int i = 0; i < L; i++) {
-        u64 hi = 0, lo = 0;
-#pragma unroll
-        for (int j = 0; j < LP; j++) mac(hi, lo, dt[j], c.phat_mod_q[j][i]);
-        add128(hi, lo, v * c.negP_mod_q[i]);
+        for (int k = 0; k < K; k++) {
+            slo += (u64)xt[k] * c.alpha_q_lo[k][i];
+            shi += (u64)xt[k] * c.alpha_q_hi[k][i];
+        }
+        u64 hi = shi >> 37, lo = shi << 27;
+        add128(hi, lo, slo);
+        add128(hi, lo, (u64)v * c.negalphaB_q[i]);
+        add128(hi, lo, mK);
+        add128(hi, lo, c.negK_q[i]);
         d[i] = barrett(hi, lo, c.m[i]);
     }
 }
@@ -79,7 +168,7 @@ SFHE_DEV void scale_round(const u64* x, const u64* xp, const RnsConsts& c, u64* 
 // generic NTT kernels over batches of polynomials
 // ------------------------------------------------------------------------
 // Polynomial (g, l): input at in + g * in_gstride + (in_l0 + l) * N, output
-// at out + g * out_gstride + (out_l0 + l) * N, prime index prime0 + l.
+// at out + g * out_gstride + (out_l0 + l) * N, prime index prime0 + l of Q.
 template <int LOGN>
 __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_ntt_fwd(const __grid_constant__ RnsConsts c, const u64* in,
                                                                  size_t in_gstride, int in_l0, u64* out,
@@ -113,9 +202,54 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_ntt_inv(const __grid_c
     u64 x[NT_::R];
 #pragma unroll
     for (int v = 0; v < NT_::R; v++) x[v] = csub(src[NT_::run_idx(v, tid)], m.q);
-    NT_::inverse(x, sm, tid, c.tw + (size_t)pi * 4 * NT_::N, m.q, c.ninv[pi], c.wlast[pi]);
+    NT_::inverse(x, sm, tid, c.tw + (size_t)pi * 4 * NT_::N, m.q, c.ninv[pi].w, c.ninv[pi].ws, c.wlast[pi].w,
+                 c.wlast[pi].ws);
 #pragma unroll
     for (int v = 0; v < NT_::R; v++) dst[NT_::inv_out_idx(v, tid)] = csub(x[v], m.q);
+}
+
+// Same over the tensor base (32-bit words, prime index into B).
+template <int LOGN>
+__global__ void __launch_bounds__(NttGeom<LOGN>::T32::NT) k_ntt32_fwd(const __grid_constant__ RnsConsts c,
+                                                                     const u32* in, size_t in_gstride, int in_l0,
+                                                                     u32* out, size_t out_gstride, int out_l0,
+                                                                     int prime0)
+{
+    using NT_ = typename NttGeom<LOGN>::T32;
+    extern __shared__ u64 sm64[];
+    u32* sm = reinterpret_cast<u32*>(sm64);
+    const int l = blockIdx.x, g = blockIdx.y, tid = threadIdx.x, pk = prime0 + l;
+    const Mod32 m = c.mb[pk];
+    const u32* src = in + g * in_gstride + (size_t)(in_l0 + l) * NT_::N;
+    u32* dst = out + g * out_gstride + (size_t)(out_l0 + l) * NT_::N;
+    u32 x[NT_::R];
+#pragma unroll
+    for (int v = 0; v < NT_::R; v++) x[v] = src[NT_::fwd_in_idx(v, tid)];  // < b: a valid forward input
+    NT_::forward(x, sm, tid, c.twb + (size_t)pk * 4 * NT_::N, m.b);
+#pragma unroll
+    for (int v = 0; v < NT_::R; v++) dst[NT_::run_idx(v, tid)] = csub32(csub32(x[v], 2 * m.b), m.b);
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(NttGeom<LOGN>::T32::NT) k_ntt32_inv(const __grid_constant__ RnsConsts c,
+                                                                     const u32* in, size_t in_gstride, int in_l0,
+                                                                     u32* out, size_t out_gstride, int out_l0,
+                                                                     int prime0)
+{
+    using NT_ = typename NttGeom<LOGN>::T32;
+    extern __shared__ u64 sm64[];
+    u32* sm = reinterpret_cast<u32*>(sm64);
+    const int l = blockIdx.x, g = blockIdx.y, tid = threadIdx.x, pk = prime0 + l;
+    const Mod32 m = c.mb[pk];
+    const u32* src = in + g * in_gstride + (size_t)(in_l0 + l) * NT_::N;
+    u32* dst = out + g * out_gstride + (size_t)(out_l0 + l) * NT_::N;
+    u32 x[NT_::R];
+#pragma unroll
+    for (int v = 0; v < NT_::R; v++) x[v] = csub32(src[NT_::run_idx(v, tid)], m.b);
+    NT_::inverse(x, sm, tid, c.twb + (size_t)pk * 4 * NT_::N, m.b, c.ninv_b[pk].w, c.ninv_b[pk].ws, c.wlast_b[pk].w,
+                 c.wlast_b[pk].ws);
+#pragma unroll
+    for (int v = 0; v < NT_::R; v++) dst[NT_::inv_out_idx(v, tid)] = csub32(x[v], m.b);
 }
 
 // ------------------------------------------------------------------------
@@ -283,72 +417,82 @@ __global__ void __launch_bounds__(256) k_decrypt(const __grid_constant__ RnsCons
 }
 
 // ------------------------------------------------------------------------
-// lift: base Q -> Q u P (centred)
+// lift: base Q -> B (centred)
 // ------------------------------------------------------------------------
-#ifdef SFHE_KERNELS_TU
-// coefficient form in: [g][L][N] (canonical), out: [g][Lp][N]
-__global__ void __launch_bounds__(256) k_lift_extend(const __grid_constant__ RnsConsts c, const u64* in, u64* out,
+// coefficient form in: [g][L][N] uint64 (canonical), out: [g][K][N] uint32.
+//   a = sum_i a~_i (Q/q_i) - v Q,  a~_i = [a_i (Q/q_i)^-1]_{q_i},
+//   v = round(sum_i a~_i / q_i) (exact: fixed-point estimate, multiword
+//   decision near a half-integer), a mod b_k from the same sum.
+template <int L, int K>
+__global__ void __launch_bounds__(256) k_lift_extend(const __grid_constant__ RnsConsts c, const u64* in, u32* out,
                                                      int ngroups)
 {
-    const int N = c.N, L = c.L, Lp = c.Lp;
+    const int N = c.N;
     const size_t idx = (size_t)blockIdx.x * 256 + threadIdx.x;
     if (idx >= (size_t)ngroups * N) return;
-    const size_t g = idx / N, k = idx % N;
-    u64 at[SFHE_MAX_L];
-    for (int i = 0; i < L; i++) at[i] = shoup(in[(g * L + i) * N + k], c.qhat_inv[i], c.m[i].q);
-    const u64 v = crt_round<0>(at, c, L);
-    for (int j = 0; j < Lp; j++) {
-        const Mod pm = c.m[L + j];
-        u64 hi = 0, lo = 0;
-        for (int i = 0; i < L; i++) mac(hi, lo, at[i], c.qhat_mod_p[i][j]);
-        add128(hi, lo, v * c.negQ_mod_p[j]);
-        out[(g * Lp + j) * N + k] = barrett(hi, lo, pm);
+    const size_t g = idx / N, e = idx % N;
+    u64 at[L];
+    u32 alo[L], ahi[L];
+#pragma unroll
+    for (int i = 0; i < L; i++) {
+        at[i] = shoup(in[(g * L + i) * N + e], c.qhat_inv[i], c.m[i].q);
+        alo[i] = (u32)(at[i] & ((1u << 27) - 1));
+        ahi[i] = (u32)(at[i] >> 27);
+    }
+    const u64 v = crt_round<L>(at, c, L);
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        u64 V = v * c.negQ_b[k];
+#pragma unroll
+        for (int i = 0; i < L; i++) V += (u64)alo[i] * c.qhat_b[i][k] + (u64)ahi[i] * c.qhat_b27[i][k];
+        out[(g * K + k) * N + e] = reduce64b(V, c.mb[k]);
     }
 }
-#endif
 
 // ------------------------------------------------------------------------
 // plain per-product path
 // ------------------------------------------------------------------------
-// block (limb l, poly p): tensor polynomial p in limb l, inverse NTT,
-// coefficient form to T[p][l][N]
-template <int LOGN>
-__global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_tensor_intt(const __grid_constant__ RnsConsts c, const u64* a,
-                                                                     const u64* b, u64* T)
+// block (k limb of B, poly p): tensor polynomial p mod b_k, inverse NTT,
+// coefficient form to T[p][k][N]
+template <int LOGN, int L>
+__global__ void __launch_bounds__(NttGeom<LOGN>::T32::NT) k_tensor_intt(const __grid_constant__ RnsConsts c, const u32* a,
+                                                                       const u32* b, u32* T)
 {
-    using NT_ = typename NttGeom<LOGN>::T;
-    constexpr int N = NT_::N;
-    extern __shared__ u64 sm[];
-    const int l = blockIdx.x, p = blockIdx.y, tid = threadIdx.x;
-    const int LQP = c.L + c.Lp;
-    const Mod m = c.m[l];
-    const size_t off1 = (size_t)LQP * N;
-    const u64* al = a + (size_t)l * N;
-    const u64* bl = b + (size_t)l * N;
-    u64 x[NT_::R];
+    using CF = Cfg<LOGN, L>;
+    using NB = typename CF::NB;
+    constexpr int N = NB::N, K = CF::K;
+    extern __shared__ u64 sm64[];
+    u32* sm = reinterpret_cast<u32*>(sm64);
+    const int k = blockIdx.x, p = blockIdx.y, tid = threadIdx.x;
+    const Mod32 m = c.mb[k];
+    const size_t off1 = (size_t)K * N;
+    const u32* ak = a + (size_t)k * N;
+    const u32* bk = b + (size_t)k * N;
+    u32 x[NB::R];
 #pragma unroll
-    for (int v = 0; v < NT_::R; v++) x[v] = tensor_coeff(p, al, bl, off1, NT_::run_idx(v, tid), m);
-    NT_::inverse(x, sm, tid, c.tw + (size_t)l * 4 * N, m.q, c.ninv[l], c.wlast[l]);
-    u64* dst = T + ((size_t)p * LQP + l) * N;
+    for (int v = 0; v < NB::R; v++) x[v] = tensor_coeff32(p, ak, bk, off1, NB::run_idx(v, tid), m);
+    NB::inverse(x, sm, tid, c.twb + (size_t)k * 4 * N, m.b, c.ninv_b[k].w, c.ninv_b[k].ws, c.wlast_b[k].w,
+                c.wlast_b[k].ws);
+    u32* dst = T + ((size_t)p * K + k) * N;
 #pragma unroll
-    for (int v = 0; v < NT_::R; v++) dst[NT_::inv_out_idx(v, tid)] = csub(x[v], m.q);
+    for (int v = 0; v < NB::R; v++) dst[NB::inv_out_idx(v, tid)] = csub32(x[v], m.b);
 }
 
-// T [3][L+Lp][N] -> D [3][L][N] (coefficient form, canonical)
-template <int L>
-__global__ void __launch_bounds__(128) k_scale_round(const __grid_constant__ RnsConsts c, const u64* T, u64* D)
+// T [3][K][N] uint32 -> D [3][L][N] uint64 (coefficient form, canonical)
+template <int LOGN, int L>
+__global__ void __launch_bounds__(128) k_scale_round(const __grid_constant__ RnsConsts c, const u32* T, u64* D)
 {
-    const int N = c.N, LQP = L + L + 1;
-    const int k = blockIdx.x * 128 + threadIdx.x, p = blockIdx.y;
-    if (k >= N) return;
-    u64 x[L], xp[L + 1], d[L];
+    using CF = Cfg<LOGN, L>;
+    constexpr int N = 1 << LOGN, K = CF::K;
+    const int e = blockIdx.x * 128 + threadIdx.x, p = blockIdx.y;
+    if (e >= N) return;
+    u32 x[K];
+    u64 d[L];
 #pragma unroll
-    for (int i = 0; i < L; i++) x[i] = T[((size_t)p * LQP + i) * N + k];
+    for (int k = 0; k < K; k++) x[k] = T[((size_t)p * K + k) * N + e];
+    scale_round_b<L, K>(x, c, d);
 #pragma unroll
-    for (int j = 0; j < L + 1; j++) xp[j] = T[((size_t)p * LQP + L + j) * N + k];
-    scale_round<L>(x, xp, c, d);
-#pragma unroll
-    for (int i = 0; i < L; i++) D[((size_t)p * L + i) * N + k] = d[i];
+    for (int i = 0; i < L; i++) D[((size_t)p * L + i) * N + e] = d[i];
 }
 
 // block (target limb i, source s): s = 0: d0_i, 1: d1_i, 2+j: [D_j]_{q_i}
@@ -391,38 +535,51 @@ __global__ void __launch_bounds__(256) k_relin_accum(const __grid_constant__ Rns
         *cp = add_mod(*cp, barrett64(acc, m), m.q);
     }
 }
+
+// raw generator words (stream-equality checks against the oracle)
+__global__ void k_prng_words(u64 seed, u64 dom, u64 o0, u64 o1, u64 o2, u64 idx0, long long n, u64* out)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    out[t] = sm_word(sm_key(seed, dom, o0, o1, o2), idx0 + (u64)t);
+}
 #endif
 
 // ------------------------------------------------------------------------
 // fused persistent matmul
 // ------------------------------------------------------------------------
 // One CTA per output entry at a time, taken from a queue in descending
-// product count.  Per product: stage T (tensor + inverse NTT of the 3 (L+Lp)
-// polynomials into the CTA's scratch), stage S (scale-and-round, then the
-// sums of d0, d1 and of the digits D_j over the entry's products).  Per
-// entry, stage R: since the NTT and the key product are linear mod q_i,
+// product count.  Per product: stage T (tensor + 3K inverse NTTs over B into
+// the CTA's scratch), stage S (B -> Q, exact scale-and-round, then the sums
+// of d0, d1 and of the digits D_j over the entry's products).  Per entry,
+// stage R: since the NTT and the key product are linear mod q_i,
 //   sum_k [NTT(d0_k) + sum_j NTT([D_jk]_{q_i}) b_j]
 //     = NTT([sum_k d0_k]_{q_i}) + sum_j NTT([sum_k D_jk]_{q_i}) b_j   (mod q_i),
 // so the relinearisation NTTs run once per entry; the result is identical,
 // limb for limb, to relinearising every product and adding.
-// Scratch per CTA: T [3][L+Lp][N], acc [3][L][N] (plain 64-bit sums of
-// canonical residues: exact for up to 1024 products), cacc [2][N].
+// Scratch per CTA: acc [3][L][N] uint64 (plain 64-bit sums of canonical
+// residues: exact for up to 1024 products), cacc [2][N] uint64, T [3][K][N]
+// uint32.
 template <int LOGN, int L>
 __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
     const __grid_constant__ RnsConsts c, const MmDesc* __restrict__ mms, const Entry* __restrict__ entries, int n_entries,
     const int2* __restrict__ rowlist, const u64* __restrict__ rlk, const u64* __restrict__ rlk_sh, u64* scratch,
     size_t scratch_stride, unsigned* queue)
 {
-    using NT_ = typename NttGeom<LOGN>::T;
-    constexpr int N = NT_::N, R = NT_::R, NTH = NT_::NT;
-    constexpr int LP = L + 1, LQP = L + LP;
+    using CF = Cfg<LOGN, L>;
+    using NQ = typename CF::NQ;
+    using NB = typename CF::NB;
+    static_assert(NQ::NT == NB::NT, "both transforms use the same CTA");
+    constexpr int N = NQ::N, NTH = NQ::NT, K = CF::K;
     extern __shared__ u64 sm[];
+    u32* sm32 = reinterpret_cast<u32*>(sm);
     __shared__ int s_entry;
     const int tid = threadIdx.x;
-    u64* T = scratch + (size_t)blockIdx.x * scratch_stride;
-    u64* acc = T + (size_t)3 * LQP * N;
-    u64* cacc = acc + (size_t)3 * L * N;
-    const size_t ext_words = (size_t)2 * LQP * N;
+    u64* base = scratch + (size_t)blockIdx.x * scratch_stride;
+    u64* acc = base;                                        // [3][L][N] u64
+    u64* cacc = acc + (size_t)3 * L * N;                    // [2][N] u64
+    u32* T = reinterpret_cast<u32*>(cacc + (size_t)2 * N);  // [3][K][N] u32
+    const size_t ext_words = (size_t)2 * K * N;
     const size_t ct_words = (size_t)2 * L * N;
 
     for (;;) {
@@ -440,22 +597,22 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
         }
         for (int pr = 0; pr < en.count; pr++) {
             const int2 it = rowlist[en.first + pr];
-            const u64* a = mm.A_ext + (size_t)it.x * ext_words;
-            const u64* b = mm.B_ext + ((size_t)it.y * mm.Nc + en.col) * ext_words;
+            const u32* a = mm.A_ext + (size_t)it.x * ext_words;
+            const u32* b = mm.B_ext + ((size_t)it.y * mm.Nc + en.col) * ext_words;
             // stage T
-            for (int l = 0; l < LQP; l++) {
-                const Mod m = c.m[l];
-                const u64* al = a + (size_t)l * N;
-                const u64* bl = b + (size_t)l * N;
-                const u64* tw = c.tw + (size_t)l * 4 * N;
+            for (int k = 0; k < K; k++) {
+                const Mod32 m = c.mb[k];
+                const u32* ak = a + (size_t)k * N;
+                const u32* bk = b + (size_t)k * N;
+                const u32* tw = c.twb + (size_t)k * 4 * N;
                 for (int p = 0; p < 3; p++) {
-                    u64 x[R];
+                    u32 x[NB::R];
 #pragma unroll
-                    for (int v = 0; v < R; v++) x[v] = tensor_coeff(p, al, bl, (size_t)LQP * N, NT_::run_idx(v, tid), m);
-                    NT_::inverse(x, sm, tid, tw, m.q, c.ninv[l], c.wlast[l]);
-                    u64* dst = T + ((size_t)p * LQP + l) * N;
+                    for (int v = 0; v < NB::R; v++) x[v] = tensor_coeff32(p, ak, bk, (size_t)K * N, NB::run_idx(v, tid), m);
+                    NB::inverse(x, sm32, tid, tw, m.b, c.ninv_b[k].w, c.ninv_b[k].ws, c.wlast_b[k].w, c.wlast_b[k].ws);
+                    u32* dst = T + ((size_t)p * K + k) * N;
 #pragma unroll
-                    for (int v = 0; v < R; v++) dst[NT_::inv_out_idx(v, tid)] = csub(x[v], m.q);
+                    for (int v = 0; v < NB::R; v++) dst[NB::inv_out_idx(v, tid)] = csub32(x[v], m.b);
                 }
             }
             __syncthreads();
@@ -463,12 +620,11 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
             for (int k = tid; k < N; k += NTH) {
 #pragma unroll 1
                 for (int p = 0; p < 3; p++) {
-                    u64 x[L], xp[LP], d[L];
+                    u32 x[K];
+                    u64 d[L];
 #pragma unroll
-                    for (int i = 0; i < L; i++) x[i] = T[((size_t)p * LQP + i) * N + k];
-#pragma unroll
-                    for (int j = 0; j < LP; j++) xp[j] = T[((size_t)p * LQP + L + j) * N + k];
-                    scale_round<L>(x, xp, c, d);
+                    for (int j = 0; j < K; j++) x[j] = T[((size_t)p * K + j) * N + k];
+                    scale_round_b<L, K>(x, c, d);
 #pragma unroll
                     for (int i = 0; i < L; i++) {
                         u64* ap = acc + ((size_t)p * L + i) * N + k;
@@ -485,13 +641,13 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
             for (int s = 0; s < L + 2; s++) {
                 // s = 0: sum d0 (limb i), 1: sum d1 (limb i), 2 + j: sum of digits j
                 const u64* src = s < 2 ? acc + ((size_t)s * L + i) * N : acc + ((size_t)2 * L + (s - 2)) * N;
-                u64 x[R];
+                u64 x[NQ::R];
 #pragma unroll
-                for (int v = 0; v < R; v++) x[v] = barrett64(src[NT_::fwd_in_idx(v, tid)], m);
-                NT_::forward(x, sm, tid, tw, m.q);
+                for (int v = 0; v < NQ::R; v++) x[v] = barrett64(src[NQ::fwd_in_idx(v, tid)], m);
+                NQ::forward(x, sm, tid, tw, m.q);
 #pragma unroll
-                for (int v = 0; v < R; v++) {
-                    const int k = NT_::run_idx(v, tid);
+                for (int v = 0; v < NQ::R; v++) {
+                    const int k = NQ::run_idx(v, tid);
                     if (s == 0) {
                         cacc[k] = x[v];
                     } else if (s == 1) {
@@ -506,21 +662,11 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                 }
             }
 #pragma unroll
-            for (int v = 0; v < R; v++) {
-                const int k = NT_::run_idx(v, tid);
+            for (int v = 0; v < NQ::R; v++) {
+                const int k = NQ::run_idx(v, tid);
                 Cout[(size_t)i * N + k] = barrett64(cacc[k], m);
                 Cout[((size_t)L + i) * N + k] = barrett64(cacc[N + k], m);
             }
         }
     }
 }
-
-#ifdef SFHE_KERNELS_TU
-// raw generator words (stream-equality checks against the oracle)
-__global__ void k_prng_words(u64 seed, u64 dom, u64 o0, u64 o1, u64 o2, u64 idx0, long long n, u64* out)
-{
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    out[t] = sm_word(sm_key(seed, dom, o0, o1, o2), idx0 + (u64)t);
-}
-#endif

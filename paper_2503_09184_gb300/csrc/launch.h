@@ -12,18 +12,23 @@ bool supported_ring(int logN, int L);
 int ntt_threads(int logN);
 size_t ntt_smem_bytes(int logN);
 
+// batches of NTTs: polynomial (g, l) at in + g * in_gstride + (in_l0 + l) N
+// -> out + g * out_gstride + (out_l0 + l) N, prime prime0 + l (of Q, or of B
+// for the 32-bit version)
 cudaError_t launch_ntt(const RnsConsts& rc, bool inverse, const u64* in, size_t in_gstride, int in_l0, u64* out,
                        size_t out_gstride, int out_l0, int prime0, int nlimbs, long long ngroups, cudaStream_t s);
+cudaError_t launch_ntt32(const RnsConsts& rc, bool inverse, const u32* in, size_t in_gstride, int in_l0, u32* out,
+                         size_t out_gstride, int out_l0, int prime0, int nlimbs, long long ngroups, cudaStream_t s);
 cudaError_t launch_keygen(const RnsConsts& rc, u64* s_ntt, signed char* s_coeff, u64* rlk, u64* rlk_sh, int* err,
                           cudaStream_t s);
 cudaError_t launch_encrypt(const RnsConsts& rc, const u64* s_ntt, const long long* vals, const int* coords, long long n,
                            u64 matrix_id, u64* ct, int* err, cudaStream_t s);
 cudaError_t launch_decrypt(const RnsConsts& rc, const u64* s_ntt, const u64* ct, long long n, long long* out,
                            cudaStream_t s);
-cudaError_t launch_lift_extend(const RnsConsts& rc, const u64* in, u64* out, long long ngroups, cudaStream_t s);
+cudaError_t launch_lift_extend(const RnsConsts& rc, const u64* in, u32* out, long long ngroups, cudaStream_t s);
 // plain per-product path
-cudaError_t launch_tensor_intt(const RnsConsts& rc, const u64* a, const u64* b, u64* T, cudaStream_t s);
-cudaError_t launch_scale_round(const RnsConsts& rc, const u64* T, u64* D, cudaStream_t s);
+cudaError_t launch_tensor_intt(const RnsConsts& rc, const u32* a, const u32* b, u32* T, cudaStream_t s);
+cudaError_t launch_scale_round(const RnsConsts& rc, const u32* T, u64* D, cudaStream_t s);
 cudaError_t launch_relin_ntt(const RnsConsts& rc, const u64* D, u64* U, cudaStream_t s);
 cudaError_t launch_relin_accum(const RnsConsts& rc, const u64* U, const u64* rlk, const u64* rlk_sh, u64* C,
                                cudaStream_t s);
@@ -34,6 +39,7 @@ template <int LOGN>
 cudaError_t persistent_launch(const RnsConsts& rc, const MmDesc* mms, const Entry* entries, int n_entries,
                               const int2* rowlist, const u64* rlk, const u64* rlk_sh, u64* scratch,
                               size_t scratch_stride, unsigned* queue, int grid, cudaStream_t s);
+// words of the per-CTA scratch of the persistent kernel (uint64 units)
 size_t persistent_scratch_words(const RnsConsts& rc);
 int persistent_ctas_per_sm(const RnsConsts& rc);
 cudaError_t launch_persistent(const RnsConsts& rc, const MmDesc* mms, const Entry* entries, int n_entries,

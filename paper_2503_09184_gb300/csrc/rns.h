@@ -2,17 +2,28 @@
 // kernels of the encrypted sparse matmul (RNS BFV, one ciphertext per matrix
 // element).  Plain structs only; filled on the host, passed to kernels by
 // value (__grid_constant__).
+//
+// Two RNS bases:
+//   Q = q_0 .. q_{L-1}: the ciphertext modulus, primes 2^53 < q < 2^54
+//       (64-bit words);
+//   B = b_0 .. b_{K-1}: the tensor base, primes 2^29 < b < 2^30 (32-bit
+//       words), large enough to hold the exact integer tensor of two
+//       ciphertexts with a 2^28 margin.
 #pragma once
 #include <stdint.h>
 
-#define SFHE_MAX_L 8               // ciphertext primes (Q base)
-#define SFHE_MAX_P (SFHE_MAX_L + 1)  // extension primes (P base), L + 1 of them
-#define SFHE_MAX_QP (SFHE_MAX_L + SFHE_MAX_P)
+#define SFHE_MAX_L 8   // ciphertext primes
+#define SFHE_MAX_K 32  // tensor-base primes
 
 typedef uint64_t u64;
 typedef uint32_t u32;
 
-// A modulus q with 2^53 < q < 2^54 and its Barrett constant floor(2^114 / q).
+// Size of the tensor base B (K primes of 30 bits) for ring degree 2^logN and
+// L ciphertext primes: B > N Q^2 2^27 holds with every prime above 2^29.9
+// and Q below 2^(54 L) (the host re-checks it exactly).
+constexpr int tensor_base_size(int logN, int L) { return (10 * (logN + 108 * L + 27) + 298) / 299; }
+
+// A 54-bit modulus q and its Barrett constant floor(2^114 / q).
 struct Mod {
     u64 q;
     u64 mu;
@@ -24,43 +35,70 @@ struct ShoupC {
     u64 ws;
 };
 
-// Everything a kernel needs about the RNS bases Q = q_0..q_{L-1} and
-// P = p_0..p_{L}.  Index convention for prime arrays over Q u P: 0..L-1 are
-// the q_i, L..L+Lp-1 the p_j.
+// A 30-bit modulus b with floor(2^61 / b) (values below 2^61) and
+// floor(2^64 / b) (any 64-bit value).
+struct Mod32 {
+    u32 b;
+    u32 mu61;
+    u64 mu64;
+};
+
+// A constant multiplier w < b with its Shoup companion floor(w 2^32 / b).
+struct Shoup32 {
+    u32 w;
+    u32 ws;
+};
+
 struct RnsConsts {
-    int N, logN, L, Lp;
+    int N, logN, L, K;
+    int Qwords;
     u64 t;
     u64 seed;
-    Mod m[SFHE_MAX_QP];
-    // NTT: twiddle tables live in device memory, [prime][4][N]:
-    // psi_rev, psi_rev_shoup, ipsi_rev, ipsi_rev_shoup (psi^(+-bitrev(k)))
+    Mod m[SFHE_MAX_L];
+    Mod32 mb[SFHE_MAX_K];
+    // NTT twiddles in device memory: Q primes [L][4][N] u64, B primes
+    // [K][4][N] u32; rows psi_rev, psi_rev_shoup, ipsi_rev, ipsi_rev_shoup
+    // (psi^(+-bitrev(k)), psi the smallest primitive 2N-th root).
     const u64* tw;
-    ShoupC ninv[SFHE_MAX_QP];    // N^-1
-    ShoupC wlast[SFHE_MAX_QP];   // ipsi_rev[1] * N^-1 (last inverse stage)
+    const u32* twb;
+    ShoupC ninv[SFHE_MAX_L], wlast[SFHE_MAX_L];
+    Shoup32 ninv_b[SFHE_MAX_K], wlast_b[SFHE_MAX_K];
 
-    // centred lift Q -> P
-    ShoupC qhat_inv[SFHE_MAX_L];                 // [(Q/q_i)^-1]_{q_i}
-    u64 qhat_mod_p[SFHE_MAX_L][SFHE_MAX_P];      // [Q/q_i]_{p_j}
-    u64 negQ_mod_p[SFHE_MAX_P];                  // [-Q]_{p_j}
-    // exact fallback of round(sum_i y_i / q_i): Q and Q/q_i as words
-    int Qwords;
+    // centred lift Q -> B:  a = sum_i a~_i (Q/q_i) - v Q,
+    // a~_i = [a_i (Q/q_i)^-1]_{q_i}; the 54-bit a~_i is split at bit 27.
+    ShoupC qhat_inv[SFHE_MAX_L];           // [(Q/q_i)^-1]_{q_i}
+    u32 qhat_b[SFHE_MAX_L][SFHE_MAX_K];     // [Q/q_i]_{b_k}
+    u32 qhat_b27[SFHE_MAX_L][SFHE_MAX_K];   // [2^27 Q/q_i]_{b_k}
+    u32 negQ_b[SFHE_MAX_K];                 // [-Q]_{b_k}
+    // exact decision of round(sum_i y_i / q_i): Q and Q/q_i as words
     u64 Qw[SFHE_MAX_L + 1];
     u64 Qhat_w[SFHE_MAX_L][SFHE_MAX_L + 1];
 
-    // scale and round by t/Q from Q u P, result first in base P
-    ShoupC qphat_inv[SFHE_MAX_L];                // [(QP/q_i)^-1]_{q_i}
-    ShoupC tP_q[SFHE_MAX_L];                     // [t P]_{q_i}
-    u64 omega[SFHE_MAX_L][SFHE_MAX_P];           // [floor(t P / q_i)]_{p_j}
-    ShoupC tQinv_p[SFHE_MAX_P];                  // [t Q^-1]_{p_j}
-    // base P -> Q (centred)
-    ShoupC phat_inv[SFHE_MAX_P];                 // [(P/p_j)^-1]_{p_j}
-    u64 phat_mod_q[SFHE_MAX_P][SFHE_MAX_L];      // [P/p_j]_{q_i}
-    u64 negP_mod_q[SFHE_MAX_L];                  // [-P]_{q_i}
+    // tensor x from B to Q:  x = sum_k x~_k (B/b_k) - v B, |x| < B 2^-27
+    Shoup32 bhat_inv[SFHE_MAX_K];           // [(B/b_k)^-1]_{b_k}
+    u32 bfrac[SFHE_MAX_K];                  // floor(2^58 / b_k)
+    u32 bhat_q_lo[SFHE_MAX_K][SFHE_MAX_L];  // [B/b_k]_{q_i} mod 2^27
+    u32 bhat_q_hi[SFHE_MAX_K][SFHE_MAX_L];  // [B/b_k]_{q_i} >> 27
+    u64 negB_q[SFHE_MAX_L];                 // [-B]_{q_i}
+
+    // scale and round by t/Q, directly from B: with t (B/b_k) = alpha_k Q + r_k
+    // and t B = alpha_B Q + r_B,
+    //   round(t x / Q) = sum_k x~_k alpha_k - v alpha_B + round(F),
+    //   F = (sum_k x~_k r_k - v r_B) / Q,
+    // F estimated with rho = floor(r 2^64 / Q), decided exactly near a half.
+    u32 rho_lo[SFHE_MAX_K], rho_hi[SFHE_MAX_K];   // rho_k split in 32-bit halves
+    u32 rhoB_lo, rhoB_hi;
+    u32 alpha_q_lo[SFHE_MAX_K][SFHE_MAX_L];       // [alpha_k]_{q_i} mod 2^27
+    u32 alpha_q_hi[SFHE_MAX_K][SFHE_MAX_L];       // [alpha_k]_{q_i} >> 27
+    u64 negalphaB_q[SFHE_MAX_L];                  // [-alpha_B]_{q_i}
+    u64 negK_q[SFHE_MAX_L];                       // [-K]_{q_i} (removes the offset K added to F)
+    u64 r_w[SFHE_MAX_K][SFHE_MAX_L + 1];          // r_k as words (exact decision)
+    u64 rB_w[SFHE_MAX_L + 1];                     // r_B as words
 
     // encryption / decryption
-    u64 delta_q[SFHE_MAX_L];                     // floor(Q/t) mod q_i
-    ShoupC t_q[SFHE_MAX_L];                      // t mod q_i
-    u64 cdt[20];                                 // Gaussian |e| table
+    u64 delta_q[SFHE_MAX_L];                // floor(Q/t) mod q_i
+    ShoupC t_q[SFHE_MAX_L];                 // t mod q_i
+    u64 cdt[20];                            // Gaussian |e| table
 };
 
 // Domains of the counter-based generator (shared written definition).

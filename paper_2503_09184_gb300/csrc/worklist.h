@@ -3,8 +3,8 @@
 #include "rns.h"
 
 struct MmDesc {
-    const u64* A_ext;  // [nct_A][2][L+Lp][N]
-    const u64* B_ext;  // [K*Nc][2][L+Lp][N]
+    const u32* A_ext;  // [nct_A][2][K][N] (tensor base B, NTT form)
+    const u32* B_ext;  // [rows_B * Nc][2][K][N]
     u64* C;            // [M*Nc][2][L][N]
     int Nc;
     int pad;

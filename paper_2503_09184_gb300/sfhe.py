@@ -34,9 +34,9 @@ class sfhe_params(ctypes.Structure):
 
 
 class sfhe_info(ctypes.Structure):
-    _fields_ = [("N", ctypes.c_uint32), ("L", ctypes.c_uint32), ("Lp", ctypes.c_uint32), ("t", ctypes.c_uint64),
-                ("q", ctypes.c_uint64 * 8), ("p", ctypes.c_uint64 * 9), ("ct_words", ctypes.c_uint64),
-                ("ext_words", ctypes.c_uint64), ("num_sms", ctypes.c_int32)]
+    _fields_ = [("N", ctypes.c_uint32), ("L", ctypes.c_uint32), ("K", ctypes.c_uint32),
+                ("t", ctypes.c_uint64), ("q", ctypes.c_uint64 * 8), ("b", ctypes.c_uint32 * 32),
+                ("ct_words", ctypes.c_uint64), ("ext_words", ctypes.c_uint64), ("num_sms", ctypes.c_int32)]
 
 
 class sfhe_matrix(ctypes.Structure):
@@ -57,7 +57,7 @@ _SIGS = {
     "sfhe_ctx_info": ([_vp, _P(sfhe_info)], ctypes.c_int),
     "sfhe_ctx_check": ([_vp, _vp], ctypes.c_int),
     "sfhe_last_error": ([], ctypes.c_char_p),
-    "sfhe_select_primes": ([_u32, _u32, _vp, _vp], ctypes.c_int),
+    "sfhe_select_primes": ([_u32, _u32, _vp, _vp, _P(_i32)], ctypes.c_int),
     "sfhe_cdt_table": ([ctypes.c_double, _vp], ctypes.c_int),
     "sfhe_encode_count": ([_vp, _i32, _i32, _i32, _P(_i32), _P(_i32)], ctypes.c_int),
     "sfhe_encode_fill": ([_vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
@@ -155,10 +155,12 @@ def sfhe_ctx_check(ctx: int, stream=None) -> None:
 
 
 def sfhe_select_primes(N: int, L: int) -> tuple[list[int], list[int]]:
+    """(ciphertext primes q, tensor-base primes b)."""
     q = np.zeros(8, dtype=np.uint64)
-    p = np.zeros(9, dtype=np.uint64)
-    _check(lib().sfhe_select_primes(N, L, _ptr(q), _ptr(p)))
-    return [int(x) for x in q[:L]], [int(x) for x in p[:L + 1]]
+    b = np.zeros(32, dtype=np.uint32)
+    K = ctypes.c_int32()
+    _check(lib().sfhe_select_primes(N, L, _ptr(q), _ptr(b), ctypes.byref(K)))
+    return [int(x) for x in q[:L]], [int(x) for x in b[:K.value]]
 
 
 def sfhe_cdt_table(sigma: float = 3.2) -> list[int]:

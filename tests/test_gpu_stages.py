@@ -1,7 +1,8 @@
 """Stage-level parity of the CUDA path with the oracle, bit-exact in every
-limb: generator words, keys, NTT form, encryption, the exact lift to Q u P,
-the tensor with its exact scale-and-round (including inputs on both
-rounding boundaries), relinearisation and decryption."""
+limb: generator words, keys, NTT form (ciphertext and tensor-base primes),
+encryption, the exact centred lift to the tensor base, the tensor with its
+exact scale-and-round (including inputs on both rounding boundaries),
+relinearisation and decryption."""
 from __future__ import annotations
 
 import numpy as np
@@ -38,7 +39,7 @@ def test_keys_match_oracle(mods, N, L):
     import torch
     api, S = mods
     ctx, octx = gpu_ctx(N, L, 1), oracle_ctx(N, L, 1)
-    assert ctx.q == octx.q and ctx.p == octx.p
+    assert ctx.q == octx.q
     assert (S.sfhe_export_secret(ctx.h).astype(np.int64) == octx.secret()).all()
     rlk = torch.empty((L, 2, L, N), dtype=torch.int64, device="cuda")
     S.sfhe_export_relin_key(ctx.h, rlk)
@@ -48,26 +49,32 @@ def test_keys_match_oracle(mods, N, L):
 @pytest.mark.parametrize("N,L", [(4096, 2), (8192, 4), (16384, 8)])
 def test_ntt_matches_definition(mods, N, L):
     """Forward NTT against the evaluation-at-odd-powers definition, for a
-    ciphertext prime and an extension prime; inverse round trip."""
+    ciphertext prime (64-bit words) and tensor-base primes (32-bit words);
+    inverse round trip."""
     import torch
     api, S = mods
     ctx = gpu_ctx(N, L, 1)
     rng = np.random.default_rng(N)
-    for pi in (0, L):
-        q = (ctx.q + ctx.p)[pi]
+    for pi in (0, L, L + ctx.K - 1):
+        q = (ctx.q + ctx.b)[pi]
         a = rng.integers(0, q, size=(3, N), dtype=np.uint64)
         a[1] = 0
         a[1, 0] = 1                       # NTT(1) = all ones
         a[2, : N // 2] = q - 1            # top of the range
-        dev = torch.from_numpy(a.view(np.int64)).cuda()
+        if pi < L:
+            dev = torch.from_numpy(a.view(np.int64)).cuda()
+            view = api.to_numpy_u64
+        else:
+            dev = torch.from_numpy(a.astype(np.uint32).view(np.int32)).cuda()
+            view = api.to_numpy_u32
         out = torch.empty_like(dev)
         S.sfhe_ntt(ctx.h, pi, False, dev, 3, out)
-        got = api.to_numpy_u64(out)
+        got = view(out).astype(np.uint64)
         assert (got[1] == 1).all()
         assert (got[0] == O.ntt_naive(q, a[0])).all()
         back = torch.empty_like(dev)
         S.sfhe_ntt(ctx.h, pi, True, out, 3, back)
-        assert (api.to_numpy_u64(back) == a).all()
+        assert (view(back).astype(np.uint64) == a).all()
 
 
 @pytest.mark.parametrize("N,L", RINGS + [(16384, 8)])
@@ -87,22 +94,22 @@ def test_encrypt_matches_oracle(mods, N, L):
         assert (got[k] == octx.encrypt(int(vals[k]), 77, k, 3 * k + 1)).all(), k
 
 
-def _lift_reference(coeff, q, p):
-    """centred lift of every coefficient, reduced mod the P primes (big ints)."""
+def _lift_reference(coeff, q, b):
+    """centred lift of every coefficient, reduced mod the tensor-base primes (big ints)."""
     Q = tb.prod(q)
-    out = np.zeros((coeff.shape[0], 2, len(p), coeff.shape[-1]), dtype=np.uint64)
+    out = np.zeros((coeff.shape[0], 2, len(b), coeff.shape[-1]), dtype=np.uint64)
     for n in range(coeff.shape[0]):
         for pl in range(2):
-            xs = tb.to_int_poly(coeff[n, pl], q)
-            for j, pj in enumerate(p):
-                out[n, pl, j] = [tb.centred(x, Q) % pj for x in xs]
+            xs = [tb.centred(x, Q) for x in tb.to_int_poly(coeff[n, pl], q)]
+            for k, bk in enumerate(b):
+                out[n, pl, k] = [x % bk for x in xs]
     return out
 
 
 @pytest.mark.parametrize("N,L", [(4096, 2), (4096, 3)])
 def test_lift_is_exact_centred_extension(mods, N, L):
-    """P limbs of the lifted ciphertext = centred lift mod p_j (big integers),
-    also for the lift boundaries (Q-1)/2 and (Q+1)/2 and values next to them."""
+    """Lifted ciphertext = centred lift mod every b_k (big integers), also for
+    the lift boundaries (Q-1)/2 and (Q+1)/2 and values next to them."""
     import torch
     api, S = mods
     ctx = gpu_ctx(N, L, 1)
@@ -115,23 +122,14 @@ def test_lift_is_exact_centred_extension(mods, N, L):
     coeff = np.stack([np.stack([tb.from_int_poly(ints[2 * n], ctx.q), tb.from_int_poly(ints[2 * n + 1], ctx.q)])
                       for n in range(2)])
     M = api.import_coeff(ctx, coeff)
-    ext = api.to_numpy_u64(M.ext)
-    # P limbs back to coefficient form, prime by prime
-    Pc = np.zeros((2, 2, L + 1, N), dtype=np.uint64)
-    for j in range(L + 1):
-        src = torch.from_numpy(np.ascontiguousarray(ext[:, :, L + j]).view(np.int64)).cuda()
-        dst = torch.empty_like(src)
-        S.sfhe_ntt(ctx.h, L + j, True, src.reshape(4, N), 4, dst.reshape(4, N))
-        Pc[:, :, j] = api.to_numpy_u64(dst)
-    assert (Pc == _lift_reference(coeff, ctx.q, ctx.p)).all()
-    # Q limbs are the ciphertext itself
-    assert (ext[:, :, :L] == api.to_numpy_u64(M.ct)).all()
+    Bc = api.ext_to_coeff(ctx, M.ext).astype(np.uint64)
+    assert (Bc == _lift_reference(coeff, ctx.q, ctx.b)).all()
 
 
 def _tensor_scale_gpu(api, S, ctx, A_ext, a, b):
     import torch
     d = torch.empty((3, ctx.L, ctx.N), dtype=torch.int64, device="cuda")
-    work = torch.empty(3 * (ctx.L + ctx.Lp) * ctx.N * 8, dtype=torch.uint8, device="cuda")
+    work = torch.empty(3 * ctx.K * ctx.N * 4, dtype=torch.uint8, device="cuda")
     S.sfhe_ct_tensor_scale(ctx.h, A_ext[a], A_ext[b], d, work)
     return api.to_numpy_u64(d)
 
@@ -169,7 +167,7 @@ def test_mul_relin_matches_oracle(mods, N, L):
     vals = np.array([[3, -11]], dtype=np.int64)
     M = api.encrypt_matrix(ctx, vals, "dense", 12)
     out = torch.empty((1, 2, L, N), dtype=torch.int64, device="cuda")
-    need = (3 * (L + L + 1) + 3 * L + (L + 2) * L) * N * 8
+    need = ((3 * ctx.K * N * 4 + 255) // 256) * 256 + (3 * L + (L + 2) * L) * N * 8
     work = torch.empty(need, dtype=torch.uint8, device="cuda")
     S.sfhe_ct_mul_relin(ctx.h, M.ext[0], M.ext[1], out[0], work)
     got = api.to_coeff(ctx, out, 1)[0]

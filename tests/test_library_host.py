@@ -38,10 +38,22 @@ def test_header_symbols_exported(S):
 
 @pytest.mark.parametrize("N,L", [(4096, 2), (8192, 4), (16384, 8), (4096, 3)])
 def test_primes_match_oracle(S, N, L):
+    """Ciphertext primes equal the oracle's; the tensor base holds the exact
+    tensor of two ciphertexts with the stated margins (big integers)."""
     from oracle import oracle as O
-    q, p = S.sfhe_select_primes(N, L)
-    ref = O.ntt_primes(N, 2 * L + 1)
-    assert q == ref[:L] and p == ref[L:]
+    q, b = S.sfhe_select_primes(N, L)
+    assert q == O.ntt_primes(N, L)
+    assert all(O.is_prime(x) and x % (2 * N) == 1 and 2**29 < x < 2**30 for x in b)
+    assert b == sorted(b, reverse=True) and len(set(b)) == len(b)
+    # no candidate of the form k 2N + 1 between 2^30 and the last prime is skipped
+    cand = [c for c in range(b[-1], 2**30, 2 * N) if O.is_prime(c)]
+    assert sorted(cand, reverse=True) == b
+    Q, B = 1, 1
+    for x in q:
+        Q *= x
+    for x in b:
+        B *= x
+    assert B > N * Q * Q * 2**27            # |tensor| < N Q^2 / 2: B / |x| > 2^28
 
 
 def test_cdt_matches_oracle_and_golden(S):
