@@ -49,7 +49,7 @@ typedef enum {
     SFHE_ESHAPE = 2,       /* operand shapes do not match */
     SFHE_ENOMEM = 3,       /* device allocation failed or workspace too small */
     SFHE_ECUDA = 4,        /* a CUDA runtime call failed */
-    SFHE_ETIMEOUT = 5,     /* reserved: a bounded device wait gave up */
+    SFHE_ETIMEOUT = 5,     /* a bounded device wait gave up (sfhe_matmul_check) */
     SFHE_EBUDGET = 6,      /* reserved: request over a memory budget */
     SFHE_EUNSUPPORTED = 7, /* parameters outside what the kernels implement */
     SFHE_EDEVICE = 8       /* a kernel reported a failure through the status word */
@@ -193,6 +193,11 @@ sfhe_status sfhe_matmul_batch(sfhe_ctx* ctx, int32_t n, const sfhe_matrix* A, co
 sfhe_status sfhe_plan_create(sfhe_ctx* ctx, int32_t n, const sfhe_matrix* A, const sfhe_matrix* B, sfhe_matrix* C,
                              uint32_t flags, void* work, size_t work_bytes, void* stream, sfhe_plan** out);
 sfhe_status sfhe_plan_execute(sfhe_plan* plan, void* stream);
+/* Synchronises `stream` and reads the status word of a matmul workspace
+ * after a PERSISTENT execution: SFHE_ETIMEOUT if one of the kernel's bounded
+ * waits for an operand copy ran out (the kernel then stopped early and C is
+ * incomplete). */
+sfhe_status sfhe_matmul_check(void* work, void* stream);
 /* products performed, output entries, own kernel launches per execute, CTAs */
 sfhe_status sfhe_plan_stats(const sfhe_plan* plan, int64_t* products, int64_t* entries, int64_t* launches,
                             int64_t* ctas);

@@ -593,7 +593,7 @@ sfhe_status launch_plan(sfhe_plan* P, cudaStream_t s)
             CUDA_TRY(cudaGraphLaunch(P->gexec, s));
             return SFHE_OK;
         }
-        CUDA_TRY(cudaMemsetAsync(P->d_queue, 0, sizeof(unsigned), s));
+        CUDA_TRY(cudaMemsetAsync(P->d_queue, 0, 2 * sizeof(unsigned), s));
         if (P->entries.empty()) return SFHE_OK;
         CUDA_TRY(launch_persistent(rc, P->d_mms, P->d_entries, (int)P->entries.size(), P->d_rowlist, c->d_rlk, c->d_rlk_sh,
                                    P->d_scratch, P->scratch_stride, P->d_queue, P->grid, s));
@@ -684,7 +684,7 @@ static sfhe_status plan_create_impl(sfhe_ctx* c, int32_t n, const sfhe_matrix* A
         if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             sfhe_status ls = SFHE_OK;
-            if (cudaMemsetAsync(P->d_queue, 0, sizeof(unsigned), cap) != cudaSuccess) ls = SFHE_ECUDA;
+            if (cudaMemsetAsync(P->d_queue, 0, 2 * sizeof(unsigned), cap) != cudaSuccess) ls = SFHE_ECUDA;
             if (ls == SFHE_OK && !P->entries.empty())
                 if (launch_persistent(c->rc, P->d_mms, P->d_entries, (int)P->entries.size(), P->d_rowlist, c->d_rlk,
                                       c->d_rlk_sh, P->d_scratch, P->scratch_stride, P->d_queue, P->grid, cap) != cudaSuccess)
@@ -715,6 +715,16 @@ extern "C" sfhe_status sfhe_plan_execute(sfhe_plan* P, void* stream)
 {
     if (!P) return fail(SFHE_EINVAL, "null plan");
     return launch_plan(P, as_stream(stream));
+}
+
+extern "C" sfhe_status sfhe_matmul_check(void* work, void* stream)
+{
+    if (!work) return fail(SFHE_EINVAL, "null workspace");
+    CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
+    unsigned err = 0;
+    CUDA_TRY(cudaMemcpy(&err, (char*)work + sizeof(unsigned), sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (err) return fail(SFHE_ETIMEOUT, "an operand copy of the persistent kernel did not complete within its wait bound");
+    return SFHE_OK;
 }
 
 extern "C" sfhe_status sfhe_plan_stats(const sfhe_plan* P, int64_t* products, int64_t* entries, int64_t* launches,

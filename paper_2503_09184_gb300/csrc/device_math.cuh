@@ -244,3 +244,50 @@ SFHE_DEV u64 to_residue(long long v, u64 q)
     u64 r = (u64)(-v) % q;
     return r ? q - r : 0;
 }
+
+// ------------------------------------------------- TMA bulk copies ---------
+// One-dimensional bulk copies global -> shared through the tensor memory
+// accelerator, completed on an mbarrier (transaction count in bytes).
+SFHE_DEV u32 smem_addr(const void* p) { return (u32)__cvta_generic_to_shared(p); }
+
+SFHE_DEV void mbar_init(u64* bar, u32 count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// make initialised mbarriers visible to the async proxy (before their first use)
+SFHE_DEV void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// the calling thread arrives and announces `bytes` of incoming transactions
+SFHE_DEV void mbar_arrive_expect_tx(u64* bar, u32 bytes)
+{
+    u64 state;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                 : "=l"(state)
+                 : "r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    (void)state;
+}
+// bytes (multiple of 16) from 16-byte aligned global src to 16-byte aligned shared dst
+SFHE_DEV void tma_load_1d(void* dst, const void* src, u32 bytes, u64* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+// order this thread's earlier generic-proxy shared-memory accesses before
+// later async-proxy (TMA) accesses
+SFHE_DEV void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// bounded wait for the phase with the given parity; false when the bound ran out
+SFHE_DEV bool mbar_wait(u64* bar, u32 parity, u32 max_tries)
+{
+    for (u32 i = 0; i < max_tries; i++) {
+        u32 done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}

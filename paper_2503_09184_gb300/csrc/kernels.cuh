@@ -548,10 +548,29 @@ __global__ void k_prng_words(u64 seed, u64 dom, u64 o0, u64 o1, u64 o2, u64 idx0
 // ------------------------------------------------------------------------
 // fused persistent matmul
 // ------------------------------------------------------------------------
+// Shared-memory plan of the persistent kernel.  Up to N = 8192 the operand
+// limbs are staged: four 4N-byte slots (a0, a1, b0, b1 of one tensor-base
+// prime) filled by TMA bulk copies behind the 32-bit NTT exchange buffer;
+// the 64-bit NTTs of stage R reuse the same bytes from offset 0.
+template <int LOGN, int L>
+struct PersistentPlan {
+    using CF = Cfg<LOGN, L>;
+    static constexpr bool STAGED = LOGN <= 13;
+    static constexpr size_t SLOT = (size_t)4 << LOGN;
+    static constexpr size_t EXB = ((size_t)CF::NB::SMEM_WORDS * 4 + 127) & ~(size_t)127;
+    static constexpr size_t NQB = (size_t)CF::NQ::SMEM_WORDS * 8;
+    static constexpr size_t STAGE_B = EXB + 4 * SLOT;
+    static constexpr size_t SMEM = STAGED ? (NQB > STAGE_B ? NQB : STAGE_B) : NQB;
+};
+
+// bound of every mbarrier wait (each try_wait may also suspend in hardware):
+// far beyond any copy's latency, short of a hung GPU
+#define SFHE_WAIT_TRIES (1u << 24)
+
 // One CTA per output entry at a time, taken from a queue in descending
 // product count.  Per product: stage T (tensor + 3K inverse NTTs over B into
-// the CTA's scratch), stage S (B -> Q, exact scale-and-round, then the sums
-// of d0, d1 and of the digits D_j over the entry's products).  Per entry,
+// the CTA's scratch), stage S (exact scale-and-round to Q, then the sums of
+// d0, d1 and of the digits D_j over the entry's products).  Per entry,
 // stage R: since the NTT and the key product are linear mod q_i,
 //   sum_k [NTT(d0_k) + sum_j NTT([D_jk]_{q_i}) b_j]
 //     = NTT([sum_k d0_k]_{q_i}) + sum_j NTT([sum_k D_jk]_{q_i}) b_j   (mod q_i),
@@ -559,7 +578,8 @@ __global__ void k_prng_words(u64 seed, u64 dom, u64 o0, u64 o1, u64 o2, u64 idx0
 // limb for limb, to relinearising every product and adding.
 // Scratch per CTA: acc [3][L][N] uint64 (plain 64-bit sums of canonical
 // residues: exact for up to 1024 products), cacc [2][N] uint64, T [3][K][N]
-// uint32.
+// uint32.  queue[0] is the entry counter, queue[1] the error word (1: an
+// operand copy did not complete within the wait bound).
 template <int LOGN, int L>
 __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
     const __grid_constant__ RnsConsts c, const MmDesc* __restrict__ mms, const Entry* __restrict__ entries, int n_entries,
@@ -569,11 +589,14 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
     using CF = Cfg<LOGN, L>;
     using NQ = typename CF::NQ;
     using NB = typename CF::NB;
+    using PP = PersistentPlan<LOGN, L>;
     static_assert(NQ::NT == NB::NT, "both transforms use the same CTA");
-    constexpr int N = NQ::N, NTH = NQ::NT, K = CF::K;
-    extern __shared__ u64 sm[];
+    constexpr int N = NQ::N, NTH = NQ::NT, K = CF::K, R = NB::R;
+    extern __shared__ __align__(128) u64 sm[];
     u32* sm32 = reinterpret_cast<u32*>(sm);
+    unsigned char* smb = reinterpret_cast<unsigned char*>(sm);
     __shared__ int s_entry;
+    __shared__ __align__(8) u64 mbar[2];
     const int tid = threadIdx.x;
     u64* base = scratch + (size_t)blockIdx.x * scratch_stride;
     u64* acc = base;                                        // [3][L][N] u64
@@ -581,6 +604,16 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
     u32* T = reinterpret_cast<u32*>(cacc + (size_t)2 * N);  // [3][K][N] u32
     const size_t ext_words = (size_t)2 * K * N;
     const size_t ct_words = (size_t)2 * L * N;
+    // staged operand slots: 0 a0, 1 a1, 2 b0, 3 b1 (limb k of the tensor base)
+    auto slot = [&](int s) { return reinterpret_cast<u32*>(smb + PP::EXB + (size_t)s * PP::SLOT); };
+    u32 ph0 = 0, ph1 = 0;
+    if constexpr (PP::STAGED) {
+        if (tid == 0) {
+            mbar_init(&mbar[0], 1);
+            mbar_init(&mbar[1], 1);
+            fence_mbar_init();
+        }
+    }
 
     for (;;) {
         __syncthreads();
@@ -595,28 +628,12 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
             for (size_t w = tid; w < ct_words; w += NTH) Cout[w] = 0;
             continue;
         }
-        for (int pr = 0; pr < en.count; pr++) {
+        auto operands = [&](int pr, const u32*& a, const u32*& b) {
             const int2 it = rowlist[en.first + pr];
-            const u32* a = mm.A_ext + (size_t)it.x * ext_words;
-            const u32* b = mm.B_ext + ((size_t)it.y * mm.Nc + en.col) * ext_words;
-            // stage T
-            for (int k = 0; k < K; k++) {
-                const Mod32 m = c.mb[k];
-                const u32* ak = a + (size_t)k * N;
-                const u32* bk = b + (size_t)k * N;
-                const u32* tw = c.twb + (size_t)k * 4 * N;
-                for (int p = 0; p < 3; p++) {
-                    u32 x[NB::R];
-#pragma unroll
-                    for (int v = 0; v < NB::R; v++) x[v] = tensor_coeff32(p, ak, bk, (size_t)K * N, NB::run_idx(v, tid), m);
-                    NB::inverse(x, sm32, tid, tw, m.b, c.ninv_b[k].w, c.ninv_b[k].ws, c.wlast_b[k].w, c.wlast_b[k].ws);
-                    u32* dst = T + ((size_t)p * K + k) * N;
-#pragma unroll
-                    for (int v = 0; v < NB::R; v++) dst[NB::inv_out_idx(v, tid)] = csub32(x[v], m.b);
-                }
-            }
-            __syncthreads();
-            // stage S
+            a = mm.A_ext + (size_t)it.x * ext_words;
+            b = mm.B_ext + ((size_t)it.y * mm.Nc + en.col) * ext_words;
+        };
+        auto stage_s = [&](int pr) {
             for (int k = tid; k < N; k += NTH) {
 #pragma unroll 1
                 for (int p = 0; p < 3; p++) {
@@ -632,7 +649,97 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                     }
                 }
             }
-            __syncthreads();
+        };
+        if constexpr (PP::STAGED) {
+            // stage T with TMA-staged operands: (a0, b0) of the next limb stream
+            // in during d2, (a1, b1) during the next d0
+            const int total = en.count * K;
+            auto issue = [&](int s, int pair) {
+                if (tid == 0) {
+                    const int pr = s / K, k = s - pr * K;
+                    const u32 *a, *b;
+                    operands(pr, a, b);
+                    const size_t off = (size_t)pair * K * N + (size_t)k * N;
+                    fence_proxy_async();
+                    mbar_arrive_expect_tx(&mbar[pair], (u32)(2 * PP::SLOT));
+                    tma_load_1d(slot(pair), a + off, (u32)PP::SLOT, &mbar[pair]);
+                    tma_load_1d(slot(2 + pair), b + off, (u32)PP::SLOT, &mbar[pair]);
+                }
+            };
+            auto wait_pair = [&](int pair) -> bool {
+                const bool ok = mbar_wait(&mbar[pair], pair ? ph1 : ph0, SFHE_WAIT_TRIES);
+                if (pair) ph1 ^= 1u;
+                else ph0 ^= 1u;
+                return !__syncthreads_or(!ok);
+            };
+            issue(0, 0);
+            issue(0, 1);
+            for (int s = 0; s < total; s++) {
+                const int pr = s / K, k = s - pr * K;
+                const Mod32 m = c.mb[k];
+                const u32* tw = c.twb + (size_t)k * 4 * N;
+                const u32 ni = c.ninv_b[k].w, nis = c.ninv_b[k].ws, wl = c.wlast_b[k].w, wls = c.wlast_b[k].ws;
+                u32 x[R];
+                for (int p = 0; p < 3; p++) {
+                    if (p < 2 && !wait_pair(p)) {
+                        if (tid == 0) {
+                            atomicExch(queue + 1, 1u);
+                            // let copies still in flight land before the CTA exits
+                            mbar_wait(&mbar[0], ph0, SFHE_WAIT_TRIES);
+                            mbar_wait(&mbar[1], ph1, SFHE_WAIT_TRIES);
+                        }
+                        return;
+                    }
+                    const u32* s0 = slot(0);
+                    const u32* s1 = slot(1);
+                    const u32* s2 = slot(2);
+                    const u32* s3 = slot(3);
+#pragma unroll
+                    for (int v = 0; v < R; v++) {
+                        const int i = NB::run_idx(v, tid);
+                        if (p == 0) x[v] = reduce61((u64)s0[i] * s2[i], m);
+                        else if (p == 1) x[v] = reduce61((u64)s0[i] * s3[i] + (u64)s1[i] * s2[i], m);
+                        else x[v] = reduce61((u64)s1[i] * s3[i], m);
+                    }
+                    NB::inverse(x, sm32, tid, tw, m.b, ni, nis, wl, wls);
+                    u32* dst = T + ((size_t)p * K + k) * N;
+#pragma unroll
+                    for (int v = 0; v < R; v++) dst[NB::inv_out_idx(v, tid)] = csub32(x[v], m.b);
+                    // every thread has read the pair this poly was the last user of
+                    if (p == 1 && s + 1 < total) issue(s + 1, 0);
+                    if (p == 2 && s + 1 < total) issue(s + 1, 1);
+                }
+                if (k == K - 1) {
+                    __syncthreads();
+                    stage_s(pr);
+                    __syncthreads();
+                }
+            }
+        } else {
+            for (int pr = 0; pr < en.count; pr++) {
+                const u32 *a, *b;
+                operands(pr, a, b);
+                // stage T
+                for (int k = 0; k < K; k++) {
+                    const Mod32 m = c.mb[k];
+                    const u32* ak = a + (size_t)k * N;
+                    const u32* bk = b + (size_t)k * N;
+                    const u32* tw = c.twb + (size_t)k * 4 * N;
+                    for (int p = 0; p < 3; p++) {
+                        u32 x[R];
+#pragma unroll
+                        for (int v = 0; v < R; v++) x[v] = tensor_coeff32(p, ak, bk, (size_t)K * N, NB::run_idx(v, tid), m);
+                        NB::inverse(x, sm32, tid, tw, m.b, c.ninv_b[k].w, c.ninv_b[k].ws, c.wlast_b[k].w,
+                                    c.wlast_b[k].ws);
+                        u32* dst = T + ((size_t)p * K + k) * N;
+#pragma unroll
+                        for (int v = 0; v < R; v++) dst[NB::inv_out_idx(v, tid)] = csub32(x[v], m.b);
+                    }
+                }
+                __syncthreads();
+                stage_s(pr);
+                __syncthreads();
+            }
         }
         // stage R
         for (int i = 0; i < L; i++) {

@@ -10,7 +10,7 @@ template <int LOGN, int L>
 static int occupancy_of()
 {
     int blocks = 0;
-    const size_t smem = smem_of<LOGN>();
+    const size_t smem = PersistentPlan<LOGN, L>::SMEM;
     if (allow_smem(k_matmul_persistent<LOGN, L>, smem) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_matmul_persistent<LOGN, L>, nt_of<LOGN>(), smem) !=
         cudaSuccess)
@@ -35,10 +35,11 @@ static cudaError_t launch_one(const RnsConsts& rc, const MmDesc* mms, const Entr
                               const int2* rowlist, const u64* rlk, const u64* rlk_sh, u64* scratch,
                               size_t scratch_stride, unsigned* queue, int grid, cudaStream_t s)
 {
-    cudaError_t e = allow_smem(k_matmul_persistent<LOGN, L>, smem_of<LOGN>());
+    const size_t smem = PersistentPlan<LOGN, L>::SMEM;
+    cudaError_t e = allow_smem(k_matmul_persistent<LOGN, L>, smem);
     if (e != cudaSuccess) return e;
-    k_matmul_persistent<LOGN, L><<<grid, nt_of<LOGN>(), smem_of<LOGN>(), s>>>(rc, mms, entries, n_entries, rowlist, rlk,
-                                                                             rlk_sh, scratch, scratch_stride, queue);
+    k_matmul_persistent<LOGN, L><<<grid, nt_of<LOGN>(), smem, s>>>(rc, mms, entries, n_entries, rowlist, rlk, rlk_sh,
+                                                                  scratch, scratch_stride, queue);
     return cudaGetLastError();
 }
 

@@ -79,6 +79,7 @@ _SIGS = {
                          ctypes.c_int),
     "sfhe_plan_execute": ([_vp, _vp], ctypes.c_int),
     "sfhe_plan_stats": ([_vp, _P(_i64), _P(_i64), _P(_i64), _P(_i64)], ctypes.c_int),
+    "sfhe_matmul_check": ([_vp, _vp], ctypes.c_int),
     "sfhe_plan_destroy": ([_vp], None),
     "sfhe_ct_tensor_scale": ([_vp, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
     "sfhe_ct_mul_relin": ([_vp, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
@@ -280,6 +281,10 @@ def sfhe_plan_stats(plan: int) -> dict:
     v = [ctypes.c_int64() for _ in range(4)]
     _check(lib().sfhe_plan_stats(plan, *[ctypes.byref(x) for x in v]))
     return dict(zip(("products", "entries", "launches", "ctas"), (x.value for x in v)))
+
+
+def sfhe_matmul_check(work, stream=None) -> None:
+    _check(lib().sfhe_matmul_check(_ptr(work), _stream(stream)))
 
 
 def sfhe_plan_destroy(plan: int) -> None:
