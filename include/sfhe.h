@@ -214,6 +214,27 @@ sfhe_status sfhe_ct_tensor_scale(sfhe_ctx* ctx, const uint32_t* a_ext, const uin
  * to 256 bytes) + (3 L + (L+2) L) N uint64 words. */
 sfhe_status sfhe_ct_mul_relin(sfhe_ctx* ctx, const uint32_t* a_ext, const uint32_t* b_ext, uint64_t* out, void* work,
                               size_t work_bytes, void* stream);
+
+/* Bytes of the library's static device scratch (one copy per device). */
+#define SFHE_STATIC_SCRATCH_BYTES (8u << 20)
+/* sfhe_ct_mul_relin without a workspace argument: the same computation and
+ * the same result, with its scratch in a fixed device array of
+ * SFHE_STATIC_SCRATCH_BYTES inside the library, so the call allocates no
+ * memory.  The paper has no counterpart: it is for callers that cannot
+ * hand over device memory (a plain C caller without a device allocator,
+ * code running during stream capture, a serving loop that must not enter an
+ * allocator).  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress) and should precede any stream capture; later
+ * calls only launch.  The context's device must be the current device.
+ * Rings whose scratch, 3 K N uint32 words (rounded up to 256 bytes) +
+ * (3 L + (L+2) L) N uint64 words, exceeds the array are rejected with
+ * SFHE_ENOMEM (N = 8192, L = 4 needs 3.9 MB and fits; N = 16384, L = 8
+ * needs 19.7 MB and does not).  Nothing in the scratch has to start at
+ * zero; `out` is cleared by the call.  All calls on one device share the
+ * array: calls that overlap in time (other streams, other threads) race
+ * and must be serialised by the caller. */
+sfhe_status sfhe_ct_mul_relin_static(sfhe_ctx* ctx, const uint32_t* a_ext, const uint32_t* b_ext, uint64_t* out,
+                                     void* stream);
 /* Forward / inverse NTT of npoly polynomials (device, [npoly][N]) modulo
  * prime `prime_index`: 0..L-1 the q_i (uint64 words), L..L+K-1 the b_k
  * (uint32 words). */

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -826,6 +827,56 @@ extern "C" sfhe_status sfhe_ct_mul_relin(sfhe_ctx* c, const uint32_t* a_ext, con
     cudaStream_t s = as_stream(stream);
     u32* T = (u32*)work;
     u64* D = (u64*)((char*)work + tw);
+    u64* U = D + 3 * L * N;
+    CUDA_TRY(cudaMemsetAsync(out, 0, 2 * L * N * 8, s));
+    CUDA_TRY(launch_tensor_intt(c->rc, a_ext, b_ext, T, s));
+    CUDA_TRY(launch_scale_round(c->rc, T, D, s));
+    CUDA_TRY(launch_relin_ntt(c->rc, D, U, s));
+    CUDA_TRY(launch_relin_accum(c->rc, U, c->d_rlk, c->d_rlk_sh, out, s));
+    return SFHE_OK;
+}
+
+// Scratch of sfhe_ct_mul_relin_static: a file-scope device array, so that the
+// call needs no workspace from its caller and allocates nothing.  Its callers
+// are those that cannot hand over device memory: a plain C caller with no
+// device allocator of its own, code that runs while a stream is being
+// captured (where cudaMalloc is not allowed), and a serving loop that must
+// not enter an allocator between requests.  One copy exists per device; its
+// address is looked up once per device, on the first call made there.
+namespace {
+__device__ __align__(256) unsigned char g_static_scratch[SFHE_STATIC_SCRATCH_BYTES];
+
+std::mutex g_static_mu;
+void* g_static_addr[64];  // per device ordinal; null until the first call there
+}  // namespace
+
+extern "C" sfhe_status sfhe_ct_mul_relin_static(sfhe_ctx* c, const uint32_t* a_ext, const uint32_t* b_ext,
+                                                uint64_t* out, void* stream)
+{
+    if (!c || !a_ext || !b_ext || !out) return fail(SFHE_EINVAL, "null argument");
+    const size_t N = c->rc.N, L = c->rc.L, K = c->rc.K;
+    const size_t tw = align256(3 * K * N * 4);
+    const size_t need = tw + (3 * L + (L + 2) * L) * N * 8;
+    if (need > SFHE_STATIC_SCRATCH_BYTES)
+        return fail(SFHE_ENOMEM, "N = %zu, L = %zu needs %zu bytes of scratch; the static scratch holds %zu", N, L,
+                    need, (size_t)SFHE_STATIC_SCRATCH_BYTES);
+    int dev = -1;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != c->device) return fail(SFHE_EINVAL, "current device %d is not the context's device %d", dev, c->device);
+    if (dev < 0 || dev >= 64) return fail(SFHE_EINVAL, "device ordinal %d out of range", dev);
+    void* base;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mu);
+        if (!g_static_addr[dev]) {
+            void* p = nullptr;
+            CUDA_TRY(cudaGetSymbolAddress(&p, g_static_scratch));
+            g_static_addr[dev] = p;
+        }
+        base = g_static_addr[dev];
+    }
+    cudaStream_t s = as_stream(stream);
+    u32* T = (u32*)base;
+    u64* D = (u64*)((char*)base + tw);
     u64* U = D + 3 * L * N;
     CUDA_TRY(cudaMemsetAsync(out, 0, 2 * L * N * 8, s));
     CUDA_TRY(launch_tensor_intt(c->rc, a_ext, b_ext, T, s));

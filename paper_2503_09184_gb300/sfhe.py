@@ -83,6 +83,7 @@ _SIGS = {
     "sfhe_plan_destroy": ([_vp], None),
     "sfhe_ct_tensor_scale": ([_vp, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
     "sfhe_ct_mul_relin": ([_vp, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
+    "sfhe_ct_mul_relin_static": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "sfhe_ntt": ([_vp, _i32, _i32, _vp, _i64, _vp, _vp], ctypes.c_int),
     "sfhe_prng_words": ([_u64, _u32, _u64, _u64, _u64, _u64, _i64, _vp, _vp], ctypes.c_int),
 }
@@ -300,6 +301,10 @@ def sfhe_ct_tensor_scale(ctx: int, a_ext, b_ext, d, work, stream=None) -> None:
 def sfhe_ct_mul_relin(ctx: int, a_ext, b_ext, out, work, stream=None) -> None:
     _check(lib().sfhe_ct_mul_relin(ctx, _ptr(a_ext), _ptr(b_ext), _ptr(out), _ptr(work),
                                    work.numel() * work.element_size(), _stream(stream)))
+
+
+def sfhe_ct_mul_relin_static(ctx: int, a_ext, b_ext, out, stream=None) -> None:
+    _check(lib().sfhe_ct_mul_relin_static(ctx, _ptr(a_ext), _ptr(b_ext), _ptr(out), _stream(stream)))
 
 
 def sfhe_ntt(ctx: int, prime_index: int, inverse: bool, inp, npoly: int, out, stream=None) -> None:
