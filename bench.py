@@ -65,7 +65,7 @@ def parse():
 # --------------------------------------------------------- algorithmic work ---
 def tensor_base_size(logN: int, L: int) -> int:
     """tensor-base primes K (as the library chooses them)."""
-    return (10 * (logN + 108 * L + 27) + 298) // 299
+    return (10 * (logN + 108 * L + 1) + 298) // 299
 
 
 def mults_per_product(N: int, L: int) -> int:

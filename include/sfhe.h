@@ -29,8 +29,8 @@
  *                  root of unity mod the limb's prime);
  *      lifted      [2][K][N] uint32, NTT form over the tensor base
  *                  B = b_0 .. b_{K-1}: the K largest primes below 2^30 with
- *                  b = 1 mod 2N, enough that B > N Q^2 2^27 (the exact
- *                  integer tensor of two ciphertexts fits with margin);
+ *                  b = 1 mod 2N, enough that B > 2 N Q^2 (twice the range
+ *                  of the exact integer tensor of two ciphertexts);
  *      coefficient [2][L][N] in coefficient form (sfhe_to_coeff).
  */
 #ifndef SFHE_H
@@ -228,8 +228,8 @@ sfhe_status sfhe_ct_mul_relin(sfhe_ctx* ctx, const uint32_t* a_ext, const uint32
  * calls only launch.  The context's device must be the current device.
  * Rings whose scratch, 3 K N uint32 words (rounded up to 256 bytes) +
  * (3 L + (L+2) L) N uint64 words, exceeds the array are rejected with
- * SFHE_ENOMEM (N = 8192, L = 4 needs 3.9 MB and fits; N = 16384, L = 8
- * needs 19.7 MB and does not).  Nothing in the scratch has to start at
+ * SFHE_ENOMEM (N = 8192, L = 4 needs 3.8 MB and fits; N = 16384, L = 8
+ * needs 19.5 MB and does not).  Nothing in the scratch has to start at
  * zero; `out` is cleared by the call.  All calls on one device share the
  * array: calls that overlap in time (other streams, other threads) race
  * and must be serialised by the caller. */

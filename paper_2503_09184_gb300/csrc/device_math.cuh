@@ -170,7 +170,7 @@ SFHE_DEV u32 reduce64b(u64 x, Mod32 m)
 }
 
 // round(sum_{k<n} y_k / b_k) for y_k in [0, b_k) when the sum is known to lie
-// within 2^-27 of an integer: with bfrac_k = floor(2^58 / b_k) the estimate
+// within 1/4 of an integer: with bfrac_k = floor(2^58 / b_k) the estimate
 // is at most n 2^-28 below the sum, which cannot cross a half-integer.
 template <int n>
 SFHE_DEV u32 round_b(const u32* y, const RnsConsts& c)

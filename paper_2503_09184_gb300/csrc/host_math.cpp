@@ -261,7 +261,7 @@ bool fill_constants(RnsConsts& rc)
 {
     const int L = rc.L, K = rc.K;
     const uint64_t t = rc.t;
-    // exact size margin: B > N Q^2 2^27 (the centred tensor |x| < N Q^2 / 2)
+    // exact size margin: B > 2 N Q^2 (the centred tensor |x| < N Q^2 / 2)
     Big Qbig = big(1), Bbig = big(1);
     for (int i = 0; i < L; ++i) mul_small(Qbig, rc.m[i].q);
     for (int k = 0; k < K; ++k) mul_small(Bbig, rc.mb[k].b);
@@ -271,7 +271,7 @@ bool fill_constants(RnsConsts& rc)
             mul_small(need_b, rc.m[i].q);
             mul_small(need_b, rc.m[i].q);
         }
-        shl(need_b, 27);
+        shl(need_b, 1);
         if (!greater(Bbig, need_b)) return false;
     }
     for (int i = 0; i < L; ++i) rc.m[i].mu = (uint64_t)(((u128)1 << 114) / rc.m[i].q);
@@ -325,15 +325,6 @@ bool fill_constants(RnsConsts& rc)
         const uint64_t b = rc.mb[k].b;
         rc.bhat_inv[k] = shoup32_of(invm(prod_b(rc, K, k, b), b), b);
         rc.bfrac[k] = (uint32_t)((1ULL << 58) / b);
-        for (int i = 0; i < L; ++i) {
-            const uint64_t c = prod_b(rc, K, k, rc.m[i].q);
-            rc.bhat_q_lo[k][i] = (uint32_t)(c & ((1ULL << 27) - 1));
-            rc.bhat_q_hi[k][i] = (uint32_t)(c >> 27);
-        }
-    }
-    for (int i = 0; i < L; ++i) {
-        const uint64_t qi = rc.m[i].q;
-        rc.negB_q[i] = (qi - prod_b(rc, K, -1, qi)) % qi;
     }
 
     // ---- scale and round directly from B: t (B/b_k) = alpha_k Q + r_k, t B = alpha_B Q + r_B
@@ -351,8 +342,9 @@ bool fill_constants(RnsConsts& rc)
         Big alpha, rem;
         uint64_t rho;
         split_const(ck, alpha, rem, rho);
-        rc.rho_lo[k] = (uint32_t)rho;
-        rc.rho_hi[k] = (uint32_t)(rho >> 32);
+        rc.rho_s[k][0] = (uint32_t)(rho & ((1ULL << 22) - 1));
+        rc.rho_s[k][1] = (uint32_t)((rho >> 22) & ((1ULL << 21) - 1));
+        rc.rho_s[k][2] = (uint32_t)(rho >> 43);
         for (int i = 0; i < L; ++i) {
             const uint64_t a = mod_small(alpha, rc.m[i].q);
             rc.alpha_q_lo[k][i] = (uint32_t)(a & ((1ULL << 27) - 1));

@@ -36,9 +36,11 @@ SFHE_DEV u32 tensor_coeff32(int poly, const u32* __restrict__ a, const u32* __re
 
 // Exact decision of round(F) + K near a half-integer: with the words of
 // Z = sum_k x~_k r_k - v r_B + K Q  (Z = (F + K) Q >= 0), the result is the
-// candidate m-1, m or m+1 for which (2c - 1) Q <= 2 Z < (2c + 1) Q.
+// candidate m-1, m or m+1 for which (2c - 1) Q <= 2 Z < (2c + 1) Q.  The
+// residues are read again from x32[k * stride] (global memory) and x~_k
+// recomputed, so that the caller's fast path keeps them in registers.
 template <int K>
-__device__ __noinline__ u64 scale_round_fallback(const u32* xt, u32 v, u64 m, const RnsConsts& c)
+__device__ __noinline__ u64 scale_round_fallback(const u32* x32, size_t stride, u32 v, u64 m, const RnsConsts& c)
 {
     const int W = c.Qwords + 1;
     u64 Z[SFHE_MAX_L + 2], R[SFHE_MAX_L + 2];
@@ -52,10 +54,11 @@ __device__ __noinline__ u64 scale_round_fallback(const u32* xt, u32 v, u64 m, co
     }
     // + sum_k x~_k r_k
     for (int k = 0; k < K; k++) {
+        const u64 xt = shoup32(x32[(size_t)k * stride], c.bhat_inv[k], c.mb[k].b);
         u64 cy = 0;
         for (int w = 0; w <= W; w++) {
             const u64 rw = w <= SFHE_MAX_L ? c.r_w[k][w] : 0;
-            u64 lo = rw * xt[k], hi = mulhi(rw, (u64)xt[k]);
+            u64 lo = rw * xt, hi = mulhi(rw, xt);
             lo += cy;
             hi += lo < cy ? 1 : 0;
             const u64 s = Z[w] + lo;
@@ -109,10 +112,10 @@ __device__ __noinline__ u64 scale_round_fallback(const u32* xt, u32 v, u64 m, co
     return res;
 }
 
-// Exact round(t x / Q) mod q_i for one tensor coefficient x given by its
-// residues x32[k] mod b_k (canonical, k < K):
+// Exact round(t x / Q) mod q_i for M tensor coefficients x, each given by
+// its residues x32[m][k * stride] mod b_k (canonical, k < K; global memory):
 //   x = sum_k x~_k (B/b_k) - v B,  x~_k = [x_k (B/b_k)^-1]_{b_k},
-//   v = round(sum_k x~_k / b_k)  (|x| < B 2^-28: never near a half-integer);
+//   v = round(sum_k x~_k / b_k)  (sum_k x~_k / b_k = v + x / B, |x| / B < 1/4);
 //   with t (B/b_k) = alpha_k Q + r_k and t B = alpha_B Q + r_B,
 //   t x / Q = sum_k x~_k alpha_k - v alpha_B + F,  F = (sum_k x~_k r_k - v r_B) / Q,
 // so round(t x / Q) = sum_k x~_k alpha_k - v alpha_B + round(F).  F + K > 0
@@ -120,48 +123,70 @@ __device__ __noinline__ u64 scale_round_fallback(const u32* xt, u32 v, u64 m, co
 // rho = floor(r 2^64 / Q); the true value lies in (G - K, G + K 2^30) / 2^64,
 // so round(F) + K = floor((G + 2^63) / 2^64) unless that interval crosses
 // the rounding point, where the decision is taken exactly (Q is odd: no ties).
-// 54-bit constants [alpha_k]_{q_i} are split at bit 27 so that every partial
-// product is one 32x32-bit multiply.
-template <int L, int K>
-SFHE_DEV void scale_round_b(const u32* x32, const RnsConsts& c, u64* d)
+// Every product is one 32x32-bit multiply into a 64-bit sum without carries:
+// rho_k is split into 22 + 21 + 21 bits (partial sums below 2^57), the
+// 54-bit [alpha_k]_{q_i} at bit 27 (below 2^62).  The M coefficients are
+// independent; they are interleaved for instruction-level parallelism.
+template <int L, int K, int M>
+SFHE_DEV void scale_round_m(const u32* const (&x32)[M], size_t stride, const RnsConsts& c, u64 (&d)[M][L])
 {
-    u32 xt[K];
-#pragma unroll
-    for (int k = 0; k < K; k++) xt[k] = shoup32(x32[k], c.bhat_inv[k], c.mb[k].b);
-    const u32 v = round_b<K>(xt, c);
-    // G = sum_k x~_k rho_k - v rho_B + K 2^64 + 2^63, as hi:lo
-    u64 ghi = (u64)K, glo = 1ULL << 63;
+    u32 xt[M][K];
 #pragma unroll
     for (int k = 0; k < K; k++) {
-        const u64 p0 = (u64)xt[k] * c.rho_lo[k], p1 = (u64)xt[k] * c.rho_hi[k];
-        add128(ghi, glo, p0);
-        add128(ghi, glo, p1 << 32);
-        ghi += p1 >> 32;
+#pragma unroll
+        for (int m = 0; m < M; m++) xt[m][k] = shoup32(x32[m][(size_t)k * stride], c.bhat_inv[k], c.mb[k].b);
     }
-    {
-        const u64 p0 = (u64)v * c.rhoB_lo, p1 = (u64)v * c.rhoB_hi;
+    u32 v[M];
+    u64 mK[M];
+#pragma unroll
+    for (int m = 0; m < M; m++) {
+        v[m] = round_b<K>(xt[m], c);
+        u64 s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            s0 += (u64)xt[m][k] * c.rho_s[k][0];
+            s1 += (u64)xt[m][k] * c.rho_s[k][1];
+            s2 += (u64)xt[m][k] * c.rho_s[k][2];
+        }
+        // G = s0 + s1 2^22 + s2 2^43 + K 2^64 + 2^63 - v rho_B   (mod 2^128)
+        u64 ghi = (u64)K + (s1 >> 42) + (s2 >> 21), glo = s0;
+        add128(ghi, glo, s1 << 22);
+        add128(ghi, glo, s2 << 43);
+        add128(ghi, glo, 1ULL << 63);
+        const u64 p0 = (u64)v[m] * c.rhoB_lo, p1 = (u64)v[m] * c.rhoB_hi;
         const u64 sub = p0 + (p1 << 32);
         const u64 subhi = (p1 >> 32) + (sub < p0 ? 1 : 0);
         ghi -= subhi + (glo < sub ? 1 : 0);
         glo -= sub;
+        mK[m] = ghi;  // round(F) + K, unless glo sits in the uncertainty band
+        if (glo < (u64)K || glo >= 0ULL - ((u64)K << 30)) mK[m] = scale_round_fallback<K>(x32[m], stride, v[m], mK[m], c);
     }
-    u64 mK = ghi;  // round(F) + K, unless glo sits in the uncertainty band
-    if (glo < (u64)K || glo >= 0ULL - ((u64)K << 30)) mK = scale_round_fallback<K>(xt, v, mK, c);
 #pragma unroll
     for (int i = 0; i < L; i++) {
-        u64 slo = 0, shi = 0;
 #pragma unroll
-        for (int k = 0; k < K; k++) {
-            slo += (u64)xt[k] * c.alpha_q_lo[k][i];
-            shi += (u64)xt[k] * c.alpha_q_hi[k][i];
+        for (int m = 0; m < M; m++) {
+            // sum_k x~_k alpha_k - v alpha_B + round(F) = shi 2^27 + slo (mod q_i)
+            u64 slo = (u64)v[m] * c.negalphaB_q[i] + mK[m] + c.negK_q[i], shi = 0;
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                slo += (u64)xt[m][k] * c.alpha_q_lo[k][i];
+                shi += (u64)xt[m][k] * c.alpha_q_hi[k][i];
+            }
+            u64 hi = shi >> 37, lo = shi << 27;
+            add128(hi, lo, slo);
+            d[m][i] = barrett(hi, lo, c.m[i]);
         }
-        u64 hi = shi >> 37, lo = shi << 27;
-        add128(hi, lo, slo);
-        add128(hi, lo, (u64)v * c.negalphaB_q[i]);
-        add128(hi, lo, mK);
-        add128(hi, lo, c.negK_q[i]);
-        d[i] = barrett(hi, lo, c.m[i]);
     }
+}
+
+template <int L, int K>
+SFHE_DEV void scale_round_b(const u32* x32, size_t stride, const RnsConsts& c, u64* d)
+{
+    const u32* src[1] = {x32};
+    u64 dd[1][L];
+    scale_round_m<L, K, 1>(src, stride, c, dd);
+#pragma unroll
+    for (int i = 0; i < L; i++) d[i] = dd[0][i];
 }
 
 // ------------------------------------------------------------------------
@@ -486,11 +511,8 @@ __global__ void __launch_bounds__(128) k_scale_round(const __grid_constant__ Rns
     constexpr int N = 1 << LOGN, K = CF::K;
     const int e = blockIdx.x * 128 + threadIdx.x, p = blockIdx.y;
     if (e >= N) return;
-    u32 x[K];
     u64 d[L];
-#pragma unroll
-    for (int k = 0; k < K; k++) x[k] = T[((size_t)p * K + k) * N + e];
-    scale_round_b<L, K>(x, c, d);
+    scale_round_b<L, K>(T + (size_t)p * K * N + e, N, c, d);
 #pragma unroll
     for (int i = 0; i < L; i++) D[((size_t)p * L + i) * N + e] = d[i];
 }
@@ -551,7 +573,8 @@ __global__ void k_prng_words(u64 seed, u64 dom, u64 o0, u64 o1, u64 o2, u64 idx0
 // Shared-memory plan of the persistent kernel.  Up to N = 8192 the operand
 // limbs are staged: four 4N-byte slots (a0, a1, b0, b1 of one tensor-base
 // prime) filled by TMA bulk copies behind the 32-bit NTT exchange buffer;
-// the 64-bit NTTs of stage R reuse the same bytes from offset 0.
+// the 64-bit NTTs of stage R reuse the same bytes from offset 0.  The rest
+// of the SM's 228 KB stays L1 cache (twiddle tables).
 template <int LOGN, int L>
 struct PersistentPlan {
     using CF = Cfg<LOGN, L>;
@@ -561,6 +584,7 @@ struct PersistentPlan {
     static constexpr size_t NQB = (size_t)CF::NQ::SMEM_WORDS * 8;
     static constexpr size_t STAGE_B = EXB + 4 * SLOT;
     static constexpr size_t SMEM = STAGED ? (NQB > STAGE_B ? NQB : STAGE_B) : NQB;
+    static_assert(SMEM <= 227 * 1024 - 256, "shared-memory plan too large");
 };
 
 // bound of every mbarrier wait (each try_wait may also suspend in hardware):
@@ -578,8 +602,9 @@ struct PersistentPlan {
 // limb for limb, to relinearising every product and adding.
 // Scratch per CTA: acc [3][L][N] uint64 (plain 64-bit sums of canonical
 // residues: exact for up to 1024 products), cacc [2][N] uint64, T [3][K][N]
-// uint32.  queue[0] is the entry counter, queue[1] the error word (1: an
-// operand copy did not complete within the wait bound).
+// uint32.  queue[0] is the entry counter, queue[1] the error word (1: a
+// bulk copy did not complete within the wait bound).  mbarriers 0 and 1
+// track the operand pairs of stage T.
 template <int LOGN, int L>
 __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
     const __grid_constant__ RnsConsts c, const MmDesc* __restrict__ mms, const Entry* __restrict__ entries, int n_entries,
@@ -606,14 +631,34 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
     const size_t ct_words = (size_t)2 * L * N;
     // staged operand slots: 0 a0, 1 a1, 2 b0, 3 b1 (limb k of the tensor base)
     auto slot = [&](int s) { return reinterpret_cast<u32*>(smb + PP::EXB + (size_t)s * PP::SLOT); };
-    u32 ph0 = 0, ph1 = 0;
+    // per mbarrier: parity of the phase to wait for next, and whether a copy
+    // is in flight (kept alike in every thread: issues and waits are uniform)
+    u32 phbits = 0, pend = 0;
     if constexpr (PP::STAGED) {
         if (tid == 0) {
-            mbar_init(&mbar[0], 1);
-            mbar_init(&mbar[1], 1);
+#pragma unroll
+            for (int i = 0; i < 2; i++) mbar_init(&mbar[i], 1);
             fence_mbar_init();
         }
     }
+    // bounded wait on mbarrier bi by every thread; false (in every thread) if
+    // any thread's wait ran out
+    auto wait_bar = [&](int bi) -> bool {
+        const bool ok = mbar_wait(&mbar[bi], (phbits >> bi) & 1u, SFHE_WAIT_TRIES);
+        if (ok) {
+            phbits ^= 1u << bi;
+            pend &= ~(1u << bi);
+        }
+        return !__syncthreads_or(!ok);
+    };
+    // error exit: flag it, let the copies still in flight land, leave
+    auto abort_cta = [&]() {
+        if (tid == 0) {
+            atomicExch(queue + 1, 1u);
+            for (int bi = 0; bi < 2; bi++)
+                if (pend & (1u << bi)) mbar_wait(&mbar[bi], (phbits >> bi) & 1u, SFHE_WAIT_TRIES);
+        }
+    };
 
     for (;;) {
         __syncthreads();
@@ -633,19 +678,25 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
             a = mm.A_ext + (size_t)it.x * ext_words;
             b = mm.B_ext + ((size_t)it.y * mm.Nc + en.col) * ext_words;
         };
+        // stage S: scale-and-round every tensor coefficient and add the result
+        // into the entry's sums, SM coefficients per thread at a time
         auto stage_s = [&](int pr) {
-            for (int k = tid; k < N; k += NTH) {
+            constexpr int SM = (K <= 16 && R <= 16) ? 2 : 1;
+            for (int k = tid; k < N; k += SM * NTH) {
 #pragma unroll 1
                 for (int p = 0; p < 3; p++) {
-                    u32 x[K];
-                    u64 d[L];
+                    const u32* src[SM];
 #pragma unroll
-                    for (int j = 0; j < K; j++) x[j] = T[((size_t)p * K + j) * N + k];
-                    scale_round_b<L, K>(x, c, d);
+                    for (int m = 0; m < SM; m++) src[m] = T + (size_t)p * K * N + k + m * NTH;
+                    u64 d[SM][L];
+                    scale_round_m<L, K, SM>(src, N, c, d);
 #pragma unroll
-                    for (int i = 0; i < L; i++) {
-                        u64* ap = acc + ((size_t)p * L + i) * N + k;
-                        *ap = pr == 0 ? d[i] : *ap + d[i];
+                    for (int m = 0; m < SM; m++) {
+#pragma unroll
+                        for (int i = 0; i < L; i++) {
+                            u64* ap = acc + ((size_t)p * L + i) * N + k + m * NTH;
+                            *ap = pr == 0 ? d[m][i] : *ap + d[m][i];
+                        }
                     }
                 }
             }
@@ -665,12 +716,7 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                     tma_load_1d(slot(pair), a + off, (u32)PP::SLOT, &mbar[pair]);
                     tma_load_1d(slot(2 + pair), b + off, (u32)PP::SLOT, &mbar[pair]);
                 }
-            };
-            auto wait_pair = [&](int pair) -> bool {
-                const bool ok = mbar_wait(&mbar[pair], pair ? ph1 : ph0, SFHE_WAIT_TRIES);
-                if (pair) ph1 ^= 1u;
-                else ph0 ^= 1u;
-                return !__syncthreads_or(!ok);
+                pend |= 1u << pair;
             };
             issue(0, 0);
             issue(0, 1);
@@ -681,13 +727,8 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                 const u32 ni = c.ninv_b[k].w, nis = c.ninv_b[k].ws, wl = c.wlast_b[k].w, wls = c.wlast_b[k].ws;
                 u32 x[R];
                 for (int p = 0; p < 3; p++) {
-                    if (p < 2 && !wait_pair(p)) {
-                        if (tid == 0) {
-                            atomicExch(queue + 1, 1u);
-                            // let copies still in flight land before the CTA exits
-                            mbar_wait(&mbar[0], ph0, SFHE_WAIT_TRIES);
-                            mbar_wait(&mbar[1], ph1, SFHE_WAIT_TRIES);
-                        }
+                    if (p < 2 && !wait_bar(p)) {
+                        abort_cta();
                         return;
                     }
                     const u32* s0 = slot(0);

@@ -122,23 +122,78 @@ struct NttT {
         for (int v = 0; v < R; v++) x[v] = sm[pad(idx<S, RR>(v, tid))];
     }
 
+    // The C twiddles (and Shoup companions) at w[ti0 .. ti0+C-1]; ti0 is a
+    // multiple of C, so they come in as 16-byte (or 8-byte) vector loads.
+    template <int C>
+    SFHE_DEV static void tw_fetch(W (&wv)[C], W (&wsv)[C], const W* __restrict__ w, const W* __restrict__ ws, int ti0)
+    {
+        constexpr int V = (16 / (int)sizeof(W)) < C ? (16 / (int)sizeof(W)) : C;  // words per load
+#pragma unroll
+        for (int i = 0; i < C; i += V) {
+            if constexpr (V == 4) {
+                const uint4 a = __ldg(reinterpret_cast<const uint4*>(w + ti0 + i));
+                const uint4 b = __ldg(reinterpret_cast<const uint4*>(ws + ti0 + i));
+                wv[i] = a.x, wv[i + 1] = a.y, wv[i + 2] = a.z, wv[i + 3] = a.w;
+                wsv[i] = b.x, wsv[i + 1] = b.y, wsv[i + 2] = b.z, wsv[i + 3] = b.w;
+            } else if constexpr (V == 2 && sizeof(W) == 4) {
+                const uint2 a = __ldg(reinterpret_cast<const uint2*>(w + ti0 + i));
+                const uint2 b = __ldg(reinterpret_cast<const uint2*>(ws + ti0 + i));
+                wv[i] = a.x, wv[i + 1] = a.y;
+                wsv[i] = b.x, wsv[i + 1] = b.y;
+            } else if constexpr (V == 2) {
+                const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2*>(w + ti0 + i));
+                const ulonglong2 b = __ldg(reinterpret_cast<const ulonglong2*>(ws + ti0 + i));
+                wv[i] = a.x, wv[i + 1] = a.y;
+                wsv[i] = b.x, wsv[i + 1] = b.y;
+            } else {
+                wv[i] = __ldg(w + ti0 + i);
+                wsv[i] = __ldg(ws + ti0 + i);
+            }
+        }
+    }
+    // twiddles held in registers at a time: 64 bytes of each table (32 when
+    // a thread holds 32 elements)
+    static constexpr int TWB = (R >= 32 ? 32 : 64) / (int)sizeof(W);
+
     // ------------------------------------------------------------ forward ---
+    // Stage D of a pass: butterflies at distance h = 2^(RR-1-D).  Register
+    // slot v = g 2^RR + u, u = t 2^(RR-D) + r (r < h), uses twiddle
+    // 2^lvl + ((G >> S) << D) + t, lvl = LOGN - (S+RR) + D: per group the 2^D
+    // twiddles are consecutive; they are fetched TWB at a time.
+    template <int S, int RR, int D>
+    SFHE_DEV static void fwd_stages(W (&x)[R], int tid, const W* __restrict__ w, const W* __restrict__ ws, W q)
+    {
+        if constexpr (D < RR) {
+            constexpr int h = 1 << (RR - 1 - D);
+            constexpr int lvl = LOGN - (S + RR) + D;
+            constexpr int C = 1 << D;
+            constexpr int CB = C < TWB ? C : TWB;
+#pragma unroll
+            for (int g = 0; g < (R >> RR); g++) {
+                const int G = g * NT + tid;
+                const int ti0 = (1 << lvl) + ((G >> S) << D);
+#pragma unroll
+                for (int t0 = 0; t0 < C; t0 += CB) {
+                    W wv[CB], wsv[CB];
+                    tw_fetch<CB>(wv, wsv, w, ws, ti0 + t0);
+#pragma unroll
+                    for (int t = 0; t < CB; t++) {
+#pragma unroll
+                        for (int r = 0; r < h; r++) {
+                            const int v = (g << RR) + ((t0 + t) << (RR - D)) + r;
+                            A::fwd(x[v], x[v + h], wv[t], wsv[t], q);
+                        }
+                    }
+                }
+            }
+            fwd_stages<S, RR, D + 1>(x, tid, w, ws, q);
+        }
+    }
+
     template <int S, int RR>
     SFHE_DEV static void fwd_pass(W (&x)[R], int tid, const W* __restrict__ w, const W* __restrict__ ws, W q)
     {
-#pragma unroll
-        for (int d = 0; d < RR; d++) {
-            const int h = 1 << (RR - 1 - d);
-            const int lvl = LOGN - (S + RR) + d;
-#pragma unroll
-            for (int v = 0; v < R; v++) {
-                const int u = v & ((1 << RR) - 1);
-                if (u & h) continue;
-                const int G = (v >> RR) * NT + tid;
-                const int ti = (1 << lvl) + (((G >> S) << d) | (u >> (RR - d)));
-                A::fwd(x[v], x[v + h], __ldg(w + ti), __ldg(ws + ti), q);
-            }
-        }
+        fwd_stages<S, RR, 0>(x, tid, w, ws, q);
     }
 
     template <int P>
@@ -171,27 +226,46 @@ struct NttT {
     }
 
     // ------------------------------------------------------------ inverse ---
+    // Stage D of a pass: butterflies at distance 2^D.  Register slot
+    // v = g 2^RR + u, u = t 2^(D+1) + r (r < 2^D), uses twiddle
+    // N / 2^(S+D+1) + ((G >> S) << (RR-D-1)) + t: per group the 2^(RR-D-1)
+    // twiddles are consecutive; they are fetched TWB at a time.  The
+    // transform's last stage multiplies by N^-1 (and the last twiddle) instead.
+    template <int S, int RR, bool LAST, int D>
+    SFHE_DEV static void inv_stages(W (&x)[R], int tid, const W* __restrict__ w, const W* __restrict__ ws, W q, W ni,
+                                    W nis, W wl, W wls)
+    {
+        if constexpr (D < RR) {
+            constexpr int C = 1 << (RR - D - 1);
+            constexpr int CB = C < TWB ? C : TWB;
+#pragma unroll
+            for (int g = 0; g < (R >> RR); g++) {
+                const int G = g * NT + tid;
+                const int ti0 = (N >> (S + D + 1)) + ((G >> S) << (RR - D - 1));
+#pragma unroll
+                for (int t0 = 0; t0 < C; t0 += CB) {
+                    W wv[CB], wsv[CB];
+                    if constexpr (!(LAST && D == RR - 1)) tw_fetch<CB>(wv, wsv, w, ws, ti0 + t0);
+#pragma unroll
+                    for (int t = 0; t < CB; t++) {
+#pragma unroll
+                        for (int r = 0; r < (1 << D); r++) {
+                            const int v = (g << RR) + ((t0 + t) << (D + 1)) + r;
+                            if constexpr (LAST && D == RR - 1) A::inv_last(x[v], x[v + (1 << D)], ni, nis, wl, wls, q);
+                            else A::inv(x[v], x[v + (1 << D)], wv[t], wsv[t], q);
+                        }
+                    }
+                }
+            }
+            inv_stages<S, RR, LAST, D + 1>(x, tid, w, ws, q, ni, nis, wl, wls);
+        }
+    }
+
     template <int S, int RR, bool LAST>
     SFHE_DEV static void inv_pass(W (&x)[R], int tid, const W* __restrict__ w, const W* __restrict__ ws, W q, W ni,
                                   W nis, W wl, W wls)
     {
-#pragma unroll
-        for (int d = 0; d < RR; d++) {
-            const bool final_stage = LAST && (d == RR - 1);
-#pragma unroll
-            for (int v = 0; v < R; v++) {
-                const int u = v & ((1 << RR) - 1);
-                if (u & (1 << d)) continue;
-                const int v2 = v + (1 << d);
-                if (final_stage) {
-                    A::inv_last(x[v], x[v2], ni, nis, wl, wls, q);
-                } else {
-                    const int G = (v >> RR) * NT + tid;
-                    const int ti = (N >> (S + d + 1)) + (((G >> S) << (RR - d - 1)) | (u >> (d + 1)));
-                    A::inv(x[v], x[v2], __ldg(w + ti), __ldg(ws + ti), q);
-                }
-            }
-        }
+        inv_stages<S, RR, LAST, 0>(x, tid, w, ws, q, ni, nis, wl, wls);
     }
 
     template <int P>

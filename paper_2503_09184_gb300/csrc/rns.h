@@ -7,8 +7,8 @@
 //   Q = q_0 .. q_{L-1}: the ciphertext modulus, primes 2^53 < q < 2^54
 //       (64-bit words);
 //   B = b_0 .. b_{K-1}: the tensor base, primes 2^29 < b < 2^30 (32-bit
-//       words), large enough to hold the exact integer tensor of two
-//       ciphertexts with a 2^28 margin.
+//       words), at least twice the range of the exact integer tensor of
+//       two ciphertexts (B > 2 N Q^2).
 #pragma once
 #include <stdint.h>
 
@@ -19,9 +19,9 @@ typedef uint64_t u64;
 typedef uint32_t u32;
 
 // Size of the tensor base B (K primes of 30 bits) for ring degree 2^logN and
-// L ciphertext primes: B > N Q^2 2^27 holds with every prime above 2^29.9
-// and Q below 2^(54 L) (the host re-checks it exactly).
-constexpr int tensor_base_size(int logN, int L) { return (10 * (logN + 108 * L + 27) + 298) / 299; }
+// L ciphertext primes: B > 2 N Q^2 holds with every prime above 2^29.9 and
+// Q below 2^(54 L) (the host re-checks it exactly).
+constexpr int tensor_base_size(int logN, int L) { return (10 * (logN + 108 * L + 1) + 298) / 299; }
 
 // A 54-bit modulus q and its Barrett constant floor(2^114 / q).
 struct Mod {
@@ -74,20 +74,17 @@ struct RnsConsts {
     u64 Qw[SFHE_MAX_L + 1];
     u64 Qhat_w[SFHE_MAX_L][SFHE_MAX_L + 1];
 
-    // tensor x from B to Q:  x = sum_k x~_k (B/b_k) - v B, |x| < B 2^-27
+    // tensor x from B:  x = sum_k x~_k (B/b_k) - v B, |x| < B / 4
     Shoup32 bhat_inv[SFHE_MAX_K];           // [(B/b_k)^-1]_{b_k}
     u32 bfrac[SFHE_MAX_K];                  // floor(2^58 / b_k)
-    u32 bhat_q_lo[SFHE_MAX_K][SFHE_MAX_L];  // [B/b_k]_{q_i} mod 2^27
-    u32 bhat_q_hi[SFHE_MAX_K][SFHE_MAX_L];  // [B/b_k]_{q_i} >> 27
-    u64 negB_q[SFHE_MAX_L];                 // [-B]_{q_i}
 
     // scale and round by t/Q, directly from B: with t (B/b_k) = alpha_k Q + r_k
     // and t B = alpha_B Q + r_B,
     //   round(t x / Q) = sum_k x~_k alpha_k - v alpha_B + round(F),
     //   F = (sum_k x~_k r_k - v r_B) / Q,
     // F estimated with rho = floor(r 2^64 / Q), decided exactly near a half.
-    u32 rho_lo[SFHE_MAX_K], rho_hi[SFHE_MAX_K];   // rho_k split in 32-bit halves
-    u32 rhoB_lo, rhoB_hi;
+    u32 rho_s[SFHE_MAX_K][3];                     // rho_k split at bits 22 and 43
+    u32 rhoB_lo, rhoB_hi;                         // rho_B split in 32-bit halves
     u32 alpha_q_lo[SFHE_MAX_K][SFHE_MAX_L];       // [alpha_k]_{q_i} mod 2^27
     u32 alpha_q_hi[SFHE_MAX_K][SFHE_MAX_L];       // [alpha_k]_{q_i} >> 27
     u64 negalphaB_q[SFHE_MAX_L];                  // [-alpha_B]_{q_i}

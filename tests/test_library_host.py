@@ -53,7 +53,7 @@ def test_primes_match_oracle(S, N, L):
         Q *= x
     for x in b:
         B *= x
-    assert B > N * Q * Q * 2**27            # |tensor| < N Q^2 / 2: B / |x| > 2^28
+    assert B > 2 * N * Q * Q                # |tensor| < N Q^2 / 2: |x| / B < 1/4
 
 
 def test_cdt_matches_oracle_and_golden(S):

@@ -31,7 +31,7 @@ def test_static_scratch_matches_workspace_call(N, L):
 
 
 def test_static_scratch_rejects_large_ring():
-    """N = 16384, L = 8 needs 19.7 MB of scratch, more than the static array
+    """N = 16384, L = 8 needs 19.5 MB of scratch, more than the static array
     holds: rejected on the host before anything is launched."""
     import torch
     api, S = gpu_modules()
