@@ -30,7 +30,10 @@
  *      lifted      [2][K][N] uint32, NTT form over the tensor base
  *                  B = b_0 .. b_{K-1}: the K largest primes below 2^30 with
  *                  b = 1 mod 2N, enough that B > 2 N Q^2 (twice the range
- *                  of the exact integer tensor of two ciphertexts);
+ *                  of the exact integer tensor of two ciphertexts), stored
+ *                  lane-interleaved: slot i at (i mod R) (N / R) + i / R,
+ *                  R = sfhe_info.ext_interleave (the layout the kernels
+ *                  read with consecutive addresses across a warp);
  *      coefficient [2][L][N] in coefficient form (sfhe_to_coeff).
  */
 #ifndef SFHE_H
@@ -81,6 +84,7 @@ typedef struct {
     uint64_t ct_words;      /* 2 L N (uint64 words) */
     uint64_t ext_words;     /* 2 K N (uint32 words) */
     int32_t num_sms;
+    uint32_t ext_interleave; /* R of the lifted layout (16, or 32 at N = 16384) */
 } sfhe_info;
 
 typedef struct sfhe_ctx sfhe_ctx;

@@ -39,6 +39,7 @@ class Context:
         self.q = [int(x) for x in info.q[: self.L]]
         self.b = [int(x) for x in info.b[: self.K]]
         self.ct_words, self.ext_words, self.num_sms = int(info.ct_words), int(info.ext_words), info.num_sms
+        self.ext_interleave = int(info.ext_interleave)
         self.seed = seed
 
     def close(self):
@@ -124,11 +125,13 @@ def import_coeff(ctx: Context, coeff: np.ndarray, lift: bool = True, stream=None
 
 
 def ext_to_coeff(ctx: Context, ext: torch.Tensor) -> np.ndarray:
-    """coefficient form of lifted ciphertexts: [n][2][K][N] uint32 residues mod b_k."""
+    """coefficient form of lifted ciphertexts: [n][2][K][N] uint32 residues mod b_k
+    (the lifted layout is undone first: slot i is stored at (i mod R)(N/R) + i/R)."""
     n = ext.shape[0]
+    R = ctx.ext_interleave
     out = np.zeros((n, 2, ctx.K, ctx.N), dtype=np.uint32)
     for k in range(ctx.K):
-        src = ext[:, :, k].contiguous()
+        src = ext[:, :, k].reshape(n, 2, R, ctx.N // R).transpose(-1, -2).contiguous().reshape(n, 2, ctx.N)
         dst = torch.empty_like(src)
         S.sfhe_ntt(ctx.h, ctx.L + k, True, src, 2 * n, dst)
         out[:, :, k] = to_numpy_u32(dst)

@@ -197,6 +197,7 @@ extern "C" sfhe_status sfhe_ctx_info(const sfhe_ctx* c, sfhe_info* out)
     out->ct_words = (uint64_t)2 * c->rc.L * c->rc.N;
     out->ext_words = (uint64_t)2 * c->rc.K * c->rc.N;
     out->num_sms = c->num_sms;
+    out->ext_interleave = (uint32_t)ext_interleave(c->rc.logN);
     return SFHE_OK;
 }
 
@@ -360,7 +361,7 @@ extern "C" sfhe_status sfhe_lift(sfhe_ctx* c, const uint64_t* ct, int64_t n, uin
         u32* dst = ext + n0 * extw;
         cudaError_t e = launch_ntt(rc, true, src, L * N, 0, wq, L * N, 0, 0, (int)L, 2 * cnt, s);
         if (e == cudaSuccess) e = launch_lift_extend(rc, wq, wb, 2 * cnt, s);
-        if (e == cudaSuccess) e = launch_ntt32(rc, false, wb, K * N, 0, dst, K * N, 0, 0, (int)K, 2 * cnt, s);
+        if (e == cudaSuccess) e = launch_ntt32(rc, false, wb, K * N, 0, dst, K * N, 0, 0, (int)K, 2 * cnt, true, s);
         if (e != cudaSuccess) return fail(SFHE_ECUDA, "lift: %s", cudaGetErrorString(e));
     }
     return SFHE_OK;
@@ -897,7 +898,7 @@ extern "C" sfhe_status sfhe_ntt(sfhe_ctx* c, int32_t prime_index, int32_t invers
                         ? launch_ntt(c->rc, inverse != 0, (const u64*)in, N, 0, (u64*)out, N, 0, prime_index, 1, npoly,
                                      as_stream(stream))
                         : launch_ntt32(c->rc, inverse != 0, (const u32*)in, N, 0, (u32*)out, N, 0,
-                                       prime_index - c->rc.L, 1, npoly, as_stream(stream));
+                                       prime_index - c->rc.L, 1, npoly, false, as_stream(stream));
     if (e != cudaSuccess) return fail(SFHE_ECUDA, "ntt: %s", cudaGetErrorString(e));
     return SFHE_OK;
 }

@@ -88,12 +88,12 @@ cudaError_t launch_ntt(const RnsConsts& rc, bool inverse, const u64* in, size_t 
                                                     prime0, nlimbs, ngroups, s));
 }
 
-template <int LOGN>
+template <int LOGN, bool ILV>
 static cudaError_t ntt32_impl(const RnsConsts& rc, bool inverse, const u32* in, size_t in_gstride, int in_l0, u32* out,
                               size_t out_gstride, int out_l0, int prime0, int nlimbs, long long ngroups, cudaStream_t s)
 {
     const size_t smem = smem32_of<LOGN>();
-    cudaError_t e = inverse ? allow_smem(k_ntt32_inv<LOGN>, smem) : allow_smem(k_ntt32_fwd<LOGN>, smem);
+    cudaError_t e = inverse ? allow_smem(k_ntt32_inv<LOGN, ILV>, smem) : allow_smem(k_ntt32_fwd<LOGN, ILV>, smem);
     if (e != cudaSuccess) return e;
     for (long long g0 = 0; g0 < ngroups; g0 += kMaxGridY) {
         const long long ng = ngroups - g0 < kMaxGridY ? ngroups - g0 : kMaxGridY;
@@ -101,10 +101,10 @@ static cudaError_t ntt32_impl(const RnsConsts& rc, bool inverse, const u32* in, 
         const u32* src = in + g0 * in_gstride;
         u32* dst = out + g0 * out_gstride;
         if (inverse)
-            k_ntt32_inv<LOGN><<<grid, nt32_of<LOGN>(), smem, s>>>(rc, src, in_gstride, in_l0, dst, out_gstride, out_l0,
+            k_ntt32_inv<LOGN, ILV><<<grid, nt32_of<LOGN>(), smem, s>>>(rc, src, in_gstride, in_l0, dst, out_gstride, out_l0,
                                                                   prime0);
         else
-            k_ntt32_fwd<LOGN><<<grid, nt32_of<LOGN>(), smem, s>>>(rc, src, in_gstride, in_l0, dst, out_gstride, out_l0,
+            k_ntt32_fwd<LOGN, ILV><<<grid, nt32_of<LOGN>(), smem, s>>>(rc, src, in_gstride, in_l0, dst, out_gstride, out_l0,
                                                                   prime0);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -112,12 +112,26 @@ static cudaError_t ntt32_impl(const RnsConsts& rc, bool inverse, const u32* in, 
     return cudaSuccess;
 }
 
+int ext_interleave(int logN)
+{
+    switch (logN) {
+    case 12: return NttGeom<12>::T32::R;
+    case 13: return NttGeom<13>::T32::R;
+    case 14: return NttGeom<14>::T32::R;
+    default: return 0;
+    }
+}
+
 cudaError_t launch_ntt32(const RnsConsts& rc, bool inverse, const u32* in, size_t in_gstride, int in_l0, u32* out,
-                         size_t out_gstride, int out_l0, int prime0, int nlimbs, long long ngroups, cudaStream_t s)
+                         size_t out_gstride, int out_l0, int prime0, int nlimbs, long long ngroups, bool interleaved,
+                         cudaStream_t s)
 {
     if (ngroups <= 0 || nlimbs <= 0) return cudaSuccess;
-    SFHE_DISPATCH_LOGN(rc.logN, return ntt32_impl<LG>(rc, inverse, in, in_gstride, in_l0, out, out_gstride, out_l0,
-                                                      prime0, nlimbs, ngroups, s));
+    if (interleaved)
+        SFHE_DISPATCH_LOGN(rc.logN, return ntt32_impl<LG, true>(rc, inverse, in, in_gstride, in_l0, out, out_gstride,
+                                                                out_l0, prime0, nlimbs, ngroups, s));
+    SFHE_DISPATCH_LOGN(rc.logN, return ntt32_impl<LG, false>(rc, inverse, in, in_gstride, in_l0, out, out_gstride,
+                                                             out_l0, prime0, nlimbs, ngroups, s));
 }
 
 template <int LOGN>

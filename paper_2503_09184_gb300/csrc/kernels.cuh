@@ -234,7 +234,9 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_ntt_inv(const __grid_c
 }
 
 // Same over the tensor base (32-bit words, prime index into B).
-template <int LOGN>
+// ILV: the NTT-form side (forward output, inverse input) is stored
+// lane-interleaved (NttT::lane_idx), the layout of lifted operands.
+template <int LOGN, bool ILV>
 __global__ void __launch_bounds__(NttGeom<LOGN>::T32::NT) k_ntt32_fwd(const __grid_constant__ RnsConsts c,
                                                                      const u32* in, size_t in_gstride, int in_l0,
                                                                      u32* out, size_t out_gstride, int out_l0,
@@ -252,10 +254,11 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T32::NT) k_ntt32_fwd(const __gr
     for (int v = 0; v < NT_::R; v++) x[v] = src[NT_::fwd_in_idx(v, tid)];  // < b: a valid forward input
     NT_::forward(x, sm, tid, c.twb + (size_t)pk * 4 * NT_::N, m.b);
 #pragma unroll
-    for (int v = 0; v < NT_::R; v++) dst[NT_::run_idx(v, tid)] = csub32(csub32(x[v], 2 * m.b), m.b);
+    for (int v = 0; v < NT_::R; v++)
+        dst[ILV ? NT_::lane_idx(v, tid) : NT_::run_idx(v, tid)] = csub32(csub32(x[v], 2 * m.b), m.b);
 }
 
-template <int LOGN>
+template <int LOGN, bool ILV>
 __global__ void __launch_bounds__(NttGeom<LOGN>::T32::NT) k_ntt32_inv(const __grid_constant__ RnsConsts c,
                                                                      const u32* in, size_t in_gstride, int in_l0,
                                                                      u32* out, size_t out_gstride, int out_l0,
@@ -270,7 +273,7 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T32::NT) k_ntt32_inv(const __gr
     u32* dst = out + g * out_gstride + (size_t)(out_l0 + l) * NT_::N;
     u32 x[NT_::R];
 #pragma unroll
-    for (int v = 0; v < NT_::R; v++) x[v] = csub32(src[NT_::run_idx(v, tid)], m.b);
+    for (int v = 0; v < NT_::R; v++) x[v] = csub32(src[ILV ? NT_::lane_idx(v, tid) : NT_::run_idx(v, tid)], m.b);
     NT_::inverse(x, sm, tid, c.twb + (size_t)pk * 4 * NT_::N, m.b, c.ninv_b[pk].w, c.ninv_b[pk].ws, c.wlast_b[pk].w,
                  c.wlast_b[pk].ws);
 #pragma unroll
@@ -495,7 +498,7 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T32::NT) k_tensor_intt(const __
     const u32* bk = b + (size_t)k * N;
     u32 x[NB::R];
 #pragma unroll
-    for (int v = 0; v < NB::R; v++) x[v] = tensor_coeff32(p, ak, bk, off1, NB::run_idx(v, tid), m);
+    for (int v = 0; v < NB::R; v++) x[v] = tensor_coeff32(p, ak, bk, off1, NB::lane_idx(v, tid), m);
     NB::inverse(x, sm, tid, c.twb + (size_t)k * 4 * N, m.b, c.ninv_b[k].w, c.ninv_b[k].ws, c.wlast_b[k].w,
                 c.wlast_b[k].ws);
     u32* dst = T + ((size_t)p * K + k) * N;
@@ -737,7 +740,7 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                     const u32* s3 = slot(3);
 #pragma unroll
                     for (int v = 0; v < R; v++) {
-                        const int i = NB::run_idx(v, tid);
+                        const int i = NB::lane_idx(v, tid);
                         if (p == 0) x[v] = reduce61((u64)s0[i] * s2[i], m);
                         else if (p == 1) x[v] = reduce61((u64)s0[i] * s3[i] + (u64)s1[i] * s2[i], m);
                         else x[v] = reduce61((u64)s1[i] * s3[i], m);
@@ -769,7 +772,7 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                     for (int p = 0; p < 3; p++) {
                         u32 x[R];
 #pragma unroll
-                        for (int v = 0; v < R; v++) x[v] = tensor_coeff32(p, ak, bk, (size_t)K * N, NB::run_idx(v, tid), m);
+                        for (int v = 0; v < R; v++) x[v] = tensor_coeff32(p, ak, bk, (size_t)K * N, NB::lane_idx(v, tid), m);
                         NB::inverse(x, sm32, tid, tw, m.b, c.ninv_b[k].w, c.ninv_b[k].ws, c.wlast_b[k].w,
                                     c.wlast_b[k].ws);
                         u32* dst = T + ((size_t)p * K + k) * N;

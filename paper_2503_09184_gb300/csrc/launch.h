@@ -17,8 +17,13 @@ size_t ntt_smem_bytes(int logN);
 // for the 32-bit version)
 cudaError_t launch_ntt(const RnsConsts& rc, bool inverse, const u64* in, size_t in_gstride, int in_l0, u64* out,
                        size_t out_gstride, int out_l0, int prime0, int nlimbs, long long ngroups, cudaStream_t s);
+// R of the lane-interleaved layout of lifted operands at ring degree 2^logN
+int ext_interleave(int logN);
+// interleaved: the NTT-form side is in the lane-interleaved layout of lifted
+// operands (NttT::lane_idx) instead of natural slot order
 cudaError_t launch_ntt32(const RnsConsts& rc, bool inverse, const u32* in, size_t in_gstride, int in_l0, u32* out,
-                         size_t out_gstride, int out_l0, int prime0, int nlimbs, long long ngroups, cudaStream_t s);
+                         size_t out_gstride, int out_l0, int prime0, int nlimbs, long long ngroups, bool interleaved,
+                         cudaStream_t s);
 cudaError_t launch_keygen(const RnsConsts& rc, u64* s_ntt, signed char* s_coeff, u64* rlk, u64* rlk_sh, int* err,
                           cudaStream_t s);
 cudaError_t launch_encrypt(const RnsConsts& rc, const u64* s_ntt, const long long* vals, const int* coords, long long n,

@@ -98,6 +98,9 @@ struct NttT {
 
     // layouts seen by callers
     SFHE_DEV static int run_idx(int v, int tid) { return tid * R + v; }  // inverse input / forward output
+    // lane-interleaved storage of the run layout: element tid * R + v is kept
+    // at v * NT + tid, so a warp's accesses to one v are consecutive words
+    SFHE_DEV static int lane_idx(int v, int tid) { return v * NT + tid; }
     SFHE_DEV static int fwd_in_idx(int v, int tid)
     {
         if constexpr (REM > 0) return idx<LOGN - REM, REM>(v, tid);
@@ -226,14 +229,19 @@ struct NttT {
     }
 
     // ------------------------------------------------------------ inverse ---
+    // The inverse transforms NP polynomials modulo the same prime at once:
+    // x[j] holds polynomial j, every twiddle is fetched once for all of them,
+    // and each exchange costs one pair of barriers (polynomial j exchanges
+    // through sm + j * SMEM_WORDS).
+    //
     // Stage D of a pass: butterflies at distance 2^D.  Register slot
     // v = g 2^RR + u, u = t 2^(D+1) + r (r < 2^D), uses twiddle
     // N / 2^(S+D+1) + ((G >> S) << (RR-D-1)) + t: per group the 2^(RR-D-1)
     // twiddles are consecutive; they are fetched TWB at a time.  The
     // transform's last stage multiplies by N^-1 (and the last twiddle) instead.
-    template <int S, int RR, bool LAST, int D>
-    SFHE_DEV static void inv_stages(W (&x)[R], int tid, const W* __restrict__ w, const W* __restrict__ ws, W q, W ni,
-                                    W nis, W wl, W wls)
+    template <int NP, int S, int RR, bool LAST, int D>
+    SFHE_DEV static void inv_stages(W (&x)[NP][R], int tid, const W* __restrict__ w, const W* __restrict__ ws, W q,
+                                    W ni, W nis, W wl, W wls)
     {
         if constexpr (D < RR) {
             constexpr int C = 1 << (RR - D - 1);
@@ -251,50 +259,61 @@ struct NttT {
 #pragma unroll
                         for (int r = 0; r < (1 << D); r++) {
                             const int v = (g << RR) + ((t0 + t) << (D + 1)) + r;
-                            if constexpr (LAST && D == RR - 1) A::inv_last(x[v], x[v + (1 << D)], ni, nis, wl, wls, q);
-                            else A::inv(x[v], x[v + (1 << D)], wv[t], wsv[t], q);
+#pragma unroll
+                            for (int j = 0; j < NP; j++) {
+                                if constexpr (LAST && D == RR - 1)
+                                    A::inv_last(x[j][v], x[j][v + (1 << D)], ni, nis, wl, wls, q);
+                                else
+                                    A::inv(x[j][v], x[j][v + (1 << D)], wv[t], wsv[t], q);
+                            }
                         }
                     }
                 }
             }
-            inv_stages<S, RR, LAST, D + 1>(x, tid, w, ws, q, ni, nis, wl, wls);
+            inv_stages<NP, S, RR, LAST, D + 1>(x, tid, w, ws, q, ni, nis, wl, wls);
         }
     }
 
-    template <int S, int RR, bool LAST>
-    SFHE_DEV static void inv_pass(W (&x)[R], int tid, const W* __restrict__ w, const W* __restrict__ ws, W q, W ni,
-                                  W nis, W wl, W wls)
+    // one exchange: store in the layout of pass (S0, RR0), load in (S1, RR1)
+    template <int NP, int S0, int RR0, int S1, int RR1>
+    SFHE_DEV static void exchange(W (&x)[NP][R], W* sm, int tid)
     {
-        inv_stages<S, RR, LAST, 0>(x, tid, w, ws, q, ni, nis, wl, wls);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < NP; j++) store<S0, RR0>(x[j], sm + (size_t)j * SMEM_WORDS, tid);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < NP; j++) load<S1, RR1>(x[j], sm + (size_t)j * SMEM_WORDS, tid);
     }
 
-    template <int P>
-    SFHE_DEV static void inv_rest(W (&x)[R], W* sm, int tid, const W* w, const W* ws, W q, W ni, W nis, W wl, W wls)
+    template <int NP, int PS>
+    SFHE_DEV static void inv_rest(W (&x)[NP][R], W* sm, int tid, const W* w, const W* ws, W q, W ni, W nis, W wl,
+                                  W wls)
     {
-        if constexpr (P < NFULL) {
-            __syncthreads();
-            store<(P - 1) * LOGR, LOGR>(x, sm, tid);
-            __syncthreads();
-            load<P * LOGR, LOGR>(x, sm, tid);
-            inv_pass<P * LOGR, LOGR, (P == NFULL - 1 && REM == 0)>(x, tid, w, ws, q, ni, nis, wl, wls);
-            inv_rest<P + 1>(x, sm, tid, w, ws, q, ni, nis, wl, wls);
-        } else if constexpr (P == NFULL && REM > 0) {
-            __syncthreads();
-            store<(NFULL - 1) * LOGR, LOGR>(x, sm, tid);
-            __syncthreads();
-            load<NFULL * LOGR, REM>(x, sm, tid);
-            inv_pass<NFULL * LOGR, REM, true>(x, tid, w, ws, q, ni, nis, wl, wls);
+        if constexpr (PS < NFULL) {
+            exchange<NP, (PS - 1) * LOGR, LOGR, PS * LOGR, LOGR>(x, sm, tid);
+            inv_stages<NP, PS * LOGR, LOGR, (PS == NFULL - 1 && REM == 0), 0>(x, tid, w, ws, q, ni, nis, wl, wls);
+            inv_rest<NP, PS + 1>(x, sm, tid, w, ws, q, ni, nis, wl, wls);
+        } else if constexpr (PS == NFULL && REM > 0) {
+            exchange<NP, (NFULL - 1) * LOGR, LOGR, NFULL * LOGR, REM>(x, sm, tid);
+            inv_stages<NP, NFULL * LOGR, REM, true, 0>(x, tid, w, ws, q, ni, nis, wl, wls);
         }
     }
 
     // x: run_idx layout in ([0, 2q)), inv_out_idx layout out ([0, 2q)).
     // (ni, nis) = N^-1 and its Shoup companion; (wl, wls) = ipsi_rev[1] N^-1.
-    SFHE_DEV static void inverse(W (&x)[R], W* sm, int tid, const W* tw, W q, W ni, W nis, W wl, W wls)
+    // sm holds NP * SMEM_WORDS words.
+    template <int NP>
+    SFHE_DEV static void inverse_m(W (&x)[NP][R], W* sm, int tid, const W* tw, W q, W ni, W nis, W wl, W wls)
     {
         const W* w = tw + 2 * N;
         const W* ws = tw + 3 * N;
-        inv_pass<0, LOGR, (NFULL == 1 && REM == 0)>(x, tid, w, ws, q, ni, nis, wl, wls);
-        inv_rest<1>(x, sm, tid, w, ws, q, ni, nis, wl, wls);
+        inv_stages<NP, 0, LOGR, (NFULL == 1 && REM == 0), 0>(x, tid, w, ws, q, ni, nis, wl, wls);
+        inv_rest<NP, 1>(x, sm, tid, w, ws, q, ni, nis, wl, wls);
+    }
+    SFHE_DEV static void inverse(W (&x)[R], W* sm, int tid, const W* tw, W q, W ni, W nis, W wl, W wls)
+    {
+        inverse_m<1>(reinterpret_cast<W(&)[1][R]>(x), sm, tid, tw, q, ni, nis, wl, wls);
     }
 };
 

@@ -36,7 +36,8 @@ class sfhe_params(ctypes.Structure):
 class sfhe_info(ctypes.Structure):
     _fields_ = [("N", ctypes.c_uint32), ("L", ctypes.c_uint32), ("K", ctypes.c_uint32),
                 ("t", ctypes.c_uint64), ("q", ctypes.c_uint64 * 8), ("b", ctypes.c_uint32 * 32),
-                ("ct_words", ctypes.c_uint64), ("ext_words", ctypes.c_uint64), ("num_sms", ctypes.c_int32)]
+                ("ct_words", ctypes.c_uint64), ("ext_words", ctypes.c_uint64), ("num_sms", ctypes.c_int32),
+                ("ext_interleave", ctypes.c_uint32)]
 
 
 class sfhe_matrix(ctypes.Structure):
