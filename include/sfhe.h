@@ -208,12 +208,12 @@ sfhe_status sfhe_plan_stats(const sfhe_plan* plan, int64_t* products, int64_t* e
 void sfhe_plan_destroy(sfhe_plan* plan);
 
 /* ------------------------------------------------- stage entry points --- */
-/* One product's tensor and exact scale-and-round (Alg. 1 "a <- a x b"):
+/* One product's tensor and exact scale-and-round (the multiply of Alg. 1):
  * d[3][L][N] (uint64, coefficient form) from lifted a, b (device).
  * Workspace: 3 K N uint32 words. */
 sfhe_status sfhe_ct_tensor_scale(sfhe_ctx* ctx, const uint32_t* a_ext, const uint32_t* b_ext, uint64_t* d, void* work,
                                  size_t work_bytes, void* stream);
-/* One product multiplied and relinearised (Alg. 1 "a <- a x b; fhe_relin"),
+/* One product multiplied and relinearised (Alg. 1's multiply and relinearisation),
  * NTT form [2][L][N] (plain path).  Workspace: 3 K N uint32 words (rounded up
  * to 256 bytes) + (3 L + (L+2) L) N uint64 words. */
 sfhe_status sfhe_ct_mul_relin(sfhe_ctx* ctx, const uint32_t* a_ext, const uint32_t* b_ext, uint64_t* out, void* work,

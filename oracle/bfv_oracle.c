@@ -11,9 +11,9 @@
  * Homomorphic Encrypted DNNs", Alg. 1 and Sec. 3.3.2):
  *   C[i][j] = sum over k in S(i,j) of Relin(Mul(A[i][k], B[k][j]))
  * where S(i,j) is the product set an encoding lists (dense: every k; naive
- * sparse / CSR / ELLPACK: the k with A[i][k] != 0).  Per product: multiply
- * (Alg. 1 "a <- a x b"), relinearise ("fhe_relin"), add into the result
- * ("fhe_add").  BFV replaces CKKS's rescale by the exact scale-and-round by
+ * sparse / CSR / ELLPACK: the k with A[i][k] != 0).  Per product, in the
+ * order of Alg. 1's inner loop: multiply the two chunks, relinearise, add
+ * into the result.  BFV replaces CKKS's rescale by the exact scale-and-round by
  * t/Q that is part of the BFV multiply (Sec. 3.1 names BFV as the integer
  * scheme).
  *
@@ -802,7 +802,7 @@ int or_mul_relin(void *vc, const u64 *a, const u64 *b, u64 *out)
     return 0;
 }
 
-/* acc += x (mod q_i), both [2][L][N]: Alg. 1's fhe_add into the result. */
+/* acc += x (mod q_i), both [2][L][N]: Alg. 1's accumulation into the result. */
 void or_add(void *vc, u64 *acc, const u64 *x)
 {
     or_ctx *c = (or_ctx *)vc;

@@ -2,11 +2,11 @@
 //
 // Storage (canonical residues):
 //   ciphertext, base Q, NTT form:          [2 (c0, c1)][L][N]  uint64
-//   lifted ciphertext, base B, NTT form:   [2][K][N]           uint32
+//   lifted ciphertext, base B, NTT form:   [2][K][N]           uint32 (lane-interleaved, NttT::lane_idx)
 //   relinearisation key, base Q, NTT form: [L digit j][2 (b, a)][L limb i][N] uint64 (+ Shoup companions)
-// Per product (Alg. 1: "a <- a x b; fhe_relin; fhe_add"):
+// Per product (Alg. 1's inner loop: multiply, relinearise, add):
 //   tensor d0 = a0 b0, d1 = a0 b1 + a1 b0, d2 = a1 b1 over B (NTT form, 30-bit
-//   arithmetic), inverse NTT: the exact integer tensor x in B (|x| < B 2^-28);
+//   arithmetic), inverse NTT: the exact integer tensor x in B (|x| < B / 4);
 //   exact scale-and-round by t/Q straight from B (the result in Q);
 //   digits D_j = [d2]_{q_j}; relinearise with the key; add into C.
 #pragma once
