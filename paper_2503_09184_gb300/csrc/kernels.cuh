@@ -575,15 +575,16 @@ __global__ void k_prng_words(u64 seed, u64 dom, u64 o0, u64 o1, u64 o2, u64 idx0
 // ------------------------------------------------------------------------
 // Shared-memory plan of the persistent kernel.  Up to N = 8192 the operand
 // limbs are staged: four 4N-byte slots (a0, a1, b0, b1 of one tensor-base
-// prime) filled by TMA bulk copies behind the 32-bit NTT exchange buffer;
-// the 64-bit NTTs of stage R reuse the same bytes from offset 0.  The rest
-// of the SM's 228 KB stays L1 cache (twiddle tables).
+// prime) filled by TMA bulk copies behind the exchange buffers of the three
+// 32-bit inverse NTTs that run together; the 64-bit NTTs of stage R reuse
+// the same bytes from offset 0.
 template <int LOGN, int L>
 struct PersistentPlan {
     using CF = Cfg<LOGN, L>;
     static constexpr bool STAGED = LOGN <= 13;
+    static constexpr int NPT = STAGED ? 3 : 1;  // polynomials per inverse-NTT pass in stage T
     static constexpr size_t SLOT = (size_t)4 << LOGN;
-    static constexpr size_t EXB = ((size_t)CF::NB::SMEM_WORDS * 4 + 127) & ~(size_t)127;
+    static constexpr size_t EXB = ((size_t)NPT * CF::NB::SMEM_WORDS * 4 + 127) & ~(size_t)127;
     static constexpr size_t NQB = (size_t)CF::NQ::SMEM_WORDS * 8;
     static constexpr size_t STAGE_B = EXB + 4 * SLOT;
     static constexpr size_t SMEM = STAGED ? (NQB > STAGE_B ? NQB : STAGE_B) : NQB;
@@ -705,8 +706,10 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
             }
         };
         if constexpr (PP::STAGED) {
-            // stage T with TMA-staged operands: (a0, b0) of the next limb stream
-            // in during d2, (a1, b1) during the next d0
+            // stage T with TMA-staged operands: per tensor-base prime, the
+            // three tensor polynomials are formed from the four staged limbs
+            // and inverse-transformed together; the next prime's limbs stream
+            // into the slots meanwhile
             const int total = en.count * K;
             auto issue = [&](int s, int pair) {
                 if (tid == 0) {
@@ -728,12 +731,12 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                 const Mod32 m = c.mb[k];
                 const u32* tw = c.twb + (size_t)k * 4 * N;
                 const u32 ni = c.ninv_b[k].w, nis = c.ninv_b[k].ws, wl = c.wlast_b[k].w, wls = c.wlast_b[k].ws;
-                u32 x[R];
-                for (int p = 0; p < 3; p++) {
-                    if (p < 2 && !wait_bar(p)) {
-                        abort_cta();
-                        return;
-                    }
+                if (!wait_bar(0) || !wait_bar(1)) {
+                    abort_cta();
+                    return;
+                }
+                u32 x[3][R];
+                {
                     const u32* s0 = slot(0);
                     const u32* s1 = slot(1);
                     const u32* s2 = slot(2);
@@ -741,17 +744,23 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
 #pragma unroll
                     for (int v = 0; v < R; v++) {
                         const int i = NB::lane_idx(v, tid);
-                        if (p == 0) x[v] = reduce61((u64)s0[i] * s2[i], m);
-                        else if (p == 1) x[v] = reduce61((u64)s0[i] * s3[i] + (u64)s1[i] * s2[i], m);
-                        else x[v] = reduce61((u64)s1[i] * s3[i], m);
+                        const u64 a0 = s0[i], a1 = s1[i], b0 = s2[i], b1 = s3[i];
+                        x[0][v] = reduce61(a0 * b0, m);
+                        x[1][v] = reduce61(a0 * b1 + a1 * b0, m);
+                        x[2][v] = reduce61(a1 * b1, m);
                     }
-                    NB::inverse(x, sm32, tid, tw, m.b, ni, nis, wl, wls);
+                }
+                __syncthreads();  // every thread has read the slots
+                if (s + 1 < total) {
+                    issue(s + 1, 0);
+                    issue(s + 1, 1);
+                }
+                NB::template inverse_m<3>(x, sm32, tid, tw, m.b, ni, nis, wl, wls);
+#pragma unroll
+                for (int p = 0; p < 3; p++) {
                     u32* dst = T + ((size_t)p * K + k) * N;
 #pragma unroll
-                    for (int v = 0; v < R; v++) dst[NB::inv_out_idx(v, tid)] = csub32(x[v], m.b);
-                    // every thread has read the pair this poly was the last user of
-                    if (p == 1 && s + 1 < total) issue(s + 1, 0);
-                    if (p == 2 && s + 1 < total) issue(s + 1, 1);
+                    for (int v = 0; v < R; v++) dst[NB::inv_out_idx(v, tid)] = csub32(x[p][v], m.b);
                 }
                 if (k == K - 1) {
                     __syncthreads();

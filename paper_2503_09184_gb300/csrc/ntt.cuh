@@ -8,8 +8,11 @@
 //
 // Each of the NT = N / R threads keeps R = 2^LOGR elements in registers and
 // runs up to LOGR butterfly stages on them (a "pass"); between passes the
-// CTA exchanges elements through shared memory, padded by one word every R
-// words so that both access patterns are (nearly) free of bank conflicts.
+// CTA exchanges elements through shared memory.  The exchange layout keeps
+// every warp access free of bank conflicts for all pass layouts: 64-bit words
+// are padded by one word every R words; 32-bit words are XOR-swizzled within
+// each 32-word row (no padding, so three polynomials' buffers fit beside the
+// staged operands of the persistent kernel).
 //
 // Register slot v of thread tid in a pass that starts at butterfly distance
 // 2^S and spans RR stages holds global index
@@ -84,9 +87,21 @@ struct NttT {
     static constexpr int NT = N >> LOGR;
     static constexpr int NFULL = LOGN / LOGR;
     static constexpr int REM = LOGN % LOGR;
-    static constexpr int SMEM_WORDS = N + (N >> LOGR);
+    static constexpr bool SWIZZLE = sizeof(W) == 4;
+    static constexpr int SMEM_WORDS = SWIZZLE ? N : N + (N >> LOGR);
+    static_assert(!SWIZZLE || LOGR == 4 || LOGR == 5, "swizzle defined for R = 16 and 32");
 
-    SFHE_DEV static int pad(int e) { return e + (e >> LOGR); }
+    // shared-memory word of element e.  R = 16: a warp's lanes vary element
+    // bits 4..8 (first pass), 0..3 and 8 (second) or 0..4 (later passes);
+    // XOR-ing bits 5..8 into bank bits 0..3 and bit 8 into bank bit 4 makes
+    // all 32 banks distinct in each case.  R = 32: lanes vary bits 5..9 or
+    // 0..4, and XOR-ing bits 5..9 into bits 0..4 does the same.
+    SFHE_DEV static int pad(int e)
+    {
+        if constexpr (!SWIZZLE) return e + (e >> LOGR);
+        else if constexpr (LOGR == 4) return e ^ (((e >> 5) & 15) | (((e >> 8) & 1) << 4));
+        else return e ^ ((e >> 5) & 31);
+    }
 
     template <int S, int RR>
     SFHE_DEV static int idx(int v, int tid)
