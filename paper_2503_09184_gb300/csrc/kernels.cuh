@@ -794,7 +794,16 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                 __syncthreads();
             }
         }
-        // stage R
+        // stage R.  The forward NTT leaves slot tid * R + v of every polynomial
+        // with thread tid, so the key products and the output are private to
+        // a thread: the sums [2][N] live in the idle operand slots (staged
+        // kernel; element v of thread tid at v * NTH + tid, free of bank
+        // conflicts) or in the CTA's scratch, and the key and C are accessed
+        // with 16-byte vectors.
+        u64* cs = PP::STAGED ? reinterpret_cast<u64*>(smb + PP::EXB) : cacc;
+        auto cpos = [&](int v) -> size_t {
+            return PP::STAGED ? (size_t)v * NTH + tid : (size_t)NQ::run_idx(v, tid);
+        };
         for (int i = 0; i < L; i++) {
             const Mod m = c.m[i];
             const u64* tw = c.tw + (size_t)i * 4 * N;
@@ -805,28 +814,37 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
 #pragma unroll
                 for (int v = 0; v < NQ::R; v++) x[v] = barrett64(src[NQ::fwd_in_idx(v, tid)], m);
                 NQ::forward(x, sm, tid, tw, m.q);
+                if (s < 2) {
 #pragma unroll
-                for (int v = 0; v < NQ::R; v++) {
-                    const int k = NQ::run_idx(v, tid);
-                    if (s == 0) {
-                        cacc[k] = x[v];
-                    } else if (s == 1) {
-                        cacc[N + k] = x[v];
-                    } else {
-                        const int j = s - 2;
-                        const size_t rb = (((size_t)j * 2 + 0) * L + i) * N + k;
-                        const size_t ra = (((size_t)j * 2 + 1) * L + i) * N + k;
-                        cacc[k] += shoup_lazy(x[v], __ldg(rlk + rb), __ldg(rlk_sh + rb), m.q);
-                        cacc[N + k] += shoup_lazy(x[v], __ldg(rlk + ra), __ldg(rlk_sh + ra), m.q);
+                    for (int v = 0; v < NQ::R; v++) cs[(size_t)s * N + cpos(v)] = x[v];
+                } else {
+                    const int j = s - 2;
+                    const size_t ob = (((size_t)j * 2 + 0) * L + i) * N + (size_t)tid * NQ::R;
+                    const size_t oa = (((size_t)j * 2 + 1) * L + i) * N + (size_t)tid * NQ::R;
+#pragma unroll
+                    for (int v = 0; v < NQ::R; v += 2) {
+                        const ulonglong2 wb = __ldg(reinterpret_cast<const ulonglong2*>(rlk + ob + v));
+                        const ulonglong2 sb = __ldg(reinterpret_cast<const ulonglong2*>(rlk_sh + ob + v));
+                        const ulonglong2 wa = __ldg(reinterpret_cast<const ulonglong2*>(rlk + oa + v));
+                        const ulonglong2 sa = __ldg(reinterpret_cast<const ulonglong2*>(rlk_sh + oa + v));
+                        cs[cpos(v)] += shoup_lazy(x[v], wb.x, sb.x, m.q);
+                        cs[cpos(v + 1)] += shoup_lazy(x[v + 1], wb.y, sb.y, m.q);
+                        cs[N + cpos(v)] += shoup_lazy(x[v], wa.x, sa.x, m.q);
+                        cs[N + cpos(v + 1)] += shoup_lazy(x[v + 1], wa.y, sa.y, m.q);
                     }
                 }
             }
+            u64* c0 = Cout + (size_t)i * N + (size_t)tid * NQ::R;
+            u64* c1 = Cout + ((size_t)L + i) * N + (size_t)tid * NQ::R;
 #pragma unroll
-            for (int v = 0; v < NQ::R; v++) {
-                const int k = NQ::run_idx(v, tid);
-                Cout[(size_t)i * N + k] = barrett64(cacc[k], m);
-                Cout[((size_t)L + i) * N + k] = barrett64(cacc[N + k], m);
+            for (int v = 0; v < NQ::R; v += 2) {
+                *reinterpret_cast<ulonglong2*>(c0 + v) =
+                    make_ulonglong2(barrett64(cs[cpos(v)], m), barrett64(cs[cpos(v + 1)], m));
+                *reinterpret_cast<ulonglong2*>(c1 + v) =
+                    make_ulonglong2(barrett64(cs[N + cpos(v)], m), barrett64(cs[N + cpos(v + 1)], m));
             }
         }
+        // the slots are refilled by bulk copies (async proxy) for the next entry
+        if constexpr (PP::STAGED) fence_proxy_async();
     }
 }
