@@ -161,6 +161,7 @@ extern "C" sfhe_status sfhe_ctx_create(const sfhe_params* params, uint64_t seed,
     std::vector<uint32_t> twb((size_t)rc.K * 4 * N);
     for (int k = 0; k < rc.K; k++)
         twiddles32(rc.mb[k].b, N, twb.data() + (size_t)k * 4 * N, &rc.ninv_b[k], &rc.wlast_b[k]);
+    fold_tensor_scaling(rc);
 
     const size_t rlk_words = (size_t)L * 2 * L * N;
     if (cudaMalloc(&c->d_tw, tw.size() * 8) != cudaSuccess || cudaMalloc(&c->d_twb, twb.size() * 4) != cudaSuccess ||

@@ -57,6 +57,12 @@ SFHE_DEV u64 barrett(u64 hi, u64 lo, Mod m)
     return csub(r, m.q);
 }
 SFHE_DEV u64 barrett64(u64 x, Mod m) { return barrett(0, x, m); }
+// the same without the final subtractions: a value in [0, 3q) congruent to x
+SFHE_DEV u64 barrett_lazy(u64 hi, u64 lo, Mod m)
+{
+    const u64 xs = (hi << 14) | (lo >> 50);
+    return lo - mulhi(xs, m.mu) * m.q;
+}
 
 // (hi:lo) += a * b
 SFHE_DEV void mac(u64& hi, u64& lo, u64 a, u64 b)

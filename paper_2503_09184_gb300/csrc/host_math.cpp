@@ -377,4 +377,13 @@ bool fill_constants(RnsConsts& rc)
     return true;
 }
 
+void fold_tensor_scaling(RnsConsts& rc)
+{
+    for (int k = 0; k < rc.K; ++k) {
+        const uint64_t b = rc.mb[k].b, h = rc.bhat_inv[k].w;
+        rc.ninv_bx[k] = shoup32_of(mulm(rc.ninv_b[k].w, h, b), b);
+        rc.wlast_bx[k] = shoup32_of(mulm(rc.wlast_b[k].w, h, b), b);
+    }
+}
+
 }  // namespace sfhe

@@ -10,6 +10,8 @@
 //   exact scale-and-round by t/Q straight from B (the result in Q);
 //   digits D_j = [d2]_{q_j}; relinearise with the key; add into C.
 #pragma once
+#include <type_traits>
+
 #include "ntt.cuh"
 #include "worklist.h"
 
@@ -37,10 +39,10 @@ SFHE_DEV u32 tensor_coeff32(int poly, const u32* __restrict__ a, const u32* __re
 // Exact decision of round(F) + K near a half-integer: with the words of
 // Z = sum_k x~_k r_k - v r_B + K Q  (Z = (F + K) Q >= 0), the result is the
 // candidate m-1, m or m+1 for which (2c - 1) Q <= 2 Z < (2c + 1) Q.  The
-// residues are read again from x32[k * stride] (global memory) and x~_k
-// recomputed, so that the caller's fast path keeps them in registers.
+// x~_k are read again from xt32[k * stride] (memory), so that the caller's
+// fast path keeps them in registers.
 template <int K>
-__device__ __noinline__ u64 scale_round_fallback(const u32* x32, size_t stride, u32 v, u64 m, const RnsConsts& c)
+__device__ __noinline__ u64 scale_round_fallback(const u32* xt32, size_t stride, u32 v, u64 m, const RnsConsts& c)
 {
     const int W = c.Qwords + 1;
     u64 Z[SFHE_MAX_L + 2], R[SFHE_MAX_L + 2];
@@ -54,7 +56,7 @@ __device__ __noinline__ u64 scale_round_fallback(const u32* x32, size_t stride, 
     }
     // + sum_k x~_k r_k
     for (int k = 0; k < K; k++) {
-        const u64 xt = shoup32(x32[(size_t)k * stride], c.bhat_inv[k], c.mb[k].b);
+        const u64 xt = xt32[(size_t)k * stride];
         u64 cy = 0;
         for (int w = 0; w <= W; w++) {
             const u64 rw = w <= SFHE_MAX_L ? c.r_w[k][w] : 0;
@@ -113,8 +115,9 @@ __device__ __noinline__ u64 scale_round_fallback(const u32* x32, size_t stride, 
 }
 
 // Exact round(t x / Q) mod q_i for M tensor coefficients x, each given by
-// its residues x32[m][k * stride] mod b_k (canonical, k < K; global memory):
-//   x = sum_k x~_k (B/b_k) - v B,  x~_k = [x_k (B/b_k)^-1]_{b_k},
+// x~_k = [x_k (B/b_k)^-1]_{b_k} at xt32[m][k * stride] (canonical, k < K; the
+// tensor stage's inverse NTT produces them):
+//   x = sum_k x~_k (B/b_k) - v B,
 //   v = round(sum_k x~_k / b_k)  (sum_k x~_k / b_k = v + x / B, |x| / B < 1/4);
 //   with t (B/b_k) = alpha_k Q + r_k and t B = alpha_B Q + r_B,
 //   t x / Q = sum_k x~_k alpha_k - v alpha_B + F,  F = (sum_k x~_k r_k - v r_B) / Q,
@@ -127,14 +130,16 @@ __device__ __noinline__ u64 scale_round_fallback(const u32* x32, size_t stride, 
 // rho_k is split into 22 + 21 + 21 bits (partial sums below 2^57), the
 // 54-bit [alpha_k]_{q_i} at bit 27 (below 2^62).  The M coefficients are
 // independent; they are interleaved for instruction-level parallelism.
-template <int L, int K, int M>
+// LAZY: d[m][i] in [0, 3 q_i) (congruent, one Barrett step without the final
+// subtractions) instead of canonical.
+template <int L, int K, int M, bool LAZY = false>
 SFHE_DEV void scale_round_m(const u32* const (&x32)[M], size_t stride, const RnsConsts& c, u64 (&d)[M][L])
 {
     u32 xt[M][K];
 #pragma unroll
     for (int k = 0; k < K; k++) {
 #pragma unroll
-        for (int m = 0; m < M; m++) xt[m][k] = shoup32(x32[m][(size_t)k * stride], c.bhat_inv[k], c.mb[k].b);
+        for (int m = 0; m < M; m++) xt[m][k] = x32[m][(size_t)k * stride];
     }
     u32 v[M];
     u64 mK[M];
@@ -174,7 +179,7 @@ SFHE_DEV void scale_round_m(const u32* const (&x32)[M], size_t stride, const Rns
             }
             u64 hi = shi >> 37, lo = shi << 27;
             add128(hi, lo, slo);
-            d[m][i] = barrett(hi, lo, c.m[i]);
+            d[m][i] = LAZY ? barrett_lazy(hi, lo, c.m[i]) : barrett(hi, lo, c.m[i]);
         }
     }
 }
@@ -499,8 +504,8 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T32::NT) k_tensor_intt(const __
     u32 x[NB::R];
 #pragma unroll
     for (int v = 0; v < NB::R; v++) x[v] = tensor_coeff32(p, ak, bk, off1, NB::lane_idx(v, tid), m);
-    NB::inverse(x, sm, tid, c.twb + (size_t)k * 4 * N, m.b, c.ninv_b[k].w, c.ninv_b[k].ws, c.wlast_b[k].w,
-                c.wlast_b[k].ws);
+    NB::inverse(x, sm, tid, c.twb + (size_t)k * 4 * N, m.b, c.ninv_bx[k].w, c.ninv_bx[k].ws, c.wlast_bx[k].w,
+                c.wlast_bx[k].ws);
     u32* dst = T + ((size_t)p * K + k) * N;
 #pragma unroll
     for (int v = 0; v < NB::R; v++) dst[NB::inv_out_idx(v, tid)] = csub32(x[v], m.b);
@@ -604,9 +609,10 @@ struct PersistentPlan {
 //     = NTT([sum_k d0_k]_{q_i}) + sum_j NTT([sum_k D_jk]_{q_i}) b_j   (mod q_i),
 // so the relinearisation NTTs run once per entry; the result is identical,
 // limb for limb, to relinearising every product and adding.
-// Scratch per CTA: acc [3][L][N] uint64 (plain 64-bit sums of canonical
-// residues: exact for up to 1024 products), cacc [2][N] uint64, T [3][K][N]
-// uint32.  queue[0] is the entry counter, queue[1] the error word (1: a
+// Scratch per CTA: acc [3][L][N] uint64 (plain 64-bit sums: of the digits
+// D_j, canonical, exact for up to 1024 products; of d0 and d1 in [0, 3 q_i),
+// folded to canonical every 256 products), cacc [2][N] uint64, T [3][K][N]
+// uint32 (x~_k, the inverse NTT's output).  queue[0] is the entry counter, queue[1] the error word (1: a
 // bulk copy did not complete within the wait bound).  mbarriers 0 and 1
 // track the operand pairs of stage T.
 template <int LOGN, int L>
@@ -683,26 +689,33 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
             b = mm.B_ext + ((size_t)it.y * mm.Nc + en.col) * ext_words;
         };
         // stage S: scale-and-round every tensor coefficient and add the result
-        // into the entry's sums, SM coefficients per thread at a time
+        // into the entry's sums, SM coefficients per thread at a time.  d0 and
+        // d1 only need to be congruent (stage R reduces their sums), so they
+        // stay in [0, 3 q_i); the digits of d2 must be canonical.
         auto stage_s = [&](int pr) {
             constexpr int SM = (K <= 16 && R <= 16) ? 2 : 1;
-            for (int k = tid; k < N; k += SM * NTH) {
-#pragma unroll 1
-                for (int p = 0; p < 3; p++) {
-                    const u32* src[SM];
+            const bool fold = pr != 0 && (pr & 255) == 0;  // sums below 2^64: fold every 256 products
+            auto poly = [&](int p, int k, auto lazy) {
+                constexpr bool LZ = decltype(lazy)::value;
+                const u32* src[SM];
 #pragma unroll
-                    for (int m = 0; m < SM; m++) src[m] = T + (size_t)p * K * N + k + m * NTH;
-                    u64 d[SM][L];
-                    scale_round_m<L, K, SM>(src, N, c, d);
+                for (int m = 0; m < SM; m++) src[m] = T + (size_t)p * K * N + k + m * NTH;
+                u64 d[SM][L];
+                scale_round_m<L, K, SM, LZ>(src, N, c, d);
 #pragma unroll
-                    for (int m = 0; m < SM; m++) {
+                for (int m = 0; m < SM; m++) {
 #pragma unroll
-                        for (int i = 0; i < L; i++) {
-                            u64* ap = acc + ((size_t)p * L + i) * N + k + m * NTH;
-                            *ap = pr == 0 ? d[m][i] : *ap + d[m][i];
-                        }
+                    for (int i = 0; i < L; i++) {
+                        u64* ap = acc + ((size_t)p * L + i) * N + k + m * NTH;
+                        if (pr == 0) *ap = d[m][i];
+                        else *ap = (LZ && fold ? barrett64(*ap, c.m[i]) : *ap) + d[m][i];
                     }
                 }
+            };
+            for (int k = tid; k < N; k += SM * NTH) {
+#pragma unroll 1
+                for (int p = 0; p < 2; p++) poly(p, k, std::true_type{});
+                poly(2, k, std::false_type{});
             }
         };
         if constexpr (PP::STAGED) {
@@ -730,7 +743,7 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                 const int pr = s / K, k = s - pr * K;
                 const Mod32 m = c.mb[k];
                 const u32* tw = c.twb + (size_t)k * 4 * N;
-                const u32 ni = c.ninv_b[k].w, nis = c.ninv_b[k].ws, wl = c.wlast_b[k].w, wls = c.wlast_b[k].ws;
+                const u32 ni = c.ninv_bx[k].w, nis = c.ninv_bx[k].ws, wl = c.wlast_bx[k].w, wls = c.wlast_bx[k].ws;
                 if (!wait_bar(0) || !wait_bar(1)) {
                     abort_cta();
                     return;
@@ -782,8 +795,8 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                         u32 x[R];
 #pragma unroll
                         for (int v = 0; v < R; v++) x[v] = tensor_coeff32(p, ak, bk, (size_t)K * N, NB::lane_idx(v, tid), m);
-                        NB::inverse(x, sm32, tid, tw, m.b, c.ninv_b[k].w, c.ninv_b[k].ws, c.wlast_b[k].w,
-                                    c.wlast_b[k].ws);
+                        NB::inverse(x, sm32, tid, tw, m.b, c.ninv_bx[k].w, c.ninv_bx[k].ws, c.wlast_bx[k].w,
+                                    c.wlast_bx[k].ws);
                         u32* dst = T + ((size_t)p * K + k) * N;
 #pragma unroll
                         for (int v = 0; v < R; v++) dst[NB::inv_out_idx(v, tid)] = csub32(x[v], m.b);

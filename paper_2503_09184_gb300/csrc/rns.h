@@ -63,6 +63,9 @@ struct RnsConsts {
     const u32* twb;
     ShoupC ninv[SFHE_MAX_L], wlast[SFHE_MAX_L];
     Shoup32 ninv_b[SFHE_MAX_K], wlast_b[SFHE_MAX_K];
+    // the same multiplied by (B/b_k)^-1: an inverse NTT with these outputs
+    // x~_k = [x_k (B/b_k)^-1]_{b_k} directly (the tensor stage)
+    Shoup32 ninv_bx[SFHE_MAX_K], wlast_bx[SFHE_MAX_K];
 
     // centred lift Q -> B:  a = sum_i a~_i (Q/q_i) - v Q,
     // a~_i = [a_i (Q/q_i)^-1]_{q_i}; the 54-bit a~_i is split at bit 27.
