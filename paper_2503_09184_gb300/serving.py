@@ -1,0 +1,244 @@
+"""Serving loop for encrypted sparse matmuls: continuous batching under an
+HBM budget.
+
+Requests (an encrypted sparse A times an encrypted dense B) arrive over time.
+A request is admitted, in arrival order, once its ciphertexts fit the device
+budget beside the requests already in flight; its operands are then
+encrypted and lifted on the device and stay there until it completes (a
+request larger than the whole budget is rejected).  Work runs in waves: a
+wave is one persistent launch (a batch plan) over row blocks taken in turn
+from every admitted request, up to a product budget, so requests that
+arrive while others are on the GPU join the next wave and their products
+overlap with those already running.  Every output entry is computed by
+exactly one wave from its own products, so a request's result is the same
+limb for limb alone and in any mix.
+
+`Scheduler` is the host-side policy (admission, row blocks, completion);
+`GpuExecutor` carries it out through the C ABI.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+from collections import deque
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    A: np.ndarray              # plaintext values of the sparse left operand (M x K)
+    B: np.ndarray              # plaintext values of the dense right operand (K x Nc)
+    arrival: float = 0.0       # seconds after the start of the run
+    # filled in by the scheduler
+    state: str = "queued"      # queued, running, done, rejected
+    admitted: float | None = None
+    finished: float | None = None
+    next_row: int = 0
+    rows_done: int = 0
+
+    @property
+    def rows(self) -> int:
+        return self.A.shape[0]
+
+    def row_products(self) -> np.ndarray:
+        """products of each output row: nonzeros of A's row times Nc."""
+        return (self.A != 0).sum(axis=1).astype(np.int64) * self.B.shape[1]
+
+    @property
+    def products(self) -> int:
+        return int(self.row_products().sum())
+
+
+def request_bytes(req: Request, ct_bytes: int, ext_bytes: int) -> int:
+    """device bytes a request holds while admitted: A's nonzeros and all of B
+    as ciphertexts plus lifted limbs, and C as ciphertexts."""
+    nnz = int((req.A != 0).sum())
+    return (nnz + req.B.size) * (ct_bytes + ext_bytes) + req.A.shape[0] * req.B.shape[1] * ct_bytes
+
+
+class Scheduler:
+    """Admission by budget (FIFO, no overtaking) and round-robin row blocks."""
+
+    def __init__(self, budget_bytes: int, wave_products: int, ct_bytes: int, ext_bytes: int):
+        self.budget = budget_bytes
+        self.wave_products = max(1, wave_products)
+        self.ct_bytes, self.ext_bytes = ct_bytes, ext_bytes
+        self.queue: deque[Request] = deque()
+        self.running: list[Request] = []
+        self.used = 0
+        self._turn = 0
+
+    def bytes_of(self, req: Request) -> int:
+        return request_bytes(req, self.ct_bytes, self.ext_bytes)
+
+    def arrive(self, req: Request):
+        if self.bytes_of(req) > self.budget:
+            req.state = "rejected"
+            return
+        self.queue.append(req)
+
+    def admit(self, now: float) -> list[Request]:
+        """admit queued requests, oldest first, while they fit the budget."""
+        out = []
+        while self.queue and self.used + self.bytes_of(self.queue[0]) <= self.budget:
+            req = self.queue.popleft()
+            req.state, req.admitted = "running", now
+            self.used += self.bytes_of(req)
+            self.running.append(req)
+            out.append(req)
+        return out
+
+    def next_wave(self) -> list[tuple[Request, int, int]]:
+        """row blocks (request, r0, r1) of the next wave: whole rows, taken in
+        turn from every running request (starting one further each wave) until
+        the wave's product budget is reached; every request with rows left
+        gets at least one row."""
+        live = [r for r in self.running if r.next_row < r.rows]
+        if not live:
+            return []
+        k = self._turn % len(live)
+        live = live[k:] + live[:k]
+        self._turn += 1
+        share = max(1, self.wave_products // len(live))
+        blocks, total = [], 0
+        for req in live:
+            rp = req.row_products()
+            r0 = r1 = req.next_row
+            taken = 0
+            while r1 < req.rows and (r1 == r0 or taken + rp[r1] <= share):
+                taken += int(rp[r1])
+                r1 += 1
+            req.next_row = r1
+            blocks.append((req, r0, r1))
+            total += taken
+        return blocks
+
+    def complete(self, blocks, now: float) -> list[Request]:
+        """mark the wave's rows done; returns the requests that finished."""
+        done = []
+        for req, r0, r1 in blocks:
+            req.rows_done += r1 - r0
+            if req.rows_done == req.rows and req.state == "running":
+                req.state, req.finished = "done", now
+                self.used -= self.bytes_of(req)
+                self.running.remove(req)
+                done.append(req)
+        return done
+
+    def idle(self) -> bool:
+        return not self.queue and not self.running
+
+
+class GpuExecutor:
+    """Device side: encryption and lift on admission, one persistent batch
+    plan per wave over CSR row blocks of A (and the matching rows of C)."""
+
+    def __init__(self, ctx, stream=None):
+        import torch
+        from . import api, sfhe as S
+        self.ctx, self.api, self.S, self.torch = ctx, api, S, torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.mats = {}
+        self.admit_s = {}
+
+    def admit(self, req: Request):
+        """encrypt and lift the request's operands on the device (the client's
+        upload); the time it takes is kept in self.admit_s[rid]."""
+        api = self.api
+        t0 = time.perf_counter()
+        A = api.encrypt_matrix(self.ctx, req.A, "csr", 2 * req.rid + 1, stream=self.stream)
+        B = api.encrypt_matrix(self.ctx, req.B, "dense", 2 * req.rid + 2, stream=self.stream)
+        C = api.result_matrix(self.ctx, req.A.shape[0], req.B.shape[1])
+        self.stream.synchronize()
+        self.admit_s[req.rid] = time.perf_counter() - t0
+        self.mats[req.rid] = (A, B, C)
+
+    def _rows(self, req: Request, r0: int, r1: int):
+        api, S = self.api, self.S
+        A, B, C = self.mats[req.rid]
+        p0, p1 = int(A.row_ptr[r0]), int(A.row_ptr[r1])
+        rp = np.ascontiguousarray(A.row_ptr[r0:r1 + 1] - p0, dtype=np.int32)
+        ci = np.ascontiguousarray(A.col_idx[p0:p1], dtype=np.int32) if p1 > p0 else np.zeros(1, np.int32)
+        q0, q1 = (p0, p1) if p1 > p0 else (0, 1)   # a block without nonzeros points at any stored ciphertext
+        Ab = api.EncMatrix(r1 - r0, A.cols, S.SFHE_ENC_CSR, p1 - p0, row_ptr=rp, col_idx=ci,
+                           ct=A.ct[q0:q1], ext=A.ext[q0:q1])
+        Cb = api.EncMatrix(r1 - r0, C.cols, S.SFHE_ENC_DENSE, (r1 - r0) * C.cols,
+                           ct=C.ct[r0 * C.cols:r1 * C.cols])
+        return Ab, B, Cb
+
+    def run_wave(self, blocks) -> int:
+        """one persistent launch over the blocks; returns the products run."""
+        api, S = self.api, self.S
+        parts = [self._rows(req, r0, r1) for req, r0, r1 in blocks]
+        As, Bs, Cs = [p[0] for p in parts], [p[1] for p in parts], [p[2] for p in parts]
+        work = api.workspace(self.ctx, As, Bs, api.PERSISTENT)
+        plan = S.sfhe_plan_create(self.ctx.h, [a.desc() for a in As], [b.desc() for b in Bs],
+                                  [c.desc() for c in Cs], api.PERSISTENT, work, self.stream)
+        products = S.sfhe_plan_stats(plan)["products"]
+        S.sfhe_plan_execute(plan, self.stream)
+        S.sfhe_matmul_check(work, self.stream)       # synchronises the stream
+        S.sfhe_plan_destroy(plan)
+        return products
+
+    def result(self, req: Request):
+        return self.mats[req.rid][2]
+
+    def release(self, req: Request):
+        self.mats.pop(req.rid, None)
+
+
+def serve(requests: list[Request], executor, budget_bytes: int, wave_products: int, ct_bytes: int,
+          ext_bytes: int, keep_results: bool = False, clock=time.perf_counter) -> dict:
+    """Run the requests (arrival times in seconds from now) through the
+    continuous-batching loop on the wall clock.  Returns per-request
+    latencies and totals; with keep_results the executor keeps every C."""
+    sched = Scheduler(budget_bytes, wave_products, ct_bytes, ext_bytes)
+    pending = deque(sorted(requests, key=lambda r: r.arrival))
+    t0 = clock()
+    waves, busy, products = 0, 0.0, 0
+    while pending or not sched.idle():
+        now = clock() - t0
+        while pending and pending[0].arrival <= now:
+            sched.arrive(pending.popleft())
+        for req in sched.admit(clock() - t0):
+            executor.admit(req)
+        blocks = sched.next_wave()
+        if not blocks:
+            if pending:   # nothing to run: wait for the next arrival
+                time.sleep(max(0.0, pending[0].arrival - (clock() - t0)))
+            continue
+        w0 = clock()
+        products += executor.run_wave(blocks)
+        busy += clock() - w0
+        waves += 1
+        for req in sched.complete(blocks, clock() - t0):
+            if not keep_results:
+                executor.release(req)
+    end = clock() - t0
+    done = [r for r in requests if r.state == "done"]
+    lat = np.array([r.finished - r.arrival for r in done]) if done else np.zeros(0)
+    return {
+        "requests": len(requests), "done": len(done),
+        "rejected": sum(1 for r in requests if r.state == "rejected"),
+        "products": products, "waves": waves, "makespan_s": end, "busy_s": busy,
+        "latency_s": lat,
+        "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
+        "p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
+        "ct_mults_per_s": products / end if end > 0 else None,
+    }
+
+
+def fifo_plain_model(requests: list[Request], service_s) -> dict:
+    """One request at a time, in arrival order, each taking service_s(req)
+    seconds: the latencies of the plain one-at-a-time server."""
+    t, lat, products = 0.0, [], 0
+    for req in sorted(requests, key=lambda r: r.arrival):
+        start = max(t, req.arrival)
+        t = start + service_s(req)
+        lat.append(t - req.arrival)
+        products += req.products
+    lat = np.array(lat)
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "makespan_s": t, "ct_mults_per_s": products / t if t > 0 else None, "latency_s": lat}
