@@ -72,6 +72,9 @@ def parse():
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: HBM ciphertext budget")
     ap.add_argument("--wave-products", type=int, default=40000, help="serve: products per wave")
     ap.add_argument("--sparsity", type=float, default=None, help="sweep / layer sparsity (default 0.5)")
+    ap.add_argument("--lazy", action="store_true",
+                    help="grouped accumulate-then-round (SFHE_EXEC_LAZY): a different valid ciphertext, "
+                         "not the paper's per-product order")
     ap.add_argument("--mixed-budget-gb", type=float, default=60.0, help="device bytes per slot for the mixed batch")
     return ap.parse_args()
 
@@ -107,8 +110,15 @@ def mults_per_entry(N: int, L: int) -> int:
     return ntts + keyprod + final
 
 
-def mults(products: int, entries: int, N: int, L: int) -> float:
-    return products * mults_per_product(N, L) + entries * mults_per_entry(N, L)
+def mults(products: int, entries: int, N: int, L: int, groups: int | None = None) -> float:
+    """work of a launch; with groups (grouped accumulate-then-round) the
+    inverse NTTs and the scale-and-round run once per group and only the
+    tensor once per product."""
+    if groups is None:
+        return products * mults_per_product(N, L) + entries * mults_per_entry(N, L)
+    K = tensor_base_size(int(math.log2(N)), L)
+    tensor = 10 * K * N
+    return products * tensor + groups * (mults_per_product(N, L) - tensor) + entries * mults_per_entry(N, L)
 
 
 # ------------------------------------------------------------------- clocks ---
@@ -254,7 +264,7 @@ def lift_launches(nct: int, chunk: int = 256) -> int:
 class Slot:
     """One full set of device operands, results and workspaces for a step."""
 
-    def __init__(self, api, S, torch, ctx, vals, stream):
+    def __init__(self, api, S, torch, ctx, vals, stream, lazy=False):
         self.As = [api.encrypt_matrix(ctx, a, ENCODING, 2 * m + 1, lift=False) for m, (a, _) in enumerate(vals)]
         self.Bs = [api.encrypt_matrix(ctx, b, "dense", 2 * m + 2, lift=False) for m, (_, b) in enumerate(vals)]
         for M in self.As + self.Bs:
@@ -262,7 +272,8 @@ class Slot:
         self.Cs = [api.result_matrix(ctx, a.shape[0], b.shape[1]) for a, b in vals]
         nmax = max(M.nct for M in self.As + self.Bs)
         self.lift_ws = torch.empty(S.sfhe_lift_workspace_size(ctx.h, nmax), dtype=torch.uint8, device="cuda")
-        self.ws = api.workspace(ctx, self.As, self.Bs, api.PERSISTENT)
+        self.flags = api.PERSISTENT | (api.LAZY if lazy else 0)
+        self.ws = api.workspace(ctx, self.As, self.Bs, self.flags)
         self.ctx, self.S = ctx, S
         self.kernel_events = []
 
@@ -271,7 +282,7 @@ class Slot:
         for M in self.As + self.Bs:
             S.sfhe_lift(ctx.h, M.ct, M.nct, M.ext, self.lift_ws, stream)
         plan = S.sfhe_plan_create(ctx.h, [a.desc() for a in self.As], [b.desc() for b in self.Bs],
-                                  [c.desc() for c in self.Cs], S.SFHE_EXEC_PERSISTENT, self.ws, stream)
+                                  [c.desc() for c in self.Cs], self.flags, self.ws, stream)
         if events is not None:
             events[0].record(stream)
         S.sfhe_plan_execute(plan, stream)
@@ -307,14 +318,16 @@ def main():
     from paper_2503_09184_gb300 import api, sfhe as S
 
     ring, vals, workload, sparsity = job_of(args)
+    if args.lazy:
+        workload += "-lazy"
     ctx = api.Context(ring.N, ring.L, seed=0)
     stream = torch.cuda.current_stream()
 
     # setup (untimed): encryption of the operands
-    slot = Slot(api, S, torch, ctx, vals, stream)
+    slot = Slot(api, S, torch, ctx, vals, stream, lazy=args.lazy)
     ctx.check()
     probe = S.sfhe_plan_create(ctx.h, [a.desc() for a in slot.As], [b.desc() for b in slot.Bs],
-                               [c.desc() for c in slot.Cs], S.SFHE_EXEC_PERSISTENT, slot.ws, stream)
+                               [c.desc() for c in slot.Cs], slot.flags, slot.ws, stream)
     stats = S.sfhe_plan_stats(probe)
     S.sfhe_plan_destroy(probe)
     products, entries, ctas = stats["products"], stats["entries"], stats["ctas"]
@@ -379,10 +392,15 @@ def main():
     nrow = len(rows) * b0.shape[1]
     pers_rows = api.to_coeff(ctx, slot.Cs[0].ct[:nrow].contiguous(), nrow)
     plain_rows = api.to_coeff(ctx, C_rows.ct, nrow)
-    plain_equal = bool((pers_rows == plain_rows).all())
+    # (the grouped mode gives other ciphertexts with the same decryption)
+    plain_equal = bool((pers_rows == plain_rows).all()) if not args.lazy else None
 
     value = products * world / (ms / 1e3)
-    work = mults(products, nonempty_entries, ring.N, ring.L)
+    groups = None
+    if args.lazy:
+        G = ctx.lazy_group
+        groups = sum(int(np.ceil((a != 0).sum(axis=1) / G).sum()) * b.shape[1] for a, b in vals)
+    work = mults(products, nonempty_entries, ring.N, ring.L, groups)
     achieved = work / (kms / 1e3) / 1e12
     sm_clock = clk.get("sm_mhz") or SM_MAX_MHZ
     peak = SM_COUNT * IMAD_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
@@ -414,6 +432,8 @@ def main():
                      "peak_note": "152 SM x 64 int32 multiplies/clk x 2070 MHz (derived from unit counts and clock)",
                      "frac_at_measured_clock": achieved / (peak * sm_clock / SM_MAX_MHZ)},
         "gpu_launches": slot.launches() * args.steps,
+        "order": ("grouped accumulate-then-round, G = %d products per rounding (not the paper's per-product order)"
+                  % ctx.lazy_group) if args.lazy else "per product (Alg. 1)",
         "clocks": clk,
         "persistent_ctas": ctas,
     }
@@ -507,7 +527,7 @@ def e2e_pipelined(args, api, S, torch, ctx, vals, slot0, products, world) -> dic
     pinned host memory.  Two slots of device buffers let step i+1's upload
     and step i-1's download run on their own streams while step i computes;
     every copy of every timed step lies inside the timed region."""
-    slots = [slot0, Slot(api, S, torch, ctx, vals, None)]
+    slots = [slot0, Slot(api, S, torch, ctx, vals, None, lazy=(slot0.flags & api.LAZY) != 0)]
     h_in = [[torch.empty(M.ct.shape, dtype=torch.int64, pin_memory=True) for M in slots[0].As + slots[0].Bs]
             for _ in slots]
     for hs in h_in:

@@ -61,11 +61,18 @@ typedef enum {
 /* Sec. 3.3: naive dense (Alg. 1), naive sparse (plaintext zero mask), CSR, ELLPACK */
 typedef enum { SFHE_ENC_DENSE = 0, SFHE_ENC_MASK = 1, SFHE_ENC_CSR = 2, SFHE_ENC_ELL = 3 } sfhe_encoding;
 
-/* execution modes of a matmul */
+/* execution modes of a matmul.  SFHE_EXEC_LAZY is not the paper's order of
+ * operations: an output entry's products (ascending k) are taken in groups of
+ * G = sfhe_info.lazy_group; each group's exact tensors are summed, scaled and
+ * rounded once and relinearised once, and the groups are added.  The result
+ * is a different ciphertext with the same decryption (the rounding and
+ * relinearisation noise is added once per group instead of once per
+ * product); G = 1 would be Alg. 1's per-product order. */
 enum {
     SFHE_EXEC_PLAIN = 1,      /* one short launch sequence per ciphertext product */
     SFHE_EXEC_PERSISTENT = 2, /* all products of all matmuls in one persistent launch */
-    SFHE_EXEC_GRAPH = 4       /* with PERSISTENT: replay the launch as a CUDA graph */
+    SFHE_EXEC_GRAPH = 4,      /* with PERSISTENT: replay the launch as a CUDA graph */
+    SFHE_EXEC_LAZY = 8        /* with PERSISTENT: grouped accumulate-then-round (below) */
 };
 
 typedef struct {
@@ -85,6 +92,7 @@ typedef struct {
     uint64_t ext_words;     /* 2 K N (uint32 words) */
     int32_t num_sms;
     uint32_t ext_interleave; /* R of the lifted layout (16, or 32 at N = 16384) */
+    int32_t lazy_group;      /* G of SFHE_EXEC_LAZY: floor(B / (2 N Q^2)), at most 1024 */
 } sfhe_info;
 
 typedef struct sfhe_ctx sfhe_ctx;

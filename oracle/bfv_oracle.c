@@ -42,6 +42,7 @@ typedef unsigned __int128 u128;
 
 #define OR_MAX_L 8
 #define OR_MAX_AUX 24
+#define OR_MAX_GROUP 1024 /* most exact tensors summed before one scale-and-round */
 #define MW 18 /* words per multiword integer: 1152 bits, enough for 2t|x| at L <= 8, N <= 2^15 */
 
 /* ------------------------------------------------------------------ */
@@ -473,10 +474,11 @@ void *or_ctx_create(int N, int L, u64 t, double sigma, u64 seed)
     crt_init(&c->Qb, L, c->q);
 
     /* auxiliary base: the largest primes below 2^53, as many as needed for
-     * a product above 4 N Q^2 (twice the largest |tensor coefficient|, with
-     * margin); the tensor is reconstructed exactly over it. */
+     * a product above 4 N Q^2 OR_MAX_GROUP (twice the largest |coefficient|
+     * of a sum of up to OR_MAX_GROUP tensors, with margin); tensors and their
+     * sums are reconstructed exactly over it. */
     mw_t bound, prod;
-    mw_set(&bound, 4ULL * (u64)N);
+    mw_set(&bound, 4ULL * (u64)N * OR_MAX_GROUP);
     {
         mw_t tmp;
         for (int i = 0; i < L; i++) { mw_mul_u64(&tmp, &bound, c->q[i]); bound = tmp; }
@@ -674,6 +676,8 @@ int or_decrypt(void *vc, const u64 *ct, int64_t *m_out, int *noise_bits)
 /* ------------------------------------------------------------------ */
 /* Centred lift of one coefficient given by its residues over Q, reduced mod
  * every auxiliary prime: X in (-Q/2, Q/2), out[k] = X mod aux_k. */
+int or_tensor_scale_sum(void *vc, int n, const u64 *const *a, const u64 *const *b, u64 *d);
+
 static void lift_centered_to_aux(const or_ctx *c, const u64 *r, u64 *out)
 {
     mw_t X, mag;
@@ -723,13 +727,12 @@ static void scale_round_coeff(const or_ctx *c, const u64 *xr, u64 *d_out)
     }
 }
 
-/* BFV tensor product and scale-and-round, coefficient form:
- *   x0 = a0 b0, x1 = a0 b1 + a1 b0, x2 = a1 b1  (exact integer negacyclic
- *   products of the centred lifts), d_k = round(t x_k / Q) mod Q.
- * a, b: [2][L][N]; d: [3][L][N]. */
-int or_tensor_scale(void *vc, const u64 *a, const u64 *b, u64 *d)
+/* Exact integer tensor of one product, as residues over the auxiliary base:
+ *   x0 = a0 b0, x1 = a0 b1 + a1 b0, x2 = a1 b1  (negacyclic products of the
+ *   centred lifts).  a, b: [2][L][N]; x: [3][nA][N], added into x when
+ *   accumulate is set. */
+static void tensor_aux(const or_ctx *c, const u64 *a, const u64 *b, u64 *x, int accumulate)
 {
-    or_ctx *c = (or_ctx *)vc;
     int N = c->N, L = c->L, nA = c->nA;
     /* lifts: [poly 4][aux k][N] */
     u64 *lift = (u64 *)malloc(sizeof(u64) * 4 * (size_t)nA * N);
@@ -742,18 +745,23 @@ int or_tensor_scale(void *vc, const u64 *a, const u64 *b, u64 *d)
         lift_centered_to_aux(c, r, o);
         for (int m = 0; m < nA; m++) lift[((size_t)pi * nA + m) * N + k] = o[m];
     }
-    /* x: [3][aux][N] */
-    u64 *x = (u64 *)malloc(sizeof(u64) * 3 * (size_t)nA * N);
     for (int m = 0; m < nA; m++) {
         u64 rm = c->aux[m];
         const u64 *A0 = lift + ((size_t)0 * nA + m) * N, *A1 = lift + ((size_t)1 * nA + m) * N;
         const u64 *B0 = lift + ((size_t)2 * nA + m) * N, *B1 = lift + ((size_t)3 * nA + m) * N;
         u64 *X0 = x + ((size_t)0 * nA + m) * N, *X1 = x + ((size_t)1 * nA + m) * N, *X2 = x + ((size_t)2 * nA + m) * N;
-        negacyclic_acc(rm, N, A0, B0, X0, 0);
-        negacyclic_acc(rm, N, A0, B1, X1, 0);
+        negacyclic_acc(rm, N, A0, B0, X0, accumulate);
+        negacyclic_acc(rm, N, A0, B1, X1, accumulate);
         negacyclic_acc(rm, N, A1, B0, X1, 1);
-        negacyclic_acc(rm, N, A1, B1, X2, 0);
+        negacyclic_acc(rm, N, A1, B1, X2, accumulate);
     }
+    free(lift);
+}
+
+/* d_k = round(t x_k / Q) mod Q for x given over the auxiliary base. */
+static void scale_round_aux(const or_ctx *c, const u64 *x, u64 *d)
+{
+    int N = c->N, L = c->L, nA = c->nA;
 #pragma omp parallel for schedule(static)
     for (int idx = 0; idx < 3 * N; idx++) {
         int pi = idx / N, k = idx % N;
@@ -762,7 +770,26 @@ int or_tensor_scale(void *vc, const u64 *a, const u64 *b, u64 *d)
         scale_round_coeff(c, xr, dd);
         for (int i = 0; i < L; i++) d[((size_t)pi * L + i) * N + k] = dd[i];
     }
-    free(lift);
+}
+
+/* BFV tensor product and scale-and-round, coefficient form:
+ *   d_k = round(t x_k / Q) mod Q with the exact tensor x of a and b.
+ * a, b: [2][L][N]; d: [3][L][N]. */
+int or_tensor_scale(void *vc, const u64 *a, const u64 *b, u64 *d)
+{
+    return or_tensor_scale_sum(vc, 1, &a, &b, d);
+}
+
+/* The same for the sum of n exact tensors (n <= OR_MAX_GROUP):
+ *   d_k = round(t (x_k(a_0, b_0) + ... + x_k(a_{n-1}, b_{n-1})) / Q) mod Q,
+ * one rounding for the whole sum (the grouped accumulate-then-round order). */
+int or_tensor_scale_sum(void *vc, int n, const u64 *const *a, const u64 *const *b, u64 *d)
+{
+    or_ctx *c = (or_ctx *)vc;
+    if (n < 1 || n > OR_MAX_GROUP) return 1;
+    u64 *x = (u64 *)malloc(sizeof(u64) * 3 * (size_t)c->nA * c->N);
+    for (int m = 0; m < n; m++) tensor_aux(c, a[m], b[m], x, m > 0);
+    scale_round_aux(c, x, d);
     free(x);
     return 0;
 }
@@ -815,16 +842,34 @@ void or_add(void *vc, u64 *acc, const u64 *x)
             }
 }
 
+/* One output entry: its products f0 .. f0+count-1 in order, in groups of
+ * `group` consecutive products; each group's exact tensors are summed,
+ * scaled and rounded once and relinearised, and the groups are added.  With
+ * group = 1 this is Alg. 1's inner loop (multiply, relinearise, add per
+ * product). */
+static void entry_grouped(void *vc, int f0, int count, const u64 *const *a_ptr, const u64 *const *b_ptr, u64 *acc,
+                          int group, u64 *d, u64 *prod)
+{
+    for (int p = 0; p < count; p += group) {
+        int n = count - p < group ? count - p : group;
+        or_tensor_scale_sum(vc, n, a_ptr + f0 + p, b_ptr + f0 + p, d);
+        or_relin(vc, d, prod);
+        or_add(vc, acc, prod);
+    }
+}
+
 /* Paper's multithreaded scheme (Sec. 3.4): result value (row, col) is
  * computed by thread (row * col) mod nthreads, each thread running the
  * product loop of Alg. 1 for its entries.  Entries e = 0..n_entries-1 list
  * (row, col, first, count) into the flat product arrays a_ptr / b_ptr, which
  * point at [2][L][N] coefficient-form ciphertexts.  out: [n_entries][2][L][N].
- * Inner parallelism is switched off for the duration. */
-int or_matmul_entries(void *vc, int n_entries, const int32_t *ent /* [n][4] */,
-                      const u64 *const *a_ptr, const u64 *const *b_ptr, u64 *out, int nthreads)
+ * group: products per rounding (1 = per product, as in Alg. 1; see
+ * entry_grouped).  Inner parallelism is switched off for the duration. */
+int or_matmul_entries_grouped(void *vc, int n_entries, const int32_t *ent /* [n][4] */,
+                              const u64 *const *a_ptr, const u64 *const *b_ptr, u64 *out, int nthreads, int group)
 {
     or_ctx *c = (or_ctx *)vc;
+    if (group < 1 || group > OR_MAX_GROUP) return 1;
     size_t ctw = 2 * (size_t)c->L * c->N;
     memset(out, 0, sizeof(u64) * ctw * (size_t)n_entries);
 #ifdef _OPENMP
@@ -835,30 +880,31 @@ int or_matmul_entries(void *vc, int n_entries, const int32_t *ent /* [n][4] */,
     {
         int tid = omp_get_thread_num(), nt = omp_get_num_threads();
         u64 *prod = (u64 *)malloc(sizeof(u64) * ctw);
+        u64 *d = (u64 *)malloc(sizeof(u64) * 3 * (size_t)c->L * c->N);
         for (int e = 0; e < n_entries; e++) {
             long long row = ent[4 * e], col = ent[4 * e + 1];
             if ((int)((row * col) % nt) != tid) continue;
-            for (int p = 0; p < ent[4 * e + 3]; p++) {
-                int f = ent[4 * e + 2] + p;
-                or_mul_relin(vc, a_ptr[f], b_ptr[f], prod);
-                or_add(vc, out + ctw * e, prod);
-            }
+            entry_grouped(vc, ent[4 * e + 2], ent[4 * e + 3], a_ptr, b_ptr, out + ctw * e, group, d, prod);
         }
         free(prod);
+        free(d);
     }
 #else
     (void)nthreads;
     u64 *prod = (u64 *)malloc(sizeof(u64) * ctw);
-    for (int e = 0; e < n_entries; e++) {
-        for (int p = 0; p < ent[4 * e + 3]; p++) {
-            int f = ent[4 * e + 2] + p;
-            or_mul_relin(vc, a_ptr[f], b_ptr[f], prod);
-            or_add(vc, out + ctw * e, prod);
-        }
-    }
+    u64 *d = (u64 *)malloc(sizeof(u64) * 3 * (size_t)c->L * c->N);
+    for (int e = 0; e < n_entries; e++)
+        entry_grouped(vc, ent[4 * e + 2], ent[4 * e + 3], a_ptr, b_ptr, out + ctw * e, group, d, prod);
     free(prod);
+    free(d);
 #endif
     return 0;
+}
+
+int or_matmul_entries(void *vc, int n_entries, const int32_t *ent, const u64 *const *a_ptr, const u64 *const *b_ptr,
+                      u64 *out, int nthreads)
+{
+    return or_matmul_entries_grouped(vc, n_entries, ent, a_ptr, b_ptr, out, nthreads, 1);
 }
 
 int or_num_threads(void)

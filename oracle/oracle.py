@@ -59,11 +59,18 @@ def lib():
         L.or_encrypt.restype = ctypes.c_int
         L.or_decrypt.argtypes = [ctypes.c_void_p, _u64p, _i64p, ctypes.POINTER(ctypes.c_int)]
         L.or_tensor_scale.argtypes = [ctypes.c_void_p, _u64p, _u64p, _u64p]
+        L.or_tensor_scale_sum.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(_u64p),
+                                          ctypes.POINTER(_u64p), _u64p]
+        L.or_tensor_scale_sum.restype = ctypes.c_int
         L.or_relin.argtypes = [ctypes.c_void_p, _u64p, _u64p]
         L.or_mul_relin.argtypes = [ctypes.c_void_p, _u64p, _u64p, _u64p]
         L.or_add.argtypes = [ctypes.c_void_p, _u64p, _u64p]
         L.or_matmul_entries.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
                                         ctypes.POINTER(_u64p), ctypes.POINTER(_u64p), _u64p, ctypes.c_int]
+        L.or_matmul_entries_grouped.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
+                                                ctypes.POINTER(_u64p), ctypes.POINTER(_u64p), _u64p, ctypes.c_int,
+                                                ctypes.c_int]
+        L.or_matmul_entries_grouped.restype = ctypes.c_int
         L.or_num_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -199,6 +206,18 @@ class OracleCtx:
         lib().or_tensor_scale(self._h, _p(a), _p(b), _p(d))
         return d
 
+    def tensor_scale_sum(self, a_list, b_list) -> np.ndarray:
+        """(d0, d1, d2) = round(t (sum of the exact tensors of the pairs) / Q):
+        one rounding for the whole sum (at most 1024 pairs)."""
+        a_list = [np.ascontiguousarray(a, dtype=np.uint64) for a in a_list]
+        b_list = [np.ascontiguousarray(b, dtype=np.uint64) for b in b_list]
+        a_arr = (_u64p * len(a_list))(*[_p(a) for a in a_list])
+        b_arr = (_u64p * len(b_list))(*[_p(b) for b in b_list])
+        d = np.zeros((3, self.L, self.N), dtype=np.uint64)
+        if lib().or_tensor_scale_sum(self._h, len(a_list), a_arr, b_arr, _p(d)):
+            raise ValueError("between 1 and 1024 pairs")
+        return d
+
     def relin(self, d: np.ndarray) -> np.ndarray:
         d = np.ascontiguousarray(d, dtype=np.uint64)
         out = np.zeros(self.ct_shape, dtype=np.uint64)
@@ -217,15 +236,18 @@ class OracleCtx:
         lib().or_add(self._h, _p(acc), _p(x))
         return acc
 
-    def matmul_entries(self, entries, a_list, b_list, nthreads: int = 0) -> np.ndarray:
+    def matmul_entries(self, entries, a_list, b_list, nthreads: int = 0, group: int = 1) -> np.ndarray:
         """Paper's multithreaded scheme (Sec. 3.4): entries = [(row, col, first, count)],
-        products first..first+count-1 of the flat lists a_list / b_list."""
+        products first..first+count-1 of the flat lists a_list / b_list; with
+        group > 1 each run of `group` consecutive products is rounded once
+        (grouped accumulate-then-round)."""
         ent = np.ascontiguousarray(np.asarray(entries, dtype=np.int32).reshape(-1, 4))
         a_arr = (_u64p * len(a_list))(*[_p(a) for a in a_list])
         b_arr = (_u64p * len(b_list))(*[_p(b) for b in b_list])
         out = np.zeros((ent.shape[0],) + self.ct_shape, dtype=np.uint64)
-        lib().or_matmul_entries(self._h, ent.shape[0], ent.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                                a_arr, b_arr, _p(out), nthreads)
+        if lib().or_matmul_entries_grouped(self._h, ent.shape[0], ent.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                           a_arr, b_arr, _p(out), nthreads, group):
+            raise ValueError("group between 1 and 1024")
         return out
 
 
@@ -335,9 +357,18 @@ class OracleMatmul:
             self._prod[key] = self.ctx.mul_relin(self.ct_a(i, k), self.ct_b(k, j))
         return self._prod[key]
 
-    def entry(self, enc: Encoded, i: int, j: int) -> np.ndarray:
-        """C[i][j]: the trivial zero ciphertext plus every listed product."""
+    def entry(self, enc: Encoded, i: int, j: int, group: int = 1) -> np.ndarray:
+        """C[i][j]: the trivial zero ciphertext plus every listed product (in
+        ascending k); with group > 1, each run of `group` consecutive products
+        is scaled and rounded once and relinearised once."""
         acc = np.zeros(self.ctx.ct_shape, dtype=np.uint64)
-        for _, k in product_set(enc, i):
-            self.ctx.add_(acc, self.product(i, k, j))
+        ks = [k for _, k in product_set(enc, i)]
+        if group == 1:
+            for k in ks:
+                self.ctx.add_(acc, self.product(i, k, j))
+            return acc
+        for p in range(0, len(ks), group):
+            run = ks[p:p + group]
+            d = self.ctx.tensor_scale_sum([self.ct_a(i, k) for k in run], [self.ct_b(k, j) for k in run])
+            self.ctx.add_(acc, self.ctx.relin(d))
         return acc

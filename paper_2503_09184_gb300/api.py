@@ -8,7 +8,7 @@ import torch
 
 from . import sfhe as S
 
-PLAIN, PERSISTENT, GRAPH = S.SFHE_EXEC_PLAIN, S.SFHE_EXEC_PERSISTENT, S.SFHE_EXEC_GRAPH
+PLAIN, PERSISTENT, GRAPH, LAZY = S.SFHE_EXEC_PLAIN, S.SFHE_EXEC_PERSISTENT, S.SFHE_EXEC_GRAPH, S.SFHE_EXEC_LAZY
 
 
 def _dev_u64(shape) -> torch.Tensor:
@@ -40,6 +40,7 @@ class Context:
         self.b = [int(x) for x in info.b[: self.K]]
         self.ct_words, self.ext_words, self.num_sms = int(info.ct_words), int(info.ext_words), info.num_sms
         self.ext_interleave = int(info.ext_interleave)
+        self.lazy_group = int(info.lazy_group)
         self.seed = seed
 
     def close(self):
@@ -154,7 +155,8 @@ def decrypt(ctx: Context, M: EncMatrix, stream=None) -> np.ndarray:
 
 
 def _flags(mode: str, graph: bool = False) -> int:
-    f = PERSISTENT if mode == "persistent" else PLAIN
+    """mode: "persistent", "plain" or "lazy" (persistent, grouped accumulate-then-round)."""
+    f = {"persistent": PERSISTENT, "plain": PLAIN, "lazy": PERSISTENT | LAZY}[mode]
     return f | (GRAPH if graph else 0)
 
 

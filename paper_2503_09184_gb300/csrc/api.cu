@@ -199,6 +199,7 @@ extern "C" sfhe_status sfhe_ctx_info(const sfhe_ctx* c, sfhe_info* out)
     out->ext_words = (uint64_t)2 * c->rc.K * c->rc.N;
     out->num_sms = c->num_sms;
     out->ext_interleave = (uint32_t)ext_interleave(c->rc.logN);
+    out->lazy_group = c->rc.lazy_group;
     return SFHE_OK;
 }
 
@@ -514,7 +515,7 @@ sfhe_status build(const sfhe_ctx* c, int32_t n, const sfhe_matrix* A, const sfhe
         d.B_ext = B[m].ext;
         d.C = C ? C[m].ct : nullptr;
         d.Nc = B[m].cols;
-        d.pad = 0;
+        d.group = (P.flags & SFHE_EXEC_LAZY) ? c->rc.lazy_group : 1;
         P.mms.push_back(d);
         P.c_words.push_back((size_t)A[m].rows * B[m].cols * ctw);
         for (int32_t i = 0; i < A[m].rows; i++) {
@@ -583,7 +584,9 @@ sfhe_status check_flags(uint32_t flags)
     const bool plain = flags & SFHE_EXEC_PLAIN, pers = flags & SFHE_EXEC_PERSISTENT;
     if (plain == pers) return fail(SFHE_EINVAL, "exactly one of PLAIN and PERSISTENT");
     if ((flags & SFHE_EXEC_GRAPH) && !pers) return fail(SFHE_EINVAL, "GRAPH needs PERSISTENT");
-    if (flags & ~(uint32_t)(SFHE_EXEC_PLAIN | SFHE_EXEC_PERSISTENT | SFHE_EXEC_GRAPH)) return fail(SFHE_EINVAL, "unknown flags");
+    if ((flags & SFHE_EXEC_LAZY) && !pers) return fail(SFHE_EINVAL, "LAZY needs PERSISTENT");
+    if (flags & ~(uint32_t)(SFHE_EXEC_PLAIN | SFHE_EXEC_PERSISTENT | SFHE_EXEC_GRAPH | SFHE_EXEC_LAZY))
+        return fail(SFHE_EINVAL, "unknown flags");
     return SFHE_OK;
 }
 
@@ -599,7 +602,8 @@ sfhe_status launch_plan(sfhe_plan* P, cudaStream_t s)
         CUDA_TRY(cudaMemsetAsync(P->d_queue, 0, 2 * sizeof(unsigned), s));
         if (P->entries.empty()) return SFHE_OK;
         CUDA_TRY(launch_persistent(rc, P->d_mms, P->d_entries, (int)P->entries.size(), P->d_rowlist, c->d_rlk, c->d_rlk_sh,
-                                   P->d_scratch, P->scratch_stride, P->d_queue, P->grid, s));
+                                   P->d_scratch, P->scratch_stride, P->d_queue, P->grid,
+                                   (P->flags & SFHE_EXEC_LAZY) != 0, s));
         return SFHE_OK;
     }
     // plain: C = 0, then one launch sequence per product
@@ -690,7 +694,8 @@ static sfhe_status plan_create_impl(sfhe_ctx* c, int32_t n, const sfhe_matrix* A
             if (cudaMemsetAsync(P->d_queue, 0, 2 * sizeof(unsigned), cap) != cudaSuccess) ls = SFHE_ECUDA;
             if (ls == SFHE_OK && !P->entries.empty())
                 if (launch_persistent(c->rc, P->d_mms, P->d_entries, (int)P->entries.size(), P->d_rowlist, c->d_rlk,
-                                      c->d_rlk_sh, P->d_scratch, P->scratch_stride, P->d_queue, P->grid, cap) != cudaSuccess)
+                                      c->d_rlk_sh, P->d_scratch, P->scratch_stride, P->d_queue, P->grid,
+                                      (P->flags & SFHE_EXEC_LAZY) != 0, cap) != cudaSuccess)
                     ls = SFHE_ECUDA;
             cudaError_t e2 = cudaStreamEndCapture(cap, &P->graph);
             if (ls != SFHE_OK || e2 != cudaSuccess) e = cudaErrorUnknown;
@@ -749,6 +754,7 @@ static sfhe_status size_impl(const sfhe_ctx* c, int32_t n, const sfhe_matrix* A,
     if (st != SFHE_OK) return st;
     sfhe_plan P;
     P.ctx = const_cast<sfhe_ctx*>(c);
+    P.flags = flags;
     st = build(c, n, A, B, nullptr, dense_loop, P);
     if (st != SFHE_OK) return st;
     int grid;

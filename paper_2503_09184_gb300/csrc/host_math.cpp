@@ -273,6 +273,13 @@ bool fill_constants(RnsConsts& rc)
         }
         shl(need_b, 1);
         if (!greater(Bbig, need_b)) return false;
+        // products one rounding may take (grouped accumulate-then-round): a
+        // sum of G tensors keeps |x| < B / 4 while G 2 N Q^2 <= B
+        Big g, r;
+        divmod(Bbig, need_b, g, r);
+        bool big_g = g.w[0] > 1024;
+        for (int w = 1; w < MWW; ++w) big_g = big_g || g.w[w] != 0;
+        rc.lazy_group = big_g ? 1024 : (g.w[0] < 1 ? 1 : (int)g.w[0]);
     }
     for (int i = 0; i < L; ++i) rc.m[i].mu = (uint64_t)(((u128)1 << 114) / rc.m[i].q);
     for (int k = 0; k < K; ++k) {

@@ -251,12 +251,12 @@ int persistent_ctas_per_sm(const RnsConsts& rc)
 
 cudaError_t launch_persistent(const RnsConsts& rc, const MmDesc* mms, const Entry* entries, int n_entries,
                               const int2* rowlist, const u64* rlk, const u64* rlk_sh, u64* scratch,
-                              size_t scratch_stride, unsigned* queue, int grid, cudaStream_t s)
+                              size_t scratch_stride, unsigned* queue, int grid, bool grouped, cudaStream_t s)
 {
     switch (rc.logN) {
-    case 12: return persistent_launch<12>(rc, mms, entries, n_entries, rowlist, rlk, rlk_sh, scratch, scratch_stride, queue, grid, s);
-    case 13: return persistent_launch<13>(rc, mms, entries, n_entries, rowlist, rlk, rlk_sh, scratch, scratch_stride, queue, grid, s);
-    case 14: return persistent_launch<14>(rc, mms, entries, n_entries, rowlist, rlk, rlk_sh, scratch, scratch_stride, queue, grid, s);
+    case 12: return persistent_launch<12>(rc, mms, entries, n_entries, rowlist, rlk, rlk_sh, scratch, scratch_stride, queue, grid, grouped, s);
+    case 13: return persistent_launch<13>(rc, mms, entries, n_entries, rowlist, rlk, rlk_sh, scratch, scratch_stride, queue, grid, grouped, s);
+    case 14: return persistent_launch<14>(rc, mms, entries, n_entries, rowlist, rlk, rlk_sh, scratch, scratch_stride, queue, grid, grouped, s);
     default: return cudaErrorInvalidValue;
     }
 }

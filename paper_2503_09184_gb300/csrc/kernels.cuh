@@ -601,7 +601,8 @@ struct PersistentPlan {
 #define SFHE_WAIT_TRIES (1u << 24)
 
 // One CTA per output entry at a time, taken from a queue in descending
-// product count.  Per product: stage T (tensor + 3K inverse NTTs over B into
+// product count.  Per product (per rounding group of mm.group products in the
+// grouped accumulate-then-round mode): stage T (tensor + 3K inverse NTTs over B into
 // the CTA's scratch), stage S (exact scale-and-round to Q, then the sums of
 // d0, d1 and of the digits D_j over the entry's products).  Per entry,
 // stage R: since the NTT and the key product are linear mod q_i,
@@ -615,7 +616,7 @@ struct PersistentPlan {
 // uint32 (x~_k, the inverse NTT's output).  queue[0] is the entry counter, queue[1] the error word (1: a
 // bulk copy did not complete within the wait bound).  mbarriers 0 and 1
 // track the operand pairs of stage T.
-template <int LOGN, int L>
+template <int LOGN, int L, bool GROUPED>
 __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
     const __grid_constant__ RnsConsts c, const MmDesc* __restrict__ mms, const Entry* __restrict__ entries, int n_entries,
     const int2* __restrict__ rowlist, const u64* __restrict__ rlk, const u64* __restrict__ rlk_sh, u64* scratch,
@@ -721,15 +722,80 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
         if constexpr (PP::STAGED) {
             // stage T with TMA-staged operands: per tensor-base prime, the
             // three tensor polynomials are formed from the four staged limbs
-            // and inverse-transformed together; the next prime's limbs stream
-            // into the slots meanwhile
-            const int total = en.count * K;
-            auto issue = [&](int s, int pair) {
-                if (tid == 0) {
+            // and inverse-transformed together; the next limbs stream into the
+            // slots meanwhile.  Products are taken in rounding groups of G
+            // (G = 1: each product rounded on its own, Alg. 1): steps run
+            // group by group, prime by prime, product by product, and a
+            // group's tensor is summed over its products before the inverse
+            // NTT (the NTT is linear), so stage S rounds it once.
+            const int G = GROUPED ? mm.group : 1;
+            if constexpr (!GROUPED) {
+                const int total = en.count * K;
+                auto issue = [&](int s, int pair) {
+                    if (tid == 0) {
+                        const int pr = s / K, k = s - pr * K;
+                        const u32 *a, *b;
+                        operands(pr, a, b);
+                        const size_t off = (size_t)pair * K * N + (size_t)k * N;
+                        fence_proxy_async();
+                        mbar_arrive_expect_tx(&mbar[pair], (u32)(2 * PP::SLOT));
+                        tma_load_1d(slot(pair), a + off, (u32)PP::SLOT, &mbar[pair]);
+                        tma_load_1d(slot(2 + pair), b + off, (u32)PP::SLOT, &mbar[pair]);
+                    }
+                    pend |= 1u << pair;
+                };
+                issue(0, 0);
+                issue(0, 1);
+                for (int s = 0; s < total; s++) {
                     const int pr = s / K, k = s - pr * K;
+                    const Mod32 m = c.mb[k];
+                    const u32* tw = c.twb + (size_t)k * 4 * N;
+                    const u32 ni = c.ninv_bx[k].w, nis = c.ninv_bx[k].ws, wl = c.wlast_bx[k].w, wls = c.wlast_bx[k].ws;
+                    if (!wait_bar(0) || !wait_bar(1)) {
+                        abort_cta();
+                        return;
+                    }
+                    u32 x[3][R];
+                    {
+                        const u32* s0 = slot(0);
+                        const u32* s1 = slot(1);
+                        const u32* s2 = slot(2);
+                        const u32* s3 = slot(3);
+    #pragma unroll
+                        for (int v = 0; v < R; v++) {
+                            const int i = NB::lane_idx(v, tid);
+                            const u64 a0 = s0[i], a1 = s1[i], b0 = s2[i], b1 = s3[i];
+                            x[0][v] = reduce61(a0 * b0, m);
+                            x[1][v] = reduce61(a0 * b1 + a1 * b0, m);
+                            x[2][v] = reduce61(a1 * b1, m);
+                        }
+                    }
+                    __syncthreads();  // every thread has read the slots
+                    if (s + 1 < total) {
+                        issue(s + 1, 0);
+                        issue(s + 1, 1);
+                    }
+                    NB::template inverse_m<3>(x, sm32, tid, tw, m.b, ni, nis, wl, wls);
+    #pragma unroll
+                    for (int p = 0; p < 3; p++) {
+                        u32* dst = T + ((size_t)p * K + k) * N;
+    #pragma unroll
+                        for (int v = 0; v < R; v++) dst[NB::inv_out_idx(v, tid)] = csub32(x[p][v], m.b);
+                    }
+                    if (k == K - 1) {
+                        __syncthreads();
+                        stage_s(pr);
+                        __syncthreads();
+                    }
+                }
+            } else {
+            // position of the next bulk copy: group, prime, product in group
+            int ig = 0, ik = 0, ip = 0, iGg = min(G, en.count);
+            auto issue = [&](int pair) {
+                if (tid == 0) {
                     const u32 *a, *b;
-                    operands(pr, a, b);
-                    const size_t off = (size_t)pair * K * N + (size_t)k * N;
+                    operands(ig * G + ip, a, b);
+                    const size_t off = (size_t)pair * K * N + (size_t)ik * N;
                     fence_proxy_async();
                     mbar_arrive_expect_tx(&mbar[pair], (u32)(2 * PP::SLOT));
                     tma_load_1d(slot(pair), a + off, (u32)PP::SLOT, &mbar[pair]);
@@ -737,64 +803,112 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                 }
                 pend |= 1u << pair;
             };
-            issue(0, 0);
-            issue(0, 1);
-            for (int s = 0; s < total; s++) {
-                const int pr = s / K, k = s - pr * K;
-                const Mod32 m = c.mb[k];
-                const u32* tw = c.twb + (size_t)k * 4 * N;
-                const u32 ni = c.ninv_bx[k].w, nis = c.ninv_bx[k].ws, wl = c.wlast_bx[k].w, wls = c.wlast_bx[k].ws;
-                if (!wait_bar(0) || !wait_bar(1)) {
-                    abort_cta();
-                    return;
-                }
-                u32 x[3][R];
-                {
-                    const u32* s0 = slot(0);
-                    const u32* s1 = slot(1);
-                    const u32* s2 = slot(2);
-                    const u32* s3 = slot(3);
+            auto advance = [&]() {  // false once every step has been issued
+                if (++ip < iGg) return true;
+                ip = 0;
+                if (++ik < K) return true;
+                ik = 0;
+                ++ig;
+                iGg = min(G, en.count - ig * G);
+                return iGg > 0;
+            };
+            issue(0);
+            issue(1);
+            bool more = advance();
+            for (int g = 0; g * G < en.count; g++) {
+                const int Gg = min(G, en.count - g * G);
+                for (int k = 0; k < K; k++) {
+                    const Mod32 m = c.mb[k];
+                    u32 x[3][R];
+                    for (int p = 0; p < Gg; p++) {
+                        if (!wait_bar(0) || !wait_bar(1)) {
+                            abort_cta();
+                            return;
+                        }
+                        const u32* s0 = slot(0);
+                        const u32* s1 = slot(1);
+                        const u32* s2 = slot(2);
+                        const u32* s3 = slot(3);
 #pragma unroll
-                    for (int v = 0; v < R; v++) {
-                        const int i = NB::lane_idx(v, tid);
-                        const u64 a0 = s0[i], a1 = s1[i], b0 = s2[i], b1 = s3[i];
-                        x[0][v] = reduce61(a0 * b0, m);
-                        x[1][v] = reduce61(a0 * b1 + a1 * b0, m);
-                        x[2][v] = reduce61(a1 * b1, m);
+                        for (int v = 0; v < R; v++) {
+                            const int i = NB::lane_idx(v, tid);
+                            const u64 a0 = s0[i], a1 = s1[i], b0 = s2[i], b1 = s3[i];
+                            const u32 t0 = reduce61(a0 * b0, m), t1 = reduce61(a0 * b1 + a1 * b0, m),
+                                      t2 = reduce61(a1 * b1, m);
+                            x[0][v] = p == 0 ? t0 : csub32(x[0][v] + t0, m.b);
+                            x[1][v] = p == 0 ? t1 : csub32(x[1][v] + t1, m.b);
+                            x[2][v] = p == 0 ? t2 : csub32(x[2][v] + t2, m.b);
+                        }
+                        __syncthreads();  // every thread has read the slots
+                        if (more) {
+                            issue(0);
+                            issue(1);
+                            more = advance();
+                        }
+                    }
+                    const u32* tw = c.twb + (size_t)k * 4 * N;
+                    NB::template inverse_m<3>(x, sm32, tid, tw, m.b, c.ninv_bx[k].w, c.ninv_bx[k].ws,
+                                              c.wlast_bx[k].w, c.wlast_bx[k].ws);
+#pragma unroll
+                    for (int p = 0; p < 3; p++) {
+                        u32* dst = T + ((size_t)p * K + k) * N;
+#pragma unroll
+                        for (int v = 0; v < R; v++) dst[NB::inv_out_idx(v, tid)] = csub32(x[p][v], m.b);
                     }
                 }
-                __syncthreads();  // every thread has read the slots
-                if (s + 1 < total) {
-                    issue(s + 1, 0);
-                    issue(s + 1, 1);
-                }
-                NB::template inverse_m<3>(x, sm32, tid, tw, m.b, ni, nis, wl, wls);
-#pragma unroll
-                for (int p = 0; p < 3; p++) {
-                    u32* dst = T + ((size_t)p * K + k) * N;
-#pragma unroll
-                    for (int v = 0; v < R; v++) dst[NB::inv_out_idx(v, tid)] = csub32(x[p][v], m.b);
-                }
-                if (k == K - 1) {
+                __syncthreads();
+                stage_s(g);
+                __syncthreads();
+            }
+            }
+        } else {
+            // operands read from global memory; rounding groups of G products
+            // as in the staged path
+            const int G = GROUPED ? mm.group : 1;
+            if constexpr (!GROUPED) {
+                for (int pr = 0; pr < en.count; pr++) {
+                    const u32 *a, *b;
+                    operands(pr, a, b);
+                    // stage T
+                    for (int k = 0; k < K; k++) {
+                        const Mod32 m = c.mb[k];
+                        const u32* ak = a + (size_t)k * N;
+                        const u32* bk = b + (size_t)k * N;
+                        const u32* tw = c.twb + (size_t)k * 4 * N;
+                        for (int p = 0; p < 3; p++) {
+                            u32 x[R];
+    #pragma unroll
+                            for (int v = 0; v < R; v++) x[v] = tensor_coeff32(p, ak, bk, (size_t)K * N, NB::lane_idx(v, tid), m);
+                            NB::inverse(x, sm32, tid, tw, m.b, c.ninv_bx[k].w, c.ninv_bx[k].ws, c.wlast_bx[k].w,
+                                        c.wlast_bx[k].ws);
+                            u32* dst = T + ((size_t)p * K + k) * N;
+    #pragma unroll
+                            for (int v = 0; v < R; v++) dst[NB::inv_out_idx(v, tid)] = csub32(x[v], m.b);
+                        }
+                    }
                     __syncthreads();
                     stage_s(pr);
                     __syncthreads();
                 }
-            }
-        } else {
-            for (int pr = 0; pr < en.count; pr++) {
-                const u32 *a, *b;
-                operands(pr, a, b);
+            } else {
+            for (int g = 0; g * G < en.count; g++) {
+                const int g0 = g * G, Gg = min(G, en.count - g0);
                 // stage T
                 for (int k = 0; k < K; k++) {
                     const Mod32 m = c.mb[k];
-                    const u32* ak = a + (size_t)k * N;
-                    const u32* bk = b + (size_t)k * N;
                     const u32* tw = c.twb + (size_t)k * 4 * N;
                     for (int p = 0; p < 3; p++) {
                         u32 x[R];
+                        for (int q = 0; q < Gg; q++) {
+                            const u32 *a, *b;
+                            operands(g0 + q, a, b);
 #pragma unroll
-                        for (int v = 0; v < R; v++) x[v] = tensor_coeff32(p, ak, bk, (size_t)K * N, NB::lane_idx(v, tid), m);
+                            for (int v = 0; v < R; v++) {
+                                const u32 t = tensor_coeff32(p, a + (size_t)k * N, b + (size_t)k * N, (size_t)K * N,
+                                                             NB::lane_idx(v, tid), m);
+                                x[v] = q == 0 ? t : csub32(x[v] + t, m.b);
+                            }
+                        }
                         NB::inverse(x, sm32, tid, tw, m.b, c.ninv_bx[k].w, c.ninv_bx[k].ws, c.wlast_bx[k].w,
                                     c.wlast_bx[k].ws);
                         u32* dst = T + ((size_t)p * K + k) * N;
@@ -803,8 +917,9 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                     }
                 }
                 __syncthreads();
-                stage_s(pr);
+                stage_s(g);
                 __syncthreads();
+            }
             }
         }
         // stage R.  The forward NTT leaves slot tid * R + v of every polynomial

@@ -43,13 +43,13 @@ int persistent_occupancy(int L);
 template <int LOGN>
 cudaError_t persistent_launch(const RnsConsts& rc, const MmDesc* mms, const Entry* entries, int n_entries,
                               const int2* rowlist, const u64* rlk, const u64* rlk_sh, u64* scratch,
-                              size_t scratch_stride, unsigned* queue, int grid, cudaStream_t s);
+                              size_t scratch_stride, unsigned* queue, int grid, bool grouped, cudaStream_t s);
 // words of the per-CTA scratch of the persistent kernel (uint64 units)
 size_t persistent_scratch_words(const RnsConsts& rc);
 int persistent_ctas_per_sm(const RnsConsts& rc);
 cudaError_t launch_persistent(const RnsConsts& rc, const MmDesc* mms, const Entry* entries, int n_entries,
                               const int2* rowlist, const u64* rlk, const u64* rlk_sh, u64* scratch,
-                              size_t scratch_stride, unsigned* queue, int grid, cudaStream_t s);
+                              size_t scratch_stride, unsigned* queue, int grid, bool grouped, cudaStream_t s);
 cudaError_t launch_prng(u64 seed, u64 dom, u64 o0, u64 o1, u64 o2, u64 idx0, long long n, u64* out, cudaStream_t s);
 
 }  // namespace sfhe

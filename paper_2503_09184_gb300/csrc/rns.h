@@ -95,6 +95,10 @@ struct RnsConsts {
     u64 r_w[SFHE_MAX_K][SFHE_MAX_L + 1];          // r_k as words (exact decision)
     u64 rB_w[SFHE_MAX_L + 1];                     // r_B as words
 
+    // products per rounding in the grouped accumulate-then-round mode:
+    // floor(B / (2 N Q^2)), at most 1024
+    int lazy_group;
+
     // encryption / decryption
     u64 delta_q[SFHE_MAX_L];                // floor(Q/t) mod q_i
     ShoupC t_q[SFHE_MAX_L];                 // t mod q_i

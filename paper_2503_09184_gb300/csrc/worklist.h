@@ -7,7 +7,7 @@ struct MmDesc {
     const u32* B_ext;  // [rows_B * Nc][2][K][N]
     u64* C;            // [M*Nc][2][L][N]
     int Nc;
-    int pad;
+    int group;  // products per scale-and-round: 1 (Alg. 1), or the grouped mode's size
 };
 
 struct Entry {

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsfhe.so")
 SFHE_OK, SFHE_EINVAL, SFHE_ESHAPE, SFHE_ENOMEM, SFHE_ECUDA = 0, 1, 2, 3, 4
 SFHE_ETIMEOUT, SFHE_EBUDGET, SFHE_EUNSUPPORTED, SFHE_EDEVICE = 5, 6, 7, 8
 SFHE_ENC_DENSE, SFHE_ENC_MASK, SFHE_ENC_CSR, SFHE_ENC_ELL = 0, 1, 2, 3
-SFHE_EXEC_PLAIN, SFHE_EXEC_PERSISTENT, SFHE_EXEC_GRAPH = 1, 2, 4
+SFHE_EXEC_PLAIN, SFHE_EXEC_PERSISTENT, SFHE_EXEC_GRAPH, SFHE_EXEC_LAZY = 1, 2, 4, 8
 ENCODINGS = {"dense": SFHE_ENC_DENSE, "mask": SFHE_ENC_MASK, "csr": SFHE_ENC_CSR, "ell": SFHE_ENC_ELL}
 
 
@@ -37,7 +37,7 @@ class sfhe_info(ctypes.Structure):
     _fields_ = [("N", ctypes.c_uint32), ("L", ctypes.c_uint32), ("K", ctypes.c_uint32),
                 ("t", ctypes.c_uint64), ("q", ctypes.c_uint64 * 8), ("b", ctypes.c_uint32 * 32),
                 ("ct_words", ctypes.c_uint64), ("ext_words", ctypes.c_uint64), ("num_sms", ctypes.c_int32),
-                ("ext_interleave", ctypes.c_uint32)]
+                ("ext_interleave", ctypes.c_uint32), ("lazy_group", ctypes.c_int32)]
 
 
 class sfhe_matrix(ctypes.Structure):

@@ -286,6 +286,54 @@ def test_tensor_scale_rounding_boundaries(which, request):
 
 
 @pytest.mark.parametrize("which", ["ctx16", "ctx16L3"])
+def test_tensor_scale_sum_matches_textbook(which, request):
+    """or_tensor_scale_sum: one exact rounding of the summed integer tensors
+    (grouped accumulate-then-round), against big-integer arithmetic; with one
+    pair it is or_tensor_scale."""
+    c = request.getfixturevalue(which)
+    pairs = [(c.encrypt(ma, 1, 0, k), c.encrypt(mb, 2, k, 0)) for k, (ma, mb) in enumerate([(7, -9), (16, 16), (-5, 3)])]
+    d = c.tensor_scale_sum([p[0] for p in pairs], [p[1] for p in pairs])
+    ref = tb.tensor_scale_sum(pairs, c.q, T)
+    for p in range(3):
+        assert (d[p] == tb.from_int_poly(ref[p], c.q)).all(), p
+    assert (c.tensor_scale_sum([pairs[0][0]], [pairs[0][1]]) == c.tensor_scale(*pairs[0])).all()
+    # a crafted pair on both rounding boundaries, summed with an ordinary one
+    a, b = boundary_pair(c.q, T, c.N, seed=9)
+    d = c.tensor_scale_sum([a, pairs[1][0]], [b, pairs[1][1]])
+    ref = tb.tensor_scale_sum([(a, b), pairs[1]], c.q, T)
+    for p in range(3):
+        assert (d[p] == tb.from_int_poly(ref[p], c.q)).all(), p
+    with pytest.raises(ValueError):
+        c.tensor_scale_sum([a] * 1025, [b] * 1025)
+
+
+def test_grouped_entries_decrypt_and_group_one_is_per_product(ctx16L3):
+    """Entries computed with groups of 1 equal Alg. 1's per-product loop; larger
+    groups give other ciphertexts with the same decryption (A B mod t) and
+    each group's result is the textbook relinearisation of the summed tensor."""
+    c = ctx16L3
+    A = np.array([[3, 0, -7, 2, 5], [0, 0, 0, 0, 0], [16, -16, 1, 0, 9]], dtype=np.int64)
+    B = np.array([[2, -1], [4, 0], [-3, 5], [7, 7], [1, -2]], dtype=np.int64)
+    mm = O.OracleMatmul(c, A, B, 1, 2)
+    enc = O.encode(A, O.CSR)
+    for i in range(A.shape[0]):
+        for j in range(B.shape[1]):
+            eager = mm.entry(enc, i, j)
+            assert (mm.entry(enc, i, j, group=1) == eager).all()
+            want = ((int(A[i] @ B[:, j]) + T // 2) % T) - T // 2
+            for g in (2, 3, 8):
+                lazy = mm.entry(enc, i, j, group=g)
+                assert c.decrypt(lazy)[0] == want, (i, j, g)
+    # one group holding all of row 0's products, against big integers
+    ks = [k for k in range(A.shape[1]) if A[0, k]]
+    pairs = [(mm.ct_a(0, k), mm.ct_b(k, 1)) for k in ks]
+    ref = tb.relin(tb.tensor_scale_sum(pairs, c.q, T), c.rlk(), c.q)
+    got = mm.entry(enc, 0, 1, group=len(ks))
+    for p in range(2):
+        assert (got[p] == tb.from_int_poly(ref[p], c.q)).all()
+
+
+@pytest.mark.parametrize("which", ["ctx16", "ctx16L3"])
 def test_mul_relin_matches_textbook(which, request):
     """or_relin / or_mul_relin: digits D_j = [d2]_{q_j}, c = (d0, d1) +
     sum_j D_j rlk_j, all in big-integer arithmetic mod Q."""

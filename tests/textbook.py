@@ -64,6 +64,21 @@ def tensor_scale(ct_a: np.ndarray, ct_b: np.ndarray, q, t: int) -> list[list[int
     return [[((2 * t * x + Q) // (2 * Q)) % Q for x in xs] for xs in (x0, x1, x2)]
 
 
+def tensor_scale_sum(pairs, q, t: int) -> list[list[int]]:
+    """round(t (x(a_0, b_0) + ... ) / Q) mod Q: one rounding of the summed
+    integer tensors."""
+    Q = prod(q)
+    N = pairs[0][0].shape[-1]
+    X = [[0] * N for _ in range(3)]
+    for ct_a, ct_b in pairs:
+        a0, a1 = ([centred(c, Q) for c in to_int_poly(ct_a[p], q)] for p in (0, 1))
+        b0, b1 = ([centred(c, Q) for c in to_int_poly(ct_b[p], q)] for p in (0, 1))
+        x1 = [u + v for u, v in zip(negacyclic(a0, b1), negacyclic(a1, b0))]
+        for p, xs in enumerate((negacyclic(a0, b0), x1, negacyclic(a1, b1))):
+            X[p] = [u + v for u, v in zip(X[p], xs)]
+    return [[((2 * t * x + Q) // (2 * Q)) % Q for x in xs] for xs in X]
+
+
 def relin(d, rlk: np.ndarray, q) -> list[list[int]]:
     """c0 = d0 + sum_j D_j b_j, c1 = d1 + sum_j D_j a_j (mod Q), D_j = d2 mod q_j."""
     Q = prod(q)
