@@ -581,18 +581,21 @@ __global__ void k_prng_words(u64 seed, u64 dom, u64 o0, u64 o1, u64 o2, u64 idx0
 // Shared-memory plan of the persistent kernel.  Up to N = 8192 the operand
 // limbs are staged: four 4N-byte slots (a0, a1, b0, b1 of one tensor-base
 // prime) filled by TMA bulk copies behind the exchange buffers of the three
-// 32-bit inverse NTTs that run together; the 64-bit NTTs of stage R reuse
-// the same bytes from offset 0.
+// 32-bit inverse NTTs that run together.  At N = 16384 two slots fit behind
+// one exchange buffer: a prime's tensor is formed in four rounds of two
+// staged limbs.  The 64-bit NTTs of stage R reuse the bytes from offset 0.
 template <int LOGN, int L>
 struct PersistentPlan {
     using CF = Cfg<LOGN, L>;
-    static constexpr bool STAGED = LOGN <= 13;
-    static constexpr int NPT = STAGED ? 3 : 1;  // polynomials per inverse-NTT pass in stage T
+    static constexpr bool STAGED = LOGN <= 13;   // four slots, three polynomials per pass
+    static constexpr bool STAGED2 = LOGN == 14;  // two slots, one polynomial per pass
+    static constexpr int NPT = STAGED ? 3 : 1;   // polynomials per inverse-NTT pass in stage T
+    static constexpr int NSLOT = STAGED ? 4 : 2;
     static constexpr size_t SLOT = (size_t)4 << LOGN;
     static constexpr size_t EXB = ((size_t)NPT * CF::NB::SMEM_WORDS * 4 + 127) & ~(size_t)127;
     static constexpr size_t NQB = (size_t)CF::NQ::SMEM_WORDS * 8;
-    static constexpr size_t STAGE_B = EXB + 4 * SLOT;
-    static constexpr size_t SMEM = STAGED ? (NQB > STAGE_B ? NQB : STAGE_B) : NQB;
+    static constexpr size_t STAGE_B = EXB + NSLOT * SLOT;
+    static constexpr size_t SMEM = (STAGED || STAGED2) ? (NQB > STAGE_B ? NQB : STAGE_B) : NQB;
     static_assert(SMEM <= 227 * 1024 - 256, "shared-memory plan too large");
 };
 
@@ -645,7 +648,7 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
     // per mbarrier: parity of the phase to wait for next, and whether a copy
     // is in flight (kept alike in every thread: issues and waits are uniform)
     u32 phbits = 0, pend = 0;
-    if constexpr (PP::STAGED) {
+    if constexpr (PP::STAGED || PP::STAGED2) {
         if (tid == 0) {
 #pragma unroll
             for (int i = 0; i < 2; i++) mbar_init(&mbar[i], 1);
@@ -865,7 +868,59 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
             // operands read from global memory; rounding groups of G products
             // as in the staged path
             const int G = GROUPED ? mm.group : 1;
-            if constexpr (!GROUPED) {
+            if constexpr (!GROUPED && PP::STAGED2) {
+                // rounds of two staged limbs per prime: 0 (a0, b0) -> d0,
+                // 1 (a1, b1) -> d2, 2 (a0, b1) and 3 (a1, b0) -> d1; each
+                // round's copy streams in during the previous inverse NTT
+                const int total = en.count * K * 4;
+                auto issue2 = [&](int st) {
+                    if (tid == 0) {
+                        const int r = st & 3, q = st >> 2, pr = q / K, k = q - pr * K;
+                        const u32 *a, *b;
+                        operands(pr, a, b);
+                        const size_t ca = (r == 1 || r == 3) ? 1 : 0, cb = (r == 1 || r == 2) ? 1 : 0;
+                        fence_proxy_async();
+                        mbar_arrive_expect_tx(&mbar[0], (u32)(2 * PP::SLOT));
+                        tma_load_1d(slot(0), a + ca * K * N + (size_t)k * N, (u32)PP::SLOT, &mbar[0]);
+                        tma_load_1d(slot(1), b + cb * K * N + (size_t)k * N, (u32)PP::SLOT, &mbar[0]);
+                    }
+                    pend |= 1u;
+                };
+                issue2(0);
+                int st = 0;
+                for (int pr = 0; pr < en.count; pr++) {
+                    for (int k = 0; k < K; k++) {
+                        const Mod32 m = c.mb[k];
+                        const u32* tw = c.twb + (size_t)k * 4 * N;
+                        u32 x[R];
+                        for (int r = 0; r < 4; r++, st++) {
+                            if (!wait_bar(0)) {
+                                abort_cta();
+                                return;
+                            }
+                            const u32* sa = slot(0);
+                            const u32* sb = slot(1);
+#pragma unroll
+                            for (int v = 0; v < R; v++) {
+                                const int i = NB::lane_idx(v, tid);
+                                const u32 t = reduce61((u64)sa[i] * sb[i], m);
+                                x[v] = r == 3 ? csub32(x[v] + t, m.b) : t;
+                            }
+                            __syncthreads();  // every thread has read the slots
+                            if (st + 1 < total) issue2(st + 1);
+                            if (r == 2) continue;
+                            NB::inverse(x, sm32, tid, tw, m.b, c.ninv_bx[k].w, c.ninv_bx[k].ws, c.wlast_bx[k].w,
+                                        c.wlast_bx[k].ws);
+                            u32* dst = T + ((size_t)(r == 0 ? 0 : (r == 1 ? 2 : 1)) * K + k) * N;
+#pragma unroll
+                            for (int v = 0; v < R; v++) dst[NB::inv_out_idx(v, tid)] = csub32(x[v], m.b);
+                        }
+                    }
+                    __syncthreads();
+                    stage_s(pr);
+                    __syncthreads();
+                }
+            } else if constexpr (!GROUPED) {
                 for (int pr = 0; pr < en.count; pr++) {
                     const u32 *a, *b;
                     operands(pr, a, b);
@@ -973,6 +1028,6 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
             }
         }
         // the slots are refilled by bulk copies (async proxy) for the next entry
-        if constexpr (PP::STAGED) fence_proxy_async();
+        if constexpr (PP::STAGED || PP::STAGED2) fence_proxy_async();
     }
 }
