@@ -979,52 +979,95 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
         }
         // stage R.  The forward NTT leaves slot tid * R + v of every polynomial
         // with thread tid, so the key products and the output are private to
-        // a thread: the sums [2][N] live in the idle operand slots (staged
-        // kernel; element v of thread tid at v * NTH + tid, free of bank
-        // conflicts) or in the CTA's scratch, and the key and C are accessed
-        // with 16-byte vectors.
-        u64* cs = PP::STAGED ? reinterpret_cast<u64*>(smb + PP::EXB) : cacc;
-        auto cpos = [&](int v) -> size_t {
-            return PP::STAGED ? (size_t)v * NTH + tid : (size_t)NQ::run_idx(v, tid);
-        };
-        for (int i = 0; i < L; i++) {
-            const Mod m = c.m[i];
-            const u64* tw = c.tw + (size_t)i * 4 * N;
-            for (int s = 0; s < L + 2; s++) {
-                // s = 0: sum d0 (limb i), 1: sum d1 (limb i), 2 + j: sum of digits j
-                const u64* src = s < 2 ? acc + ((size_t)s * L + i) * N : acc + ((size_t)2 * L + (s - 2)) * N;
-                u64 x[NQ::R];
+        // a thread, and the key and C are accessed with 16-byte vectors.  Up
+        // to N = 8192 the sums [2][N] live in the idle operand slots (element
+        // v of thread tid at v * NTH + tid, free of bank conflicts).  At
+        // N = 16384 they do not fit: the L + 2 transforms of a limb go to the
+        // idle tensor scratch and one pass forms both sums in registers.
+        if constexpr (PP::STAGED) {
+            u64* cs = PP::STAGED ? reinterpret_cast<u64*>(smb + PP::EXB) : cacc;
+            auto cpos = [&](int v) -> size_t {
+                return PP::STAGED ? (size_t)v * NTH + tid : (size_t)NQ::run_idx(v, tid);
+            };
+            for (int i = 0; i < L; i++) {
+                const Mod m = c.m[i];
+                const u64* tw = c.tw + (size_t)i * 4 * N;
+                for (int s = 0; s < L + 2; s++) {
+                    // s = 0: sum d0 (limb i), 1: sum d1 (limb i), 2 + j: sum of digits j
+                    const u64* src = s < 2 ? acc + ((size_t)s * L + i) * N : acc + ((size_t)2 * L + (s - 2)) * N;
+                    u64 x[NQ::R];
 #pragma unroll
-                for (int v = 0; v < NQ::R; v++) x[v] = barrett64(src[NQ::fwd_in_idx(v, tid)], m);
-                NQ::forward(x, sm, tid, tw, m.q);
-                if (s < 2) {
+                    for (int v = 0; v < NQ::R; v++) x[v] = barrett64(src[NQ::fwd_in_idx(v, tid)], m);
+                    NQ::forward(x, sm, tid, tw, m.q);
+                    if (s < 2) {
 #pragma unroll
-                    for (int v = 0; v < NQ::R; v++) cs[(size_t)s * N + cpos(v)] = x[v];
-                } else {
-                    const int j = s - 2;
-                    const size_t ob = (((size_t)j * 2 + 0) * L + i) * N + (size_t)tid * NQ::R;
-                    const size_t oa = (((size_t)j * 2 + 1) * L + i) * N + (size_t)tid * NQ::R;
+                        for (int v = 0; v < NQ::R; v++) cs[(size_t)s * N + cpos(v)] = x[v];
+                    } else {
+                        const int j = s - 2;
+                        const size_t ob = (((size_t)j * 2 + 0) * L + i) * N + (size_t)tid * NQ::R;
+                        const size_t oa = (((size_t)j * 2 + 1) * L + i) * N + (size_t)tid * NQ::R;
 #pragma unroll
-                    for (int v = 0; v < NQ::R; v += 2) {
-                        const ulonglong2 wb = __ldg(reinterpret_cast<const ulonglong2*>(rlk + ob + v));
-                        const ulonglong2 sb = __ldg(reinterpret_cast<const ulonglong2*>(rlk_sh + ob + v));
-                        const ulonglong2 wa = __ldg(reinterpret_cast<const ulonglong2*>(rlk + oa + v));
-                        const ulonglong2 sa = __ldg(reinterpret_cast<const ulonglong2*>(rlk_sh + oa + v));
-                        cs[cpos(v)] += shoup_lazy(x[v], wb.x, sb.x, m.q);
-                        cs[cpos(v + 1)] += shoup_lazy(x[v + 1], wb.y, sb.y, m.q);
-                        cs[N + cpos(v)] += shoup_lazy(x[v], wa.x, sa.x, m.q);
-                        cs[N + cpos(v + 1)] += shoup_lazy(x[v + 1], wa.y, sa.y, m.q);
+                        for (int v = 0; v < NQ::R; v += 2) {
+                            const ulonglong2 wb = __ldg(reinterpret_cast<const ulonglong2*>(rlk + ob + v));
+                            const ulonglong2 sb = __ldg(reinterpret_cast<const ulonglong2*>(rlk_sh + ob + v));
+                            const ulonglong2 wa = __ldg(reinterpret_cast<const ulonglong2*>(rlk + oa + v));
+                            const ulonglong2 sa = __ldg(reinterpret_cast<const ulonglong2*>(rlk_sh + oa + v));
+                            cs[cpos(v)] += shoup_lazy(x[v], wb.x, sb.x, m.q);
+                            cs[cpos(v + 1)] += shoup_lazy(x[v + 1], wb.y, sb.y, m.q);
+                            cs[N + cpos(v)] += shoup_lazy(x[v], wa.x, sa.x, m.q);
+                            cs[N + cpos(v + 1)] += shoup_lazy(x[v + 1], wa.y, sa.y, m.q);
+                        }
                     }
                 }
-            }
-            u64* c0 = Cout + (size_t)i * N + (size_t)tid * NQ::R;
-            u64* c1 = Cout + ((size_t)L + i) * N + (size_t)tid * NQ::R;
+                u64* c0 = Cout + (size_t)i * N + (size_t)tid * NQ::R;
+                u64* c1 = Cout + ((size_t)L + i) * N + (size_t)tid * NQ::R;
 #pragma unroll
-            for (int v = 0; v < NQ::R; v += 2) {
-                *reinterpret_cast<ulonglong2*>(c0 + v) =
-                    make_ulonglong2(barrett64(cs[cpos(v)], m), barrett64(cs[cpos(v + 1)], m));
-                *reinterpret_cast<ulonglong2*>(c1 + v) =
-                    make_ulonglong2(barrett64(cs[N + cpos(v)], m), barrett64(cs[N + cpos(v + 1)], m));
+                for (int v = 0; v < NQ::R; v += 2) {
+                    *reinterpret_cast<ulonglong2*>(c0 + v) =
+                        make_ulonglong2(barrett64(cs[cpos(v)], m), barrett64(cs[cpos(v + 1)], m));
+                    *reinterpret_cast<ulonglong2*>(c1 + v) =
+                        make_ulonglong2(barrett64(cs[N + cpos(v)], m), barrett64(cs[N + cpos(v + 1)], m));
+                }
+            }
+        } else {
+            u64* U = reinterpret_cast<u64*>(T);  // [L + 2][N], slot tid * R + v at its place
+            for (int i = 0; i < L; i++) {
+                const Mod m = c.m[i];
+                const u64* tw = c.tw + (size_t)i * 4 * N;
+                for (int s = 0; s < L + 2; s++) {
+                    const u64* src = s < 2 ? acc + ((size_t)s * L + i) * N : acc + ((size_t)2 * L + (s - 2)) * N;
+                    u64 x[NQ::R];
+#pragma unroll
+                    for (int v = 0; v < NQ::R; v++) x[v] = barrett64(src[NQ::fwd_in_idx(v, tid)], m);
+                    NQ::forward(x, sm, tid, tw, m.q);
+                    u64* dst = U + (size_t)s * N + (size_t)tid * NQ::R;
+#pragma unroll
+                    for (int v = 0; v < NQ::R; v += 2)
+                        *reinterpret_cast<ulonglong2*>(dst + v) = make_ulonglong2(x[v], x[v + 1]);
+                }
+                const size_t e0 = (size_t)tid * NQ::R;
+                u64* c0 = Cout + (size_t)i * N + e0;
+                u64* c1 = Cout + ((size_t)L + i) * N + e0;
+                for (int v = 0; v < NQ::R; v += 2) {
+                    const ulonglong2 u0 = *reinterpret_cast<const ulonglong2*>(U + e0 + v);
+                    const ulonglong2 u1 = *reinterpret_cast<const ulonglong2*>(U + N + e0 + v);
+                    u64 b0 = u0.x, b1 = u0.y, a0 = u1.x, a1 = u1.y;
+                    for (int j = 0; j < L; j++) {
+                        const ulonglong2 d = *reinterpret_cast<const ulonglong2*>(U + (size_t)(2 + j) * N + e0 + v);
+                        const size_t ob = (((size_t)j * 2 + 0) * L + i) * N + e0 + v;
+                        const size_t oa = (((size_t)j * 2 + 1) * L + i) * N + e0 + v;
+                        const ulonglong2 wb = __ldg(reinterpret_cast<const ulonglong2*>(rlk + ob));
+                        const ulonglong2 sb = __ldg(reinterpret_cast<const ulonglong2*>(rlk_sh + ob));
+                        const ulonglong2 wa = __ldg(reinterpret_cast<const ulonglong2*>(rlk + oa));
+                        const ulonglong2 sa = __ldg(reinterpret_cast<const ulonglong2*>(rlk_sh + oa));
+                        b0 += shoup_lazy(d.x, wb.x, sb.x, m.q);
+                        b1 += shoup_lazy(d.y, wb.y, sb.y, m.q);
+                        a0 += shoup_lazy(d.x, wa.x, sa.x, m.q);
+                        a1 += shoup_lazy(d.y, wa.y, sa.y, m.q);
+                    }
+                    *reinterpret_cast<ulonglong2*>(c0 + v) = make_ulonglong2(barrett64(b0, m), barrett64(b1, m));
+                    *reinterpret_cast<ulonglong2*>(c1 + v) = make_ulonglong2(barrett64(a0, m), barrett64(a1, m));
+                }
             }
         }
         // the slots are refilled by bulk copies (async proxy) for the next entry

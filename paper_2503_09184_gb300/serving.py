@@ -135,10 +135,13 @@ class GpuExecutor:
     """Device side: encryption and lift on admission, one persistent batch
     plan per wave over CSR row blocks of A (and the matching rows of C)."""
 
-    def __init__(self, ctx, stream=None):
+    def __init__(self, ctx, stream=None, lazy: bool = False):
+        """lazy: run the waves in the grouped accumulate-then-round mode
+        (SFHE_EXEC_LAZY) instead of the per-product order."""
         import torch
         from . import api, sfhe as S
         self.ctx, self.api, self.S, self.torch = ctx, api, S, torch
+        self.flags = api.PERSISTENT | (api.LAZY if lazy else 0)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.mats = {}
         self.admit_s = {}
@@ -173,9 +176,9 @@ class GpuExecutor:
         api, S = self.api, self.S
         parts = [self._rows(req, r0, r1) for req, r0, r1 in blocks]
         As, Bs, Cs = [p[0] for p in parts], [p[1] for p in parts], [p[2] for p in parts]
-        work = api.workspace(self.ctx, As, Bs, api.PERSISTENT)
+        work = api.workspace(self.ctx, As, Bs, self.flags)
         plan = S.sfhe_plan_create(self.ctx.h, [a.desc() for a in As], [b.desc() for b in Bs],
-                                  [c.desc() for c in Cs], api.PERSISTENT, work, self.stream)
+                                  [c.desc() for c in Cs], self.flags, work, self.stream)
         products = S.sfhe_plan_stats(plan)["products"]
         S.sfhe_plan_execute(plan, self.stream)
         S.sfhe_matmul_check(work, self.stream)       # synchronises the stream
