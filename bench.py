@@ -490,11 +490,12 @@ def run_serve(args):
     plain_rate = plan.stats["products"] / (time.perf_counter() - t0)
     plan.close()
     # warm-up of the served path
-    SV.serve(serve_requests(args, 100.0, 99)[:2], SV.GpuExecutor(ctx), budget, args.wave_products, ct_b, ext_b)
+    SV.serve(serve_requests(args, 100.0, 99)[:2], SV.GpuExecutor(ctx, lazy=args.lazy), budget, args.wave_products,
+             ct_b, ext_b)
     sweep = []
     for n, rate in enumerate(float(x) for x in args.rates.split(",")):
         reqs = serve_requests(args, rate, seed=10 + n)
-        ex = SV.GpuExecutor(ctx)
+        ex = SV.GpuExecutor(ctx, lazy=args.lazy)
         out = SV.serve(reqs, ex, budget, args.wave_products, ct_b, ext_b)
         plain = SV.fifo_plain_model(reqs, lambda r: ex.admit_s.get(r.rid, 0.0) + r.products / plain_rate)
         sweep.append({"rate_per_s": rate, "requests": out["requests"], "done": out["done"],
@@ -507,7 +508,8 @@ def run_serve(args):
     line = {"metric": METRIC, "value": best["ct_mults_per_s"], "unit": UNIT, "n_gpus": 1, "steps": len(sweep),
             "warmup": 1, "ms_per_step": 1e3 * best["makespan_s"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": f"serve-mixed{args.serve_dims.replace(',', '-')}-N{ring.N}-L{ring.L}",
+            "config": {"workload": f"serve-mixed{args.serve_dims.replace(',', '-')}-N{ring.N}-L{ring.L}"
+                                   + ("-lazy" if args.lazy else ""),
                        "N": ring.N, "L": ring.L, "t": W.T_PLAIN, "budget_gb": args.budget_gb,
                        "wave_products": args.wave_products, "requests_per_rate": args.requests,
                        "dims": args.serve_dims, "sparsity": "U[0.30, 0.95]"},

@@ -920,6 +920,74 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                     stage_s(pr);
                     __syncthreads();
                 }
+            } else if constexpr (GROUPED && PP::STAGED2) {
+                // the same rounds, each over the group's products (the
+                // group's tensor polynomial is summed before its inverse NTT)
+                int ig = 0, ik = 0, ir = 0, ip = 0, iGg = min(G, en.count);
+                auto issue2 = [&]() {
+                    if (tid == 0) {
+                        const u32 *a, *b;
+                        operands(ig * G + ip, a, b);
+                        const size_t ca = (ir == 1 || ir == 3) ? 1 : 0, cb = (ir == 1 || ir == 2) ? 1 : 0;
+                        fence_proxy_async();
+                        mbar_arrive_expect_tx(&mbar[0], (u32)(2 * PP::SLOT));
+                        tma_load_1d(slot(0), a + ca * K * N + (size_t)ik * N, (u32)PP::SLOT, &mbar[0]);
+                        tma_load_1d(slot(1), b + cb * K * N + (size_t)ik * N, (u32)PP::SLOT, &mbar[0]);
+                    }
+                    pend |= 1u;
+                };
+                auto advance = [&]() {  // false once every step has been issued
+                    if (++ip < iGg) return true;
+                    ip = 0;
+                    if (++ir < 4) return true;
+                    ir = 0;
+                    if (++ik < K) return true;
+                    ik = 0;
+                    ++ig;
+                    iGg = min(G, en.count - ig * G);
+                    return iGg > 0;
+                };
+                issue2();
+                bool more = advance();
+                for (int g = 0; g * G < en.count; g++) {
+                    const int Gg = min(G, en.count - g * G);
+                    for (int k = 0; k < K; k++) {
+                        const Mod32 m = c.mb[k];
+                        const u32* tw = c.twb + (size_t)k * 4 * N;
+                        u32 x[R];
+                        for (int r = 0; r < 4; r++) {
+                            for (int p = 0; p < Gg; p++) {
+                                if (!wait_bar(0)) {
+                                    abort_cta();
+                                    return;
+                                }
+                                const u32* sa = slot(0);
+                                const u32* sb = slot(1);
+                                const bool fresh = p == 0 && r != 3;
+#pragma unroll
+                                for (int v = 0; v < R; v++) {
+                                    const int i = NB::lane_idx(v, tid);
+                                    const u32 t = reduce61((u64)sa[i] * sb[i], m);
+                                    x[v] = fresh ? t : csub32(x[v] + t, m.b);
+                                }
+                                __syncthreads();  // every thread has read the slots
+                                if (more) {
+                                    issue2();
+                                    more = advance();
+                                }
+                            }
+                            if (r == 2) continue;
+                            NB::inverse(x, sm32, tid, tw, m.b, c.ninv_bx[k].w, c.ninv_bx[k].ws, c.wlast_bx[k].w,
+                                        c.wlast_bx[k].ws);
+                            u32* dst = T + ((size_t)(r == 0 ? 0 : (r == 1 ? 2 : 1)) * K + k) * N;
+#pragma unroll
+                            for (int v = 0; v < R; v++) dst[NB::inv_out_idx(v, tid)] = csub32(x[v], m.b);
+                        }
+                    }
+                    __syncthreads();
+                    stage_s(g);
+                    __syncthreads();
+                }
             } else if constexpr (!GROUPED) {
                 for (int pr = 0; pr < en.count; pr++) {
                     const u32 *a, *b;
@@ -1048,10 +1116,12 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                 const size_t e0 = (size_t)tid * NQ::R;
                 u64* c0 = Cout + (size_t)i * N + e0;
                 u64* c1 = Cout + ((size_t)L + i) * N + e0;
+#pragma unroll 2
                 for (int v = 0; v < NQ::R; v += 2) {
                     const ulonglong2 u0 = *reinterpret_cast<const ulonglong2*>(U + e0 + v);
                     const ulonglong2 u1 = *reinterpret_cast<const ulonglong2*>(U + N + e0 + v);
                     u64 b0 = u0.x, b1 = u0.y, a0 = u1.x, a1 = u1.y;
+#pragma unroll
                     for (int j = 0; j < L; j++) {
                         const ulonglong2 d = *reinterpret_cast<const ulonglong2*>(U + (size_t)(2 + j) * N + e0 + v);
                         const size_t ob = (((size_t)j * 2 + 0) * L + i) * N + e0 + v;
