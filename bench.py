@@ -220,6 +220,20 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# --------------------------------------------------------------- multi-rank ---
+def aggregate_over_ranks(ms: float, products: int, world: int, device) -> tuple[float, float]:
+    """The step time is the maximum over the ranks; every rank runs its own
+    replica of the workload (no data-path collective), so the whole-job
+    throughput is the units of all ranks over that time."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, products * world / (ms / 1e3)
+
+
 # ---------------------------------------------------------------- workloads ---
 def job_of(args):
     """(ring, [(A values, B values)], workload name, sparsity) of the selected workload."""
@@ -353,11 +367,7 @@ def main():
     t1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = t0.elapsed_time(t1) / args.steps
-    if world > 1:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms, value = aggregate_over_ranks(t0.elapsed_time(t1) / args.steps, products, world, "cuda")
     kms = statistics.mean(a.elapsed_time(b) for a, b in kernel_ms)
 
     # correctness of the timed result: decrypt every C and compare with A B mod t
@@ -395,7 +405,6 @@ def main():
     # (the grouped mode gives other ciphertexts with the same decryption)
     plain_equal = bool((pers_rows == plain_rows).all()) if not args.lazy else None
 
-    value = products * world / (ms / 1e3)
     groups = None
     if args.lazy:
         G = ctx.lazy_group
