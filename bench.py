@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--serve-dims", default="16,32,64", help="serve: M, K, Nc drawn from these")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: HBM ciphertext budget")
     ap.add_argument("--wave-products", type=int, default=40000, help="serve: products per wave")
+    ap.add_argument("--serve-set", default="poisson", choices=["poisson", "mixed64"],
+                    help="serve: Poisson requests, or the 64 matmuls of the mixed workload arriving at once")
     ap.add_argument("--sparsity", type=float, default=None, help="sweep / layer sparsity (default 0.5)")
     ap.add_argument("--lazy", action="store_true",
                     help="grouped accumulate-then-round (SFHE_EXEC_LAZY): a different valid ciphertext, "
@@ -458,8 +460,11 @@ def main():
 
 def serve_requests(args, rate: float, seed: int):
     """requests of the mixed distribution (sizes from --serve-dims, sparsity
-    U[0.30, 0.95], ints in [-8, 8]) with Poisson arrival times."""
+    U[0.30, 0.95], ints in [-8, 8]) with Poisson arrival times; or (mixed64)
+    the 64 matmuls of the mixed workload, all arriving at time 0."""
     from paper_2503_09184_gb300.serving import Request
+    if args.serve_set == "mixed64":
+        return [Request(rid, *W.operands(sh), 0.0) for rid, sh in enumerate(W.mixed(64))]
     dims = [int(x) for x in args.serve_dims.split(",")]
     rng = np.random.default_rng(seed)
     arrivals = W.poisson_arrivals(rate, args.requests, seed=seed + 1)
@@ -502,7 +507,8 @@ def run_serve(args):
     SV.serve(serve_requests(args, 100.0, 99)[:2], SV.GpuExecutor(ctx, lazy=args.lazy), budget, args.wave_products,
              ct_b, ext_b)
     sweep = []
-    for n, rate in enumerate(float(x) for x in args.rates.split(",")):
+    rates = [0.0] if args.serve_set == "mixed64" else [float(x) for x in args.rates.split(",")]
+    for n, rate in enumerate(rates):
         reqs = serve_requests(args, rate, seed=10 + n)
         ex = SV.GpuExecutor(ctx, lazy=args.lazy)
         out = SV.serve(reqs, ex, budget, args.wave_products, ct_b, ext_b)
@@ -517,7 +523,8 @@ def run_serve(args):
     line = {"metric": METRIC, "value": best["ct_mults_per_s"], "unit": UNIT, "n_gpus": 1, "steps": len(sweep),
             "warmup": 1, "ms_per_step": 1e3 * best["makespan_s"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": f"serve-mixed{args.serve_dims.replace(',', '-')}-N{ring.N}-L{ring.L}"
+            "config": {"workload": (f"serve-mixed{args.serve_dims.replace(',', '-')}-N{ring.N}-L{ring.L}"
+                                    if args.serve_set == "poisson" else f"mixed64-waves-N{ring.N}-L{ring.L}")
                                    + ("-lazy" if args.lazy else ""),
                        "N": ring.N, "L": ring.L, "t": W.T_PLAIN, "budget_gb": args.budget_gb,
                        "wave_products": args.wave_products, "requests_per_rate": args.requests,

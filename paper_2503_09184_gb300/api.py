@@ -82,12 +82,19 @@ class EncMatrix:
 
 
 def encrypt_matrix(ctx: Context, values: np.ndarray, encoding: int | str, matrix_id: int, lift: bool = True,
-                   stream=None) -> EncMatrix:
+                   stream=None, col_offset: int = 0) -> EncMatrix:
+    """col_offset: the matrix is a column block of a larger one starting at
+    that column; elements are encrypted under their coordinates in the larger
+    matrix (the same ciphertexts as encrypting it whole)."""
     if isinstance(encoding, str):
         encoding = S.ENCODINGS[encoding]
     values = np.ascontiguousarray(values, dtype=np.int64)
     rows, cols = values.shape
     f = S.sfhe_encode_fill(values, encoding)
+    if col_offset:
+        if encoding != S.SFHE_ENC_DENSE:
+            raise ValueError("column blocks of DENSE matrices only")
+        f["ct_coords"][1::2] += col_offset
     nct = f["nct"]
     M = EncMatrix(rows, cols, encoding, nct, f["ell_width"], f["mask"], f["row_ptr"], f["col_idx"], f["ell_col"])
     M.ct = _dev_u64((max(nct, 1), 2, ctx.L, ctx.N))

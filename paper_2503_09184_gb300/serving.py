@@ -4,8 +4,10 @@ HBM budget.
 Requests (an encrypted sparse A times an encrypted dense B) arrive over time.
 A request is admitted, in arrival order, once its ciphertexts fit the device
 budget beside the requests already in flight; its operands are then
-encrypted and lifted on the device and stay there until it completes (a
-request larger than the whole budget is rejected).  Work runs in waves: a
+encrypted and lifted on the device and stay there until it completes.  A
+request larger than the whole budget runs as column tiles (B and C split
+by columns, A with each tile) that each fit; one whose A alone does not fit
+is rejected.  Work runs in waves: a
 wave is one persistent launch (a batch plan) over row blocks taken in turn
 from every admitted request, up to a product budget, so requests that
 arrive while others are on the GPU join the next wave and their products
@@ -31,12 +33,20 @@ class Request:
     A: np.ndarray              # plaintext values of the sparse left operand (M x K)
     B: np.ndarray              # plaintext values of the dense right operand (K x Nc)
     arrival: float = 0.0       # seconds after the start of the run
+    # column tile of a larger request: its first column there and the request
+    col0: int = 0
+    parent: "Request | None" = None
     # filled in by the scheduler
     state: str = "queued"      # queued, running, done, rejected
     admitted: float | None = None
     finished: float | None = None
     next_row: int = 0
     rows_done: int = 0
+    tiles_left: int = 0
+
+    @property
+    def key(self):
+        return (self.rid, self.col0)
 
     @property
     def rows(self) -> int:
@@ -73,18 +83,38 @@ class Scheduler:
     def bytes_of(self, req: Request) -> int:
         return request_bytes(req, self.ct_bytes, self.ext_bytes)
 
+    def column_tiles(self, req: Request) -> list[Request]:
+        """the widest column tiles (B[:, c0:c1] with C's columns) that fit the
+        budget; [] if not even one column does."""
+        nnz = int((req.A != 0).sum())
+        K, M, Nc = req.B.shape[0], req.A.shape[0], req.B.shape[1]
+        per_col = K * (self.ct_bytes + self.ext_bytes) + M * self.ct_bytes
+        room = self.budget - nnz * (self.ct_bytes + self.ext_bytes)
+        width = min(Nc, room // per_col) if room > 0 else 0
+        if width < 1:
+            return []
+        return [Request(req.rid, req.A, req.B[:, c0:c0 + width], req.arrival, col0=c0, parent=req)
+                for c0 in range(0, Nc, width)]
+
     def arrive(self, req: Request):
-        if self.bytes_of(req) > self.budget:
+        if self.bytes_of(req) <= self.budget:
+            self.queue.append(req)
+            return
+        tiles = self.column_tiles(req)
+        if not tiles:
             req.state = "rejected"
             return
-        self.queue.append(req)
+        req.tiles_left = len(tiles)
+        self.queue.extend(tiles)
 
     def admit(self, now: float) -> list[Request]:
-        """admit queued requests, oldest first, while they fit the budget."""
+        """admit queued requests (or tiles), oldest first, while they fit."""
         out = []
         while self.queue and self.used + self.bytes_of(self.queue[0]) <= self.budget:
             req = self.queue.popleft()
             req.state, req.admitted = "running", now
+            if req.parent is not None and req.parent.admitted is None:
+                req.parent.state, req.parent.admitted = "running", now
             self.used += self.bytes_of(req)
             self.running.append(req)
             out.append(req)
@@ -125,6 +155,10 @@ class Scheduler:
                 self.used -= self.bytes_of(req)
                 self.running.remove(req)
                 done.append(req)
+                if req.parent is not None:
+                    req.parent.tiles_left -= 1
+                    if req.parent.tiles_left == 0:
+                        req.parent.state, req.parent.finished = "done", now
         return done
 
     def idle(self) -> bool:
@@ -152,15 +186,15 @@ class GpuExecutor:
         api = self.api
         t0 = time.perf_counter()
         A = api.encrypt_matrix(self.ctx, req.A, "csr", 2 * req.rid + 1, stream=self.stream)
-        B = api.encrypt_matrix(self.ctx, req.B, "dense", 2 * req.rid + 2, stream=self.stream)
+        B = api.encrypt_matrix(self.ctx, req.B, "dense", 2 * req.rid + 2, stream=self.stream, col_offset=req.col0)
         C = api.result_matrix(self.ctx, req.A.shape[0], req.B.shape[1])
         self.stream.synchronize()
-        self.admit_s[req.rid] = time.perf_counter() - t0
-        self.mats[req.rid] = (A, B, C)
+        self.admit_s[req.rid] = self.admit_s.get(req.rid, 0.0) + time.perf_counter() - t0
+        self.mats[req.key] = (A, B, C)
 
     def _rows(self, req: Request, r0: int, r1: int):
         api, S = self.api, self.S
-        A, B, C = self.mats[req.rid]
+        A, B, C = self.mats[req.key]
         p0, p1 = int(A.row_ptr[r0]), int(A.row_ptr[r1])
         rp = np.ascontiguousarray(A.row_ptr[r0:r1 + 1] - p0, dtype=np.int32)
         ci = np.ascontiguousarray(A.col_idx[p0:p1], dtype=np.int32) if p1 > p0 else np.zeros(1, np.int32)
@@ -185,11 +219,12 @@ class GpuExecutor:
         S.sfhe_plan_destroy(plan)
         return products
 
-    def result(self, req: Request):
-        return self.mats[req.rid][2]
+    def result(self, req: Request, col0: int = 0):
+        """C of a request, or of its column tile starting at col0."""
+        return self.mats[(req.rid, col0)][2]
 
     def release(self, req: Request):
-        self.mats.pop(req.rid, None)
+        self.mats.pop(req.key, None)
 
 
 def serve(requests: list[Request], executor, budget_bytes: int, wave_products: int, ct_bytes: int,

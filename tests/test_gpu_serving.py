@@ -36,3 +36,26 @@ def test_requests_alone_and_in_the_mix_are_identical():
         assert (api.to_coeff(ctx, C_mix.ct, n) == api.to_coeff(ctx, C_alone.ct, n)).all(), r.rid
         want = ((r.A @ r.B + W.T_PLAIN // 2) % W.T_PLAIN) - W.T_PLAIN // 2
         assert (api.decrypt(ctx, C_mix) == want).all()
+
+
+def test_column_tiles_equal_the_untiled_request():
+    """A request over the budget runs as column tiles; every tile's C equals
+    the matching columns of the request run alone, limb for limb."""
+    api, S = gpu_modules()
+    from paper_2503_09184_gb300 import serving as SV
+    ctx = gpu_ctx(4096, 2, 0)
+    A, B = W.operands(W.MatmulShape(6, 8, 10, 0.4, -16, 16, 300))
+    req = SV.Request(7, A, B, arrival=0.0)
+    ct_b, ext_b = 2 * ctx.L * ctx.N * 8, 2 * ctx.K * ctx.N * 4
+    nnz = int((A != 0).sum())
+    budget = nnz * (ct_b + ext_b) + 4 * (8 * (ct_b + ext_b) + 6 * ct_b)      # four columns per tile
+    ex = SV.GpuExecutor(ctx)
+    out = SV.serve([req], ex, budget, wave_products=64, ct_bytes=ct_b, ext_bytes=ext_b, keep_results=True)
+    assert out["done"] == 1 and req.state == "done"
+    Ae = api.encrypt_matrix(ctx, A, "csr", 2 * req.rid + 1)
+    Be = api.encrypt_matrix(ctx, B, "dense", 2 * req.rid + 2)
+    whole = api.to_coeff(ctx, api.matmul(ctx, Ae, Be).ct, 60).reshape(6, 10, 2, ctx.L, ctx.N)
+    for c0 in (0, 4, 8):
+        w = min(4, 10 - c0)
+        tile = api.to_coeff(ctx, ex.result(req, c0).ct, 6 * w).reshape(6, w, 2, ctx.L, ctx.N)
+        assert (tile == whole[:, c0:c0 + w]).all(), c0

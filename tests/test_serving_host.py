@@ -84,13 +84,13 @@ class FakeExecutor:
         self.admitted = []
 
     def admit(self, req):
-        self.admitted.append(req.rid)
-        self.rows[req.rid] = []
+        self.admitted.append(req.key)
+        self.rows[req.key] = []
 
     def run_wave(self, blocks):
         n = 0
         for req, r0, r1 in blocks:
-            self.rows[req.rid].extend(range(r0, r1))
+            self.rows[req.key].extend(range(r0, r1))
             n += int(req.row_products()[r0:r1].sum())
         return n
 
@@ -105,8 +105,40 @@ def test_serve_loop_with_fake_executor():
     out = serve(reqs, ex, budget_bytes=2 * one, wave_products=8, ct_bytes=CT, ext_bytes=EXT)
     assert out["done"] == 5 and out["rejected"] == 0
     assert out["products"] == sum(r.products for r in reqs)
-    assert ex.admitted == [0, 1, 2, 3, 4]
+    assert ex.admitted == [(i, 0) for i in range(5)]
     for r in reqs:
-        assert ex.rows[r.rid] == list(range(r.rows))
+        assert ex.rows[r.key] == list(range(r.rows))
         assert r.finished >= r.arrival
     assert out["p99_s"] >= out["p50_s"] >= 0.0
+
+
+def test_over_budget_request_runs_as_column_tiles():
+    big = _req(0, 6, 5, 9, density=0.8)
+    small = _req(1, 3, 4, 2, arrival=0.0)
+    nnz = int((big.A != 0).sum())
+    # room for A and three columns of B and C, not for all nine
+    budget = nnz * (CT + EXT) + 3 * (5 * (CT + EXT) + 6 * CT)
+    assert request_bytes(big, CT, EXT) > budget
+    s = Scheduler(budget_bytes=budget, wave_products=50, ct_bytes=CT, ext_bytes=EXT)
+    s.arrive(big)
+    s.arrive(small)
+    tiles = [t for t in s.queue if t.parent is big]
+    assert [t.col0 for t in tiles] == [0, 3, 6] and big.tiles_left == 3
+    assert all(t.B.shape[1] == 3 and (t.B == big.B[:, t.col0:t.col0 + 3]).all() for t in tiles)
+    assert all(request_bytes(t, CT, EXT) <= budget for t in tiles)
+    t = 0.0
+    while not s.idle():
+        s.admit(t)
+        assert s.used <= budget
+        s.complete(s.next_wave(), t)
+        t += 1.0
+    assert big.state == "done" and big.tiles_left == 0 and small.state == "done"
+    assert big.finished == max(x.finished for x in tiles)
+    assert s.used == 0
+
+
+def test_request_whose_left_operand_alone_exceeds_the_budget_is_rejected():
+    big = _req(0, 8, 8, 2, density=1.0)
+    s = Scheduler(budget_bytes=64 * (CT + EXT) - 1, wave_products=10, ct_bytes=CT, ext_bytes=EXT)
+    s.arrive(big)
+    assert big.state == "rejected" and not s.queue
