@@ -517,6 +517,7 @@ def run_serve(args):
                       "rejected": out["rejected"], "products": out["products"], "waves": out["waves"],
                       "ct_mults_per_s": out["ct_mults_per_s"], "busy_ct_mults_per_s": out["products"] / out["busy_s"],
                       "p50_s": out["p50_s"], "p99_s": out["p99_s"], "makespan_s": out["makespan_s"],
+                      "busy_s": out["busy_s"], "admission_s": sum(ex.admit_s.values()),
                       "plain_one_at_a_time": {"p50_s": plain["p50_s"], "p99_s": plain["p99_s"],
                                               "ct_mults_per_s": plain["ct_mults_per_s"]}})
     best = max(sweep, key=lambda d: d["ct_mults_per_s"] or 0)

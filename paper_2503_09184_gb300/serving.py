@@ -6,8 +6,9 @@ A request is admitted, in arrival order, once its ciphertexts fit the device
 budget beside the requests already in flight; its operands are then
 encrypted and lifted on the device and stay there until it completes.  A
 request larger than the whole budget runs as column tiles (B and C split
-by columns, A with each tile) that each fit; one whose A alone does not fit
-is rejected.  Work runs in waves: a
+by columns) that each fit beside its A, which is encrypted once and stays
+resident until the last tile completes; one whose A alone does not fit is
+rejected.  Work runs in waves: a
 wave is one persistent launch (a batch plan) over row blocks taken in turn
 from every admitted request, up to a product budget, so requests that
 arrive while others are on the GPU join the next wave and their products
@@ -43,6 +44,7 @@ class Request:
     next_row: int = 0
     rows_done: int = 0
     tiles_left: int = 0
+    a_resident: bool = False
 
     @property
     def key(self):
@@ -61,11 +63,20 @@ class Request:
         return int(self.row_products().sum())
 
 
+def a_bytes(req: Request, ct_bytes: int, ext_bytes: int) -> int:
+    """device bytes of A: its nonzeros as ciphertexts plus lifted limbs."""
+    return int((req.A != 0).sum()) * (ct_bytes + ext_bytes)
+
+
+def bc_bytes(req: Request, ct_bytes: int, ext_bytes: int) -> int:
+    """device bytes of B (ciphertexts plus lifted limbs) and C (ciphertexts)."""
+    return req.B.size * (ct_bytes + ext_bytes) + req.A.shape[0] * req.B.shape[1] * ct_bytes
+
+
 def request_bytes(req: Request, ct_bytes: int, ext_bytes: int) -> int:
     """device bytes a request holds while admitted: A's nonzeros and all of B
     as ciphertexts plus lifted limbs, and C as ciphertexts."""
-    nnz = int((req.A != 0).sum())
-    return (nnz + req.B.size) * (ct_bytes + ext_bytes) + req.A.shape[0] * req.B.shape[1] * ct_bytes
+    return a_bytes(req, ct_bytes, ext_bytes) + bc_bytes(req, ct_bytes, ext_bytes)
 
 
 class Scheduler:
@@ -81,7 +92,12 @@ class Scheduler:
         self._turn = 0
 
     def bytes_of(self, req: Request) -> int:
-        return request_bytes(req, self.ct_bytes, self.ext_bytes)
+        """bytes admitting req adds: a tile adds its B and C blocks, plus its
+        request's A if that is not resident yet."""
+        if req.parent is None:
+            return request_bytes(req, self.ct_bytes, self.ext_bytes)
+        n = bc_bytes(req, self.ct_bytes, self.ext_bytes)
+        return n if req.parent.a_resident else n + a_bytes(req.parent, self.ct_bytes, self.ext_bytes)
 
     def column_tiles(self, req: Request) -> list[Request]:
         """the widest column tiles (B[:, c0:c1] with C's columns) that fit the
@@ -97,7 +113,7 @@ class Scheduler:
                 for c0 in range(0, Nc, width)]
 
     def arrive(self, req: Request):
-        if self.bytes_of(req) <= self.budget:
+        if request_bytes(req, self.ct_bytes, self.ext_bytes) <= self.budget:
             self.queue.append(req)
             return
         tiles = self.column_tiles(req)
@@ -113,9 +129,11 @@ class Scheduler:
         while self.queue and self.used + self.bytes_of(self.queue[0]) <= self.budget:
             req = self.queue.popleft()
             req.state, req.admitted = "running", now
-            if req.parent is not None and req.parent.admitted is None:
-                req.parent.state, req.parent.admitted = "running", now
             self.used += self.bytes_of(req)
+            if req.parent is not None:
+                if req.parent.admitted is None:
+                    req.parent.state, req.parent.admitted = "running", now
+                req.parent.a_resident = True
             self.running.append(req)
             out.append(req)
         return out
@@ -152,13 +170,18 @@ class Scheduler:
             req.rows_done += r1 - r0
             if req.rows_done == req.rows and req.state == "running":
                 req.state, req.finished = "done", now
-                self.used -= self.bytes_of(req)
                 self.running.remove(req)
                 done.append(req)
-                if req.parent is not None:
-                    req.parent.tiles_left -= 1
-                    if req.parent.tiles_left == 0:
-                        req.parent.state, req.parent.finished = "done", now
+                if req.parent is None:
+                    self.used -= request_bytes(req, self.ct_bytes, self.ext_bytes)
+                    continue
+                self.used -= bc_bytes(req, self.ct_bytes, self.ext_bytes)
+                req.parent.tiles_left -= 1
+                if req.parent.tiles_left == 0:
+                    req.parent.state, req.parent.finished = "done", now
+                    req.parent.a_resident = False
+                    self.used -= a_bytes(req.parent, self.ct_bytes, self.ext_bytes)
+                    done.append(req.parent)
         return done
 
     def idle(self) -> bool:
@@ -178,14 +201,21 @@ class GpuExecutor:
         self.flags = api.PERSISTENT | (api.LAZY if lazy else 0)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.mats = {}
+        self.a_cache = {}
         self.admit_s = {}
 
     def admit(self, req: Request):
         """encrypt and lift the request's operands on the device (the client's
-        upload); the time it takes is kept in self.admit_s[rid]."""
+        upload); a tile reuses its request's A.  The time it takes is kept in
+        self.admit_s[rid]."""
         api = self.api
         t0 = time.perf_counter()
-        A = api.encrypt_matrix(self.ctx, req.A, "csr", 2 * req.rid + 1, stream=self.stream)
+        if req.parent is not None and req.rid in self.a_cache:
+            A = self.a_cache[req.rid]
+        else:
+            A = api.encrypt_matrix(self.ctx, req.A, "csr", 2 * req.rid + 1, stream=self.stream)
+            if req.parent is not None:
+                self.a_cache[req.rid] = A
         B = api.encrypt_matrix(self.ctx, req.B, "dense", 2 * req.rid + 2, stream=self.stream, col_offset=req.col0)
         C = api.result_matrix(self.ctx, req.A.shape[0], req.B.shape[1])
         self.stream.synchronize()
@@ -224,7 +254,11 @@ class GpuExecutor:
         return self.mats[(req.rid, col0)][2]
 
     def release(self, req: Request):
+        """drop a finished request's (or tile's) device buffers; a request
+        split into tiles also drops its shared A."""
         self.mats.pop(req.key, None)
+        if req.tiles_left == 0 and req.parent is None:
+            self.a_cache.pop(req.rid, None)
 
 
 def serve(requests: list[Request], executor, budget_bytes: int, wave_products: int, ct_bytes: int,

@@ -126,7 +126,11 @@ def test_over_budget_request_runs_as_column_tiles():
     assert [t.col0 for t in tiles] == [0, 3, 6] and big.tiles_left == 3
     assert all(t.B.shape[1] == 3 and (t.B == big.B[:, t.col0:t.col0 + 3]).all() for t in tiles)
     assert all(request_bytes(t, CT, EXT) <= budget for t in tiles)
-    t = 0.0
+    from paper_2503_09184_gb300.serving import a_bytes, bc_bytes
+    first = s.admit(0.0)
+    assert first == [tiles[0]] and big.a_resident                 # A charged once, with the first tile
+    assert s.used == a_bytes(big, CT, EXT) + bc_bytes(tiles[0], CT, EXT)
+    t = 1.0
     while not s.idle():
         s.admit(t)
         assert s.used <= budget
