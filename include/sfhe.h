@@ -147,7 +147,8 @@ sfhe_status sfhe_cdt_table(double sigma, uint64_t* T20);
 
 /* ---------------------------------------------------------- operands --- */
 /* Structure of a plaintext matrix (host values[rows*cols], row-major) under
- * an encoding: fills *nct and *ell_width. */
+ * an encoding (Sec. 3.3.2: the naive sparse mask, CSR, ELLPACK): fills *nct
+ * and *ell_width. */
 sfhe_status sfhe_encode_count(const int64_t* values, int32_t rows, int32_t cols, int32_t encoding, int32_t* nct,
                               int32_t* ell_width);
 /* Fills the structure arrays (each may be NULL when the encoding has none)
@@ -158,12 +159,14 @@ sfhe_status sfhe_encode_fill(const int64_t* values, int32_t rows, int32_t cols, 
                              int32_t* row_ptr, int32_t* col_idx, int32_t* ell_col, int64_t* ct_values,
                              int32_t* ct_coords);
 
-/* Secret-key encryption: ct[n] (device, [n][2][L][N], NTT form) encrypts
+/* Secret-key BFV encryption (the scheme of Sec. 3.1, one element per
+ * ciphertext as in the c = 1 setting of Sec. 3.2): ct[n] (device, [n][2][L][N], NTT form) encrypts
  * values[n] (host) in the constant coefficient; the randomness of
  * ciphertext n is drawn from the stream (matrix_id, coords[2n], coords[2n+1]). */
 sfhe_status sfhe_encrypt(sfhe_ctx* ctx, const int64_t* values, const int32_t* coords, int64_t n, uint64_t matrix_id,
                          uint64_t* ct, void* stream);
-/* Exact centred lift to the tensor base: ext[n] (device, uint32) from ct[n]
+/* Exact centred lift to the tensor base (the first step of the BFV multiply
+ * of Alg. 1, done once per ciphertext): ext[n] (device, uint32) from ct[n]
  * (device): every coefficient's representative in (-Q/2, Q/2) reduced mod
  * each b_k, NTT form.  Needs sfhe_lift_workspace_size() bytes of device
  * workspace (a smaller workspace processes the ciphertexts in chunks). */
@@ -186,15 +189,19 @@ sfhe_status sfhe_export_relin_key(sfhe_ctx* ctx, uint64_t* out, void* stream);
 /* Workspace (device bytes) for n matmuls A[m] x B[m] under `flags`. */
 sfhe_status sfhe_matmul_workspace_size(const sfhe_ctx* ctx, int32_t n, const sfhe_matrix* A, const sfhe_matrix* B,
                                        uint32_t flags, size_t* bytes);
-/* C = A x B with the k-loop over every k (A must be DENSE-encoded). */
+/* C = A x B with the k-loop over every k: the naive dense loop of Alg. 1
+ * (Sec. 3.3.1), each product multiplied, relinearised and added (A must be
+ * DENSE-encoded). */
 sfhe_status sfhe_matmul_dense(sfhe_ctx* ctx, const sfhe_matrix* A, const sfhe_matrix* B, sfhe_matrix* C, uint32_t flags,
                               void* work, size_t work_bytes, void* stream);
 /* C = A x B with the k-loop over the nonzeros of A as `encoding` lists them
- * (A must carry that encoding; EINVAL otherwise). */
+ * (Sec. 3.3.2; A must carry that encoding; EINVAL otherwise). */
 sfhe_status sfhe_matmul_sparse(sfhe_ctx* ctx, const sfhe_matrix* A, const sfhe_matrix* B, int32_t encoding,
                                sfhe_matrix* C, uint32_t flags, void* work, size_t work_bytes, void* stream);
 /* n independent matmuls C[m] = A[m] x B[m] (each A in its own encoding) in
- * one execution. */
+ * one execution.  No counterpart in the paper, whose Sec. 3.4 spreads one
+ * matmul's output entries over CPU threads; here the entries of all n
+ * matmuls share one persistent launch. */
 sfhe_status sfhe_matmul_batch(sfhe_ctx* ctx, int32_t n, const sfhe_matrix* A, const sfhe_matrix* B, sfhe_matrix* C,
                               uint32_t flags, void* work, size_t work_bytes, void* stream);
 
