@@ -704,15 +704,23 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                 const u32* src[SM];
 #pragma unroll
                 for (int m = 0; m < SM; m++) src[m] = T + (size_t)p * K * N + k + m * NTH;
+                // the sums so far, loaded ahead of the arithmetic so that their
+                // latency overlaps it
+                u64 prev[SM][L];
+#pragma unroll
+                for (int m = 0; m < SM; m++) {
+#pragma unroll
+                    for (int i = 0; i < L; i++)
+                        prev[m][i] = pr == 0 ? 0 : acc[((size_t)p * L + i) * N + k + m * NTH];
+                }
                 u64 d[SM][L];
                 scale_round_m<L, K, SM, LZ>(src, N, c, d);
 #pragma unroll
                 for (int m = 0; m < SM; m++) {
 #pragma unroll
                     for (int i = 0; i < L; i++) {
-                        u64* ap = acc + ((size_t)p * L + i) * N + k + m * NTH;
-                        if (pr == 0) *ap = d[m][i];
-                        else *ap = (LZ && fold ? barrett64(*ap, c.m[i]) : *ap) + d[m][i];
+                        const u64 base = LZ && fold ? barrett64(prev[m][i], c.m[i]) : prev[m][i];
+                        acc[((size_t)p * L + i) * N + k + m * NTH] = base + d[m][i];
                     }
                 }
             };
