@@ -168,6 +168,14 @@ SFHE_DEV u32 reduce61(u64 x, Mod32 m)
     return csub32(r, m.b);
 }
 
+// Montgomery reduction: x 2^-32 mod b, in [0, 2b), for x < b 2^32, with
+// binv = -b^-1 mod 2^32 (x + q b is divisible by 2^32 for q = x binv mod 2^32).
+SFHE_DEV u32 redc32(u64 x, Mod32 m)
+{
+    const u32 q = (u32)x * m.binv;
+    return (u32)((x + (u64)q * m.b) >> 32);
+}
+
 // x mod b for any 64-bit x with mu64 = floor(2^64 / b) (estimate at most 1 low).
 SFHE_DEV u32 reduce64b(u64 x, Mod32 m)
 {

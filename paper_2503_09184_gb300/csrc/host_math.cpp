@@ -286,6 +286,10 @@ bool fill_constants(RnsConsts& rc)
         const uint64_t b = rc.mb[k].b;
         rc.mb[k].mu61 = (uint32_t)((1ULL << 61) / b);
         rc.mb[k].mu64 = (uint64_t)(((u128)1 << 64) / b);
+        uint32_t inv = 1;  // b^-1 mod 2^32 by Newton's iteration (b odd)
+        for (int it = 0; it < 5; ++it) inv *= 2u - (uint32_t)b * inv;
+        rc.mb[k].binv = 0u - inv;
+        rc.mb[k].pad = 0;
     }
 
     // ---- Q side, lift Q -> B and the exact-rounding words
@@ -387,7 +391,7 @@ bool fill_constants(RnsConsts& rc)
 void fold_tensor_scaling(RnsConsts& rc)
 {
     for (int k = 0; k < rc.K; ++k) {
-        const uint64_t b = rc.mb[k].b, h = rc.bhat_inv[k].w;
+        const uint64_t b = rc.mb[k].b, h = mulm(rc.bhat_inv[k].w, (1ULL << 32) % b, b);
         rc.ninv_bx[k] = shoup32_of(mulm(rc.ninv_b[k].w, h, b), b);
         rc.wlast_bx[k] = shoup32_of(mulm(rc.wlast_b[k].w, h, b), b);
     }

@@ -24,8 +24,9 @@ void twiddles32(uint32_t b, uint32_t N, uint32_t* out4N, Shoup32* ninv, Shoup32*
 // rc.mb[].b, rc.L, rc.K, rc.t, rc.N set).  Returns false if a size
 // margin does not hold.
 bool fill_constants(RnsConsts& rc);
-// ninv_bx / wlast_bx from ninv_b, wlast_b (twiddles32) and bhat_inv
-// (fill_constants).
+// ninv_bx / wlast_bx = ninv_b, wlast_b (twiddles32) times 2^32 bhat_inv
+// (fill_constants): the tensor stage's inverse NTT takes its input in
+// Montgomery form and outputs x~_k.
 void fold_tensor_scaling(RnsConsts& rc);
 
 }  // namespace sfhe

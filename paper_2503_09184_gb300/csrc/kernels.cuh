@@ -26,14 +26,16 @@ struct Cfg {
 // elementwise pieces
 // ------------------------------------------------------------------------
 // coefficient e of tensor polynomial `poly` (0: a0 b0, 1: a0 b1 + a1 b0,
-// 2: a1 b1) mod b; a, b point at limb k of c0 of lifted ciphertexts, off1
-// is the distance to the same limb of c1.
+// 2: a1 b1) times 2^-32 mod b, in [0, 2b) (Montgomery form: the tensor
+// stage's inverse NTT multiplies the 2^32 back in with its last-stage
+// constants); a, b point at limb k of c0 of lifted ciphertexts, off1 is the
+// distance to the same limb of c1.
 SFHE_DEV u32 tensor_coeff32(int poly, const u32* __restrict__ a, const u32* __restrict__ b, size_t off1, int e,
                             Mod32 m)
 {
-    if (poly == 0) return reduce61((u64)__ldg(a + e) * __ldg(b + e), m);
-    if (poly == 2) return reduce61((u64)__ldg(a + off1 + e) * __ldg(b + off1 + e), m);
-    return reduce61((u64)__ldg(a + e) * __ldg(b + off1 + e) + (u64)__ldg(a + off1 + e) * __ldg(b + e), m);
+    if (poly == 0) return redc32((u64)__ldg(a + e) * __ldg(b + e), m);
+    if (poly == 2) return redc32((u64)__ldg(a + off1 + e) * __ldg(b + off1 + e), m);
+    return redc32((u64)__ldg(a + e) * __ldg(b + off1 + e) + (u64)__ldg(a + off1 + e) * __ldg(b + e), m);
 }
 
 // Exact decision of round(F) + K near a half-integer: with the words of
@@ -776,9 +778,9 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                         for (int v = 0; v < R; v++) {
                             const int i = NB::lane_idx(v, tid);
                             const u64 a0 = s0[i], a1 = s1[i], b0 = s2[i], b1 = s3[i];
-                            x[0][v] = reduce61(a0 * b0, m);
-                            x[1][v] = reduce61(a0 * b1 + a1 * b0, m);
-                            x[2][v] = reduce61(a1 * b1, m);
+                            x[0][v] = redc32(a0 * b0, m);
+                            x[1][v] = redc32(a0 * b1 + a1 * b0, m);
+                            x[2][v] = redc32(a1 * b1, m);
                         }
                     }
                     __syncthreads();  // every thread has read the slots
@@ -844,11 +846,11 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                         for (int v = 0; v < R; v++) {
                             const int i = NB::lane_idx(v, tid);
                             const u64 a0 = s0[i], a1 = s1[i], b0 = s2[i], b1 = s3[i];
-                            const u32 t0 = reduce61(a0 * b0, m), t1 = reduce61(a0 * b1 + a1 * b0, m),
-                                      t2 = reduce61(a1 * b1, m);
-                            x[0][v] = p == 0 ? t0 : csub32(x[0][v] + t0, m.b);
-                            x[1][v] = p == 0 ? t1 : csub32(x[1][v] + t1, m.b);
-                            x[2][v] = p == 0 ? t2 : csub32(x[2][v] + t2, m.b);
+                            const u32 t0 = redc32(a0 * b0, m), t1 = redc32(a0 * b1 + a1 * b0, m),
+                                      t2 = redc32(a1 * b1, m);
+                            x[0][v] = p == 0 ? t0 : csub32(x[0][v] + t0, 2 * m.b);
+                            x[1][v] = p == 0 ? t1 : csub32(x[1][v] + t1, 2 * m.b);
+                            x[2][v] = p == 0 ? t2 : csub32(x[2][v] + t2, 2 * m.b);
                         }
                         __syncthreads();  // every thread has read the slots
                         if (more) {
@@ -911,8 +913,8 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
 #pragma unroll
                             for (int v = 0; v < R; v++) {
                                 const int i = NB::lane_idx(v, tid);
-                                const u32 t = reduce61((u64)sa[i] * sb[i], m);
-                                x[v] = r == 3 ? csub32(x[v] + t, m.b) : t;
+                                const u32 t = redc32((u64)sa[i] * sb[i], m);
+                                x[v] = r == 3 ? csub32(x[v] + t, 2 * m.b) : t;
                             }
                             __syncthreads();  // every thread has read the slots
                             if (st + 1 < total) issue2(st + 1);
@@ -975,8 +977,8 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
 #pragma unroll
                                 for (int v = 0; v < R; v++) {
                                     const int i = NB::lane_idx(v, tid);
-                                    const u32 t = reduce61((u64)sa[i] * sb[i], m);
-                                    x[v] = fresh ? t : csub32(x[v] + t, m.b);
+                                    const u32 t = redc32((u64)sa[i] * sb[i], m);
+                                    x[v] = fresh ? t : csub32(x[v] + t, 2 * m.b);
                                 }
                                 __syncthreads();  // every thread has read the slots
                                 if (more) {
@@ -1037,7 +1039,7 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                             for (int v = 0; v < R; v++) {
                                 const u32 t = tensor_coeff32(p, a + (size_t)k * N, b + (size_t)k * N, (size_t)K * N,
                                                              NB::lane_idx(v, tid), m);
-                                x[v] = q == 0 ? t : csub32(x[v] + t, m.b);
+                                x[v] = q == 0 ? t : csub32(x[v] + t, 2 * m.b);
                             }
                         }
                         NB::inverse(x, sm32, tid, tw, m.b, c.ninv_bx[k].w, c.ninv_bx[k].ws, c.wlast_bx[k].w,

@@ -41,6 +41,8 @@ struct Mod32 {
     u32 b;
     u32 mu61;
     u64 mu64;
+    u32 binv;  // -b^-1 mod 2^32 (Montgomery reduction)
+    u32 pad;
 };
 
 // A constant multiplier w < b with its Shoup companion floor(w 2^32 / b).
@@ -63,8 +65,9 @@ struct RnsConsts {
     const u32* twb;
     ShoupC ninv[SFHE_MAX_L], wlast[SFHE_MAX_L];
     Shoup32 ninv_b[SFHE_MAX_K], wlast_b[SFHE_MAX_K];
-    // the same multiplied by (B/b_k)^-1: an inverse NTT with these outputs
-    // x~_k = [x_k (B/b_k)^-1]_{b_k} directly (the tensor stage)
+    // the same multiplied by 2^32 (B/b_k)^-1: an inverse NTT of the tensor in
+    // Montgomery form with these outputs x~_k = [x_k (B/b_k)^-1]_{b_k}
+    // directly (the tensor stage)
     Shoup32 ninv_bx[SFHE_MAX_K], wlast_bx[SFHE_MAX_K];
 
     // centred lift Q -> B:  a = sum_i a~_i (Q/q_i) - v Q,
