@@ -832,7 +832,11 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                 const int Gg = min(G, en.count - g * G);
                 for (int k = 0; k < K; k++) {
                     const Mod32 m = c.mb[k];
-                    u32 x[3][R];
+                    // the group's tensor polynomials are summed in the idle
+                    // exchange buffers (each thread at its own interleaved
+                    // positions), not in registers kept across the copy waits
+                    u32* acc3 = sm32;
+                    __syncthreads();  // every thread is past the last transform's exchanges
                     for (int p = 0; p < Gg; p++) {
                         if (!wait_bar(0) || !wait_bar(1)) {
                             abort_cta();
@@ -848,9 +852,12 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                             const u64 a0 = s0[i], a1 = s1[i], b0 = s2[i], b1 = s3[i];
                             const u32 t0 = redc32(a0 * b0, m), t1 = redc32(a0 * b1 + a1 * b0, m),
                                       t2 = redc32(a1 * b1, m);
-                            x[0][v] = p == 0 ? t0 : csub32(x[0][v] + t0, 2 * m.b);
-                            x[1][v] = p == 0 ? t1 : csub32(x[1][v] + t1, 2 * m.b);
-                            x[2][v] = p == 0 ? t2 : csub32(x[2][v] + t2, 2 * m.b);
+                            u32* q0 = acc3 + i;
+                            u32* q1 = acc3 + NB::SMEM_WORDS + i;
+                            u32* q2 = acc3 + 2 * NB::SMEM_WORDS + i;
+                            *q0 = p == 0 ? t0 : csub32(*q0 + t0, 2 * m.b);
+                            *q1 = p == 0 ? t1 : csub32(*q1 + t1, 2 * m.b);
+                            *q2 = p == 0 ? t2 : csub32(*q2 + t2, 2 * m.b);
                         }
                         __syncthreads();  // every thread has read the slots
                         if (more) {
@@ -858,6 +865,12 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                             issue(1);
                             more = advance();
                         }
+                    }
+                    u32 x[3][R];
+#pragma unroll
+                    for (int j = 0; j < 3; j++) {
+#pragma unroll
+                        for (int v = 0; v < R; v++) x[j][v] = acc3[j * NB::SMEM_WORDS + NB::lane_idx(v, tid)];
                     }
                     const u32* tw = c.twb + (size_t)k * 4 * N;
                     NB::template inverse_m<3>(x, sm32, tid, tw, m.b, c.ninv_bx[k].w, c.ninv_bx[k].ws,
