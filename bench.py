@@ -77,6 +77,9 @@ def parse():
     ap.add_argument("--lazy", action="store_true",
                     help="grouped accumulate-then-round (SFHE_EXEC_LAZY): a different valid ciphertext, "
                          "not the paper's per-product order")
+    ap.add_argument("--b-sparse", action="store_true",
+                    help="sweep / layer: B drawn with the same sparsity and MASK-encoded, so products are skipped "
+                         "where either operand is zero (naive sparse over both operands, Sec. 3.3.2)")
     ap.add_argument("--mixed-budget-gb", type=float, default=60.0, help="device bytes per slot for the mixed batch")
     return ap.parse_args()
 
@@ -170,13 +173,13 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- CPU oracle ---
-def cpu_oracle_rate(ring, A, B, n_products: int, seed: int = 0) -> dict:
+def cpu_oracle_rate(ring, A, B, n_products: int, seed: int = 0, skip_b_zeros: bool = False) -> dict:
     """The oracle as it stands (OpenMP over the host cores) on a bounded
     sample: the first n_products nonzero products of row-major order."""
     from oracle import oracle as O
     octx = O.OracleCtx(ring.N, ring.L, seed=seed)
     pairs = [(i, k, j) for i in range(A.shape[0]) for k in range(A.shape[1]) if A[i, k] != 0
-             for j in range(B.shape[1])][:n_products]
+             for j in range(B.shape[1]) if not (skip_b_zeros and B[k, j] == 0)][:n_products]
     ops = [(octx.encrypt(int(A[i, k]), 1, i, k), octx.encrypt(int(B[k, j]), 2, k, j)) for i, k, j in pairs]
     t0 = time.perf_counter()
     acc = np.zeros(octx.ct_shape, dtype=np.uint64)
@@ -194,10 +197,11 @@ def run_reference(args):
         return
     ring, vals, workload, sparsity = job_of(args)
     A, B = vals[0]
+    skip_b_zeros = args.b_sparse
     from oracle import oracle as O
     octx = O.OracleCtx(ring.N, ring.L, seed=0)
     pairs = [(i, k, j) for i in range(A.shape[0]) for k in range(A.shape[1]) if A[i, k] != 0
-             for j in range(B.shape[1])]
+             for j in range(B.shape[1]) if not (skip_b_zeros and B[k, j] == 0)]
     per_step = 2
     need = (args.warmup + args.steps) * per_step
     ops = [(octx.encrypt(int(A[i, k]), 1, i, k), octx.encrypt(int(B[k, j]), 2, k, j)) for i, k, j in pairs[:need]]
@@ -248,12 +252,15 @@ def job_of(args):
             M, K, Nc = (int(x) for x in args.shape.split(","))
             shape = W.MatmulShape(M, K, Nc, s, shape.lo, shape.hi, shape.seed)
             name = f"sweep-{M}x{K}x{Nc}-s{s:g}"
-        return W.SWEEP_RING, [W.operands(shape)], name, s
+        if args.b_sparse:
+            name += "-bmask"
+        return W.SWEEP_RING, [W.operands(shape, b_sparse=args.b_sparse)], name, s
     if wl == "tiny":
         return W.TINY_RING, [W.operands(W.TINY)], "tiny-8x8x8-s0.5", W.TINY.sparsity
     if wl == "layer":
         s = 0.5 if args.sparsity is None else args.sparsity
-        return W.LAYER_RING, [W.operands(W.layer(s))], f"layer-128x256x16-s{s:g}", s
+        return (W.LAYER_RING, [W.operands(W.layer(s), b_sparse=args.b_sparse)],
+                f"layer-128x256x16-s{s:g}" + ("-bmask" if args.b_sparse else ""), s)
     # mixed: the matmuls of the 64-matmul distribution in order, each taken
     # if it still fits the device budget of one slot (ciphertexts and lifted
     # limbs)
@@ -277,12 +284,30 @@ def lift_launches(nct: int, chunk: int = 256) -> int:
     return 3 * math.ceil(nct / chunk)
 
 
+def operand_memory(S, ring, vals) -> dict:
+    """Bytes the left operands would hold under each encoding (ciphertexts,
+    their lift, plaintext structure; Sec. 4.6's memory per scheme), from
+    sfhe_matrix_bytes on the encoders' counts."""
+    out = {}
+    for name, e in S.ENCODINGS.items():
+        tot = {"ct": 0, "ext": 0, "meta": 0}
+        for a, _ in vals:
+            nct, width = S.sfhe_encode_count(a, e)
+            m = S.sfhe_matrix_bytes(ring.N, ring.L, S.sfhe_matrix(a.shape[0], a.shape[1], e, nct, width, None, None,
+                                                                  None, None, None, None))
+            for k in tot:
+                tot[k] += m[k]
+        out[name] = tot
+    return out
+
+
 class Slot:
     """One full set of device operands, results and workspaces for a step."""
 
-    def __init__(self, api, S, torch, ctx, vals, stream, lazy=False):
+    def __init__(self, api, S, torch, ctx, vals, stream, lazy=False, b_encoding="dense"):
         self.As = [api.encrypt_matrix(ctx, a, ENCODING, 2 * m + 1, lift=False) for m, (a, _) in enumerate(vals)]
-        self.Bs = [api.encrypt_matrix(ctx, b, "dense", 2 * m + 2, lift=False) for m, (_, b) in enumerate(vals)]
+        self.Bs = [api.encrypt_matrix(ctx, b, b_encoding, 2 * m + 2, lift=False) for m, (_, b) in enumerate(vals)]
+        self.b_encoding = b_encoding
         for M in self.As + self.Bs:
             M.ext = api._dev_u32((max(M.nct, 1), 2, ctx.K, ctx.N))
         self.Cs = [api.result_matrix(ctx, a.shape[0], b.shape[1]) for a, b in vals]
@@ -340,7 +365,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     # setup (untimed): encryption of the operands
-    slot = Slot(api, S, torch, ctx, vals, stream, lazy=args.lazy)
+    slot = Slot(api, S, torch, ctx, vals, stream, lazy=args.lazy, b_encoding="mask" if args.b_sparse else "dense")
     ctx.check()
     probe = S.sfhe_plan_create(ctx.h, [a.desc() for a in slot.As], [b.desc() for b in slot.Bs],
                                [c.desc() for c in slot.Cs], slot.flags, slot.ws, stream)
@@ -424,8 +449,8 @@ def main():
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": workload, "matmuls": len(vals),
                    "shapes": [f"{a.shape[0]}x{a.shape[1]}x{b.shape[1]}" for a, b in vals][:8],
-                   "sparsity": sparsity, "encoding": ENCODING, "N": ring.N, "L": ring.L, "t": W.T_PLAIN,
-                   "products_per_step": products, "dense_products": dense_products,
+                   "sparsity": sparsity, "encoding": ENCODING, "b_encoding": slot.b_encoding, "N": ring.N,
+                   "L": ring.L, "t": W.T_PLAIN, "products_per_step": products, "dense_products": dense_products,
                    "l2": f"inputs larger than L2 (lifted operands: {lifted / 1e9:.1f} GB)",
                    "step": "lift A and B + work list + persistent matmul", "parallelism": f"replicas x{world}"},
         "matmul_ms": ms,
@@ -447,10 +472,11 @@ def main():
                   % ctx.lazy_group) if args.lazy else "per product (Alg. 1)",
         "clocks": clk,
         "persistent_ctas": ctas,
+        "operand_memory": operand_memory(S, ring, vals),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n_cpu = args.cpu_products or {4096: 48, 8192: 12, 16384: 2}[ring.N]
-        line["cpu_baseline"] = cpu_oracle_rate(ring, a0, b0, n_cpu)
+        line["cpu_baseline"] = cpu_oracle_rate(ring, a0, b0, n_cpu, skip_b_zeros=args.b_sparse)
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
@@ -546,7 +572,8 @@ def e2e_pipelined(args, api, S, torch, ctx, vals, slot0, products, world) -> dic
     pinned host memory.  Two slots of device buffers let step i+1's upload
     and step i-1's download run on their own streams while step i computes;
     every copy of every timed step lies inside the timed region."""
-    slots = [slot0, Slot(api, S, torch, ctx, vals, None, lazy=(slot0.flags & api.LAZY) != 0)]
+    slots = [slot0, Slot(api, S, torch, ctx, vals, None, lazy=(slot0.flags & api.LAZY) != 0,
+                         b_encoding=slot0.b_encoding)]
     h_in = [[torch.empty(M.ct.shape, dtype=torch.int64, pin_memory=True) for M in slots[0].As + slots[0].Bs]
             for _ in slots]
     for hs in h_in:
@@ -583,7 +610,9 @@ def e2e_pipelined(args, api, S, torch, ctx, vals, slot0, products, world) -> dic
         torch.cuda.synchronize()
 
     run(2)  # warm-up
-    n = max(3, args.steps)
+    # at least 6 steps, so that the pipeline's fill (the first upload) and
+    # drain (the last download) weigh as little as in a steady stream
+    n = max(6, args.steps)
     t0 = time.perf_counter()
     run(n)
     e2e_ms = 1e3 * (time.perf_counter() - t0) / n

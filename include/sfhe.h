@@ -103,7 +103,11 @@ typedef struct sfhe_plan sfhe_plan;
  * are host memory; ciphertext storage is device memory.
  *   DENSE: nct = rows*cols, ciphertext r*cols + c encrypts element (r, c).
  *   MASK:  as DENSE plus mask[rows*cols], 1 where the element is zero
- *          (B_ik = [M_ik = 0]); products with a set mask are skipped.
+ *          (B_ik = [M_ik = 0]); products with a set mask are skipped.  A
+ *          right operand may be MASK-encoded too: the sparse matmuls then
+ *          skip k wherever A[i][k] or B[k][j] is zero, the naive sparse
+ *          condition of Sec. 3.3.2 over both operands (the dense loop of
+ *          Alg. 1 still takes every k).
  *   CSR:   row_ptr[rows+1], col_idx[nct]; ciphertext t encrypts the t-th
  *          nonzero in row-major order.
  *   ELL:   ell_width slots per row, ell_col[rows*ell_width] (-1 = padding);
@@ -158,6 +162,16 @@ sfhe_status sfhe_encode_count(const int64_t* values, int32_t rows, int32_t cols,
 sfhe_status sfhe_encode_fill(const int64_t* values, int32_t rows, int32_t cols, int32_t encoding, uint8_t* mask,
                              int32_t* row_ptr, int32_t* col_idx, int32_t* ell_col, int64_t* ct_values,
                              int32_t* ct_coords);
+
+/* Memory an encoded operand holds (the per-scheme ciphertext memory of
+ * Sec. 4.6, Fig. 4), host only: *ct_bytes = nct * 2 * L * N * 8 (the
+ * ciphertexts), *ext_bytes = nct * 2 * K * N * 4 (their lift to the tensor
+ * base), *meta_bytes = the plaintext structure: 0 (DENSE), rows*cols (MASK,
+ * one byte per element), (rows + 1 + nct) * 4 (CSR), rows * ell_width * 4
+ * (ELL).  Reads only the descriptor's sizes and encoding.  Errors: EINVAL
+ * (null, bad encoding), EUNSUPPORTED (N, L), ESHAPE (negative sizes). */
+sfhe_status sfhe_matrix_bytes(uint32_t N, uint32_t L, const sfhe_matrix* M, uint64_t* ct_bytes, uint64_t* ext_bytes,
+                              uint64_t* meta_bytes);
 
 /* Secret-key BFV encryption (the scheme of Sec. 3.1, one element per
  * ciphertext as in the c = 1 setting of Sec. 3.2): ct[n] (device, [n][2][L][N], NTT form) encrypts

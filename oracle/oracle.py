@@ -11,7 +11,9 @@ The encodings follow Sec. 3.3.2 of the paper ("Exploiting Unstructured
 Sparsity in Fully Homomorphic Encrypted DNNs"):
   * naive dense (Alg. 1): every k of the shared dimension;
   * naive sparse: a plaintext mask B_ik = [A_ik == 0], products skipped where
-    the mask is set (B is dense here, so only the left mask matters);
+    the mask is set; when the right operand carries its mask too, a product
+    is skipped where either mask is set (the condition of Sec. 3.3.2 over
+    both operands; `b_mask` below);
   * CSR: nonzeros of each row with a row-pointer array and a column array;
   * ELLPACK: each row holds j = max nonzeros-per-row slots, the nonzeros first
     and encrypted zero padding after, with a parallel column matrix.
@@ -325,6 +327,17 @@ def product_set(enc: Encoded, i: int) -> list[tuple[int, int]]:
     raise ValueError(enc.encoding)
 
 
+def entry_products(enc: Encoded, i: int, j: int, b_mask: np.ndarray | None = None) -> list[tuple[int, int]]:
+    """(stored ciphertext index, k) pairs entry (i, j) multiplies: row i's
+    pairs as A's encoding lists them; with a right-operand mask
+    (b_mask[k, j] = 1 where B[k][j] == 0), those whose B element is zero are
+    skipped too.  The dense loop of Alg. 1 skips nothing."""
+    ps = product_set(enc, i)
+    if b_mask is None or enc.encoding == DENSE:
+        return ps
+    return [(t, k) for t, k in ps if not b_mask[k, j]]
+
+
 class OracleMatmul:
     """Encrypts plaintext operands and evaluates entries of C = A x B.
 
@@ -357,12 +370,13 @@ class OracleMatmul:
             self._prod[key] = self.ctx.mul_relin(self.ct_a(i, k), self.ct_b(k, j))
         return self._prod[key]
 
-    def entry(self, enc: Encoded, i: int, j: int, group: int = 1) -> np.ndarray:
+    def entry(self, enc: Encoded, i: int, j: int, group: int = 1, b_mask: np.ndarray | None = None) -> np.ndarray:
         """C[i][j]: the trivial zero ciphertext plus every listed product (in
-        ascending k); with group > 1, each run of `group` consecutive products
-        is scaled and rounded once and relinearised once."""
+        ascending k; with b_mask, only k where B[k][j] is nonzero too); with
+        group > 1, each run of `group` consecutive products is scaled and
+        rounded once and relinearised once."""
         acc = np.zeros(self.ctx.ct_shape, dtype=np.uint64)
-        ks = [k for _, k in product_set(enc, i)]
+        ks = [k for _, k in entry_products(enc, i, j, b_mask)]
         if group == 1:
             for k in ks:
                 self.ctx.add_(acc, self.product(i, k, j))

@@ -73,12 +73,10 @@ class EncMatrix:
         return S.sfhe_matrix(self.rows, self.cols, self.encoding, self.nct, self.ell_width, p(self.mask),
                               p(self.row_ptr), p(self.col_idx), p(self.ell_col), p(self.ct), p(self.ext))
 
-    def bytes(self) -> int:
-        n = 0
-        for t in (self.ct, self.ext):
-            if t is not None:
-                n += t.numel() * 8
-        return n
+    def memory(self, ctx: "Context") -> dict:
+        """bytes of the ciphertexts, of their lift and of the plaintext
+        structure this encoding holds (sfhe_matrix_bytes)."""
+        return S.sfhe_matrix_bytes(ctx.N, ctx.L, self.desc())
 
 
 def encrypt_matrix(ctx: Context, values: np.ndarray, encoding: int | str, matrix_id: int, lift: bool = True,

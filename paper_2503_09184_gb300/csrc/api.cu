@@ -245,6 +245,29 @@ extern "C" sfhe_status sfhe_encode_count(const int64_t* values, int32_t rows, in
     return SFHE_OK;
 }
 
+extern "C" sfhe_status sfhe_matrix_bytes(uint32_t N, uint32_t L, const sfhe_matrix* M, uint64_t* ct_bytes,
+                                         uint64_t* ext_bytes, uint64_t* meta_bytes)
+{
+    if (!M || !ct_bytes || !ext_bytes || !meta_bytes) return fail(SFHE_EINVAL, "null argument");
+    int logN = 0;
+    while ((1u << logN) < N) logN++;
+    if ((1u << logN) != N || logN < 1 || logN > 15 || L < 1 || L > SFHE_MAX_L)
+        return fail(SFHE_EUNSUPPORTED, "N=%u L=%u", N, L);
+    if (M->rows < 0 || M->cols < 0 || M->nct < 0 || M->ell_width < 0) return fail(SFHE_ESHAPE, "negative size");
+    const uint64_t K = (uint64_t)tensor_base_size(logN, (int)L);
+    const uint64_t nct = (uint64_t)M->nct, cells = (uint64_t)M->rows * (uint64_t)M->cols;
+    *ct_bytes = nct * 2 * L * N * 8;
+    *ext_bytes = nct * 2 * K * N * 4;
+    switch (M->encoding) {
+    case SFHE_ENC_DENSE: *meta_bytes = 0; break;
+    case SFHE_ENC_MASK: *meta_bytes = cells; break;
+    case SFHE_ENC_CSR: *meta_bytes = ((uint64_t)M->rows + 1 + nct) * 4; break;
+    case SFHE_ENC_ELL: *meta_bytes = (uint64_t)M->rows * (uint64_t)M->ell_width * 4; break;
+    default: return fail(SFHE_EINVAL, "bad encoding");
+    }
+    return SFHE_OK;
+}
+
 extern "C" sfhe_status sfhe_encode_fill(const int64_t* values, int32_t rows, int32_t cols, int32_t encoding,
                                         uint8_t* mask, int32_t* row_ptr, int32_t* col_idx, int32_t* ell_col,
                                         int64_t* ct_values, int32_t* ct_coords)
@@ -500,7 +523,8 @@ sfhe_status build(const sfhe_ctx* c, int32_t n, const sfhe_matrix* A, const sfhe
         sfhe_status st = validate_matrix(A[m], "A");
         if (st == SFHE_OK) st = validate_matrix(B[m], "B");
         if (st != SFHE_OK) return st;
-        if (B[m].encoding != SFHE_ENC_DENSE) return fail(SFHE_EINVAL, "B must be DENSE-encoded");
+        if (B[m].encoding != SFHE_ENC_DENSE && B[m].encoding != SFHE_ENC_MASK)
+            return fail(SFHE_EINVAL, "B must be DENSE- or MASK-encoded");
         if (A[m].cols != B[m].rows) return fail(SFHE_ESHAPE, "A is %dx%d, B is %dx%d", A[m].rows, A[m].cols, B[m].rows, B[m].cols);
         if (C) {
             if (C[m].rows != A[m].rows || C[m].cols != B[m].cols) return fail(SFHE_ESHAPE, "C shape mismatch");
@@ -518,12 +542,26 @@ sfhe_status build(const sfhe_ctx* c, int32_t n, const sfhe_matrix* A, const sfhe
         d.group = (P.flags & SFHE_EXEC_LAZY) ? c->rc.lazy_group : 1;
         P.mms.push_back(d);
         P.c_words.push_back((size_t)A[m].rows * B[m].cols * ctw);
+        // with a masked B the naive sparse scheme also skips k where B[k][j]
+        // is zero (Sec. 3.3.2: a product is skipped when either mask is set),
+        // so every entry gets its own list; otherwise the entries of a row
+        // share the row's list
+        const bool b_mask = B[m].encoding == SFHE_ENC_MASK && !dense_loop[m];
+        const int32_t Nc = B[m].cols;
+        std::vector<int2> row;
         for (int32_t i = 0; i < A[m].rows; i++) {
-            const int first = (int)P.rowlist.size();
-            row_pairs(A[m], i, dense_loop[m], P.rowlist);
-            const int count = (int)P.rowlist.size() - first;
-            if (count > 1024) return fail(SFHE_EUNSUPPORTED, "more than 1024 products per output entry");
-            for (int32_t j = 0; j < B[m].cols; j++) {
+            row.clear();
+            row_pairs(A[m], i, dense_loop[m], row);
+            int first = (int)P.rowlist.size();
+            if (!b_mask) P.rowlist.insert(P.rowlist.end(), row.begin(), row.end());
+            for (int32_t j = 0; j < Nc; j++) {
+                if (b_mask) {
+                    first = (int)P.rowlist.size();
+                    for (const int2& it : row)
+                        if (!B[m].mask[(int64_t)it.y * Nc + j]) P.rowlist.push_back(it);
+                }
+                const int count = b_mask ? (int)P.rowlist.size() - first : (int)row.size();
+                if (count > 1024) return fail(SFHE_EUNSUPPORTED, "more than 1024 products per output entry");
                 Entry en;
                 memset(&en, 0, sizeof(en));
                 en.mm = m;

@@ -62,6 +62,7 @@ _SIGS = {
     "sfhe_cdt_table": ([ctypes.c_double, _vp], ctypes.c_int),
     "sfhe_encode_count": ([_vp, _i32, _i32, _i32, _P(_i32), _P(_i32)], ctypes.c_int),
     "sfhe_encode_fill": ([_vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "sfhe_matrix_bytes": ([_u32, _u32, _P(sfhe_matrix), _P(_u64), _P(_u64), _P(_u64)], ctypes.c_int),
     "sfhe_encrypt": ([_vp, _vp, _vp, _i64, _u64, _vp, _vp], ctypes.c_int),
     "sfhe_lift_workspace_size": ([_vp, _i64, _P(_sz)], ctypes.c_int),
     "sfhe_lift": ([_vp, _vp, _i64, _vp, _vp, _sz, _vp], ctypes.c_int),
@@ -197,6 +198,14 @@ def sfhe_encode_fill(values: np.ndarray, encoding: int) -> dict:
                                   _ptr(out["col_idx"]), _ptr(out["ell_col"]), _ptr(out["ct_values"]),
                                   _ptr(out["ct_coords"])))
     return out
+
+
+def sfhe_matrix_bytes(N: int, L: int, M) -> dict:
+    """{"ct", "ext", "meta"}: bytes of an encoded operand's ciphertexts, of
+    their lift to the tensor base and of its plaintext structure."""
+    v = [ctypes.c_uint64() for _ in range(3)]
+    _check(lib().sfhe_matrix_bytes(N, L, ctypes.byref(M), *[ctypes.byref(x) for x in v]))
+    return dict(zip(("ct", "ext", "meta"), (x.value for x in v)))
 
 
 def sfhe_encrypt(ctx: int, values: np.ndarray, coords: np.ndarray, matrix_id: int, ct, stream=None) -> None:

@@ -92,3 +92,30 @@ def test_encoder_edge_cases(S):
     with pytest.raises(S.SfheError) as e:
         S.sfhe_encode_count(Z, 9)
     assert e.value.status == S.SFHE_EINVAL
+
+
+def test_matrix_bytes_per_encoding(S):
+    """sfhe_matrix_bytes (the per-scheme memory of Sec. 4.6): ciphertexts
+    2 L N words of 8 bytes each, their lift 2 K N words of 4 bytes, and the
+    structure arrays each encoding keeps; on a 50%-sparse matrix CSR and
+    ELL hold fewer ciphertexts than the dense and mask encodings."""
+    from workloads import sparse_int_matrix
+    A = sparse_int_matrix(6, 10, 0.5, -16, 16, 4)
+    A[3, :] = 0
+    N, L = 8192, 4
+    K = len(S.sfhe_select_primes(N, L)[1])
+    nnz, width = int((A != 0).sum()), int((A != 0).sum(axis=1).max())
+    want_nct = {"dense": 60, "mask": 60, "csr": nnz, "ell": 6 * width}
+    want_meta = {"dense": 0, "mask": 60, "csr": (6 + 1 + nnz) * 4, "ell": 6 * width * 4}
+    got = {}
+    for enc, e in S.ENCODINGS.items():
+        f = S.sfhe_encode_fill(A, e)
+        M = S.sfhe_matrix(6, 10, e, f["nct"], f["ell_width"], None, None, None, None, None, None)
+        got[enc] = S.sfhe_matrix_bytes(N, L, M)
+        assert f["nct"] == want_nct[enc]
+        assert got[enc] == {"ct": want_nct[enc] * 2 * L * N * 8, "ext": want_nct[enc] * 2 * K * N * 4,
+                            "meta": want_meta[enc]}, enc
+    assert got["csr"]["ct"] < got["ell"]["ct"] < got["dense"]["ct"] == got["mask"]["ct"]
+    with pytest.raises(S.SfheError) as e:
+        S.sfhe_matrix_bytes(1000, 4, S.sfhe_matrix(1, 1, 0, 1, 0, None, None, None, None, None, None))
+    assert e.value.status == S.SFHE_EUNSUPPORTED

@@ -454,6 +454,47 @@ def test_encoding_structures():
         assert [k for _, k in O.product_set(O.encode(A, O.DENSE), i)] == [0, 1, 2, 3]
 
 
+def test_two_sided_mask_skips_where_either_operand_is_zero():
+    """Naive sparse over both operands (Sec. 3.3.2): entry (i, j) takes the k
+    with A[i][k] != 0 and B[k][j] != 0 (checked against that definition);
+    its ciphertext equals the one-sided entry of A with A[i][k] zeroed
+    wherever B[k][j] is zero (the same encryptions, keyed by coordinates),
+    it decrypts to (A B)[i][j] in per-product and grouped order, and it
+    differs from the one-sided entry where a zero of B was skipped."""
+    c, A, B = _matmul_case(M=3, K=6, Nc=3, seed=7)
+    A[0, :] = [5, -3, 0, 7, 1, 2]
+    B[[1, 3, 4], 0] = 0
+    B[5, 2] = 0
+    B[:, 1] = np.where(B[:, 1] == 0, 1, B[:, 1])       # column 1 without zeros
+    bm = (B == 0).astype(np.uint8)
+    assert bm[1, 0] and not bm[1, 1]                    # the mask is not symmetric in use
+    mm = O.OracleMatmul(c, A, B, 1, 2)
+    skipped = 0
+    for name in ("mask", "csr", "ell"):
+        enc = O.encode(A, O.ENCODINGS[name])
+        for i in range(A.shape[0]):
+            for j in range(B.shape[1]):
+                ks = [k for _, k in O.entry_products(enc, i, j, bm)]
+                assert ks == [k for k in range(A.shape[1]) if A[i, k] != 0 and B[k, j] != 0], (name, i, j)
+                got = mm.entry(enc, i, j, b_mask=bm)
+                A1 = A.copy()
+                A1[i, B[:, j] == 0] = 0
+                one = O.OracleMatmul(c, A1, B, 1, 2).entry(O.encode(A1, O.CSR), i, j)
+                assert (got == one).all(), (name, i, j)
+                want = ((int(A[i] @ B[:, j]) + T // 2) % T) - T // 2
+                assert c.decrypt(got)[0] == want
+                assert c.decrypt(mm.entry(enc, i, j, group=2, b_mask=bm))[0] == want
+                full = mm.entry(enc, i, j)
+                if len(ks) < len(O.product_set(enc, i)):
+                    skipped += 1
+                    assert not (got == full).all(), (name, i, j)
+                else:
+                    assert (got == full).all(), (name, i, j)
+    assert skipped >= 3
+    dense = O.encode(A, O.DENSE)
+    assert O.entry_products(dense, 0, 0, bm) == O.product_set(dense, 0)   # Alg. 1 skips nothing
+
+
 def test_paper_threading_scheme_matches_serial():
     """or_matmul_entries (one result entry per thread, (row*col) mod n) gives
     the same ciphertexts as the serial product loop."""

@@ -54,9 +54,23 @@ def dense_int_matrix(rows: int, cols: int, lo: int, hi: int, seed: int) -> np.nd
     return rng.integers(lo, hi + 1, size=(rows, cols), dtype=np.int64)
 
 
-def operands(shape: MatmulShape) -> tuple[np.ndarray, np.ndarray]:
+def sparsify(M: np.ndarray, sparsity: float, seed: int) -> np.ndarray:
+    """A copy of M with an independent Bernoulli(sparsity) draw of elements set to zero."""
+    rng = np.random.default_rng(seed)
+    out = np.array(M, dtype=np.int64, copy=True)
+    out[rng.random(out.shape) < sparsity] = 0
+    return out
+
+
+def operands(shape: MatmulShape, b_sparse: bool = False) -> tuple[np.ndarray, np.ndarray]:
+    """A with the shape's sparsity; B dense (uniform with 0), or with
+    b_sparse both operands at the shape's sparsity (the paper draws both
+    operands of its sweeps with the same fraction of zeros, Sec. 4.1)."""
     A = sparse_int_matrix(shape.M, shape.K, shape.sparsity, shape.lo, shape.hi, shape.seed)
-    B = dense_int_matrix(shape.K, shape.Nc, shape.lo, shape.hi, shape.seed + 1_000_003)
+    if b_sparse:
+        B = sparse_int_matrix(shape.K, shape.Nc, shape.sparsity, shape.lo, shape.hi, shape.seed + 1_000_003)
+    else:
+        B = dense_int_matrix(shape.K, shape.Nc, shape.lo, shape.hi, shape.seed + 1_000_003)
     return A, B
 
 
