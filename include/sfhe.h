@@ -199,6 +199,16 @@ sfhe_status sfhe_from_coeff(sfhe_ctx* ctx, const uint64_t* in, int64_t npoly, ui
 sfhe_status sfhe_export_secret(sfhe_ctx* ctx, int8_t* s_host);
 sfhe_status sfhe_export_relin_key(sfhe_ctx* ctx, uint64_t* out, void* stream);
 
+/* Measured rate of the 32-bit Shoup modular multiply a w mod b (three
+ * 32-bit multiplies: the high product with the precomputed companion and two
+ * low products; the butterfly multiply of the tensor stage's inverse NTTs)
+ * on the current device, all SMs at full occupancy, eight independent chains
+ * per thread: *per_s = multiplies per second.  A measured reference for the
+ * integer roofline beside the peak derived from unit counts and clocks.
+ * Uses the context's first tensor-base prime; synchronises `stream`.
+ * Errors: EINVAL (null), ECUDA. */
+sfhe_status sfhe_measure_mulmod32(sfhe_ctx* ctx, double* per_s, void* stream);
+
 /* ------------------------------------------------------------ matmul --- */
 /* Workspace (device bytes) for n matmuls A[m] x B[m] under `flags`. */
 sfhe_status sfhe_matmul_workspace_size(const sfhe_ctx* ctx, int32_t n, const sfhe_matrix* A, const sfhe_matrix* B,

@@ -773,6 +773,15 @@ extern "C" sfhe_status sfhe_matmul_check(void* work, void* stream)
     return SFHE_OK;
 }
 
+extern "C" sfhe_status sfhe_measure_mulmod32(sfhe_ctx* c, double* per_s, void* stream)
+{
+    if (!c || !per_s) return fail(SFHE_EINVAL, "null argument");
+    const u32 b = c->rc.mb[0].b, w = b - 12345u;
+    const u32 ws = (u32)(((u64)w << 32) / b);
+    CUDA_TRY(measure_mulmod32(b, w, ws, per_s, as_stream(stream)));
+    return SFHE_OK;
+}
+
 extern "C" sfhe_status sfhe_plan_stats(const sfhe_plan* P, int64_t* products, int64_t* entries, int64_t* launches,
                                        int64_t* ctas)
 {

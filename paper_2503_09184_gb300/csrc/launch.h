@@ -50,6 +50,9 @@ int persistent_ctas_per_sm(const RnsConsts& rc);
 cudaError_t launch_persistent(const RnsConsts& rc, const MmDesc* mms, const Entry* entries, int n_entries,
                               const int2* rowlist, const u64* rlk, const u64* rlk_sh, u64* scratch,
                               size_t scratch_stride, unsigned* queue, int grid, bool grouped, cudaStream_t s);
+// multiplies per second of shoup32_lazy over all SMs (8 independent chains
+// per thread, full occupancy), timed with events on s; synchronises s
+cudaError_t measure_mulmod32(u32 b, u32 w, u32 ws, double* per_s, cudaStream_t s);
 cudaError_t launch_prng(u64 seed, u64 dom, u64 o0, u64 o1, u64 o2, u64 idx0, long long n, u64* out, cudaStream_t s);
 
 }  // namespace sfhe

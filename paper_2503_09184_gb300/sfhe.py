@@ -80,6 +80,7 @@ _SIGS = {
     "sfhe_plan_create": ([_vp, _i32, _P(sfhe_matrix), _P(sfhe_matrix), _P(sfhe_matrix), _u32, _vp, _sz, _vp, _P(_vp)],
                          ctypes.c_int),
     "sfhe_plan_execute": ([_vp, _vp], ctypes.c_int),
+    "sfhe_measure_mulmod32": ([_vp, _P(ctypes.c_double), _vp], ctypes.c_int),
     "sfhe_plan_stats": ([_vp, _P(_i64), _P(_i64), _P(_i64), _P(_i64)], ctypes.c_int),
     "sfhe_matmul_check": ([_vp, _vp], ctypes.c_int),
     "sfhe_plan_destroy": ([_vp], None),
@@ -286,6 +287,13 @@ def sfhe_plan_create(ctx: int, A: list, B: list, C: list, flags: int, work, stre
 
 def sfhe_plan_execute(plan: int, stream=None) -> None:
     _check(lib().sfhe_plan_execute(plan, _stream(stream)))
+
+
+def sfhe_measure_mulmod32(ctx: int, stream=None) -> float:
+    """32-bit Shoup modular multiplies per second over all SMs."""
+    r = ctypes.c_double()
+    _check(lib().sfhe_measure_mulmod32(ctx, ctypes.byref(r), _stream(stream)))
+    return r.value
 
 
 def sfhe_plan_stats(plan: int) -> dict:

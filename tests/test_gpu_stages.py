@@ -187,3 +187,16 @@ def test_decrypt_matches_oracle(mods, N, L):
     assert (got == want).all()
     coeff = coeff_of(api, ctx, M)
     assert [octx.decrypt(coeff[k])[0] for k in range(vals.shape[1])] == list(got)
+
+
+def test_measured_mulmod_rate_is_below_the_derived_peak():
+    """sfhe_measure_mulmod32: a positive rate whose three 32-bit multiplies
+    per modular multiply stay below 152 SMs x 64 multiplies per clock at the
+    GPU's maximum clock (the derived integer peak)."""
+    import torch
+    api, S = gpu_modules()
+    ctx = gpu_ctx(8192, 4, 0)
+    r = S.sfhe_measure_mulmod32(ctx.h, torch.cuda.current_stream())
+    props = torch.cuda.get_device_properties(0)
+    peak = props.multi_processor_count * 64 * 2.07e9
+    assert 0 < 3 * r <= 1.05 * peak, (r, peak)
