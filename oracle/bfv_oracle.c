@@ -346,7 +346,7 @@ static u64 sm_mix(u64 z)
 }
 static u64 sm_absorb(u64 h, u64 x) { return sm_mix(h ^ sm_mix(x + SM_GAMMA)); }
 
-enum { DOM_SECRET = 1, DOM_RLK_A = 2, DOM_RLK_E = 3, DOM_ENC_A = 4, DOM_ENC_E = 5 };
+enum { DOM_SECRET = 1, DOM_RLK_A = 2, DOM_RLK_E = 3, DOM_ENC_A = 4, DOM_ENC_E = 5, DOM_GAL_A = 6, DOM_GAL_E = 7 };
 
 /* Key of the stream for (seed, domain, object) and its word number idx:
  *   key  = absorb(absorb(absorb(absorb(mix(seed + G), domain), o0), o1), o2)
@@ -597,7 +597,10 @@ void or_get_delta(void *vc, u64 *words, int nwords)
  *   c1 = a,  c0 = -a s + e + Delta [m]_t   (mod each q_i)
  * a uniform per limb, e Gaussian (shared by all limbs).  The stream object
  * is (matrix_id, row, col).  ct layout: [2][L][N], coefficient form. */
-int or_encrypt(void *vc, int64_t m, u64 mid, u64 row, u64 col, u64 *ct)
+/* The same with a whole plaintext polynomial m (coefficients in [0, t)):
+ *   c0 = -a s + e + Delta m  (mod each q_i), every coefficient carrying its
+ * own message digit (the slot-packed encoding of Sec. 3.2's chunks). */
+int or_encrypt_poly(void *vc, const u64 *m, u64 mid, u64 row, u64 col, u64 *ct)
 {
     or_ctx *c = (or_ctx *)vc;
     int N = c->N, L = c->L;
@@ -606,8 +609,6 @@ int or_encrypt(void *vc, int64_t m, u64 mid, u64 row, u64 col, u64 *ct)
     int64_t *e = (int64_t *)malloc(sizeof(int64_t) * N);
     u64 *as = (u64 *)malloc(sizeof(u64) * N);
     for (int k = 0; k < N; k++) e[k] = sample_gauss(ke, (u64)k, c->cdt);
-    int64_t mt = m % (int64_t)c->t;
-    if (mt < 0) mt += (int64_t)c->t;
     int rc = 0;
     for (int i = 0; i < L; i++) {
         u64 qi = c->q[i];
@@ -618,12 +619,24 @@ int or_encrypt(void *vc, int64_t m, u64 mid, u64 row, u64 col, u64 *ct)
         for (int k = 0; k < N; k++) {
             u64 ek = e[k] >= 0 ? (u64)e[k] : qi - (u64)(-e[k]);
             u64 v = submod(ek, as[k], qi);
-            if (k == 0) v = addmod(v, mulmod(c->delta_q[i], (u64)mt, qi), qi);
+            if (m[k]) v = addmod(v, mulmod(c->delta_q[i], m[k] % c->t, qi), qi);
             c0[k] = v;
         }
     }
     free(e);
     free(as);
+    return rc;
+}
+
+int or_encrypt(void *vc, int64_t m, u64 mid, u64 row, u64 col, u64 *ct)
+{
+    or_ctx *c = (or_ctx *)vc;
+    u64 *poly = (u64 *)calloc((size_t)c->N, sizeof(u64));
+    int64_t mt = m % (int64_t)c->t;
+    if (mt < 0) mt += (int64_t)c->t;
+    poly[0] = (u64)mt;
+    int rc = or_encrypt_poly(vc, poly, mid, row, col, ct);
+    free(poly);
     return rc;
 }
 
@@ -914,4 +927,203 @@ int or_num_threads(void)
 #else
     return 1;
 #endif
+}
+
+
+/* ------------------------------------------------------------------ */
+/* slot packing, rotations and the slot-zero mask (Sec. 3.2, Alg. 1      */
+/* with chunk size c > 1)                                               */
+/* ------------------------------------------------------------------ */
+/* Slots of a plaintext polynomial m in Z_t[X]/(X^N + 1), t prime with
+ * t = 1 mod 2N: slot s = (r, j), r = s / (N/2), j = s mod (N/2), holds
+ * m(zeta^e_s) with e_s = 3^j mod 2N for r = 0 and -3^j mod 2N for r = 1,
+ * zeta the smallest primitive 2N-th root of unity mod t.  X -> X^(3^k)
+ * then moves slot (r, j + k) to slot (r, j): a left rotation by k of each
+ * row of N/2 slots. */
+static int slot_exp(int N, int s)
+{
+    int half = N / 2, j = s % half, r = s / half;
+    u64 e = 1;
+    for (int i = 0; i < j; i++) e = e * 3 % (2 * (u64)N);
+    return r == 0 ? (int)e : (int)(2 * (u64)N - e);
+}
+
+/* vals[s] = m(zeta^e_s), by direct evaluation */
+int or_slots_decode(int N, u64 t, const u64 *poly, u64 *vals)
+{
+    u64 zeta = or_psi(t, N);
+    if (!zeta) return 1;
+    u64 *zp = (u64 *)malloc(sizeof(u64) * 2 * (size_t)N);  /* zeta^x, x < 2N */
+    zp[0] = 1;
+    for (int x = 1; x < 2 * N; x++) zp[x] = mulmod(zp[x - 1], zeta, t);
+#pragma omp parallel for schedule(static)
+    for (int s = 0; s < N; s++) {
+        u64 e = (u64)slot_exp(N, s), acc = 0;
+        for (int k = 0; k < N; k++) acc = addmod(acc, mulmod(poly[k] % t, zp[(e * (u64)k) % (2 * (u64)N)], t), t);
+        vals[s] = acc;
+    }
+    free(zp);
+    return 0;
+}
+
+/* the polynomial with the given slots: m_k = N^-1 sum_s vals[s] zeta^(-e_s k)
+ * (the e_s run over every odd residue mod 2N, and zeta^2 is a primitive
+ * N-th root, so this inverts the evaluation above) */
+int or_slots_encode(int N, u64 t, const u64 *vals, u64 *poly)
+{
+    u64 zeta = or_psi(t, N);
+    if (!zeta) return 1;
+    u64 zinv = invmod(zeta, t), ninv = invmod((u64)N % t, t);
+    u64 *zm = (u64 *)malloc(sizeof(u64) * 2 * (size_t)N);  /* zeta^-x, x < 2N */
+    int *ex = (int *)malloc(sizeof(int) * (size_t)N);
+    zm[0] = 1;
+    for (int x = 1; x < 2 * N; x++) zm[x] = mulmod(zm[x - 1], zinv, t);
+    for (int s = 0; s < N; s++) ex[s] = slot_exp(N, s);
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < N; k++) {
+        u64 acc = 0;
+        for (int s = 0; s < N; s++) acc = addmod(acc, mulmod(vals[s] % t, zm[((u64)ex[s] * (u64)k) % (2 * (u64)N)], t), t);
+        poly[k] = mulmod(acc, ninv, t);
+    }
+    free(zm);
+    free(ex);
+    return 0;
+}
+
+/* every coefficient of the message: m_k = floor((t v_k + floor(Q/2)) / Q)
+ * mod t in [0, t), v = [c0 + c1 s]_Q; noise_bits as in or_decrypt, against
+ * the whole polynomial Delta m */
+int or_decrypt_poly(void *vc, const u64 *ct, u64 *m_out, int *noise_bits)
+{
+    or_ctx *c = (or_ctx *)vc;
+    int N = c->N, L = c->L;
+    u64 *v = (u64 *)malloc(sizeof(u64) * (size_t)L * N);
+    for (int i = 0; i < L; i++) {
+        u64 qi = c->q[i];
+        or_negacyclic(qi, N, ct + ((size_t)L + i) * N, c->s_mod + (size_t)i * N, v + (size_t)i * N);
+        for (int k = 0; k < N; k++) v[(size_t)i * N + k] = addmod(v[(size_t)i * N + k], ct[(size_t)i * N + k] % qi, qi);
+    }
+    int maxbits = 0;
+    for (int k = 0; k < N; k++) {
+        u64 r[OR_MAX_L];
+        for (int i = 0; i < L; i++) r[i] = v[(size_t)i * N + k];
+        mw_t V, num, quo, dm, tmp;
+        crt_reconstruct(&c->Qb, r, &V);
+        mw_mul_u64(&num, &V, c->t);
+        mw_add(&num, &num, &c->Qb.half);
+        mw_divmod(&num, &c->Qb.M, &quo, NULL);
+        u64 mu = mw_mod_u64(&quo, c->t);
+        m_out[k] = mu;
+        mw_mul_u64(&dm, &c->Delta, mu);
+        while (mw_cmp(&dm, &c->Qb.M) >= 0) mw_sub(&dm, &dm, &c->Qb.M);
+        if (mw_cmp(&V, &dm) >= 0) mw_sub(&tmp, &V, &dm);
+        else { mw_sub(&tmp, &c->Qb.M, &dm); mw_add(&tmp, &tmp, &V); }
+        if (mw_cmp(&tmp, &c->Qb.half) > 0) mw_sub(&tmp, &c->Qb.M, &tmp);
+        int bits = mw_bitlen(&tmp);
+        if (bits > maxbits) maxbits = bits;
+    }
+    if (noise_bits) *noise_bits = maxbits;
+    free(v);
+    return 0;
+}
+
+/* sigma_g: X -> X^g (g odd) on one polynomial mod q in coefficient form:
+ * coefficient k moves to k g mod 2N, negated when that lands at or past N */
+static void automorphism(int N, u64 q, u64 g, const u64 *in, u64 *out)
+{
+    for (int k = 0; k < N; k++) {
+        u64 d = ((u64)k * g) % (2 * (u64)N);
+        if (d < (u64)N) out[d] = in[k] % q;
+        else out[d - N] = submod(0, in[k] % q, q);
+    }
+}
+
+/* Galois key for g, same layout as the relinearisation key
+ * ([L digit j][2 (b, a)][L limb i][N]):
+ *   b_j = -a_j s + e_j + g_j sigma_g(s),  a_j uniform,
+ * g_j the gadget of or_ctx_create (g_j == delta_ij mod q_i).  a_j from the
+ * stream (DOM_GAL_A, g, j) at index i N + k, e_j from (DOM_GAL_E, g, j). */
+int or_galois_key(void *vc, u64 g, u64 *key)
+{
+    or_ctx *c = (or_ctx *)vc;
+    int N = c->N, L = c->L;
+    if (!(g & 1)) return 1;
+    u64 *tmp = (u64 *)malloc(sizeof(u64) * N);
+    u64 *sg = (u64 *)malloc(sizeof(u64) * N);
+    int64_t *e = (int64_t *)malloc(sizeof(int64_t) * N);
+    int rc = 0;
+    for (int j = 0; j < L; j++) {
+        u64 ka = sm_key(c->seed, DOM_GAL_A, g, (u64)j, 0);
+        u64 ke = sm_key(c->seed, DOM_GAL_E, g, (u64)j, 0);
+        for (int k = 0; k < N; k++) e[k] = sample_gauss(ke, (u64)k, c->cdt);
+        for (int i = 0; i < L; i++) {
+            u64 qi = c->q[i];
+            u64 *a = key + (((size_t)j * 2 + 1) * L + i) * N, *b = key + (((size_t)j * 2 + 0) * L + i) * N;
+            for (int k = 0; k < N; k++)
+                if (sample_uniform(ka, (u64)i * N + k, qi, &a[k])) rc = -1;
+            or_negacyclic(qi, N, a, c->s_mod + (size_t)i * N, tmp);
+            automorphism(N, qi, g, c->s_mod + (size_t)i * N, sg);
+            for (int k = 0; k < N; k++) {
+                u64 ek = e[k] >= 0 ? (u64)e[k] : qi - (u64)(-e[k]);
+                u64 v = submod(ek, tmp[k], qi);
+                if (i == j) v = addmod(v, sg[k], qi);
+                b[k] = v;
+            }
+        }
+    }
+    free(tmp);
+    free(sg);
+    free(e);
+    return rc;
+}
+
+/* Rotation: (c0', c1') = (sigma_g(c0), sigma_g(c1)) decrypts under
+ * sigma_g(s); switch it back to s with the Galois key, digits
+ * D_j = [c1']_{q_j} in [0, q_j):
+ *   out = (c0' + sum_j D_j b_j,  sum_j D_j a_j)   (mod each q_i). */
+int or_rotate(void *vc, const u64 *ct, u64 g, const u64 *key, u64 *out)
+{
+    or_ctx *c = (or_ctx *)vc;
+    int N = c->N, L = c->L;
+    u64 *c1g = (u64 *)malloc(sizeof(u64) * (size_t)L * N);
+    u64 *Dm = (u64 *)malloc(sizeof(u64) * N);
+    for (int i = 0; i < L; i++) {
+        automorphism(N, c->q[i], g, ct + (size_t)i * N, out + (size_t)i * N);
+        automorphism(N, c->q[i], g, ct + ((size_t)L + i) * N, c1g + (size_t)i * N);
+        memset(out + ((size_t)L + i) * N, 0, sizeof(u64) * N);
+    }
+    for (int i = 0; i < L; i++) {
+        u64 qi = c->q[i];
+        u64 *c0 = out + (size_t)i * N, *c1 = out + ((size_t)L + i) * N;
+        for (int j = 0; j < L; j++) {
+            const u64 *Dj = c1g + (size_t)j * N;
+            for (int k = 0; k < N; k++) Dm[k] = Dj[k] % qi;
+            negacyclic_acc(qi, N, Dm, key + (((size_t)j * 2 + 0) * L + i) * N, c0, 1);
+            negacyclic_acc(qi, N, Dm, key + (((size_t)j * 2 + 1) * L + i) * N, c1, 1);
+        }
+    }
+    free(c1g);
+    free(Dm);
+    return 0;
+}
+
+/* ciphertext times plaintext polynomial pt (coefficients in [0, t), lifted
+ * to their centred representatives in (-t/2, t/2]): (c0 pt, c1 pt) mod q_i;
+ * it decrypts to the slot-wise product of the two messages */
+int or_mul_plain(void *vc, const u64 *ct, const u64 *pt, u64 *out)
+{
+    or_ctx *c = (or_ctx *)vc;
+    int N = c->N, L = c->L;
+    u64 *pm = (u64 *)malloc(sizeof(u64) * N);
+    for (int i = 0; i < L; i++) {
+        u64 qi = c->q[i];
+        for (int k = 0; k < N; k++) {
+            u64 v = pt[k] % c->t;
+            pm[k] = v > c->t / 2 ? qi - (c->t - v) : v;
+        }
+        for (int p = 0; p < 2; p++)
+            or_negacyclic(qi, N, ct + ((size_t)p * L + i) * N, pm, out + ((size_t)p * L + i) * N);
+    }
+    free(pm);
+    return 0;
 }

@@ -74,6 +74,15 @@ def lib():
                                                 ctypes.c_int]
         L.or_matmul_entries_grouped.restype = ctypes.c_int
         L.or_num_threads.restype = ctypes.c_int
+        L.or_slots_encode.argtypes = [ctypes.c_int, ctypes.c_uint64, _u64p, _u64p]
+        L.or_slots_decode.argtypes = [ctypes.c_int, ctypes.c_uint64, _u64p, _u64p]
+        L.or_encrypt_poly.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _u64p]
+        L.or_encrypt_poly.restype = ctypes.c_int
+        L.or_decrypt_poly.argtypes = [ctypes.c_void_p, _u64p, _u64p, ctypes.POINTER(ctypes.c_int)]
+        L.or_galois_key.argtypes = [ctypes.c_void_p, ctypes.c_uint64, _u64p]
+        L.or_galois_key.restype = ctypes.c_int
+        L.or_rotate.argtypes = [ctypes.c_void_p, _u64p, ctypes.c_uint64, _u64p, _u64p]
+        L.or_mul_plain.argtypes = [ctypes.c_void_p, _u64p, _u64p, _u64p]
         _lib = L
     return _lib
 
@@ -138,6 +147,34 @@ def num_threads() -> int:
     return int(lib().or_num_threads())
 
 
+# ---------------------------------------------------------------------------
+# slot packing (Sec. 3.2's chunks of c values per ciphertext)
+# ---------------------------------------------------------------------------
+def slots_encode(N: int, t: int, vals) -> np.ndarray:
+    """plaintext polynomial [N] (coefficients in [0, t)) whose slots are vals
+    (slot s = (row s // (N/2), column s % (N/2)); see or_slots_encode)."""
+    v = np.ascontiguousarray(np.asarray(vals, dtype=np.int64) % t, dtype=np.uint64)
+    assert v.size == N
+    out = np.zeros(N, dtype=np.uint64)
+    if lib().or_slots_encode(N, t, _p(v), _p(out)):
+        raise ValueError("t has no primitive 2N-th root of unity")
+    return out
+
+
+def slots_decode(N: int, t: int, poly) -> np.ndarray:
+    p = np.ascontiguousarray(np.asarray(poly, dtype=np.uint64))
+    out = np.zeros(N, dtype=np.uint64)
+    if lib().or_slots_decode(N, t, _p(p), _p(out)):
+        raise ValueError("t has no primitive 2N-th root of unity")
+    return out
+
+
+def rotation_element(N: int, k: int) -> int:
+    """Galois element of a left rotation of each slot row by k (negative k:
+    right): 3^(k mod N/2) mod 2N."""
+    return pow(3, k % (N // 2), 2 * N)
+
+
 class OracleCtx:
     """Keys and per-ciphertext operations of the oracle (coefficient form)."""
 
@@ -199,6 +236,43 @@ class OracleCtx:
         nb = ctypes.c_int()
         lib().or_decrypt(self._h, _p(ct), ctypes.byref(m), ctypes.byref(nb))
         return int(m.value), int(nb.value)
+
+    def encrypt_poly(self, m, matrix_id: int, row: int, col: int) -> np.ndarray:
+        """encryption of a plaintext polynomial m [N] (coefficients mod t)"""
+        mm = np.ascontiguousarray(np.asarray(m, dtype=np.int64) % self.t, dtype=np.uint64)
+        ct = np.zeros(self.ct_shape, dtype=np.uint64)
+        if lib().or_encrypt_poly(self._h, _p(mm), matrix_id, row, col, _p(ct)) != 0:
+            raise RuntimeError("sampling failed")
+        return ct
+
+    def decrypt_poly(self, ct: np.ndarray) -> tuple[np.ndarray, int]:
+        """(message polynomial [N] in [0, t), noise bits)"""
+        ct = np.ascontiguousarray(ct, dtype=np.uint64)
+        m = np.zeros(self.N, dtype=np.uint64)
+        nb = ctypes.c_int()
+        lib().or_decrypt_poly(self._h, _p(ct), _p(m), ctypes.byref(nb))
+        return m, int(nb.value)
+
+    def galois_key(self, g: int) -> np.ndarray:
+        """[L digit][2 (b, a)][L limb][N], coefficient form"""
+        out = np.zeros((self.L, 2, self.L, self.N), dtype=np.uint64)
+        if lib().or_galois_key(self._h, g, _p(out)) != 0:
+            raise ValueError("g must be odd; or sampling failed")
+        return out
+
+    def rotate(self, ct: np.ndarray, g: int, key: np.ndarray) -> np.ndarray:
+        ct = np.ascontiguousarray(ct, dtype=np.uint64)
+        key = np.ascontiguousarray(key, dtype=np.uint64)
+        out = np.zeros(self.ct_shape, dtype=np.uint64)
+        lib().or_rotate(self._h, _p(ct), g, _p(key), _p(out))
+        return out
+
+    def mul_plain(self, ct: np.ndarray, pt) -> np.ndarray:
+        ct = np.ascontiguousarray(ct, dtype=np.uint64)
+        pt = np.ascontiguousarray(np.asarray(pt, dtype=np.uint64))
+        out = np.zeros(self.ct_shape, dtype=np.uint64)
+        lib().or_mul_plain(self._h, _p(ct), _p(pt), _p(out))
+        return out
 
     def tensor_scale(self, a: np.ndarray, b: np.ndarray) -> np.ndarray:
         """(d0, d1, d2) after the exact scale-and-round, [3][L][N]."""
@@ -386,3 +460,80 @@ class OracleMatmul:
             d = self.ctx.tensor_scale_sum([self.ct_a(i, k) for k in run], [self.ct_b(k, j) for k in run])
             self.ctx.add_(acc, self.ctx.relin(d))
         return acc
+
+
+class OracleChunked:
+    """Alg. 1 with chunk size c > 1 (Sec. 3.2): every matrix is stored
+    row-major in chunks of c consecutive elements, one chunk per ciphertext
+    holding its elements in slots 0 .. c-1 (the other slots 0).  For every
+    listed product (i, k, j): rotate A's chunk so that A[i][k] is in slot 0,
+    the same for B[k][j]; multiply and relinearise (the BFV multiply rounds
+    exactly, in place of CKKS's rescale); multiply by the slot-0 mask; rotate
+    right to the result's offset; add into the result chunk.  A rotation by
+    0 is the identity and is skipped.  With skip_zeros, products where A[i][k]
+    or B[k][j] is zero are skipped (the naive sparse scheme's two masks)."""
+
+    def __init__(self, ctx: OracleCtx, A: np.ndarray, B: np.ndarray, c: int, a_id: int, b_id: int):
+        self.ctx, self.A, self.B, self.c = ctx, np.asarray(A), np.asarray(B), c
+        assert 1 <= c <= ctx.N // 2
+        self.a_ct = self._chunks(self.A, a_id)
+        self.b_ct = self._chunks(self.B, b_id)
+        self._keys = {}
+        mask = np.zeros(ctx.N, dtype=np.int64)
+        mask[0] = 1
+        self.mask = slots_encode(ctx.N, ctx.t, mask)
+
+    def _chunks(self, M: np.ndarray, mid: int) -> list:
+        flat = M.reshape(-1)
+        out = []
+        for q in range(-(-flat.size // self.c)):
+            v = np.zeros(self.ctx.N, dtype=np.int64)
+            part = flat[q * self.c:(q + 1) * self.c]
+            v[:part.size] = part
+            out.append(self.ctx.encrypt_poly(slots_encode(self.ctx.N, self.ctx.t, v), mid, q, 0))
+        return out
+
+    def key(self, g: int) -> np.ndarray:
+        if g not in self._keys:
+            self._keys[g] = self.ctx.galois_key(g)
+        return self._keys[g]
+
+    def rot(self, ct: np.ndarray, k: int) -> np.ndarray:
+        if k % (self.ctx.N // 2) == 0:
+            return ct
+        g = rotation_element(self.ctx.N, k)
+        return self.ctx.rotate(ct, g, self.key(g))
+
+    def product(self, i: int, k: int, j: int) -> np.ndarray:
+        """one iteration of Alg. 1's inner loop, before the accumulation"""
+        Kd, Nc, c = self.A.shape[1], self.B.shape[1], self.c
+        ia, ib, ir = i * Kd + k, k * Nc + j, i * Nc + j
+        a = self.rot(self.a_ct[ia // c], ia % c)
+        b = self.rot(self.b_ct[ib // c], ib % c)
+        x = self.ctx.mul_relin(a, b)
+        x = self.ctx.mul_plain(x, self.mask)
+        return self.rot(x, -(ir % c))
+
+    def result(self, skip_zeros: bool = False) -> list:
+        M, Kd = self.A.shape
+        Nc = self.B.shape[1]
+        nchunks = -(-(M * Nc) // self.c)
+        R = [np.zeros(self.ctx.ct_shape, dtype=np.uint64) for _ in range(nchunks)]
+        for i in range(M):
+            for j in range(Nc):
+                for k in range(Kd):
+                    if skip_zeros and (self.A[i, k] == 0 or self.B[k, j] == 0):
+                        continue
+                    self.ctx.add_(R[(i * Nc + j) // self.c], self.product(i, k, j))
+        return R
+
+    def decode(self, R: list) -> np.ndarray:
+        """the result matrix from its chunks (centred mod t)"""
+        M, Nc = self.A.shape[0], self.B.shape[1]
+        vals = []
+        for ct in R:
+            m, _ = self.ctx.decrypt_poly(ct)
+            vals.extend(int(x) for x in slots_decode(self.ctx.N, self.ctx.t, m)[:self.c])
+        flat = np.array(vals[:M * Nc], dtype=np.int64)
+        t = self.ctx.t
+        return (((flat + t // 2) % t) - t // 2).reshape(M, Nc)

@@ -520,3 +520,103 @@ def test_plaintext_wraps_mod_t():
     a = c.encrypt(300, 1, 0, 0)
     b = c.encrypt(300, 2, 0, 0)
     assert c.decrypt(c.mul_relin(a, b))[0] == ((90000 + T // 2) % T) - T // 2
+
+
+# ---------------------------------------------------- slot packing (N3) ----
+def _rot_rows(v, k):
+    """left rotation by k of each half of v (the two slot rows)"""
+    h = len(v) // 2
+    return np.concatenate([np.roll(v[:h], -k), np.roll(v[h:], -k)])
+
+
+@pytest.mark.parametrize("N", [16, 32])
+def test_slots_are_a_ring_isomorphism(N):
+    """Slot encoding: decode(encode(v)) = v; a constant vector encodes to the
+    constant polynomial; the negacyclic product of two encodings (big
+    integers, mod t) decodes to the slot-wise product."""
+    rng = np.random.default_rng(N)
+    u = rng.integers(0, T, size=N)
+    v = rng.integers(0, T, size=N)
+    mu, mv = O.slots_encode(N, T, u), O.slots_encode(N, T, v)
+    assert (O.slots_decode(N, T, mu) == u).all()
+    const = O.slots_encode(N, T, np.full(N, 4242))
+    assert int(const[0]) == 4242 and not const[1:].any()
+    prod = [x % T for x in tb.negacyclic([int(x) for x in mu], [int(x) for x in mv])]
+    assert [int(x) for x in O.slots_decode(N, T, prod)] == [int(a) * int(b) % T for a, b in zip(u, v)]
+
+
+def test_poly_encryption_and_decryption(ctx16):
+    """encrypt_poly of [m, 0, ..., 0] is the scalar encryption of m, limb
+    for limb; decrypt_poly returns every coefficient of an encrypted
+    polynomial with the noise of a fresh ciphertext."""
+    c = ctx16
+    for m in (0, 5, -7, 32768):
+        poly = np.zeros(c.N, dtype=np.int64)
+        poly[0] = m
+        assert (c.encrypt_poly(poly, 3, 1, 2) == c.encrypt(m, 3, 1, 2)).all()
+    poly = np.random.default_rng(1).integers(0, T, size=c.N)
+    got, bits = c.decrypt_poly(c.encrypt_poly(poly, 4, 0, 0))
+    assert (got == poly).all() and bits <= 5
+
+
+@pytest.mark.parametrize("k", [1, 3, -1, -5])
+def test_rotation_moves_slots(ctx16, k):
+    """A key-switched automorphism X -> X^(3^k) rotates each slot row left
+    by k (right for negative k); the Galois key is b_j + a_j s -
+    delta_ij s(X^g) = one small error polynomial in every limb."""
+    c = ctx16
+    N = c.N
+    g = O.rotation_element(N, k)
+    key = c.galois_key(g)
+    s = [int(x) for x in c.secret()]
+    sg = [0] * N
+    for i, x in enumerate(s):          # s(X^g) by the definition of X -> X^g
+        d = i * g % (2 * N)
+        if d < N:
+            sg[d] += x
+        else:
+            sg[d - N] -= x
+    for j in range(c.L):
+        errs = []
+        for i, qi in enumerate(c.q):
+            b = [int(x) for x in key[j, 0, i]]
+            a = [int(x) for x in key[j, 1, i]]
+            e = [(x + y - (z if i == j else 0)) % qi for x, y, z in zip(b, tb.negacyclic(a, s), sg)]
+            e = [x - qi if x > qi // 2 else x for x in e]
+            assert max(abs(x) for x in e) <= 19
+            errs.append(e)
+        assert all(e == errs[0] for e in errs)
+    v = np.random.default_rng(7).integers(0, T, size=N)
+    ct = c.encrypt_poly(O.slots_encode(N, T, v), 5, 0, 0)
+    m, bits = c.decrypt_poly(c.rotate(ct, g, key))
+    assert (O.slots_decode(N, T, m) == _rot_rows(v, k)).all()
+    assert 2**bits < tb.prod(c.q) // (2 * T)
+
+
+def test_mul_plain_is_slotwise(ctx16):
+    c = ctx16
+    rng = np.random.default_rng(3)
+    u, w = rng.integers(0, T, size=c.N), rng.integers(0, T, size=c.N)
+    ct = c.encrypt_poly(O.slots_encode(c.N, T, u), 6, 0, 0)
+    m, bits = c.decrypt_poly(c.mul_plain(ct, O.slots_encode(c.N, T, w)))
+    assert [int(x) for x in O.slots_decode(c.N, T, m)] == [int(a) * int(b) % T for a, b in zip(u, w)]
+    assert 2**bits < tb.prod(c.q) // (2 * T)
+
+
+@pytest.mark.parametrize("chunk", [1, 3, 4])
+def test_chunked_alg1_decrypts_to_the_product(chunk):
+    """Alg. 1 over chunks of c values (rotate both operands into slot 0,
+    multiply and relinearise, mask slot 0, rotate to the result offset,
+    add): the result chunks decode to A B mod t, with and without the
+    two-sided zero skip; skipping changes the ciphertexts (fewer products)
+    but not the decryption."""
+    c = O.OracleCtx(32, 3, seed=13)
+    A = np.array([[3, 0, -7], [0, 5, 2]], dtype=np.int64)
+    B = np.array([[2, -1], [0, 4], [6, 0]], dtype=np.int64)
+    oc = O.OracleChunked(c, A, B, chunk, 1, 2)
+    assert len(oc.a_ct) == -(-6 // chunk) and len(oc.b_ct) == -(-6 // chunk)
+    full = oc.result()
+    assert (oc.decode(full) == A @ B).all()
+    skip = oc.result(skip_zeros=True)
+    assert (oc.decode(skip) == A @ B).all()
+    assert any(not (x == y).all() for x, y in zip(full, skip))
