@@ -199,6 +199,70 @@ sfhe_status sfhe_from_coeff(sfhe_ctx* ctx, const uint64_t* in, int64_t npoly, ui
 sfhe_status sfhe_export_secret(sfhe_ctx* ctx, int8_t* s_host);
 sfhe_status sfhe_export_relin_key(sfhe_ctx* ctx, uint64_t* out, void* stream);
 
+/* ------------------------------------------------ slot-packed chunks --- */
+/* Alg. 1 with chunk size c > 1 (Sec. 3.2): a chunk ciphertext holds c
+ * consecutive row-major matrix elements in its slots 0 .. c-1 (BFV batching,
+ * t prime and 1 mod 2N).  Slot s = (r, j) = (s / (N/2), s mod (N/2)) of a
+ * plaintext polynomial m is m(zeta^e) with e = 3^j (r = 0) or -3^j (r = 1)
+ * mod 2N, zeta the smallest primitive 2N-th root of unity mod t, so the
+ * automorphism X -> X^(3^k) rotates each row of N/2 slots left by k.
+ *
+ * Host only: slots <-> plaintext polynomial (values and coefficients mod t;
+ * outputs in [0, t)).  EUNSUPPORTED if t is not a prime 1 mod 2N. */
+sfhe_status sfhe_slots_encode(uint32_t N, uint64_t t, const int64_t* values, int64_t* poly);
+sfhe_status sfhe_slots_decode(uint32_t N, uint64_t t, const int64_t* poly, int64_t* values);
+/* Galois element of a left rotation by k (right for k < 0): 3^(k mod N/2)
+ * mod 2N; 0 if N is not a power of two >= 4.  Host only. */
+uint32_t sfhe_rotation_element(uint32_t N, int32_t k);
+/* Secret-key encryption of whole plaintext polynomials polys[n][N] (host,
+ * coefficients mod t): c0 = -a s + e + Delta m, the stream as sfhe_encrypt
+ * (a polynomial with only a constant coefficient gives sfhe_encrypt's
+ * ciphertext). ct: device [n][2][L][N], NTT form. */
+sfhe_status sfhe_encrypt_poly(sfhe_ctx* ctx, const int64_t* polys, const int32_t* coords, int64_t n,
+                              uint64_t matrix_id, uint64_t* ct, void* stream);
+/* Every coefficient of the messages: out (device [n][N]) in [0, t). */
+sfhe_status sfhe_decrypt_poly(sfhe_ctx* ctx, const uint64_t* ct, int64_t n, int64_t* out, void* stream);
+/* Galois key for g (odd, < 2N): key and key_sh (device, [L digit][2 (b,
+ * a)][L limb][N] each, NTT form and Shoup companions): b_j = -a_j s + e_j +
+ * g_j s(X^g), the gadget of the relinearisation key; randomness from its
+ * own stream (domains 6 and 7, objects (g, j)). */
+sfhe_status sfhe_galois_keygen(sfhe_ctx* ctx, uint32_t g, uint64_t* key, uint64_t* key_sh, void* stream);
+/* Rotation (fhe_rotate of Alg. 1): out[n] = the key switch back to s of
+ * (c0(X^g), c1(X^g)): (c0' + sum_j D_j b_j, sum_j D_j a_j), unsigned digits
+ * D_j = [c1']_{q_j}.  in and out device, distinct; needs
+ * sfhe_rotate_workspace_size() bytes of device workspace. */
+sfhe_status sfhe_rotate_workspace_size(const sfhe_ctx* ctx, size_t* bytes);
+sfhe_status sfhe_rotate(sfhe_ctx* ctx, const uint64_t* in, int64_t n, uint32_t g, const uint64_t* key,
+                        const uint64_t* key_sh, uint64_t* out, void* work, size_t work_bytes, void* stream);
+/* A plaintext polynomial (host [N] mod t, lifted to its centred
+ * representatives) in NTT form over Q: pt device [L][N].  Synchronous. */
+sfhe_status sfhe_plain_ntt(sfhe_ctx* ctx, const int64_t* poly, uint64_t* pt, void* stream);
+/* ct[n] *= pt (Alg. 1's multiply by the slot-zero mask): decrypts to the
+ * slot-wise product.  In place, device. */
+sfhe_status sfhe_mul_plain(sfhe_ctx* ctx, uint64_t* ct, int64_t n, const uint64_t* pt, void* stream);
+/* acc[n] += x[n] (mod q_i), device. */
+sfhe_status sfhe_add(sfhe_ctx* ctx, uint64_t* acc, const uint64_t* x, int64_t n, void* stream);
+/* Rotation keys for chunk size c: left and right rotations by 1 .. c-1
+ * (2 (c - 1) Galois keys, device memory owned by the object). */
+typedef struct sfhe_rotkeys sfhe_rotkeys;
+sfhe_status sfhe_rotkeys_create(sfhe_ctx* ctx, int32_t c, void* stream, sfhe_rotkeys** out);
+void sfhe_rotkeys_destroy(sfhe_rotkeys* rk);
+/* Alg. 1 over chunks (Sec. 3.2, Alg. 1 with c > 1): A holds ceil(M K / c)
+ * chunk ciphertexts of the M x K matrix (row-major, element e in slot
+ * e mod c of chunk e / c), B ceil(K Nc / c) of the K x Nc one, C receives
+ * ceil(M Nc / c).  For every (i, j) and k: rotate A's chunk so that A[i][k]
+ * is in slot 0 and B's so that B[k][j] is, multiply and relinearise (the
+ * BFV multiply's exact scale-and-round stands in for CKKS's rescale),
+ * multiply by the slot-0 mask, rotate right to (i Nc + j) mod c, add into C.
+ * Rotations by 0 are skipped.  a_zero / b_zero (host, may be NULL): the
+ * naive sparse masks; products with a set mask are skipped.  *products (may
+ * be NULL) receives the count.  The workspace (device) holds the
+ * per-product temporaries. */
+sfhe_status sfhe_matmul_chunked_workspace_size(const sfhe_ctx* ctx, size_t* bytes);
+sfhe_status sfhe_matmul_chunked(sfhe_ctx* ctx, const sfhe_rotkeys* rk, int32_t M, int32_t K, int32_t Nc,
+                                const uint64_t* A, const uint64_t* B, uint64_t* C, const uint8_t* a_zero,
+                                const uint8_t* b_zero, void* work, size_t work_bytes, void* stream, int64_t* products);
+
 /* Measured rate of the 32-bit Shoup modular multiply a w mod b (three
  * 32-bit multiplies: the high product with the precomputed companion and two
  * low products; the butterfly multiply of the tensor stage's inverse NTTs)

@@ -227,3 +227,88 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------ slot-packed chunks -------
+class ChunkedMatrix:
+    """A matrix stored as Alg. 1's chunks (Sec. 3.2): element e of the
+    row-major order in slot e mod c of chunk ciphertext e / c."""
+
+    def __init__(self, rows: int, cols: int, c: int, ct: torch.Tensor, zero: np.ndarray | None = None):
+        self.rows, self.cols, self.c, self.ct, self.zero = rows, cols, c, ct, zero
+
+    @property
+    def nchunks(self) -> int:
+        return -(-(self.rows * self.cols) // self.c)
+
+
+def encrypt_chunked(ctx: Context, values: np.ndarray, c: int, matrix_id: int, stream=None) -> ChunkedMatrix:
+    """chunk q encrypted under the stream object (matrix_id, q, 0)"""
+    values = np.ascontiguousarray(values, dtype=np.int64)
+    flat = values.reshape(-1)
+    n = -(-flat.size // c)
+    polys = np.zeros((max(n, 1), ctx.N), dtype=np.int64)
+    for q in range(n):
+        v = np.zeros(ctx.N, dtype=np.int64)
+        part = flat[q * c:(q + 1) * c]
+        v[:part.size] = part
+        polys[q] = S.sfhe_slots_encode(ctx.N, ctx.t, v)
+    coords = np.zeros((max(n, 1), 2), dtype=np.int32)
+    coords[:, 0] = np.arange(max(n, 1))
+    ct = _dev_u64((max(n, 1), 2, ctx.L, ctx.N))
+    if n:
+        S.sfhe_encrypt_poly(ctx.h, polys[:n], coords[:n], matrix_id, ct, stream)
+    return ChunkedMatrix(values.shape[0], values.shape[1], c, ct, (values == 0).astype(np.uint8))
+
+
+def decrypt_chunked(ctx: Context, M: ChunkedMatrix, stream=None) -> np.ndarray:
+    """the matrix, centred mod t"""
+    n = M.nchunks
+    out = torch.empty((max(n, 1), ctx.N), dtype=torch.int64, device="cuda")
+    S.sfhe_decrypt_poly(ctx.h, M.ct, n, out, stream)
+    (torch.cuda.current_stream() if stream is None else stream).synchronize()
+    polys = out.cpu().numpy()
+    vals = []
+    for q in range(n):
+        vals.extend(int(x) for x in S.sfhe_slots_decode(ctx.N, ctx.t, polys[q])[:M.c])
+    t = ctx.t
+    flat = np.array(vals[:M.rows * M.cols], dtype=np.int64)
+    return (((flat + t // 2) % t) - t // 2).reshape(M.rows, M.cols)
+
+
+class RotationKeys:
+    """Galois keys of the left and right rotations by 1 .. c-1."""
+
+    def __init__(self, ctx: Context, c: int, stream=None):
+        self.ctx, self.c = ctx, c
+        self.h = S.sfhe_rotkeys_create(ctx.h, c, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            torch.cuda.synchronize()
+            S.sfhe_rotkeys_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def matmul_chunked(ctx: Context, A: ChunkedMatrix, B: ChunkedMatrix, rk: RotationKeys, *, skip_zeros: bool = False,
+                   stream=None, work: torch.Tensor | None = None) -> tuple[ChunkedMatrix, int]:
+    """C = A x B by Alg. 1 over chunks; skip_zeros: the naive sparse scheme's
+    two masks (products where A[i][k] or B[k][j] is zero are skipped).
+    Returns (C, products performed)."""
+    assert A.c == B.c == rk.c and A.cols == B.rows
+    c = A.c
+    nC = -(-(A.rows * B.cols) // c)
+    C = ChunkedMatrix(A.rows, B.cols, c, _dev_u64((max(nC, 1), 2, ctx.L, ctx.N)))
+    if work is None:
+        work = torch.empty(S.sfhe_matmul_chunked_workspace_size(ctx.h), dtype=torch.uint8, device="cuda")
+    az = np.ascontiguousarray(A.zero.reshape(-1)) if skip_zeros else None
+    bz = np.ascontiguousarray(B.zero.reshape(-1)) if skip_zeros else None
+    n = S.sfhe_matmul_chunked(ctx.h, rk.h, A.rows, A.cols, B.cols, A.ct, B.ct, C.ct, az, bz, work, stream)
+    C._work = work
+    return C, n

@@ -965,3 +965,295 @@ extern "C" sfhe_status sfhe_prng_words(uint64_t seed, uint32_t domain, uint64_t 
     CUDA_TRY(launch_prng(seed, domain, o0, o1, o2, idx0, n, out, as_stream(stream)));
     return SFHE_OK;
 }
+
+// ------------------------------------------------- slot-packed chunks ---
+// Alg. 1 with chunk size c > 1 (Sec. 3.2): c values per ciphertext in its
+// slots, rotations to and from slot 0, the slot-0 mask.
+
+extern "C" sfhe_status sfhe_slots_encode(uint32_t N, uint64_t t, const int64_t* values, int64_t* poly)
+{
+    if (!values || !poly) return fail(SFHE_EINVAL, "null argument");
+    if (!slots_encode(N, t, values, poly)) return fail(SFHE_EUNSUPPORTED, "N=%u t=%llu", N, (unsigned long long)t);
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_slots_decode(uint32_t N, uint64_t t, const int64_t* poly, int64_t* values)
+{
+    if (!values || !poly) return fail(SFHE_EINVAL, "null argument");
+    if (!slots_decode(N, t, poly, values)) return fail(SFHE_EUNSUPPORTED, "N=%u t=%llu", N, (unsigned long long)t);
+    return SFHE_OK;
+}
+
+extern "C" uint32_t sfhe_rotation_element(uint32_t N, int32_t k)
+{
+    if (N < 4 || (N & (N - 1))) return 0;
+    const int64_t half = N / 2;
+    const uint64_t e = (uint64_t)(((k % half) + half) % half);
+    uint64_t g = 1;
+    for (uint64_t i = 0; i < e; i++) g = g * 3 % (2ULL * N);
+    return (uint32_t)g;
+}
+
+extern "C" sfhe_status sfhe_encrypt_poly(sfhe_ctx* c, const int64_t* polys, const int32_t* coords, int64_t n,
+                                         uint64_t matrix_id, uint64_t* ct, void* stream)
+{
+    if (!c) return fail(SFHE_EINVAL, "null context");
+    if (n < 0) return fail(SFHE_ESHAPE, "negative count");
+    if (n == 0) return SFHE_OK;
+    if (!polys || !coords || !ct) return fail(SFHE_EINVAL, "null argument");
+    cudaStream_t s = as_stream(stream);
+    const size_t N = c->rc.N;
+    long long* d_polys = nullptr;
+    int* d_coords = nullptr;
+    CUDA_TRY(cudaMallocAsync((void**)&d_polys, n * N * sizeof(long long), s));
+    CUDA_TRY(cudaMallocAsync((void**)&d_coords, n * 2 * sizeof(int), s));
+    CUDA_TRY(cudaMemcpyAsync(d_polys, polys, n * N * sizeof(long long), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(d_coords, coords, n * 2 * sizeof(int), cudaMemcpyHostToDevice, s));
+    cudaError_t e = launch_encrypt_poly(c->rc, c->d_s, d_polys, d_coords, n, matrix_id, ct, c->d_err, s);
+    cudaFreeAsync(d_polys, s);
+    cudaFreeAsync(d_coords, s);
+    if (e != cudaSuccess) return fail(SFHE_ECUDA, "encrypt_poly: %s", cudaGetErrorString(e));
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_decrypt_poly(sfhe_ctx* c, const uint64_t* ct, int64_t n, int64_t* out, void* stream)
+{
+    if (!c) return fail(SFHE_EINVAL, "null context");
+    if (n < 0) return fail(SFHE_ESHAPE, "negative count");
+    if (n == 0) return SFHE_OK;
+    if (!ct || !out) return fail(SFHE_EINVAL, "null argument");
+    cudaStream_t s = as_stream(stream);
+    u64* w = nullptr;
+    CUDA_TRY(cudaMallocAsync((void**)&w, (size_t)n * c->rc.L * c->rc.N * 8, s));
+    cudaError_t e = launch_decrypt_poly(c->rc, c->d_s, ct, n, w, (long long*)out, s);
+    cudaFreeAsync(w, s);
+    if (e != cudaSuccess) return fail(SFHE_ECUDA, "decrypt_poly: %s", cudaGetErrorString(e));
+    return SFHE_OK;
+}
+
+static size_t key_words(const RnsConsts& rc) { return (size_t)rc.L * 2 * rc.L * rc.N; }
+
+extern "C" sfhe_status sfhe_galois_keygen(sfhe_ctx* c, uint32_t g, uint64_t* key, uint64_t* key_sh, void* stream)
+{
+    if (!c || !key || !key_sh) return fail(SFHE_EINVAL, "null argument");
+    if (!(g & 1) || g >= 2 * c->rc.N) return fail(SFHE_EINVAL, "g must be odd and below 2N");
+    cudaError_t e = launch_galois_keygen(c->rc, c->d_s, g, key, key_sh, c->d_err, as_stream(stream));
+    if (e != cudaSuccess) return fail(SFHE_ECUDA, "galois keygen: %s", cudaGetErrorString(e));
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_rotate_workspace_size(const sfhe_ctx* c, size_t* bytes)
+{
+    if (!c || !bytes) return fail(SFHE_EINVAL, "null argument");
+    *bytes = rotate_work_words(c->rc) * 8;
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_rotate(sfhe_ctx* c, const uint64_t* in, int64_t n, uint32_t g, const uint64_t* key,
+                                   const uint64_t* key_sh, uint64_t* out, void* work, size_t work_bytes, void* stream)
+{
+    if (!c) return fail(SFHE_EINVAL, "null context");
+    if (n < 0) return fail(SFHE_ESHAPE, "negative count");
+    if (n == 0) return SFHE_OK;
+    if (!in || !key || !key_sh || !out || !work) return fail(SFHE_EINVAL, "null argument");
+    if (in == out) return fail(SFHE_EINVAL, "in and out must not overlap");
+    if (!(g & 1) || g >= 2 * c->rc.N) return fail(SFHE_EINVAL, "g must be odd and below 2N");
+    if (work_bytes < rotate_work_words(c->rc) * 8) return fail(SFHE_ENOMEM, "rotation workspace too small");
+    const size_t ctw = (size_t)2 * c->rc.L * c->rc.N;
+    for (int64_t i = 0; i < n; i++) {
+        cudaError_t e = launch_rotate(c->rc, in + i * ctw, g, key, key_sh, out + i * ctw, (u64*)work, as_stream(stream));
+        if (e != cudaSuccess) return fail(SFHE_ECUDA, "rotate: %s", cudaGetErrorString(e));
+    }
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_plain_ntt(sfhe_ctx* c, const int64_t* poly, uint64_t* pt, void* stream)
+{
+    if (!c || !poly || !pt) return fail(SFHE_EINVAL, "null argument");
+    const RnsConsts& rc = c->rc;
+    const size_t N = rc.N, L = rc.L;
+    std::vector<u64> h(L * N);
+    const int64_t t = (int64_t)rc.t;
+    for (size_t k = 0; k < N; k++) {
+        int64_t v = poly[k] % t;
+        if (v < 0) v += t;
+        if (v > t / 2) v -= t;  // centred representative
+        for (size_t i = 0; i < L; i++) h[i * N + k] = v >= 0 ? (u64)v : rc.m[i].q - (u64)(-v);
+    }
+    cudaStream_t s = as_stream(stream);
+    u64* d = nullptr;
+    CUDA_TRY(cudaMallocAsync((void**)&d, L * N * 8, s));
+    CUDA_TRY(cudaMemcpyAsync(d, h.data(), L * N * 8, cudaMemcpyHostToDevice, s));
+    cudaError_t e = launch_ntt(rc, false, d, L * N, 0, pt, L * N, 0, 0, (int)L, 1, s);
+    cudaFreeAsync(d, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(SFHE_ECUDA, "plain ntt: %s", cudaGetErrorString(e));
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_mul_plain(sfhe_ctx* c, uint64_t* ct, int64_t n, const uint64_t* pt, void* stream)
+{
+    if (!c || (n > 0 && (!ct || !pt))) return fail(SFHE_EINVAL, "null argument");
+    if (n < 0) return fail(SFHE_ESHAPE, "negative count");
+    cudaError_t e = n ? launch_mul_plain(c->rc, ct, n, pt, as_stream(stream)) : cudaSuccess;
+    if (e != cudaSuccess) return fail(SFHE_ECUDA, "mul_plain: %s", cudaGetErrorString(e));
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_add(sfhe_ctx* c, uint64_t* acc, const uint64_t* x, int64_t n, void* stream)
+{
+    if (!c || (n > 0 && (!acc || !x))) return fail(SFHE_EINVAL, "null argument");
+    if (n < 0) return fail(SFHE_ESHAPE, "negative count");
+    cudaError_t e = n ? launch_add_ct(c->rc, acc, x, n, as_stream(stream)) : cudaSuccess;
+    if (e != cudaSuccess) return fail(SFHE_ECUDA, "add: %s", cudaGetErrorString(e));
+    return SFHE_OK;
+}
+
+// rotation keys of one chunk size: left and right rotations by 1 .. c-1
+struct sfhe_rotkeys {
+    sfhe_ctx* ctx;
+    int32_t c;
+    u64* d_keys;  // [2 (left, right)][c - 1][2 (key, companions)][key_words]
+};
+
+static const u64* rotkey(const sfhe_rotkeys* rk, int right, int off, int sh)
+{
+    const size_t kw = key_words(rk->ctx->rc);
+    return rk->d_keys + (((size_t)right * (rk->c - 1) + (off - 1)) * 2 + sh) * kw;
+}
+
+extern "C" sfhe_status sfhe_rotkeys_create(sfhe_ctx* c, int32_t chunk, void* stream, sfhe_rotkeys** out)
+{
+    if (!c || !out) return fail(SFHE_EINVAL, "null argument");
+    *out = nullptr;
+    if (chunk < 1 || chunk > (int32_t)(c->rc.N / 2)) return fail(SFHE_ESHAPE, "chunk size outside 1 .. N/2");
+    sfhe_rotkeys* rk = new sfhe_rotkeys();
+    rk->ctx = c;
+    rk->c = chunk;
+    rk->d_keys = nullptr;
+    const size_t kw = key_words(c->rc), nkeys = 2 * (size_t)(chunk - 1);
+    cudaStream_t s = as_stream(stream);
+    if (nkeys) {
+        if (cudaMalloc((void**)&rk->d_keys, nkeys * 2 * kw * 8) != cudaSuccess) {
+            delete rk;
+            return fail(SFHE_ENOMEM, "rotation keys: %zu bytes", nkeys * 2 * kw * 8);
+        }
+        for (int right = 0; right < 2; right++)
+            for (int off = 1; off < chunk; off++) {
+                const uint32_t g = sfhe_rotation_element(c->rc.N, right ? -off : off);
+                cudaError_t e = launch_galois_keygen(c->rc, c->d_s, g, (u64*)rotkey(rk, right, off, 0),
+                                                     (u64*)rotkey(rk, right, off, 1), c->d_err, s);
+                if (e != cudaSuccess) {
+                    cudaFree(rk->d_keys);
+                    delete rk;
+                    return fail(SFHE_ECUDA, "rotation keys: %s", cudaGetErrorString(e));
+                }
+            }
+    }
+    *out = rk;
+    return SFHE_OK;
+}
+
+extern "C" void sfhe_rotkeys_destroy(sfhe_rotkeys* rk)
+{
+    if (!rk) return;
+    if (rk->d_keys) cudaFree(rk->d_keys);
+    delete rk;
+}
+
+// workspace of sfhe_matmul_chunked (bytes): rotation scratch; four
+// ciphertexts (the two rotated operands, the product, the rotated product);
+// the lift of two ciphertexts and its scratch; the tensor T [3][K][N] u32;
+// D [3][L][N], U [(L+2)][L][N]; the mask [L][N]
+static size_t chunked_words(const RnsConsts& rc)
+{
+    const size_t LN = (size_t)rc.L * rc.N, KN = (size_t)rc.K * rc.N;
+    return rotate_work_words(rc) + 4 * 2 * LN + 2 * KN /* ext a, b: 2 x [2][K][N] u32 */ +
+           (2 * LN + KN) /* lift scratch of one ciphertext */ + (3 * KN + 1) / 2 + 3 * LN + (rc.L + 2) * LN + LN;
+}
+
+extern "C" sfhe_status sfhe_matmul_chunked_workspace_size(const sfhe_ctx* c, size_t* bytes)
+{
+    if (!c || !bytes) return fail(SFHE_EINVAL, "null argument");
+    *bytes = chunked_words(c->rc) * 8;
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_matmul_chunked(sfhe_ctx* c, const sfhe_rotkeys* rk, int32_t M, int32_t K, int32_t Nc,
+                                          const uint64_t* A, const uint64_t* B, uint64_t* C, const uint8_t* a_zero,
+                                          const uint8_t* b_zero, void* work, size_t work_bytes, void* stream,
+                                          int64_t* products)
+{
+    if (!c || !rk || !work) return fail(SFHE_EINVAL, "null argument");
+    if (rk->ctx != c) return fail(SFHE_EINVAL, "rotation keys of another context");
+    if (M < 0 || K < 0 || Nc < 0) return fail(SFHE_ESHAPE, "negative shape");
+    if (work_bytes < chunked_words(c->rc) * 8) return fail(SFHE_ENOMEM, "chunked workspace too small");
+    const RnsConsts& rc = c->rc;
+    const int32_t ch = rk->c;
+    const size_t LN = (size_t)rc.L * rc.N, KN = (size_t)rc.K * rc.N, ctw = 2 * LN;
+    const int64_t nC = ((int64_t)M * Nc + ch - 1) / ch;
+    if (nC > 0 && (!A || !B || !C)) return fail(SFHE_EINVAL, "null operand");
+    cudaStream_t s = as_stream(stream);
+    u64* w = (u64*)work;
+    u64* rot_work = w;
+    w += rotate_work_words(rc);
+    u64 *ra = w, *rb = w + ctw, *prod = w + 2 * ctw, *rr = w + 3 * ctw;
+    w += 4 * ctw;
+    u32* ea = (u32*)w;
+    u32* eb = ea + 2 * KN;
+    w += 2 * KN;
+    u64* lift_ws = w;
+    const size_t lift_bytes = (2 * LN + KN) * 8;
+    w += 2 * LN + KN;
+    u32* T = (u32*)w;
+    w += (3 * KN + 1) / 2;
+    u64* D = w;
+    w += 3 * LN;
+    u64* U = w;
+    w += (rc.L + 2) * LN;
+    u64* mask = w;
+    // the slot-0 mask: one-hot plaintext in NTT form
+    {
+        std::vector<int64_t> v(rc.N, 0), poly(rc.N);
+        v[0] = 1;
+        if (!slots_encode((uint32_t)rc.N, rc.t, v.data(), poly.data())) return fail(SFHE_EUNSUPPORTED, "slots");
+        sfhe_status st = sfhe_plain_ntt(c, poly.data(), mask, stream);
+        if (st != SFHE_OK) return st;
+    }
+    if (nC > 0) CUDA_TRY(cudaMemsetAsync(C, 0, (size_t)nC * ctw * 8, s));
+    auto rotated = [&](const u64* src, int off, bool right, u64* dst) -> const u64* {
+        if (off == 0) return src;
+        if (launch_rotate(rc, src, sfhe_rotation_element(rc.N, right ? -off : off), rotkey(rk, right, off, 0),
+                          rotkey(rk, right, off, 1), dst, rot_work, s) != cudaSuccess)
+            return nullptr;
+        return dst;
+    };
+    int64_t done = 0;
+    for (int32_t i = 0; i < M; i++)
+        for (int32_t j = 0; j < Nc; j++)
+            for (int32_t k = 0; k < K; k++) {
+                if (a_zero && a_zero[(int64_t)i * K + k]) continue;
+                if (b_zero && b_zero[(int64_t)k * Nc + j]) continue;
+                const int64_t ia = (int64_t)i * K + k, ib = (int64_t)k * Nc + j, ir = (int64_t)i * Nc + j;
+                const u64* a = rotated(A + (ia / ch) * ctw, (int)(ia % ch), false, ra);
+                const u64* b = rotated(B + (ib / ch) * ctw, (int)(ib % ch), false, rb);
+                if (!a || !b) return fail(SFHE_ECUDA, "rotation: %s", cudaGetErrorString(cudaGetLastError()));
+                sfhe_status st = sfhe_lift(c, a, 1, ea, lift_ws, lift_bytes, stream);
+                if (st == SFHE_OK) st = sfhe_lift(c, b, 1, eb, lift_ws, lift_bytes, stream);
+                if (st != SFHE_OK) return st;
+                cudaError_t e = launch_tensor_intt(rc, ea, eb, T, s);
+                if (e == cudaSuccess) e = launch_scale_round(rc, T, D, s);
+                if (e == cudaSuccess) e = launch_relin_ntt(rc, D, U, s);
+                if (e == cudaSuccess) e = cudaMemsetAsync(prod, 0, ctw * 8, s);
+                if (e == cudaSuccess) e = launch_relin_accum(rc, U, c->d_rlk, c->d_rlk_sh, prod, s);
+                if (e == cudaSuccess) e = launch_mul_plain(rc, prod, 1, mask, s);
+                if (e != cudaSuccess) return fail(SFHE_ECUDA, "chunked product: %s", cudaGetErrorString(e));
+                const u64* r = rotated(prod, (int)(ir % ch), true, rr);
+                if (!r) return fail(SFHE_ECUDA, "rotation: %s", cudaGetErrorString(cudaGetLastError()));
+                e = launch_add_ct(rc, C + (ir / ch) * ctw, r, 1, s);
+                if (e != cudaSuccess) return fail(SFHE_ECUDA, "accumulate: %s", cudaGetErrorString(e));
+                done++;
+            }
+    if (products) *products = done;
+    return SFHE_OK;
+}

@@ -1,6 +1,8 @@
 // host_math.cpp -- number theory on the host for the RNS bases.
 #include "host_math.h"
 
+#include <utility>
+
 #include <math.h>
 #include <string.h>
 
@@ -94,6 +96,94 @@ uint64_t min_primitive_2n_root(uint64_t q, uint32_t N)
         if (cur < best) best = cur;
     }
     return best;
+}
+
+// ------------------------------------------------------------- slots ---
+// slot s = (r, j) = (s / (N/2), s mod (N/2)) holds m(zeta^e_s), e_s = 3^j
+// (r = 0) or -3^j (r = 1) mod 2N, zeta the smallest primitive 2N-th root of
+// unity mod t; the e_s are the odd residues mod 2N, so the slots are the
+// negacyclic transform m(zeta^(2i+1)), i = (e_s - 1) / 2, reordered.
+static void slot_positions(uint32_t N, std::vector<uint32_t>& pos)
+{
+    pos.resize(N);
+    uint64_t x = 1;
+    for (uint32_t j = 0; j < N / 2; ++j) {
+        pos[j] = (uint32_t)((x - 1) / 2);
+        pos[N / 2 + j] = (uint32_t)((2ULL * N - x - 1) / 2);
+        x = x * 3 % (2ULL * N);
+    }
+}
+
+// y_i = sum_k a_k w^(ik), natural order, w of order N (radix-2, in place)
+static void cyclic_dft(std::vector<uint64_t>& a, uint64_t w, uint64_t t)
+{
+    const uint32_t N = (uint32_t)a.size();
+    int bits = 0;
+    while ((1u << bits) < N) ++bits;
+    for (uint32_t i = 0; i < N; ++i) {
+        uint32_t r = 0;
+        for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1u) << (bits - 1 - b);
+        if (i < r) std::swap(a[i], a[r]);
+    }
+    for (uint32_t len = 2; len <= N; len <<= 1) {
+        const uint64_t wl = powm(w, N / len, t);
+        for (uint32_t i = 0; i < N; i += len) {
+            uint64_t x = 1;
+            for (uint32_t k = 0; k < len / 2; ++k) {
+                const uint64_t u = a[i + k], v = mulm(a[i + k + len / 2], x, t);
+                a[i + k] = (u + v) % t;
+                a[i + k + len / 2] = (u + t - v) % t;
+                x = mulm(x, wl, t);
+            }
+        }
+    }
+}
+
+static bool slot_params(uint32_t N, uint64_t t, uint64_t& zeta)
+{
+    if (N < 4 || (N & (N - 1)) || t < 3 || (t - 1) % (2ULL * N) || !is_prime_u64(t)) return false;
+    zeta = min_primitive_2n_root(t, N);
+    return zeta != 0;
+}
+
+bool slots_decode(uint32_t N, uint64_t t, const int64_t* poly, int64_t* vals)
+{
+    uint64_t zeta;
+    if (!slot_params(N, t, zeta)) return false;
+    std::vector<uint64_t> a(N);
+    uint64_t z = 1;
+    for (uint32_t k = 0; k < N; ++k) {
+        const int64_t m = poly[k] % (int64_t)t;
+        a[k] = mulm(m < 0 ? (uint64_t)(m + (int64_t)t) : (uint64_t)m, z, t);
+        z = mulm(z, zeta, t);
+    }
+    cyclic_dft(a, mulm(zeta, zeta, t), t);
+    std::vector<uint32_t> pos;
+    slot_positions(N, pos);
+    for (uint32_t s = 0; s < N; ++s) vals[s] = (int64_t)a[pos[s]];
+    return true;
+}
+
+bool slots_encode(uint32_t N, uint64_t t, const int64_t* vals, int64_t* poly)
+{
+    uint64_t zeta;
+    if (!slot_params(N, t, zeta)) return false;
+    std::vector<uint32_t> pos;
+    slot_positions(N, pos);
+    std::vector<uint64_t> y(N);
+    for (uint32_t s = 0; s < N; ++s) {
+        const int64_t v = vals[s] % (int64_t)t;
+        y[pos[s]] = v < 0 ? (uint64_t)(v + (int64_t)t) : (uint64_t)v;
+    }
+    const uint64_t zi = invm(zeta, t);
+    cyclic_dft(y, mulm(zi, zi, t), t);
+    const uint64_t ninv = invm(N % t, t);
+    uint64_t z = 1;
+    for (uint32_t k = 0; k < N; ++k) {
+        poly[k] = (int64_t)mulm(mulm(y[k], ninv, t), z, t);
+        z = mulm(z, zi, t);
+    }
+    return true;
 }
 
 void cdt_table(double sigma, uint64_t* T)

@@ -12,6 +12,12 @@ bool is_prime_u64(uint64_t n);
 bool ntt_primes(uint32_t N, int count, std::vector<uint64_t>& out, int bits = 54);
 // Smallest primitive 2N-th root of unity mod q.
 uint64_t min_primitive_2n_root(uint64_t q, uint32_t N);
+// Slot packing over Z_t[X]/(X^N + 1), t prime and 1 mod 2N: slot s of m is
+// m(zeta^e_s), s = (r, j) = (s / (N/2), s mod (N/2)), e_s = 3^j (r = 0) or
+// -3^j (r = 1) mod 2N, zeta the smallest primitive 2N-th root of unity mod
+// t.  Outputs in [0, t); false if t or N does not fit.
+bool slots_encode(uint32_t N, uint64_t t, const int64_t* vals, int64_t* poly);
+bool slots_decode(uint32_t N, uint64_t t, const int64_t* poly, int64_t* vals);
 // Rounded-Gaussian |e| table (20 entries) for width sigma.
 void cdt_table(double sigma, uint64_t* T);
 // Twiddle tables of one prime: [4][N] = psi_rev, psi_rev_shoup, ipsi_rev,

@@ -50,6 +50,20 @@ int persistent_ctas_per_sm(const RnsConsts& rc);
 cudaError_t launch_persistent(const RnsConsts& rc, const MmDesc* mms, const Entry* entries, int n_entries,
                               const int2* rowlist, const u64* rlk, const u64* rlk_sh, u64* scratch,
                               size_t scratch_stride, unsigned* queue, int grid, bool grouped, cudaStream_t s);
+// slot-packed ciphertexts (slots.cu)
+cudaError_t launch_galois_keygen(const RnsConsts& rc, const u64* s_ntt, u32 g, u64* key, u64* key_sh, int* err,
+                                 cudaStream_t s);
+cudaError_t launch_encrypt_poly(const RnsConsts& rc, const u64* s_ntt, const long long* polys, const int* coords,
+                                long long n, u64 matrix_id, u64* ct, int* err, cudaStream_t s);
+// w: n L N words of scratch; out: n N message digits in [0, t) (device)
+cudaError_t launch_decrypt_poly(const RnsConsts& rc, const u64* s_ntt, const u64* ct, long long n, u64* w,
+                                long long* out, cudaStream_t s);
+cudaError_t launch_galois_apply(const RnsConsts& rc, const u64* in, long long n, u32 g, u64* out, cudaStream_t s);
+cudaError_t launch_mul_plain(const RnsConsts& rc, u64* ct, long long n, const u64* pt, cudaStream_t s);
+cudaError_t launch_add_ct(const RnsConsts& rc, u64* acc, const u64* x, long long n, cudaStream_t s);
+size_t rotate_work_words(const RnsConsts& rc);
+cudaError_t launch_rotate(const RnsConsts& rc, const u64* in, u32 g, const u64* key, const u64* key_sh, u64* out,
+                          u64* work, cudaStream_t s);
 // multiplies per second of shoup32_lazy over all SMs (8 independent chains
 // per thread, full occupancy), timed with events on s; synchronises s
 cudaError_t measure_mulmod32(u32 b, u32 w, u32 ws, double* per_s, cudaStream_t s);

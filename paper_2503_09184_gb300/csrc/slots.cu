@@ -1,0 +1,325 @@
+// slots.cu -- slot-packed ciphertexts for Alg. 1 with chunk size c > 1
+// (Sec. 3.2): encryption of whole plaintext polynomials, decryption of every
+// coefficient, Galois keys, rotations (automorphism + key switch),
+// ciphertext x plaintext products and additions.
+//
+// Automorphisms act on the NTT form as a permutation: slot i holds the
+// evaluation at psi^e_i, e_i = 2 bitrev(i) + 1, and X -> X^g evaluates the
+// input at psi^(g e_i), which is the input's slot with e = g e_i mod 2N.
+#include "launch.h"
+#include "launch_util.cuh"
+
+namespace sfhe {
+
+namespace {
+
+// stream domains of the Galois keys (after those of rns.h: secret 1,
+// relinearisation key 2 and 3, encryption 4 and 5)
+constexpr u64 SFHE_DOM_GAL_A = 6, SFHE_DOM_GAL_E = 7;
+
+#define SLOTS_DISPATCH_LOGN(logN, ...)              \
+    switch (logN) {                                 \
+    case 12: { constexpr int LG = 12; __VA_ARGS__; } \
+    case 13: { constexpr int LG = 13; __VA_ARGS__; } \
+    case 14: { constexpr int LG = 14; __VA_ARGS__; } \
+    default: return cudaErrorInvalidValue;          \
+    }
+
+// the input slot whose evaluation point is psi^(g e_i)
+template <int LOGN>
+SFHE_DEV int galois_src(int i, u32 g)
+{
+    constexpr u64 twoN = 2ull << LOGN;
+    const u64 e = 2ull * (__brev((unsigned)i) >> (32 - LOGN)) + 1ull;
+    const u64 f = (e * g) & (twoN - 1);
+    return (int)(__brev((unsigned)((f - 1) >> 1)) >> (32 - LOGN));
+}
+
+// Galois key for g, block (limb i, digit j), same layout as the
+// relinearisation key ([L digit][2 (b, a)][L limb][N], NTT form, Shoup
+// companions beside):  b_j = -a_j s + e_j + delta_ij s(X^g),  a_j uniform;
+// a_j from the stream (DOM_GAL_A, g, j) at index i N + k (coefficient k),
+// e_j from (DOM_GAL_E, g, j) at index k.
+template <int LOGN>
+__global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_galois_keygen(const __grid_constant__ RnsConsts c,
+                                                                       const u64* s_ntt, u32 g, u64* key, u64* key_sh,
+                                                                       int* err)
+{
+    using NT_ = typename NttGeom<LOGN>::T;
+    constexpr int N = NT_::N;
+    extern __shared__ u64 sm[];
+    const int i = blockIdx.x, j = blockIdx.y, tid = threadIdx.x, L = c.L;
+    const Mod m = c.m[i];
+    const u64* tw = c.tw + (size_t)i * 4 * N;
+    int fail = 0;
+    const u64 ka = sm_key(c.seed, SFHE_DOM_GAL_A, (u64)g, (u64)j, 0);
+    const u64 ke = sm_key(c.seed, SFHE_DOM_GAL_E, (u64)g, (u64)j, 0);
+    u64 a[NT_::R], e[NT_::R];
+#pragma unroll
+    for (int v = 0; v < NT_::R; v++) {
+        const int k = NT_::fwd_in_idx(v, tid);
+        a[v] = sample_uniform(ka, (u64)i * N + k, m.q, &fail);
+        e[v] = to_residue(sample_gauss(ke, (u64)k, c.cdt), m.q);
+    }
+    NT_::forward(a, sm, tid, tw, m.q);
+    NT_::forward(e, sm, tid, tw, m.q);
+    u64* b_out = key + (((size_t)j * 2 + 0) * L + i) * N;
+    u64* a_out = key + (((size_t)j * 2 + 1) * L + i) * N;
+    u64* bs_out = key_sh + (((size_t)j * 2 + 0) * L + i) * N;
+    u64* as_out = key_sh + (((size_t)j * 2 + 1) * L + i) * N;
+    const u64* s = s_ntt + (size_t)i * N;
+#pragma unroll
+    for (int v = 0; v < NT_::R; v++) {
+        const int k = NT_::run_idx(v, tid);
+        const u64 av = barrett64(a[v], m), ev = barrett64(e[v], m);
+        u64 bv = sub_mod(ev, mul_mod(av, s[k], m), m.q);
+        if (i == j) bv = add_mod(bv, s[galois_src<LOGN>(k, g)], m.q);
+        b_out[k] = bv;
+        a_out[k] = av;
+        bs_out[k] = (u64)(((unsigned __int128)bv << 64) / m.q);
+        as_out[k] = (u64)(((unsigned __int128)av << 64) / m.q);
+    }
+    if (fail) atomicExch(err, 1);
+}
+
+// Secret-key encryption of plaintext polynomials polys[n][N] (every
+// coefficient a message digit mod t), block (limb l, ciphertext n):
+// c1 = a, c0 = -a s + e + Delta m; stream object (matrix_id, coords[2n],
+// coords[2n+1]) as for one value in the constant coefficient.
+template <int LOGN>
+__global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_encrypt_poly(const __grid_constant__ RnsConsts c,
+                                                                      const u64* s_ntt, const long long* polys,
+                                                                      const int* coords, u64 matrix_id, u64* ct, int* err)
+{
+    using NT_ = typename NttGeom<LOGN>::T;
+    constexpr int N = NT_::N;
+    extern __shared__ u64 sm[];
+    const int l = blockIdx.x, n = blockIdx.y, tid = threadIdx.x, L = c.L;
+    const Mod m = c.m[l];
+    const u64* tw = c.tw + (size_t)l * 4 * N;
+    const u64 row = (u64)(unsigned)coords[2 * n], col = (u64)(unsigned)coords[2 * n + 1];
+    const u64 ka = sm_key(c.seed, SFHE_DOM_ENC_A, matrix_id, row, col);
+    const u64 ke = sm_key(c.seed, SFHE_DOM_ENC_E, matrix_id, row, col);
+    const long long* msg = polys + (size_t)n * N;
+    int fail = 0;
+    u64 a[NT_::R], e[NT_::R];
+#pragma unroll
+    for (int v = 0; v < NT_::R; v++) {
+        const int k = NT_::fwd_in_idx(v, tid);
+        a[v] = sample_uniform(ka, (u64)l * N + k, m.q, &fail);
+        long long mt = msg[k] % (long long)c.t;
+        if (mt < 0) mt += (long long)c.t;
+        e[v] = add_mod(to_residue(sample_gauss(ke, (u64)k, c.cdt), m.q), mul_mod(c.delta_q[l], (u64)mt, m), m.q);
+    }
+    NT_::forward(a, sm, tid, tw, m.q);
+    NT_::forward(e, sm, tid, tw, m.q);
+    u64* c0 = ct + ((size_t)n * 2 * L + l) * N;
+    u64* c1 = c0 + (size_t)L * N;
+#pragma unroll
+    for (int v = 0; v < NT_::R; v++) {
+        const int k = NT_::run_idx(v, tid);
+        const u64 av = barrett64(a[v], m);
+        c0[k] = sub_mod(barrett64(e[v], m), mul_mod(av, s_ntt[(size_t)l * N + k], m), m.q);
+        c1[k] = av;
+    }
+    if (fail) atomicExch(err, 1);
+}
+
+// w[n][l] = c0 + c1 s  (NTT form, canonical)
+__global__ void __launch_bounds__(256) k_dec_phase(const __grid_constant__ RnsConsts c, const u64* s_ntt, const u64* ct,
+                                                   u64* w)
+{
+    const int N = c.N, L = c.L;
+    const int k = blockIdx.x * 256 + threadIdx.x, l = blockIdx.y, n = blockIdx.z;
+    if (k >= N) return;
+    const Mod m = c.m[l];
+    const u64* c0 = ct + ((size_t)n * 2 * L + l) * N;
+    const u64* c1 = c0 + (size_t)L * N;
+    w[((size_t)n * L + l) * N + k] = add_mod(csub(c0[k], m.q), mul_mod(c1[k], s_ntt[(size_t)l * N + k], m), m.q);
+}
+
+// every coefficient of the message, from v = [c0 + c1 s] in coefficient form
+// (canonical residues [n][L][N]): m = [sum_i floor(x~_i t / q_i) +
+// round(sum_i y_i / q_i)]_t with x~_i = [v_i (Q/q_i)^-1]_{q_i},
+// x~_i t = u_i q_i + y_i, in [0, t)
+__global__ void __launch_bounds__(256) k_dec_round(const __grid_constant__ RnsConsts c, const u64* v, long long* out,
+                                                   long long n_total)
+{
+    const int N = c.N, L = c.L;
+    const long long idx = (long long)blockIdx.x * 256 + threadIdx.x;
+    if (idx >= n_total) return;
+    const long long n = idx / N;
+    const int k = (int)(idx - n * N);
+    u64 y[SFHE_MAX_L];
+    u64 usum = 0;
+    for (int i = 0; i < L; i++) {
+        const u64 qi = c.m[i].q;
+        const u64 xt = shoup(v[((size_t)n * L + i) * N + k], c.qhat_inv[i], qi);
+        u64 quo;
+        y[i] = shoup_quot(xt, c.t_q[i], qi, quo);
+        usum += quo;
+    }
+    const u64 kk = crt_round<0>(y, c, L);
+    out[idx] = (long long)((usum + kk) % c.t);
+}
+
+// out = ct with X -> X^g applied to both polynomials (NTT form: a gather)
+template <int LOGN>
+__global__ void __launch_bounds__(256) k_galois_apply(const __grid_constant__ RnsConsts c, const u64* in, u32 g, u64* out)
+{
+    constexpr int N = 1 << LOGN;
+    const int k = blockIdx.x * 256 + threadIdx.x;
+    const size_t poly = blockIdx.y;  // n * 2L + p L + l
+    if (k >= N) return;
+    out[poly * N + k] = in[poly * N + galois_src<LOGN>(k, g)];
+}
+
+// ct[n][p][l] *= pt[l] (NTT form)
+__global__ void __launch_bounds__(256) k_mul_plain(const __grid_constant__ RnsConsts c, u64* ct, const u64* pt)
+{
+    const int N = c.N, L = c.L;
+    const int k = blockIdx.x * 256 + threadIdx.x, l = blockIdx.y;
+    if (k >= N) return;
+    const Mod m = c.m[l];
+    const size_t o = ((size_t)blockIdx.z * L + l) * N + k;  // z = n * 2 + p
+    ct[o] = mul_mod(csub(ct[o], m.q), pt[(size_t)l * N + k], m);
+}
+
+// acc += x (mod q_l), [n][2][L][N]
+__global__ void __launch_bounds__(256) k_add_ct(const __grid_constant__ RnsConsts c, u64* acc, const u64* x)
+{
+    const int N = c.N, L = c.L;
+    const int k = blockIdx.x * 256 + threadIdx.x, l = blockIdx.y;
+    if (k >= N) return;
+    const u64 q = c.m[l].q;
+    const size_t o = ((size_t)blockIdx.z * L + l) * N + k;
+    acc[o] = add_mod(csub(acc[o], q), csub(x[o], q), q);
+}
+
+template <int LOGN>
+cudaError_t galois_keygen_impl(const RnsConsts& rc, const u64* s_ntt, u32 g, u64* key, u64* key_sh, int* err,
+                               cudaStream_t s)
+{
+    cudaError_t e = allow_smem(k_galois_keygen<LOGN>, smem_of<LOGN>());
+    if (e != cudaSuccess) return e;
+    k_galois_keygen<LOGN><<<dim3(rc.L, rc.L), nt_of<LOGN>(), smem_of<LOGN>(), s>>>(rc, s_ntt, g, key, key_sh, err);
+    return cudaGetLastError();
+}
+
+template <int LOGN>
+cudaError_t encrypt_poly_impl(const RnsConsts& rc, const u64* s_ntt, const long long* polys, const int* coords,
+                              long long n, u64 matrix_id, u64* ct, int* err, cudaStream_t s)
+{
+    cudaError_t e = allow_smem(k_encrypt_poly<LOGN>, smem_of<LOGN>());
+    if (e != cudaSuccess) return e;
+    for (long long n0 = 0; n0 < n; n0 += 65535) {
+        const long long cnt = n - n0 < 65535 ? n - n0 : 65535;
+        k_encrypt_poly<LOGN><<<dim3(rc.L, (unsigned)cnt), nt_of<LOGN>(), smem_of<LOGN>(), s>>>(
+            rc, s_ntt, polys + n0 * rc.N, coords + 2 * n0, matrix_id, ct + (size_t)n0 * 2 * rc.L * rc.N, err);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_galois_keygen(const RnsConsts& rc, const u64* s_ntt, u32 g, u64* key, u64* key_sh, int* err,
+                                 cudaStream_t s)
+{
+    SLOTS_DISPATCH_LOGN(rc.logN, return galois_keygen_impl<LG>(rc, s_ntt, g, key, key_sh, err, s));
+}
+
+cudaError_t launch_encrypt_poly(const RnsConsts& rc, const u64* s_ntt, const long long* polys, const int* coords,
+                                long long n, u64 matrix_id, u64* ct, int* err, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    SLOTS_DISPATCH_LOGN(rc.logN, return encrypt_poly_impl<LG>(rc, s_ntt, polys, coords, n, matrix_id, ct, err, s));
+}
+
+cudaError_t launch_decrypt_poly(const RnsConsts& rc, const u64* s_ntt, const u64* ct, long long n, u64* w,
+                                long long* out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const unsigned bx = (unsigned)((rc.N + 255) / 256);
+    for (long long n0 = 0; n0 < n; n0 += 65535) {
+        const long long cnt = n - n0 < 65535 ? n - n0 : 65535;
+        k_dec_phase<<<dim3(bx, rc.L, (unsigned)cnt), 256, 0, s>>>(rc, s_ntt, ct + (size_t)n0 * 2 * rc.L * rc.N,
+                                                                  w + (size_t)n0 * rc.L * rc.N);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = launch_ntt(rc, true, w, (size_t)rc.L * rc.N, 0, w, (size_t)rc.L * rc.N, 0, 0, rc.L, n, s);
+    if (e != cudaSuccess) return e;
+    const long long total = n * rc.N;
+    k_dec_round<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(rc, w, out, total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_galois_apply(const RnsConsts& rc, const u64* in, long long n, u32 g, u64* out, cudaStream_t s)
+{
+    const unsigned bx = (unsigned)((rc.N + 255) / 256);
+    const long long polys = n * 2 * rc.L;
+    for (long long p0 = 0; p0 < polys; p0 += 65535) {
+        const long long cnt = polys - p0 < 65535 ? polys - p0 : 65535;
+        SLOTS_DISPATCH_LOGN(rc.logN, {
+            k_galois_apply<LG><<<dim3(bx, (unsigned)cnt), 256, 0, s>>>(rc, in + (size_t)p0 * rc.N, g,
+                                                                        out + (size_t)p0 * rc.N);
+            break;
+        });
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_mul_plain(const RnsConsts& rc, u64* ct, long long n, const u64* pt, cudaStream_t s)
+{
+    const unsigned bx = (unsigned)((rc.N + 255) / 256);
+    for (long long z0 = 0; z0 < 2 * n; z0 += 65535) {
+        const long long cnt = 2 * n - z0 < 65535 ? 2 * n - z0 : 65535;
+        k_mul_plain<<<dim3(bx, rc.L, (unsigned)cnt), 256, 0, s>>>(rc, ct + (size_t)z0 * rc.L * rc.N, pt);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_add_ct(const RnsConsts& rc, u64* acc, const u64* x, long long n, cudaStream_t s)
+{
+    const unsigned bx = (unsigned)((rc.N + 255) / 256);
+    for (long long z0 = 0; z0 < 2 * n; z0 += 65535) {
+        const long long cnt = 2 * n - z0 < 65535 ? 2 * n - z0 : 65535;
+        k_add_ct<<<dim3(bx, rc.L, (unsigned)cnt), 256, 0, s>>>(rc, acc + (size_t)z0 * rc.L * rc.N,
+                                                               x + (size_t)z0 * rc.L * rc.N);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Rotation of one ciphertext: P = sigma_g(in) (NTT form); its two
+// polynomials back to coefficient form give d0 = sigma_g(c0) and the digits
+// D_j = [sigma_g(c1)]_{q_j} (canonical); with d1 = 0 the relinearisation
+// kernels then form out = (d0 + sum_j D_j b_j, sum_j D_j a_j) with the
+// Galois key in place of the relinearisation key.
+// work: P [2][L][N], D [3][L][N], U [(L+2)][L][N] (uint64).
+size_t rotate_work_words(const RnsConsts& rc) { return (size_t)(2 + 3 + rc.L + 2) * rc.L * rc.N; }
+
+cudaError_t launch_rotate(const RnsConsts& rc, const u64* in, u32 g, const u64* key, const u64* key_sh, u64* out,
+                          u64* work, cudaStream_t s)
+{
+    const size_t LN = (size_t)rc.L * rc.N;
+    u64* P = work;
+    u64* D = P + 2 * LN;
+    u64* U = D + 3 * LN;
+    cudaError_t e = launch_galois_apply(rc, in, 1, g, P, s);
+    if (e == cudaSuccess) e = launch_ntt(rc, true, P, LN, 0, D, LN, 0, 0, rc.L, 1, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(D + LN, 0, LN * 8, s);
+    if (e == cudaSuccess) e = launch_ntt(rc, true, P + LN, LN, 0, D + 2 * LN, LN, 0, 0, rc.L, 1, s);
+    if (e == cudaSuccess) e = launch_relin_ntt(rc, D, U, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, 2 * LN * 8, s);
+    if (e == cudaSuccess) e = launch_relin_accum(rc, U, key, key_sh, out, s);
+    return e;
+}
+
+}  // namespace sfhe

@@ -80,6 +80,22 @@ _SIGS = {
     "sfhe_plan_create": ([_vp, _i32, _P(sfhe_matrix), _P(sfhe_matrix), _P(sfhe_matrix), _u32, _vp, _sz, _vp, _P(_vp)],
                          ctypes.c_int),
     "sfhe_plan_execute": ([_vp, _vp], ctypes.c_int),
+    "sfhe_slots_encode": ([_u32, _u64, _vp, _vp], ctypes.c_int),
+    "sfhe_slots_decode": ([_u32, _u64, _vp, _vp], ctypes.c_int),
+    "sfhe_rotation_element": ([_u32, _i32], _u32),
+    "sfhe_encrypt_poly": ([_vp, _vp, _vp, _i64, _u64, _vp, _vp], ctypes.c_int),
+    "sfhe_decrypt_poly": ([_vp, _vp, _i64, _vp, _vp], ctypes.c_int),
+    "sfhe_galois_keygen": ([_vp, _u32, _vp, _vp, _vp], ctypes.c_int),
+    "sfhe_rotate_workspace_size": ([_vp, _P(_sz)], ctypes.c_int),
+    "sfhe_rotate": ([_vp, _vp, _i64, _u32, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
+    "sfhe_plain_ntt": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+    "sfhe_mul_plain": ([_vp, _vp, _i64, _vp, _vp], ctypes.c_int),
+    "sfhe_add": ([_vp, _vp, _vp, _i64, _vp], ctypes.c_int),
+    "sfhe_rotkeys_create": ([_vp, _i32, _vp, _P(_vp)], ctypes.c_int),
+    "sfhe_rotkeys_destroy": ([_vp], None),
+    "sfhe_matmul_chunked_workspace_size": ([_vp, _P(_sz)], ctypes.c_int),
+    "sfhe_matmul_chunked": ([_vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp, _P(_i64)],
+                            ctypes.c_int),
     "sfhe_measure_mulmod32": ([_vp, _P(ctypes.c_double), _vp], ctypes.c_int),
     "sfhe_plan_stats": ([_vp, _P(_i64), _P(_i64), _P(_i64), _P(_i64)], ctypes.c_int),
     "sfhe_matmul_check": ([_vp, _vp], ctypes.c_int),
@@ -287,6 +303,89 @@ def sfhe_plan_create(ctx: int, A: list, B: list, C: list, flags: int, work, stre
 
 def sfhe_plan_execute(plan: int, stream=None) -> None:
     _check(lib().sfhe_plan_execute(plan, _stream(stream)))
+
+
+# ------------------------------------------------ slot-packed chunks ---
+def sfhe_slots_encode(N: int, t: int, values) -> np.ndarray:
+    v = np.ascontiguousarray(np.asarray(values, dtype=np.int64))
+    out = np.zeros(N, dtype=np.int64)
+    _check(lib().sfhe_slots_encode(N, t, _ptr(v), _ptr(out)))
+    return out
+
+
+def sfhe_slots_decode(N: int, t: int, poly) -> np.ndarray:
+    p = np.ascontiguousarray(np.asarray(poly, dtype=np.int64))
+    out = np.zeros(N, dtype=np.int64)
+    _check(lib().sfhe_slots_decode(N, t, _ptr(p), _ptr(out)))
+    return out
+
+
+def sfhe_rotation_element(N: int, k: int) -> int:
+    return int(lib().sfhe_rotation_element(N, k))
+
+
+def sfhe_encrypt_poly(ctx: int, polys: np.ndarray, coords: np.ndarray, matrix_id: int, ct, stream=None) -> None:
+    polys = np.ascontiguousarray(polys, dtype=np.int64)
+    coords = np.ascontiguousarray(coords, dtype=np.int32)
+    _check(lib().sfhe_encrypt_poly(ctx, _ptr(polys), _ptr(coords), polys.shape[0], matrix_id, _ptr(ct),
+                                   _stream(stream)))
+
+
+def sfhe_decrypt_poly(ctx: int, ct, n: int, out, stream=None) -> None:
+    _check(lib().sfhe_decrypt_poly(ctx, _ptr(ct), n, _ptr(out), _stream(stream)))
+
+
+def sfhe_galois_keygen(ctx: int, g: int, key, key_sh, stream=None) -> None:
+    _check(lib().sfhe_galois_keygen(ctx, g, _ptr(key), _ptr(key_sh), _stream(stream)))
+
+
+def sfhe_rotate_workspace_size(ctx: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().sfhe_rotate_workspace_size(ctx, ctypes.byref(b)))
+    return b.value
+
+
+def sfhe_rotate(ctx: int, ct_in, n: int, g: int, key, key_sh, ct_out, work, stream=None) -> None:
+    _check(lib().sfhe_rotate(ctx, _ptr(ct_in), n, g, _ptr(key), _ptr(key_sh), _ptr(ct_out), _ptr(work),
+                             work.numel() * work.element_size(), _stream(stream)))
+
+
+def sfhe_plain_ntt(ctx: int, poly, pt, stream=None) -> None:
+    p = np.ascontiguousarray(np.asarray(poly, dtype=np.int64))
+    _check(lib().sfhe_plain_ntt(ctx, _ptr(p), _ptr(pt), _stream(stream)))
+
+
+def sfhe_mul_plain(ctx: int, ct, n: int, pt, stream=None) -> None:
+    _check(lib().sfhe_mul_plain(ctx, _ptr(ct), n, _ptr(pt), _stream(stream)))
+
+
+def sfhe_add(ctx: int, acc, x, n: int, stream=None) -> None:
+    _check(lib().sfhe_add(ctx, _ptr(acc), _ptr(x), n, _stream(stream)))
+
+
+def sfhe_rotkeys_create(ctx: int, c: int, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().sfhe_rotkeys_create(ctx, c, _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def sfhe_rotkeys_destroy(rk: int) -> None:
+    lib().sfhe_rotkeys_destroy(rk)
+
+
+def sfhe_matmul_chunked_workspace_size(ctx: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().sfhe_matmul_chunked_workspace_size(ctx, ctypes.byref(b)))
+    return b.value
+
+
+def sfhe_matmul_chunked(ctx: int, rk: int, M: int, K: int, Nc: int, A, B, C, a_zero, b_zero, work,
+                        stream=None) -> int:
+    n = ctypes.c_int64()
+    _check(lib().sfhe_matmul_chunked(ctx, rk, M, K, Nc, _ptr(A), _ptr(B), _ptr(C), _ptr(a_zero), _ptr(b_zero),
+                                     _ptr(work), work.numel() * work.element_size(), _stream(stream),
+                                     ctypes.byref(n)))
+    return n.value
 
 
 def sfhe_measure_mulmod32(ctx: int, stream=None) -> float:

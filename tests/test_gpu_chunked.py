@@ -1,0 +1,128 @@
+"""Alg. 1 with chunk size c > 1 (Sec. 3.2) on the GPU against the oracle,
+limb for limb: encryption of whole plaintext polynomials, Galois keys,
+rotations, the slot-0 mask multiply (N = 4096, L = 2), and the chunked
+matmul with and without the naive sparse skip (N = 4096, L = 3: the
+rotations before the multiply switch keys without a special prime, adding
+noise of order N q_j sigma that the multiply scales by about t N, which two
+primes cannot hold); a larger chunked matmul by decryption."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from gpu_common import gpu_ctx, gpu_modules, oracle_ctx
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+T = 65537
+N, L, SEED = 4096, 2, 7
+
+
+def _coeff(api, ctx, ct):
+    n = ct.shape[0]
+    return api.to_coeff(ctx, ct.contiguous(), n)
+
+
+def _setup():
+    api, S = gpu_modules()
+    return api, S, gpu_ctx(N, L, SEED), oracle_ctx(N, L, SEED)
+
+
+def _enc_slots(api, S, ctx, vals, mid):
+    import torch
+    polys = np.stack([S.sfhe_slots_encode(N, T, v) for v in vals])
+    coords = np.array([[q, 0] for q in range(len(vals))], dtype=np.int32)
+    ct = torch.empty((len(vals), 2, L, N), dtype=torch.int64, device="cuda")
+    S.sfhe_encrypt_poly(ctx.h, polys, coords, mid, ct)
+    return polys, ct
+
+
+def test_poly_encryption_matches_oracle():
+    import torch
+    api, S, ctx, octx = _setup()
+    vals = np.random.default_rng(1).integers(0, T, size=(2, N))
+    polys, ct = _enc_slots(api, S, ctx, vals, 9)
+    got = _coeff(api, ctx, ct)
+    for q in range(2):
+        assert (got[q] == octx.encrypt_poly(polys[q], 9, q, 0)).all(), q
+    out = torch.empty((2, N), dtype=torch.int64, device="cuda")
+    S.sfhe_decrypt_poly(ctx.h, ct, 2, out)
+    assert (out.cpu().numpy() == polys).all()
+
+
+@pytest.mark.parametrize("k", [1, -3])
+def test_rotation_matches_oracle(k):
+    import torch
+    api, S, ctx, octx = _setup()
+    g = S.sfhe_rotation_element(N, k)
+    key = torch.empty((L, 2, L, N), dtype=torch.int64, device="cuda")
+    key_sh = torch.empty_like(key)
+    S.sfhe_galois_keygen(ctx.h, g, key, key_sh)
+    okey = octx.galois_key(g)
+    assert (api.to_coeff(ctx, key.contiguous(), L) == okey).all()   # L digits x (b, a): 2L polynomials
+    vals = np.random.default_rng(2).integers(0, T, size=(1, N))
+    polys, ct = _enc_slots(api, S, ctx, vals, 3)
+    out = torch.empty_like(ct)
+    work = torch.empty(S.sfhe_rotate_workspace_size(ctx.h), dtype=torch.uint8, device="cuda")
+    S.sfhe_rotate(ctx.h, ct, 1, g, key, key_sh, out, work)
+    want = octx.rotate(octx.encrypt_poly(polys[0], 3, 0, 0), g, okey)
+    assert (_coeff(api, ctx, out)[0] == want).all()
+    dec = torch.empty((1, N), dtype=torch.int64, device="cuda")
+    S.sfhe_decrypt_poly(ctx.h, out, 1, dec)
+    slots = S.sfhe_slots_decode(N, T, dec.cpu().numpy()[0])
+    h = N // 2
+    assert (slots == np.concatenate([np.roll(vals[0][:h], -k), np.roll(vals[0][h:], -k)])).all()
+
+
+def test_mul_plain_matches_oracle():
+    import torch
+    api, S, ctx, octx = _setup()
+    rng = np.random.default_rng(3)
+    vals = rng.integers(0, T, size=(1, N))
+    w = rng.integers(0, T, size=N)
+    polys, ct = _enc_slots(api, S, ctx, vals, 4)
+    pw = S.sfhe_slots_encode(N, T, w)
+    pt = torch.empty((L, N), dtype=torch.int64, device="cuda")
+    S.sfhe_plain_ntt(ctx.h, pw, pt)
+    S.sfhe_mul_plain(ctx.h, ct, 1, pt)
+    want = octx.mul_plain(octx.encrypt_poly(polys[0], 4, 0, 0), pw.astype(np.uint64))
+    assert (_coeff(api, ctx, ct)[0] == want).all()
+
+
+@pytest.mark.parametrize("chunk", [3, 4])
+def test_chunked_matmul_matches_oracle(chunk):
+    api, S = gpu_modules()
+    ctx, octx = gpu_ctx(N, 3, SEED), oracle_ctx(N, 3, SEED)
+    A = np.array([[3, 0, -7], [0, 5, 2]], dtype=np.int64)
+    B = np.array([[2, -1], [0, 4], [6, 0]], dtype=np.int64)
+    oc = O.OracleChunked(octx, A, B, chunk, 1, 2)
+    Ae = api.encrypt_chunked(ctx, A, chunk, 1)
+    Be = api.encrypt_chunked(ctx, B, chunk, 2)
+    ga = _coeff(api, ctx, Ae.ct)
+    assert all((ga[q] == oc.a_ct[q]).all() for q in range(Ae.nchunks))
+    rk = api.RotationKeys(ctx, chunk)
+    for skip in ((False, True) if chunk == 4 else (True,)):
+        C, n = api.matmul_chunked(ctx, Ae, Be, rk, skip_zeros=skip)
+        assert n == (int(((A != 0).astype(int) @ (B != 0).astype(int)).sum()) if skip else 12)
+        got = _coeff(api, ctx, C.ct)
+        want = oc.result(skip_zeros=skip)
+        for q in range(C.nchunks):
+            assert (got[q] == want[q]).all(), (chunk, skip, q)
+        assert (api.decrypt_chunked(ctx, C) == A @ B).all()
+    rk.close()
+
+
+def test_chunked_matmul_8192_decrypts():
+    api, S = gpu_modules()
+    ctx = gpu_ctx(8192, 4, 0)
+    rng = np.random.default_rng(5)
+    A = rng.integers(-16, 17, size=(6, 8)) * (rng.random((6, 8)) < 0.5)
+    B = rng.integers(-16, 17, size=(8, 5))
+    Ae = api.encrypt_chunked(ctx, A, 8, 11)
+    Be = api.encrypt_chunked(ctx, B, 8, 12)
+    rk = api.RotationKeys(ctx, 8)
+    C, n = api.matmul_chunked(ctx, Ae, Be, rk, skip_zeros=True)
+    assert n == int(((A != 0).astype(int) @ (B != 0).astype(int)).sum())
+    want = ((A @ B + T // 2) % T) - T // 2
+    assert (api.decrypt_chunked(ctx, C) == want).all()
+    rk.close()

@@ -119,3 +119,22 @@ def test_matrix_bytes_per_encoding(S):
     with pytest.raises(S.SfheError) as e:
         S.sfhe_matrix_bytes(1000, 4, S.sfhe_matrix(1, 1, 0, 1, 0, None, None, None, None, None, None))
     assert e.value.status == S.SFHE_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("N", [16, 4096])
+def test_slot_codec_matches_oracle(S, N):
+    """The library's slot encoding (a fast negacyclic transform mod t) and
+    the oracle's (direct evaluation and interpolation) agree on random
+    vectors both ways; rotation elements are 3^k mod 2N."""
+    from oracle import oracle as O
+    T = 65537
+    v = np.random.default_rng(N).integers(-T // 2, T // 2, size=N)
+    poly = S.sfhe_slots_encode(N, T, v)
+    assert (poly == O.slots_encode(N, T, v).astype(np.int64)).all()
+    assert (S.sfhe_slots_decode(N, T, poly) == v % T).all()
+    assert (O.slots_decode(N, T, poly.astype(np.uint64)).astype(np.int64) == v % T).all()
+    for k in (0, 1, 5, -1, -3, N // 2):
+        assert S.sfhe_rotation_element(N, k) == O.rotation_element(N, k) == pow(3, k % (N // 2), 2 * N)
+    with pytest.raises(S.SfheError) as e:
+        S.sfhe_slots_encode(N, 65539, v)          # 65539 is not 1 mod 2N
+    assert e.value.status == S.SFHE_EUNSUPPORTED
