@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--workload", default="sweep", choices=["sweep", "tiny", "layer", "mixed", "serve", "chunked"])
     ap.add_argument("--chunk", type=int, default=8, help="chunked: values per ciphertext (Alg. 1 with c > 1)")
     ap.add_argument("--chunked-shape", default="16,16,16", help="chunked: M,K,Nc")
+    ap.add_argument("--alg1-order", action="store_true",
+                    help="chunked: three rotations per product in Alg. 1's order (default: operand rotations once "
+                         "per element, inner sums on the persistent kernel, one result rotation per entry)")
     ap.add_argument("--rates", default="0.5,1,2,4", help="serve: Poisson arrival rates (requests/s)")
     ap.add_argument("--requests", type=int, default=16, help="serve: requests per rate")
     ap.add_argument("--serve-dims", default="16,32,64", help="serve: M, K, Nc drawn from these")
@@ -533,16 +536,22 @@ def run_chunked(args):
     Ae = api.encrypt_chunked(ctx, A, args.chunk, 1)
     Be = api.encrypt_chunked(ctx, B, args.chunk, 2)
     rk = api.RotationKeys(ctx, args.chunk)
-    work = torch.empty(S.sfhe_matmul_chunked_workspace_size(ctx.h), dtype=torch.uint8, device="cuda")
+    fused = not args.alg1_order
+    if fused:
+        n_bytes = S.sfhe_matmul_chunked_fused_workspace_size(ctx.h, M, K, Nc, Ae.zero.reshape(-1),
+                                                             Be.zero.reshape(-1))
+    else:
+        n_bytes = S.sfhe_matmul_chunked_workspace_size(ctx.h)
+    work = torch.empty(n_bytes, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
-        C, products = api.matmul_chunked(ctx, Ae, Be, rk, skip_zeros=True, work=work)
+        C, products = api.matmul_chunked(ctx, Ae, Be, rk, skip_zeros=True, fused=fused, work=work)
     torch.cuda.synchronize()
     clocks = ClockSampler(0)
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        C, products = api.matmul_chunked(ctx, Ae, Be, rk, skip_zeros=True, work=work)
+        C, products = api.matmul_chunked(ctx, Ae, Be, rk, skip_zeros=True, fused=fused, work=work)
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -552,11 +561,14 @@ def run_chunked(args):
     line = {"metric": METRIC, "value": products / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": f"chunked-{M}x{K}x{Nc}-c{args.chunk}-s0.5", "N": ring.N, "L": ring.L,
+            "config": {"workload": f"chunked-{M}x{K}x{Nc}-c{args.chunk}-s0.5" + ("" if fused else "-alg1order"),
+                       "N": ring.N, "L": ring.L,
                        "t": W.T_PLAIN, "chunk": args.chunk, "products_per_step": products,
                        "chunks": {"A": Ae.nchunks, "B": Be.nchunks, "C": C.nchunks},
-                       "step": "Alg. 1 over chunks: 3 rotations (key switches), multiply + relinearise, "
-                               "slot-0 mask, add per product; one launch sequence per product"},
+                       "step": ("operand rotations once per element, inner sums of the products on the persistent "
+                                "kernel, slot-0 mask and result rotation per entry" if fused else
+                                "Alg. 1 over chunks: 3 rotations (key switches), multiply + relinearise, slot-0 mask, "
+                                "add per product; one launch sequence per product")},
             "correct": correct, "e2e": None, "roofline": None, "clocks": clk,
             "note": "the paper's general chunked scheme, op by op; the persistent per-element path is the headline"}
     print(json.dumps(line))

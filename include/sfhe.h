@@ -262,6 +262,21 @@ sfhe_status sfhe_matmul_chunked_workspace_size(const sfhe_ctx* ctx, size_t* byte
 sfhe_status sfhe_matmul_chunked(sfhe_ctx* ctx, const sfhe_rotkeys* rk, int32_t M, int32_t K, int32_t Nc,
                                 const uint64_t* A, const uint64_t* B, uint64_t* C, const uint8_t* a_zero,
                                 const uint8_t* b_zero, void* work, size_t work_bytes, void* stream, int64_t* products);
+/* The same products with the operand rotations taken once per element
+ * and the inner sums on the persistent kernel: a_ik = rot(A's chunk,
+ * offset of (i, k)) and b_kj likewise (the operands of Alg. 1's products,
+ * identical), e_ij = sum_k Relin(a_ik x b_kj) (per product, as Alg. 1),
+ * then C[chunk of (i, j)] += rot(mask x e_ij, -offset of (i, j)): the mask
+ * and the last rotation act on each entry's sum, so C is another ciphertext
+ * with the same decryption.  M K + K Nc + M Nc rotations instead of three
+ * per product.  Workspace (device) from the size call, which needs the same
+ * masks. */
+sfhe_status sfhe_matmul_chunked_fused_workspace_size(const sfhe_ctx* ctx, int32_t M, int32_t K, int32_t Nc,
+                                                     const uint8_t* a_zero, const uint8_t* b_zero, size_t* bytes);
+sfhe_status sfhe_matmul_chunked_fused(sfhe_ctx* ctx, const sfhe_rotkeys* rk, int32_t M, int32_t K, int32_t Nc,
+                                      const uint64_t* A, const uint64_t* B, uint64_t* C, const uint8_t* a_zero,
+                                      const uint8_t* b_zero, void* work, size_t work_bytes, void* stream,
+                                      int64_t* products);
 
 /* Measured rate of the 32-bit Shoup modular multiply a w mod b (three
  * 32-bit multiplies: the high product with the precomputed companion and two

@@ -527,6 +527,30 @@ class OracleChunked:
                     self.ctx.add_(R[(i * Nc + j) // self.c], self.product(i, k, j))
         return R
 
+    def result_fused(self, skip_zeros: bool = False) -> list:
+        """the same products with the mask and the result rotation applied to
+        each entry's sum of relinearised products instead of to each product
+        (a different ciphertext with the same decryption; equal to result()
+        wherever the entry sits at offset 0 of its chunk)"""
+        M, Kd = self.A.shape
+        Nc = self.B.shape[1]
+        nchunks = -(-(M * Nc) // self.c)
+        R = [np.zeros(self.ctx.ct_shape, dtype=np.uint64) for _ in range(nchunks)]
+        for i in range(M):
+            for j in range(Nc):
+                e = np.zeros(self.ctx.ct_shape, dtype=np.uint64)
+                for k in range(Kd):
+                    if skip_zeros and (self.A[i, k] == 0 or self.B[k, j] == 0):
+                        continue
+                    ia, ib = i * Kd + k, k * Nc + j
+                    a = self.rot(self.a_ct[ia // self.c], ia % self.c)
+                    b = self.rot(self.b_ct[ib // self.c], ib % self.c)
+                    self.ctx.add_(e, self.ctx.mul_relin(a, b))
+                ir = i * Nc + j
+                x = self.rot(self.ctx.mul_plain(e, self.mask), -(ir % self.c))
+                self.ctx.add_(R[ir // self.c], x)
+        return R
+
     def decode(self, R: list) -> np.ndarray:
         """the result matrix from its chunks (centred mod t)"""
         M, Nc = self.A.shape[0], self.B.shape[1]

@@ -297,18 +297,26 @@ class RotationKeys:
 
 
 def matmul_chunked(ctx: Context, A: ChunkedMatrix, B: ChunkedMatrix, rk: RotationKeys, *, skip_zeros: bool = False,
-                   stream=None, work: torch.Tensor | None = None) -> tuple[ChunkedMatrix, int]:
+                   fused: bool = False, stream=None, work: torch.Tensor | None = None) -> tuple[ChunkedMatrix, int]:
     """C = A x B by Alg. 1 over chunks; skip_zeros: the naive sparse scheme's
-    two masks (products where A[i][k] or B[k][j] is zero are skipped).
+    two masks (products where A[i][k] or B[k][j] is zero are skipped); fused:
+    operand rotations once per element, inner sums on the persistent kernel,
+    mask and result rotation per entry (same decryption, other ciphertext).
     Returns (C, products performed)."""
     assert A.c == B.c == rk.c and A.cols == B.rows
     c = A.c
     nC = -(-(A.rows * B.cols) // c)
     C = ChunkedMatrix(A.rows, B.cols, c, _dev_u64((max(nC, 1), 2, ctx.L, ctx.N)))
-    if work is None:
-        work = torch.empty(S.sfhe_matmul_chunked_workspace_size(ctx.h), dtype=torch.uint8, device="cuda")
     az = np.ascontiguousarray(A.zero.reshape(-1)) if skip_zeros else None
     bz = np.ascontiguousarray(B.zero.reshape(-1)) if skip_zeros else None
-    n = S.sfhe_matmul_chunked(ctx.h, rk.h, A.rows, A.cols, B.cols, A.ct, B.ct, C.ct, az, bz, work, stream)
+    if fused:
+        if work is None:
+            n_bytes = S.sfhe_matmul_chunked_fused_workspace_size(ctx.h, A.rows, A.cols, B.cols, az, bz)
+            work = torch.empty(n_bytes, dtype=torch.uint8, device="cuda")
+        n = S.sfhe_matmul_chunked_fused(ctx.h, rk.h, A.rows, A.cols, B.cols, A.ct, B.ct, C.ct, az, bz, work, stream)
+    else:
+        if work is None:
+            work = torch.empty(S.sfhe_matmul_chunked_workspace_size(ctx.h), dtype=torch.uint8, device="cuda")
+        n = S.sfhe_matmul_chunked(ctx.h, rk.h, A.rows, A.cols, B.cols, A.ct, B.ct, C.ct, az, bz, work, stream)
     C._work = work
     return C, n

@@ -1257,3 +1257,161 @@ extern "C" sfhe_status sfhe_matmul_chunked(sfhe_ctx* c, const sfhe_rotkeys* rk, 
     if (products) *products = done;
     return SFHE_OK;
 }
+
+// Alg. 1 over chunks with the operand rotations taken once per element and
+// the inner sums on the persistent kernel:
+//   a_ik = rot(A chunk of (i, k), offset of (i, k)),  b_kj likewise;
+//   e_ij = sum_k Relin(a_ik x b_kj)        (persistent matmul, per product)
+//   C[chunk of (i, j)] += rot(mask x e_ij, -(offset of (i, j)))
+// The operands' rotations and every product equal Alg. 1's; the mask and
+// the last rotation act on the entry's sum instead of on each product, so
+// the result is another ciphertext with the same decryption.
+namespace {
+struct FusedLayout {
+    size_t rot, arot, brot, cel, rr, ea, eb, lift, mask, plan, total, lift_bytes, plan_bytes;
+};
+
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+sfhe_status fused_layout(const sfhe_ctx* c, int32_t M, int32_t K, int32_t Nc, const sfhe_matrix& Ad,
+                         const sfhe_matrix& Bd, FusedLayout& Lo)
+{
+    const RnsConsts& rc = c->rc;
+    const size_t ctb = (size_t)2 * rc.L * rc.N * 8, extb = (size_t)2 * rc.K * rc.N * 4;
+    const size_t nA = (size_t)M * K, nB = (size_t)K * Nc, nC = (size_t)M * Nc;
+    size_t off = 0;
+    Lo.rot = off, off += al256(rotate_work_words(rc) * 8);
+    Lo.arot = off, off += al256(std::max<size_t>(nA, 1) * ctb);
+    Lo.brot = off, off += al256(std::max<size_t>(nB, 1) * ctb);
+    Lo.cel = off, off += al256(std::max<size_t>(nC, 1) * ctb);
+    Lo.rr = off, off += al256(ctb);
+    Lo.ea = off, off += al256(std::max<size_t>(nA, 1) * extb);
+    Lo.eb = off, off += al256(std::max<size_t>(nB, 1) * extb);
+    sfhe_status st = sfhe_lift_workspace_size(c, (int64_t)std::max(nA, nB), &Lo.lift_bytes);
+    if (st != SFHE_OK) return st;
+    Lo.lift = off, off += al256(Lo.lift_bytes);
+    Lo.mask = off, off += al256((size_t)rc.L * rc.N * 8);
+    const bool dl = false;
+    st = size_impl(c, 1, &Ad, &Bd, &dl, SFHE_EXEC_PERSISTENT, &Lo.plan_bytes);
+    if (st != SFHE_OK) return st;
+    Lo.plan = off, off += al256(Lo.plan_bytes);
+    Lo.total = off;
+    return SFHE_OK;
+}
+
+// descriptors of the rotated operands: MASK-encoded where a zero mask is
+// given (the sparse matmul skips those products), DENSE otherwise
+sfhe_matrix element_desc(int32_t rows, int32_t cols, const uint8_t* zero, uint64_t* ct, uint32_t* ext)
+{
+    sfhe_matrix d;
+    memset(&d, 0, sizeof(d));
+    d.rows = rows;
+    d.cols = cols;
+    d.encoding = zero ? SFHE_ENC_MASK : SFHE_ENC_DENSE;
+    d.nct = rows * cols;
+    d.mask = zero;
+    d.ct = ct;
+    d.ext = ext;
+    return d;
+}
+}  // namespace
+
+extern "C" sfhe_status sfhe_matmul_chunked_fused_workspace_size(const sfhe_ctx* c, int32_t M, int32_t K, int32_t Nc,
+                                                                const uint8_t* a_zero, const uint8_t* b_zero,
+                                                                size_t* bytes)
+{
+    if (!c || !bytes) return fail(SFHE_EINVAL, "null argument");
+    if (M < 0 || K < 0 || Nc < 0) return fail(SFHE_ESHAPE, "negative shape");
+    sfhe_matrix Ad = element_desc(M, K, a_zero, (uint64_t*)16, (uint32_t*)16);
+    sfhe_matrix Bd = element_desc(K, Nc, b_zero, (uint64_t*)16, (uint32_t*)16);
+    FusedLayout Lo;
+    sfhe_status st = fused_layout(c, M, K, Nc, Ad, Bd, Lo);
+    if (st != SFHE_OK) return st;
+    *bytes = Lo.total;
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_matmul_chunked_fused(sfhe_ctx* c, const sfhe_rotkeys* rk, int32_t M, int32_t K,
+                                                int32_t Nc, const uint64_t* A, const uint64_t* B, uint64_t* C,
+                                                const uint8_t* a_zero, const uint8_t* b_zero, void* work,
+                                                size_t work_bytes, void* stream, int64_t* products)
+{
+    if (!c || !rk || !work) return fail(SFHE_EINVAL, "null argument");
+    if (rk->ctx != c) return fail(SFHE_EINVAL, "rotation keys of another context");
+    if (M < 0 || K < 0 || Nc < 0) return fail(SFHE_ESHAPE, "negative shape");
+    const RnsConsts& rc = c->rc;
+    const int32_t ch = rk->c;
+    const size_t ctw = (size_t)2 * rc.L * rc.N;
+    const int64_t nC = ((int64_t)M * Nc + ch - 1) / ch;
+    if (nC > 0 && (!A || !B || !C)) return fail(SFHE_EINVAL, "null operand");
+    char* w = (char*)work;
+    sfhe_matrix Ad = element_desc(M, K, a_zero, nullptr, nullptr), Bd = element_desc(K, Nc, b_zero, nullptr, nullptr);
+    Ad.ct = (uint64_t*)16, Ad.ext = (uint32_t*)16, Bd.ct = (uint64_t*)16, Bd.ext = (uint32_t*)16;
+    FusedLayout Lo;
+    sfhe_status st = fused_layout(c, M, K, Nc, Ad, Bd, Lo);
+    if (st != SFHE_OK) return st;
+    if (work_bytes < Lo.total) return fail(SFHE_ENOMEM, "workspace of %zu bytes needed, %zu given", Lo.total, work_bytes);
+    cudaStream_t s = as_stream(stream);
+    u64* rot_work = (u64*)(w + Lo.rot);
+    u64 *arot = (u64*)(w + Lo.arot), *brot = (u64*)(w + Lo.brot), *cel = (u64*)(w + Lo.cel), *rr = (u64*)(w + Lo.rr);
+    u32 *ea = (u32*)(w + Lo.ea), *eb = (u32*)(w + Lo.eb);
+    u64* mask = (u64*)(w + Lo.mask);
+    {
+        std::vector<int64_t> v(rc.N, 0), poly(rc.N);
+        v[0] = 1;
+        if (!slots_encode((uint32_t)rc.N, rc.t, v.data(), poly.data())) return fail(SFHE_EUNSUPPORTED, "slots");
+        st = sfhe_plain_ntt(c, poly.data(), mask, stream);
+        if (st != SFHE_OK) return st;
+    }
+    // every operand element rotated into slot 0 of its own ciphertext (the
+    // skipped ones zero: the lift reads them, the matmul does not)
+    if (a_zero) CUDA_TRY(cudaMemsetAsync(arot, 0, (size_t)M * K * ctw * 8, s));
+    if (b_zero) CUDA_TRY(cudaMemsetAsync(brot, 0, (size_t)K * Nc * ctw * 8, s));
+    auto place = [&](const u64* chunks, int64_t e, u64* dst) -> cudaError_t {
+        const u64* src = chunks + (e / ch) * ctw;
+        const int off = (int)(e % ch);
+        if (off == 0) return cudaMemcpyAsync(dst, src, ctw * 8, cudaMemcpyDeviceToDevice, s);
+        return launch_rotate(rc, src, sfhe_rotation_element(rc.N, off), rotkey(rk, 0, off, 0), rotkey(rk, 0, off, 1),
+                             dst, rot_work, s);
+    };
+    for (int64_t e = 0; e < (int64_t)M * K; e++) {
+        if (a_zero && a_zero[e]) continue;
+        cudaError_t err = place(A, e, arot + e * ctw);
+        if (err != cudaSuccess) return fail(SFHE_ECUDA, "rotation: %s", cudaGetErrorString(err));
+    }
+    for (int64_t e = 0; e < (int64_t)K * Nc; e++) {
+        if (b_zero && b_zero[e]) continue;
+        cudaError_t err = place(B, e, brot + e * ctw);
+        if (err != cudaSuccess) return fail(SFHE_ECUDA, "rotation: %s", cudaGetErrorString(err));
+    }
+    // skipped elements are never read: the work list leaves them out
+    st = sfhe_lift(c, arot, (int64_t)M * K, ea, w + Lo.lift, Lo.lift_bytes, stream);
+    if (st == SFHE_OK) st = sfhe_lift(c, brot, (int64_t)K * Nc, eb, w + Lo.lift, Lo.lift_bytes, stream);
+    if (st != SFHE_OK) return st;
+    Ad = element_desc(M, K, a_zero, arot, ea);
+    Bd = element_desc(K, Nc, b_zero, brot, eb);
+    sfhe_matrix Cd = element_desc(M, Nc, nullptr, cel, nullptr);
+    const bool dl = false;
+    sfhe_plan* P = nullptr;
+    st = plan_create_impl(c, 1, &Ad, &Bd, &Cd, &dl, SFHE_EXEC_PERSISTENT, w + Lo.plan, Lo.plan_bytes, stream, &P);
+    if (st != SFHE_OK) return st;
+    st = launch_plan(P, s);
+    const int64_t prods = P->products;
+    sfhe_plan_destroy(P);
+    if (st != SFHE_OK) return st;
+    if (nC > 0) CUDA_TRY(cudaMemsetAsync(C, 0, (size_t)nC * ctw * 8, s));
+    cudaError_t e = (int64_t)M * Nc > 0 ? launch_mul_plain(rc, cel, (int64_t)M * Nc, mask, s) : cudaSuccess;
+    for (int64_t ir = 0; e == cudaSuccess && ir < (int64_t)M * Nc; ir++) {
+        const int off = (int)(ir % ch);
+        const u64* r = cel + ir * ctw;
+        if (off) {
+            e = launch_rotate(rc, r, sfhe_rotation_element(rc.N, -off), rotkey(rk, 1, off, 0), rotkey(rk, 1, off, 1),
+                              rr, rot_work, s);
+            r = rr;
+        }
+        if (e == cudaSuccess) e = launch_add_ct(rc, C + (ir / ch) * ctw, r, 1, s);
+    }
+    if (e != cudaSuccess) return fail(SFHE_ECUDA, "chunked results: %s", cudaGetErrorString(e));
+    if (products) *products = prods;
+    return SFHE_OK;
+}

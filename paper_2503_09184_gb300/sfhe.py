@@ -96,6 +96,9 @@ _SIGS = {
     "sfhe_matmul_chunked_workspace_size": ([_vp, _P(_sz)], ctypes.c_int),
     "sfhe_matmul_chunked": ([_vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp, _P(_i64)],
                             ctypes.c_int),
+    "sfhe_matmul_chunked_fused_workspace_size": ([_vp, _i32, _i32, _i32, _vp, _vp, _P(_sz)], ctypes.c_int),
+    "sfhe_matmul_chunked_fused": ([_vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp, _P(_i64)],
+                                  ctypes.c_int),
     "sfhe_measure_mulmod32": ([_vp, _P(ctypes.c_double), _vp], ctypes.c_int),
     "sfhe_plan_stats": ([_vp, _P(_i64), _P(_i64), _P(_i64), _P(_i64)], ctypes.c_int),
     "sfhe_matmul_check": ([_vp, _vp], ctypes.c_int),
@@ -385,6 +388,22 @@ def sfhe_matmul_chunked(ctx: int, rk: int, M: int, K: int, Nc: int, A, B, C, a_z
     _check(lib().sfhe_matmul_chunked(ctx, rk, M, K, Nc, _ptr(A), _ptr(B), _ptr(C), _ptr(a_zero), _ptr(b_zero),
                                      _ptr(work), work.numel() * work.element_size(), _stream(stream),
                                      ctypes.byref(n)))
+    return n.value
+
+
+def sfhe_matmul_chunked_fused_workspace_size(ctx: int, M: int, K: int, Nc: int, a_zero, b_zero) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().sfhe_matmul_chunked_fused_workspace_size(ctx, M, K, Nc, _ptr(a_zero), _ptr(b_zero),
+                                                          ctypes.byref(b)))
+    return b.value
+
+
+def sfhe_matmul_chunked_fused(ctx: int, rk: int, M: int, K: int, Nc: int, A, B, C, a_zero, b_zero, work,
+                              stream=None) -> int:
+    n = ctypes.c_int64()
+    _check(lib().sfhe_matmul_chunked_fused(ctx, rk, M, K, Nc, _ptr(A), _ptr(B), _ptr(C), _ptr(a_zero), _ptr(b_zero),
+                                           _ptr(work), work.numel() * work.element_size(), _stream(stream),
+                                           ctypes.byref(n)))
     return n.value
 
 

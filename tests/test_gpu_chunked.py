@@ -126,3 +126,42 @@ def test_chunked_matmul_8192_decrypts():
     want = ((A @ B + T // 2) % T) - T // 2
     assert (api.decrypt_chunked(ctx, C) == want).all()
     rk.close()
+
+
+def test_chunked_fused_matches_oracle():
+    """operand rotations once per element, inner sums on the persistent
+    kernel, mask and result rotation per entry: limb for limb the oracle's
+    fused order, decrypting to A B"""
+    api, S = gpu_modules()
+    ctx, octx = gpu_ctx(N, 3, SEED), oracle_ctx(N, 3, SEED)
+    A = np.array([[3, 0, -7, 1], [0, 5, 2, 0], [4, 4, 0, -2]], dtype=np.int64)
+    B = np.array([[2, -1], [0, 4], [6, 0], [1, 1]], dtype=np.int64)
+    oc = O.OracleChunked(octx, A, B, 4, 1, 2)
+    Ae = api.encrypt_chunked(ctx, A, 4, 1)
+    Be = api.encrypt_chunked(ctx, B, 4, 2)
+    rk = api.RotationKeys(ctx, 4)
+    for skip in (False, True):
+        C, n = api.matmul_chunked(ctx, Ae, Be, rk, skip_zeros=skip, fused=True)
+        assert n == (int(((A != 0).astype(int) @ (B != 0).astype(int)).sum()) if skip else A.size * B.shape[1])
+        got = _coeff(api, ctx, C.ct)
+        want = oc.result_fused(skip_zeros=skip)
+        for q in range(C.nchunks):
+            assert (got[q] == want[q]).all(), (skip, q)
+        assert (api.decrypt_chunked(ctx, C) == A @ B).all()
+    rk.close()
+
+
+def test_chunked_fused_8192_decrypts():
+    api, S = gpu_modules()
+    ctx = gpu_ctx(8192, 4, 0)
+    rng = np.random.default_rng(6)
+    A = rng.integers(-16, 17, size=(12, 16)) * (rng.random((12, 16)) < 0.5)
+    B = rng.integers(-16, 17, size=(16, 10))
+    Ae = api.encrypt_chunked(ctx, A, 8, 11)
+    Be = api.encrypt_chunked(ctx, B, 8, 12)
+    rk = api.RotationKeys(ctx, 8)
+    C, n = api.matmul_chunked(ctx, Ae, Be, rk, skip_zeros=True, fused=True)
+    assert n == int(((A != 0).astype(int) @ (B != 0).astype(int)).sum())
+    want = ((A @ B + T // 2) % T) - T // 2
+    assert (api.decrypt_chunked(ctx, C) == want).all()
+    rk.close()

@@ -620,3 +620,17 @@ def test_chunked_alg1_decrypts_to_the_product(chunk):
     skip = oc.result(skip_zeros=True)
     assert (oc.decode(skip) == A @ B).all()
     assert any(not (x == y).all() for x, y in zip(full, skip))
+
+
+def test_chunked_fused_order_pins():
+    """The fused order (mask and result rotation on each entry's sum)
+    decrypts to A B mod t, and equals the per-product order exactly for
+    c = 1 (no result rotation, and the mask multiply is exact and linear)."""
+    c = O.OracleCtx(32, 3, seed=14)
+    A = np.array([[3, 0, -7], [0, 5, 2]], dtype=np.int64)
+    B = np.array([[2, -1], [0, 4], [6, 0]], dtype=np.int64)
+    oc = O.OracleChunked(c, A, B, 4, 1, 2)
+    assert (oc.decode(oc.result_fused()) == A @ B).all()
+    assert (oc.decode(oc.result_fused(skip_zeros=True)) == A @ B).all()
+    o1 = O.OracleChunked(c, A, B, 1, 1, 2)
+    assert all((x == y).all() for x, y in zip(o1.result(), o1.result_fused()))
