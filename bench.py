@@ -538,7 +538,7 @@ def run_chunked(args):
     rk = api.RotationKeys(ctx, args.chunk)
     fused = not args.alg1_order
     if fused:
-        n_bytes = S.sfhe_matmul_chunked_fused_workspace_size(ctx.h, M, K, Nc, Ae.zero.reshape(-1),
+        n_bytes = S.sfhe_matmul_chunked_fused_workspace_size(ctx.h, args.chunk, M, K, Nc, Ae.zero.reshape(-1),
                                                              Be.zero.reshape(-1))
     else:
         n_bytes = S.sfhe_matmul_chunked_workspace_size(ctx.h)

@@ -269,9 +269,9 @@ sfhe_status sfhe_matmul_chunked(sfhe_ctx* ctx, const sfhe_rotkeys* rk, int32_t M
  * then C[chunk of (i, j)] += rot(mask x e_ij, -offset of (i, j)): the mask
  * and the last rotation act on each entry's sum, so C is another ciphertext
  * with the same decryption.  M K + K Nc + M Nc rotations instead of three
- * per product.  Workspace (device) from the size call, which needs the same
- * masks. */
-sfhe_status sfhe_matmul_chunked_fused_workspace_size(const sfhe_ctx* ctx, int32_t M, int32_t K, int32_t Nc,
+ * per product, batched by rotation amount.  Workspace (device) from the size
+ * call, which needs the same chunk size and masks. */
+sfhe_status sfhe_matmul_chunked_fused_workspace_size(const sfhe_ctx* ctx, int32_t c, int32_t M, int32_t K, int32_t Nc,
                                                      const uint8_t* a_zero, const uint8_t* b_zero, size_t* bytes);
 sfhe_status sfhe_matmul_chunked_fused(sfhe_ctx* ctx, const sfhe_rotkeys* rk, int32_t M, int32_t K, int32_t Nc,
                                       const uint64_t* A, const uint64_t* B, uint64_t* C, const uint8_t* a_zero,

@@ -311,7 +311,7 @@ def matmul_chunked(ctx: Context, A: ChunkedMatrix, B: ChunkedMatrix, rk: Rotatio
     bz = np.ascontiguousarray(B.zero.reshape(-1)) if skip_zeros else None
     if fused:
         if work is None:
-            n_bytes = S.sfhe_matmul_chunked_fused_workspace_size(ctx.h, A.rows, A.cols, B.cols, az, bz)
+            n_bytes = S.sfhe_matmul_chunked_fused_workspace_size(ctx.h, c, A.rows, A.cols, B.cols, az, bz)
             work = torch.empty(n_bytes, dtype=torch.uint8, device="cuda")
         n = S.sfhe_matmul_chunked_fused(ctx.h, rk.h, A.rows, A.cols, B.cols, A.ct, B.ct, C.ct, az, bz, work, stream)
     else:

@@ -1267,24 +1267,27 @@ extern "C" sfhe_status sfhe_matmul_chunked(sfhe_ctx* c, const sfhe_rotkeys* rk, 
 // the last rotation act on the entry's sum instead of on each product, so
 // the result is another ciphertext with the same decryption.
 namespace {
+// ciphertexts per batched key switch (the rotation scratch holds this many)
+const long long kRotBatch = 128;
+
 struct FusedLayout {
     size_t rot, arot, brot, cel, rr, ea, eb, lift, mask, plan, total, lift_bytes, plan_bytes;
 };
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-sfhe_status fused_layout(const sfhe_ctx* c, int32_t M, int32_t K, int32_t Nc, const sfhe_matrix& Ad,
+sfhe_status fused_layout(const sfhe_ctx* c, int32_t M, int32_t K, int32_t Nc, int32_t c_chunk, const sfhe_matrix& Ad,
                          const sfhe_matrix& Bd, FusedLayout& Lo)
 {
     const RnsConsts& rc = c->rc;
     const size_t ctb = (size_t)2 * rc.L * rc.N * 8, extb = (size_t)2 * rc.K * rc.N * 4;
     const size_t nA = (size_t)M * K, nB = (size_t)K * Nc, nC = (size_t)M * Nc;
     size_t off = 0;
-    Lo.rot = off, off += al256(rotate_work_words(rc) * 8);
+    Lo.rot = off, off += al256(rotate_batch_words(rc, kRotBatch) * 8);
     Lo.arot = off, off += al256(std::max<size_t>(nA, 1) * ctb);
     Lo.brot = off, off += al256(std::max<size_t>(nB, 1) * ctb);
     Lo.cel = off, off += al256(std::max<size_t>(nC, 1) * ctb);
-    Lo.rr = off, off += al256(ctb);
+    Lo.rr = off, off += al256(std::max<size_t>((nC + (size_t)c_chunk - 1) / (size_t)c_chunk, 1) * ctb);
     Lo.ea = off, off += al256(std::max<size_t>(nA, 1) * extb);
     Lo.eb = off, off += al256(std::max<size_t>(nB, 1) * extb);
     sfhe_status st = sfhe_lift_workspace_size(c, (int64_t)std::max(nA, nB), &Lo.lift_bytes);
@@ -1316,16 +1319,16 @@ sfhe_matrix element_desc(int32_t rows, int32_t cols, const uint8_t* zero, uint64
 }
 }  // namespace
 
-extern "C" sfhe_status sfhe_matmul_chunked_fused_workspace_size(const sfhe_ctx* c, int32_t M, int32_t K, int32_t Nc,
-                                                                const uint8_t* a_zero, const uint8_t* b_zero,
-                                                                size_t* bytes)
+extern "C" sfhe_status sfhe_matmul_chunked_fused_workspace_size(const sfhe_ctx* c, int32_t chunk, int32_t M, int32_t K,
+                                                                int32_t Nc, const uint8_t* a_zero,
+                                                                const uint8_t* b_zero, size_t* bytes)
 {
     if (!c || !bytes) return fail(SFHE_EINVAL, "null argument");
-    if (M < 0 || K < 0 || Nc < 0) return fail(SFHE_ESHAPE, "negative shape");
+    if (M < 0 || K < 0 || Nc < 0 || chunk < 1) return fail(SFHE_ESHAPE, "negative shape or chunk size");
     sfhe_matrix Ad = element_desc(M, K, a_zero, (uint64_t*)16, (uint32_t*)16);
     sfhe_matrix Bd = element_desc(K, Nc, b_zero, (uint64_t*)16, (uint32_t*)16);
     FusedLayout Lo;
-    sfhe_status st = fused_layout(c, M, K, Nc, Ad, Bd, Lo);
+    sfhe_status st = fused_layout(c, M, K, Nc, chunk, Ad, Bd, Lo);
     if (st != SFHE_OK) return st;
     *bytes = Lo.total;
     return SFHE_OK;
@@ -1348,7 +1351,7 @@ extern "C" sfhe_status sfhe_matmul_chunked_fused(sfhe_ctx* c, const sfhe_rotkeys
     sfhe_matrix Ad = element_desc(M, K, a_zero, nullptr, nullptr), Bd = element_desc(K, Nc, b_zero, nullptr, nullptr);
     Ad.ct = (uint64_t*)16, Ad.ext = (uint32_t*)16, Bd.ct = (uint64_t*)16, Bd.ext = (uint32_t*)16;
     FusedLayout Lo;
-    sfhe_status st = fused_layout(c, M, K, Nc, Ad, Bd, Lo);
+    sfhe_status st = fused_layout(c, M, K, Nc, ch, Ad, Bd, Lo);
     if (st != SFHE_OK) return st;
     if (work_bytes < Lo.total) return fail(SFHE_ENOMEM, "workspace of %zu bytes needed, %zu given", Lo.total, work_bytes);
     cudaStream_t s = as_stream(stream);
@@ -1363,27 +1366,30 @@ extern "C" sfhe_status sfhe_matmul_chunked_fused(sfhe_ctx* c, const sfhe_rotkeys
         st = sfhe_plain_ntt(c, poly.data(), mask, stream);
         if (st != SFHE_OK) return st;
     }
-    // every operand element rotated into slot 0 of its own ciphertext (the
-    // skipped ones zero: the lift reads them, the matmul does not)
-    if (a_zero) CUDA_TRY(cudaMemsetAsync(arot, 0, (size_t)M * K * ctw * 8, s));
-    if (b_zero) CUDA_TRY(cudaMemsetAsync(brot, 0, (size_t)K * Nc * ctw * 8, s));
-    auto place = [&](const u64* chunks, int64_t e, u64* dst) -> cudaError_t {
-        const u64* src = chunks + (e / ch) * ctw;
-        const int off = (int)(e % ch);
-        if (off == 0) return cudaMemcpyAsync(dst, src, ctw * 8, cudaMemcpyDeviceToDevice, s);
-        return launch_rotate(rc, src, sfhe_rotation_element(rc.N, off), rotkey(rk, 0, off, 0), rotkey(rk, 0, off, 1),
-                             dst, rot_work, s);
+    // every operand element rotated into slot 0 of its own ciphertext:
+    // element q c + o of a matrix is chunk q rotated left by o, so each
+    // offset o is one batched key switch over all chunks
+    auto place_all = [&](const u64* chunks, int64_t n_el, u64* dst) -> cudaError_t {
+        const int64_t nq = (n_el + ch - 1) / ch;
+        for (int off = 0; off < ch; off++) {
+            const int64_t cnt = off < n_el ? (n_el - off + ch - 1) / ch : 0;  // q with q c + off < n_el
+            if (cnt == 0) continue;
+            cudaError_t e;
+            if (off == 0)
+                e = cudaMemcpy2DAsync(dst, (size_t)ch * ctw * 8, chunks, ctw * 8, ctw * 8, (size_t)cnt,
+                                      cudaMemcpyDeviceToDevice, s);
+            else
+                e = launch_rotate_batch(rc, chunks, ctw, cnt, sfhe_rotation_element(rc.N, off), rotkey(rk, 0, off, 0),
+                                        rotkey(rk, 0, off, 1), dst + (size_t)off * ctw, (size_t)ch * ctw, rot_work,
+                                        kRotBatch, s);
+            if (e != cudaSuccess) return e;
+        }
+        (void)nq;
+        return cudaSuccess;
     };
-    for (int64_t e = 0; e < (int64_t)M * K; e++) {
-        if (a_zero && a_zero[e]) continue;
-        cudaError_t err = place(A, e, arot + e * ctw);
-        if (err != cudaSuccess) return fail(SFHE_ECUDA, "rotation: %s", cudaGetErrorString(err));
-    }
-    for (int64_t e = 0; e < (int64_t)K * Nc; e++) {
-        if (b_zero && b_zero[e]) continue;
-        cudaError_t err = place(B, e, brot + e * ctw);
-        if (err != cudaSuccess) return fail(SFHE_ECUDA, "rotation: %s", cudaGetErrorString(err));
-    }
+    cudaError_t err = place_all(A, (int64_t)M * K, arot);
+    if (err == cudaSuccess) err = place_all(B, (int64_t)K * Nc, brot);
+    if (err != cudaSuccess) return fail(SFHE_ECUDA, "rotation: %s", cudaGetErrorString(err));
     // skipped elements are never read: the work list leaves them out
     st = sfhe_lift(c, arot, (int64_t)M * K, ea, w + Lo.lift, Lo.lift_bytes, stream);
     if (st == SFHE_OK) st = sfhe_lift(c, brot, (int64_t)K * Nc, eb, w + Lo.lift, Lo.lift_bytes, stream);
@@ -1400,16 +1406,21 @@ extern "C" sfhe_status sfhe_matmul_chunked_fused(sfhe_ctx* c, const sfhe_rotkeys
     sfhe_plan_destroy(P);
     if (st != SFHE_OK) return st;
     if (nC > 0) CUDA_TRY(cudaMemsetAsync(C, 0, (size_t)nC * ctw * 8, s));
-    cudaError_t e = (int64_t)M * Nc > 0 ? launch_mul_plain(rc, cel, (int64_t)M * Nc, mask, s) : cudaSuccess;
-    for (int64_t ir = 0; e == cudaSuccess && ir < (int64_t)M * Nc; ir++) {
-        const int off = (int)(ir % ch);
-        const u64* r = cel + ir * ctw;
-        if (off) {
-            e = launch_rotate(rc, r, sfhe_rotation_element(rc.N, -off), rotkey(rk, 1, off, 0), rotkey(rk, 1, off, 1),
-                              rr, rot_work, s);
-            r = rr;
-        }
-        if (e == cudaSuccess) e = launch_add_ct(rc, C + (ir / ch) * ctw, r, 1, s);
+    const int64_t nel = (int64_t)M * Nc;
+    cudaError_t e = nel > 0 ? launch_mul_plain(rc, cel, nel, mask, s) : cudaSuccess;
+    // entry q c + o goes to slot o of chunk q: one batched rotation right by
+    // o over the entries at offset o, then one add into the chunks
+    for (int off = 0; e == cudaSuccess && off < ch; off++) {
+        const int64_t cnt = off < nel ? (nel - off + ch - 1) / ch : 0;
+        if (cnt == 0) continue;
+        if (off == 0)
+            e = cudaMemcpy2DAsync(rr, ctw * 8, cel, (size_t)ch * ctw * 8, ctw * 8, (size_t)cnt,
+                                  cudaMemcpyDeviceToDevice, s);
+        else
+            e = launch_rotate_batch(rc, cel + (size_t)off * ctw, (size_t)ch * ctw, cnt,
+                                    sfhe_rotation_element(rc.N, -off), rotkey(rk, 1, off, 0), rotkey(rk, 1, off, 1),
+                                    rr, ctw, rot_work, kRotBatch, s);
+        if (e == cudaSuccess) e = launch_add_ct(rc, C, rr, cnt, s);
     }
     if (e != cudaSuccess) return fail(SFHE_ECUDA, "chunked results: %s", cudaGetErrorString(e));
     if (products) *products = prods;

@@ -62,6 +62,10 @@ cudaError_t launch_galois_apply(const RnsConsts& rc, const u64* in, long long n,
 cudaError_t launch_mul_plain(const RnsConsts& rc, u64* ct, long long n, const u64* pt, cudaStream_t s);
 cudaError_t launch_add_ct(const RnsConsts& rc, u64* acc, const u64* x, long long n, cudaStream_t s);
 size_t rotate_work_words(const RnsConsts& rc);
+size_t rotate_batch_words(const RnsConsts& rc, long long n);
+cudaError_t launch_rotate_batch(const RnsConsts& rc, const u64* in, size_t in_stride, long long n, u32 g,
+                                const u64* key, const u64* key_sh, u64* out, size_t out_stride, u64* work,
+                                long long batch, cudaStream_t s);
 cudaError_t launch_rotate(const RnsConsts& rc, const u64* in, u32 g, const u64* key, const u64* key_sh, u64* out,
                           u64* work, cudaStream_t s);
 // multiplies per second of shoup32_lazy over all SMs (8 independent chains

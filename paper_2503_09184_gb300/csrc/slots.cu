@@ -196,6 +196,84 @@ __global__ void __launch_bounds__(256) k_add_ct(const __grid_constant__ RnsConst
     acc[o] = add_mod(csub(acc[o], q), csub(x[o], q), q);
 }
 
+// batched key switching: ciphertext z of a batch at its own stride
+template <int LOGN>
+__global__ void __launch_bounds__(256) k_galois_apply_b(const __grid_constant__ RnsConsts c, const u64* in,
+                                                        size_t in_stride, u32 g, u64* out, size_t out_stride)
+{
+    constexpr int N = 1 << LOGN;
+    const int k = blockIdx.x * 256 + threadIdx.x;
+    const size_t poly = blockIdx.y;  // p L + l
+    if (k >= N) return;
+    out[blockIdx.z * out_stride + poly * N + k] = in[blockIdx.z * in_stride + poly * N + galois_src<LOGN>(k, g)];
+}
+
+// block (target limb i, source s, ciphertext z): forward NTT of d0 limb i
+// (s = 0), of d1 limb i (s = 1), of digit j = s - 2 mod q_i (s >= 2)
+template <int LOGN>
+__global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_ks_ntt(const __grid_constant__ RnsConsts c, const u64* D,
+                                                                size_t d_stride, u64* U, size_t u_stride)
+{
+    using NT_ = typename NttGeom<LOGN>::T;
+    constexpr int N = NT_::N;
+    extern __shared__ u64 sm[];
+    const int i = blockIdx.x, s = blockIdx.y, tid = threadIdx.x, L = c.L;
+    const Mod m = c.m[i];
+    const u64* Dz = D + blockIdx.z * d_stride;
+    const u64* src = s == 0 ? Dz + (size_t)i * N : (s == 1 ? Dz + ((size_t)L + i) * N : Dz + ((size_t)2 * L + (s - 2)) * N);
+    u64 x[NT_::R];
+#pragma unroll
+    for (int v = 0; v < NT_::R; v++) x[v] = src[NT_::fwd_in_idx(v, tid)];
+    NT_::forward(x, sm, tid, c.tw + (size_t)i * 4 * N, m.q);
+    u64* dst = U + blockIdx.z * u_stride + ((size_t)s * L + i) * N;
+#pragma unroll
+    for (int v = 0; v < NT_::R; v++) dst[NT_::run_idx(v, tid)] = barrett64(x[v], m);
+}
+
+// out[p][i] = U[p][i] + sum_j U[2+j][i] key[j][p][i]   (p = 0: b, 1: a)
+__global__ void __launch_bounds__(256) k_ks_accum(const __grid_constant__ RnsConsts c, const u64* U, size_t u_stride,
+                                                  const u64* key, const u64* key_sh, u64* out, size_t out_stride)
+{
+    const int N = c.N, L = c.L;
+    const int k = blockIdx.x * 256 + threadIdx.x, i = blockIdx.y;
+    if (k >= N) return;
+    const Mod m = c.m[i];
+    const u64* Uz = U + blockIdx.z * u_stride;
+    for (int p = 0; p < 2; p++) {
+        u64 acc = Uz[((size_t)p * L + i) * N + k];
+        for (int j = 0; j < L; j++) {
+            const size_t ro = (((size_t)j * 2 + p) * L + i) * N + k;
+            acc += shoup_lazy(Uz[((size_t)(2 + j) * L + i) * N + k], key[ro], key_sh[ro], m.q);
+        }
+        out[blockIdx.z * out_stride + ((size_t)p * L + i) * N + k] = barrett64(acc, m);
+    }
+}
+
+template <int LOGN>
+cudaError_t rotate_batch_impl(const RnsConsts& rc, const u64* in, size_t in_stride, long long n, u32 g, const u64* key,
+                              const u64* key_sh, u64* out, size_t out_stride, u64* work, cudaStream_t s)
+{
+    const size_t LN = (size_t)rc.L * rc.N;
+    const size_t pw = 2 * LN, dw = 3 * LN, uw = (size_t)(rc.L + 2) * LN;
+    u64* P = work;
+    u64* D = P + (size_t)n * pw;
+    u64* U = D + (size_t)n * dw;
+    const unsigned bx = (unsigned)((rc.N + 255) / 256);
+    k_galois_apply_b<LOGN><<<dim3(bx, 2 * rc.L, (unsigned)n), 256, 0, s>>>(rc, in, in_stride, g, P, pw);
+    cudaError_t e = cudaGetLastError();
+    // d0 = sigma_g(c0), d1 = 0, d2 = sigma_g(c1), coefficient form (canonical)
+    if (e == cudaSuccess) e = launch_ntt(rc, true, P, pw, 0, D, dw, 0, 0, rc.L, n, s);
+    if (e == cudaSuccess) e = launch_ntt(rc, true, P, pw, rc.L, D, dw, 2 * rc.L, 0, rc.L, n, s);
+    if (e == cudaSuccess) e = cudaMemset2DAsync(D + LN, dw * 8, 0, LN * 8, (size_t)n, s);
+    if (e != cudaSuccess) return e;
+    e = allow_smem(k_ks_ntt<LOGN>, smem_of<LOGN>());
+    if (e != cudaSuccess) return e;
+    k_ks_ntt<LOGN><<<dim3(rc.L, rc.L + 2, (unsigned)n), nt_of<LOGN>(), smem_of<LOGN>(), s>>>(rc, D, dw, U, uw);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_ks_accum<<<dim3(bx, rc.L, (unsigned)n), 256, 0, s>>>(rc, U, uw, key, key_sh, out, out_stride);
+    return cudaGetLastError();
+}
+
 template <int LOGN>
 cudaError_t galois_keygen_impl(const RnsConsts& rc, const u64* s_ntt, u32 g, u64* key, u64* key_sh, int* err,
                                cudaStream_t s)
@@ -292,6 +370,27 @@ cudaError_t launch_add_ct(const RnsConsts& rc, u64* acc, const u64* x, long long
         k_add_ct<<<dim3(bx, rc.L, (unsigned)cnt), 256, 0, s>>>(rc, acc + (size_t)z0 * rc.L * rc.N,
                                                                x + (size_t)z0 * rc.L * rc.N);
         cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+size_t rotate_batch_words(const RnsConsts& rc, long long n) { return (size_t)n * rotate_work_words(rc); }
+
+// n ciphertexts at in + z in_stride -> out + z out_stride (words), in
+// batches of at most `batch` (the workspace holds rotate_batch_words(batch))
+cudaError_t launch_rotate_batch(const RnsConsts& rc, const u64* in, size_t in_stride, long long n, u32 g,
+                                const u64* key, const u64* key_sh, u64* out, size_t out_stride, u64* work,
+                                long long batch, cudaStream_t s)
+{
+    for (long long z0 = 0; z0 < n; z0 += batch) {
+        const long long cnt = n - z0 < batch ? n - z0 : batch;
+        cudaError_t e;
+        SLOTS_DISPATCH_LOGN(rc.logN, {
+            e = rotate_batch_impl<LG>(rc, in + z0 * in_stride, in_stride, cnt, g, key, key_sh, out + z0 * out_stride,
+                                      out_stride, work, s);
+            break;
+        });
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

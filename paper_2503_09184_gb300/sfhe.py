@@ -96,7 +96,7 @@ _SIGS = {
     "sfhe_matmul_chunked_workspace_size": ([_vp, _P(_sz)], ctypes.c_int),
     "sfhe_matmul_chunked": ([_vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp, _P(_i64)],
                             ctypes.c_int),
-    "sfhe_matmul_chunked_fused_workspace_size": ([_vp, _i32, _i32, _i32, _vp, _vp, _P(_sz)], ctypes.c_int),
+    "sfhe_matmul_chunked_fused_workspace_size": ([_vp, _i32, _i32, _i32, _i32, _vp, _vp, _P(_sz)], ctypes.c_int),
     "sfhe_matmul_chunked_fused": ([_vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp, _P(_i64)],
                                   ctypes.c_int),
     "sfhe_measure_mulmod32": ([_vp, _P(ctypes.c_double), _vp], ctypes.c_int),
@@ -391,9 +391,9 @@ def sfhe_matmul_chunked(ctx: int, rk: int, M: int, K: int, Nc: int, A, B, C, a_z
     return n.value
 
 
-def sfhe_matmul_chunked_fused_workspace_size(ctx: int, M: int, K: int, Nc: int, a_zero, b_zero) -> int:
+def sfhe_matmul_chunked_fused_workspace_size(ctx: int, c: int, M: int, K: int, Nc: int, a_zero, b_zero) -> int:
     b = ctypes.c_size_t()
-    _check(lib().sfhe_matmul_chunked_fused_workspace_size(ctx, M, K, Nc, _ptr(a_zero), _ptr(b_zero),
+    _check(lib().sfhe_matmul_chunked_fused_workspace_size(ctx, c, M, K, Nc, _ptr(a_zero), _ptr(b_zero),
                                                           ctypes.byref(b)))
     return b.value
 
