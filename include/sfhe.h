@@ -230,7 +230,8 @@ sfhe_status sfhe_galois_keygen(sfhe_ctx* ctx, uint32_t g, uint64_t* key, uint64_
 /* Rotation (fhe_rotate of Alg. 1): out[n] = the key switch back to s of
  * (c0(X^g), c1(X^g)): (c0' + sum_j D_j b_j, sum_j D_j a_j), unsigned digits
  * D_j = [c1']_{q_j}.  in and out device, distinct; needs
- * sfhe_rotate_workspace_size() bytes of device workspace. */
+ * sfhe_rotate_workspace_size() bytes of device workspace per ciphertext
+ * switched at once (a larger workspace batches more). */
 sfhe_status sfhe_rotate_workspace_size(const sfhe_ctx* ctx, size_t* bytes);
 sfhe_status sfhe_rotate(sfhe_ctx* ctx, const uint64_t* in, int64_t n, uint32_t g, const uint64_t* key,
                         const uint64_t* key_sh, uint64_t* out, void* work, size_t work_bytes, void* stream);
@@ -320,6 +321,13 @@ sfhe_status sfhe_plan_execute(sfhe_plan* plan, void* stream);
  * waits for an operand copy ran out (the kernel then stopped early and C is
  * incomplete). */
 sfhe_status sfhe_matmul_check(void* work, void* stream);
+/* Self-test of the bounded device waits (no fault is involved): one thread
+ * waits on an mbarrier that nothing arrives at, gives up after `tries`
+ * attempts (1 .. 2^20) and sets the status word of `work` (device, at
+ * least 256 bytes, its first 8 bytes zeroed by the caller) as the
+ * persistent kernel does; sfhe_matmul_check(work) then reports
+ * SFHE_ETIMEOUT. */
+sfhe_status sfhe_selftest_wait_bound(void* work, uint32_t tries, void* stream);
 /* products performed, output entries, own kernel launches per execute, CTAs */
 sfhe_status sfhe_plan_stats(const sfhe_plan* plan, int64_t* products, int64_t* entries, int64_t* launches,
                             int64_t* ctas);

@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/sfhe.h"
 #include "host_math.h"
 #include "launch.h"
@@ -15,6 +17,12 @@
 using namespace sfhe;
 
 namespace {
+
+// an NVTX range over one entry point (visible to profilers; free otherwise)
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 thread_local std::string g_last_error;
 
@@ -336,6 +344,7 @@ extern "C" sfhe_status sfhe_encode_fill(const int64_t* values, int32_t rows, int
 extern "C" sfhe_status sfhe_encrypt(sfhe_ctx* c, const int64_t* values, const int32_t* coords, int64_t n,
                                     uint64_t matrix_id, uint64_t* ct, void* stream)
 {
+    Range range("sfhe_encrypt");
     if (!c) return fail(SFHE_EINVAL, "null context");
     if (n < 0) return fail(SFHE_ESHAPE, "negative count");
     if (n == 0) return SFHE_OK;
@@ -367,6 +376,7 @@ extern "C" sfhe_status sfhe_lift_workspace_size(const sfhe_ctx* c, int64_t n, si
 extern "C" sfhe_status sfhe_lift(sfhe_ctx* c, const uint64_t* ct, int64_t n, uint32_t* ext, void* work,
                                  size_t work_bytes, void* stream)
 {
+    Range range("sfhe_lift");
     if (!c) return fail(SFHE_EINVAL, "null context");
     if (n < 0) return fail(SFHE_ESHAPE, "negative count");
     if (n == 0) return SFHE_OK;
@@ -759,8 +769,17 @@ extern "C" sfhe_status sfhe_plan_create(sfhe_ctx* c, int32_t n, const sfhe_matri
 
 extern "C" sfhe_status sfhe_plan_execute(sfhe_plan* P, void* stream)
 {
+    Range range("sfhe_plan_execute");
     if (!P) return fail(SFHE_EINVAL, "null plan");
     return launch_plan(P, as_stream(stream));
+}
+
+extern "C" sfhe_status sfhe_selftest_wait_bound(void* work, uint32_t tries, void* stream)
+{
+    if (!work) return fail(SFHE_EINVAL, "null workspace");
+    if (tries == 0 || tries > (1u << 20)) return fail(SFHE_EINVAL, "tries must be in 1 .. 2^20");
+    CUDA_TRY(launch_wait_selftest((unsigned*)work, tries, as_stream(stream)));
+    return SFHE_OK;
 }
 
 extern "C" sfhe_status sfhe_matmul_check(void* work, void* stream)
@@ -820,6 +839,7 @@ extern "C" sfhe_status sfhe_matmul_workspace_size(const sfhe_ctx* c, int32_t n, 
 static sfhe_status one_shot(sfhe_ctx* c, int32_t n, const sfhe_matrix* A, const sfhe_matrix* B, sfhe_matrix* C,
                             const bool* dense_loop, uint32_t flags, void* work, size_t work_bytes, void* stream)
 {
+    Range range("sfhe_matmul");
     sfhe_plan* P = nullptr;
     // a one-shot call launches directly; graphs are for replayed plans
     sfhe_status st = plan_create_impl(c, n, A, B, C, dense_loop, flags & ~(uint32_t)SFHE_EXEC_GRAPH, work, work_bytes,
@@ -1052,6 +1072,7 @@ extern "C" sfhe_status sfhe_rotate_workspace_size(const sfhe_ctx* c, size_t* byt
 extern "C" sfhe_status sfhe_rotate(sfhe_ctx* c, const uint64_t* in, int64_t n, uint32_t g, const uint64_t* key,
                                    const uint64_t* key_sh, uint64_t* out, void* work, size_t work_bytes, void* stream)
 {
+    Range range("sfhe_rotate");
     if (!c) return fail(SFHE_EINVAL, "null context");
     if (n < 0) return fail(SFHE_ESHAPE, "negative count");
     if (n == 0) return SFHE_OK;
@@ -1060,10 +1081,11 @@ extern "C" sfhe_status sfhe_rotate(sfhe_ctx* c, const uint64_t* in, int64_t n, u
     if (!(g & 1) || g >= 2 * c->rc.N) return fail(SFHE_EINVAL, "g must be odd and below 2N");
     if (work_bytes < rotate_work_words(c->rc) * 8) return fail(SFHE_ENOMEM, "rotation workspace too small");
     const size_t ctw = (size_t)2 * c->rc.L * c->rc.N;
-    for (int64_t i = 0; i < n; i++) {
-        cudaError_t e = launch_rotate(c->rc, in + i * ctw, g, key, key_sh, out + i * ctw, (u64*)work, as_stream(stream));
-        if (e != cudaSuccess) return fail(SFHE_ECUDA, "rotate: %s", cudaGetErrorString(e));
-    }
+    // as many ciphertexts per batched key switch as the workspace holds
+    const long long batch = (long long)(work_bytes / (rotate_work_words(c->rc) * 8));
+    cudaError_t e = launch_rotate_batch(c->rc, in, ctw, n, g, key, key_sh, out, ctw, (u64*)work,
+                                        std::min<long long>(batch, 4096), as_stream(stream));
+    if (e != cudaSuccess) return fail(SFHE_ECUDA, "rotate: %s", cudaGetErrorString(e));
     return SFHE_OK;
 }
 
@@ -1184,6 +1206,7 @@ extern "C" sfhe_status sfhe_matmul_chunked(sfhe_ctx* c, const sfhe_rotkeys* rk, 
                                           const uint8_t* b_zero, void* work, size_t work_bytes, void* stream,
                                           int64_t* products)
 {
+    Range range("sfhe_matmul_chunked");
     if (!c || !rk || !work) return fail(SFHE_EINVAL, "null argument");
     if (rk->ctx != c) return fail(SFHE_EINVAL, "rotation keys of another context");
     if (M < 0 || K < 0 || Nc < 0) return fail(SFHE_ESHAPE, "negative shape");
@@ -1339,6 +1362,7 @@ extern "C" sfhe_status sfhe_matmul_chunked_fused(sfhe_ctx* c, const sfhe_rotkeys
                                                 const uint8_t* a_zero, const uint8_t* b_zero, void* work,
                                                 size_t work_bytes, void* stream, int64_t* products)
 {
+    Range range("sfhe_matmul_chunked_fused");
     if (!c || !rk || !work) return fail(SFHE_EINVAL, "null argument");
     if (rk->ctx != c) return fail(SFHE_EINVAL, "rotation keys of another context");
     if (M < 0 || K < 0 || Nc < 0) return fail(SFHE_ESHAPE, "negative shape");

@@ -102,6 +102,7 @@ _SIGS = {
     "sfhe_measure_mulmod32": ([_vp, _P(ctypes.c_double), _vp], ctypes.c_int),
     "sfhe_plan_stats": ([_vp, _P(_i64), _P(_i64), _P(_i64), _P(_i64)], ctypes.c_int),
     "sfhe_matmul_check": ([_vp, _vp], ctypes.c_int),
+    "sfhe_selftest_wait_bound": ([_vp, _u32, _vp], ctypes.c_int),
     "sfhe_plan_destroy": ([_vp], None),
     "sfhe_ct_tensor_scale": ([_vp, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
     "sfhe_ct_mul_relin": ([_vp, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
@@ -422,6 +423,10 @@ def sfhe_plan_stats(plan: int) -> dict:
 
 def sfhe_matmul_check(work, stream=None) -> None:
     _check(lib().sfhe_matmul_check(_ptr(work), _stream(stream)))
+
+
+def sfhe_selftest_wait_bound(work, tries: int, stream=None) -> None:
+    _check(lib().sfhe_selftest_wait_bound(_ptr(work), tries, _stream(stream)))
 
 
 def sfhe_plan_destroy(plan: int) -> None:

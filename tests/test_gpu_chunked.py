@@ -165,3 +165,24 @@ def test_chunked_fused_8192_decrypts():
     want = ((A @ B + T // 2) % T) - T // 2
     assert (api.decrypt_chunked(ctx, C) == want).all()
     rk.close()
+
+
+def test_rotation_batches_equal_single_rotations():
+    """sfhe_rotate over several ciphertexts with a workspace for two at a
+    time (batches of 2 and a partial one) equals rotating each alone"""
+    import torch
+    api, S, ctx, octx = _setup()
+    g = S.sfhe_rotation_element(N, 2)
+    key = torch.empty((L, 2, L, N), dtype=torch.int64, device="cuda")
+    key_sh = torch.empty_like(key)
+    S.sfhe_galois_keygen(ctx.h, g, key, key_sh)
+    vals = np.random.default_rng(8).integers(0, T, size=(5, N))
+    _, ct = _enc_slots(api, S, ctx, vals, 6)
+    one = S.sfhe_rotate_workspace_size(ctx.h)
+    out = torch.empty_like(ct)
+    S.sfhe_rotate(ctx.h, ct, 5, g, key, key_sh, out, torch.empty(2 * one, dtype=torch.uint8, device="cuda"))
+    w1 = torch.empty(one, dtype=torch.uint8, device="cuda")
+    for q in range(5):
+        single = torch.empty_like(ct[q:q + 1])
+        S.sfhe_rotate(ctx.h, ct[q:q + 1].contiguous(), 1, g, key, key_sh, single, w1)
+        assert torch.equal(single[0], out[q]), q
