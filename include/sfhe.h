@@ -294,12 +294,13 @@ sfhe_status sfhe_measure_mulmod32(sfhe_ctx* ctx, double* per_s, void* stream);
 sfhe_status sfhe_matmul_workspace_size(const sfhe_ctx* ctx, int32_t n, const sfhe_matrix* A, const sfhe_matrix* B,
                                        uint32_t flags, size_t* bytes);
 /* C = A x B with the k-loop over every k: the naive dense loop of Alg. 1
- * (Sec. 3.3.1), each product multiplied, relinearised and added (A must be
- * DENSE-encoded). */
+ * (Sec. 3.3.1), each product multiplied, relinearised and added (A must
+ * store every element: DENSE or MASK; masks are ignored). */
 sfhe_status sfhe_matmul_dense(sfhe_ctx* ctx, const sfhe_matrix* A, const sfhe_matrix* B, sfhe_matrix* C, uint32_t flags,
                               void* work, size_t work_bytes, void* stream);
 /* C = A x B with the k-loop over the nonzeros of A as `encoding` lists them
- * (Sec. 3.3.2; A must carry that encoding; EINVAL otherwise). */
+ * (Sec. 3.3.2; A must carry that encoding; EINVAL otherwise); a MASK-encoded
+ * B also skips the k where B[k][j] is zero. */
 sfhe_status sfhe_matmul_sparse(sfhe_ctx* ctx, const sfhe_matrix* A, const sfhe_matrix* B, int32_t encoding,
                                sfhe_matrix* C, uint32_t flags, void* work, size_t work_bytes, void* stream);
 /* n independent matmuls C[m] = A[m] x B[m] (each A in its own encoding) in

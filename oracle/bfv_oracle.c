@@ -1,7 +1,9 @@
 /*
  * bfv_oracle.c -- plain, slow, CPU-only oracle for encrypted sparse matrix
- * multiplication under RNS BFV (one ciphertext per matrix element, value in
- * the constant coefficient).
+ * multiplication under RNS BFV: one ciphertext per matrix element with the
+ * value in the constant coefficient, and (at the end of the file) the
+ * chunked form of Sec. 3.2 with c values per ciphertext in its slots,
+ * rotations and the slot-0 mask.
  *
  * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and
  * bench.py's CPU-baseline / reference arm may load this library.  It shares

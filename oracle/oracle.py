@@ -5,7 +5,10 @@ CPU-baseline / reference leg of bench.py may import this module.  It shares no
 code with the CUDA path (paper_2503_09184_gb300) and never imports it.
 
 Layouts: a ciphertext is a uint64 array [2][L][N] in coefficient form with
-canonical residues in [0, q_i) (c0 first, then c1).
+canonical residues in [0, q_i) (c0 first, then c1).  Besides the
+per-element form (value in the constant coefficient), OracleChunked runs
+Alg. 1 over chunks of c values per ciphertext (Sec. 3.2: slots, rotations,
+the slot-0 mask).
 
 The encodings follow Sec. 3.3.2 of the paper ("Exploiting Unstructured
 Sparsity in Fully Homomorphic Encrypted DNNs"):
