@@ -443,9 +443,11 @@ bool fill_constants(RnsConsts& rc)
         Big alpha, rem;
         uint64_t rho;
         split_const(ck, alpha, rem, rho);
-        rc.rho_s[k][0] = (uint32_t)(rho & ((1ULL << 22) - 1));
-        rc.rho_s[k][1] = (uint32_t)((rho >> 22) & ((1ULL << 21) - 1));
-        rc.rho_s[k][2] = (uint32_t)(rho >> 43);
+        // the estimate of F uses rho_k without its low 6 bits, in two
+        // 29-bit parts: each product with a 30-bit residue stays below 2^59,
+        // so the sums of up to 31 of them need no carries
+        rc.rho_s[k][0] = (uint32_t)((rho >> 6) & ((1ULL << 29) - 1));
+        rc.rho_s[k][1] = (uint32_t)(rho >> 35);
         for (int i = 0; i < L; ++i) {
             const uint64_t a = mod_small(alpha, rc.m[i].q);
             rc.alpha_q_lo[k][i] = (uint32_t)(a & ((1ULL << 27) - 1));

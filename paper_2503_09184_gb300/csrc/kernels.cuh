@@ -125,12 +125,14 @@ __device__ __noinline__ u64 scale_round_fallback(const u32* xt32, size_t stride,
 //   t x / Q = sum_k x~_k alpha_k - v alpha_B + F,  F = (sum_k x~_k r_k - v r_B) / Q,
 // so round(t x / Q) = sum_k x~_k alpha_k - v alpha_B + round(F).  F + K > 0
 // is estimated as G / 2^64 with G = sum_k x~_k rho_k - v rho_B + K 2^64,
-// rho = floor(r 2^64 / Q); the true value lies in (G - K, G + K 2^30) / 2^64,
+// rho = floor(r 2^64 / Q); with the exact rho_k the true value lies in
+// (G - K, G + K 2^30) / 2^64,
 // so round(F) + K = floor((G + 2^63) / 2^64) unless that interval crosses
 // the rounding point, where the decision is taken exactly (Q is odd: no ties).
 // Every product is one 32x32-bit multiply into a 64-bit sum without carries:
-// rho_k is split into 22 + 21 + 21 bits (partial sums below 2^57), the
-// 54-bit [alpha_k]_{q_i} at bit 27 (below 2^62).  The M coefficients are
+// G takes rho_k without its low 6 bits, in two 29-bit parts (products below
+// 2^59), which widens the band to (G - K, G + K 2^37); the 54-bit
+// [alpha_k]_{q_i} is split at bit 27 (below 2^62).  The M coefficients are
 // independent; they are interleaved for instruction-level parallelism.
 // LAZY: d[m][i] in [0, 3 q_i) (congruent, one Barrett step without the final
 // subtractions) instead of canonical.
@@ -148,17 +150,15 @@ SFHE_DEV void scale_round_m(const u32* const (&x32)[M], size_t stride, const Rns
 #pragma unroll
     for (int m = 0; m < M; m++) {
         v[m] = round_b<K>(xt[m], c);
-        u64 s0 = 0, s1 = 0, s2 = 0;
+        u64 s0 = 0, s1 = 0;
 #pragma unroll
         for (int k = 0; k < K; k++) {
             s0 += (u64)xt[m][k] * c.rho_s[k][0];
             s1 += (u64)xt[m][k] * c.rho_s[k][1];
-            s2 += (u64)xt[m][k] * c.rho_s[k][2];
         }
-        // G = s0 + s1 2^22 + s2 2^43 + K 2^64 + 2^63 - v rho_B   (mod 2^128)
-        u64 ghi = (u64)K + (s1 >> 42) + (s2 >> 21), glo = s0;
-        add128(ghi, glo, s1 << 22);
-        add128(ghi, glo, s2 << 43);
+        // G = s0 2^6 + s1 2^35 + K 2^64 + 2^63 - v rho_B   (mod 2^128)
+        u64 ghi = (u64)K + (s0 >> 58) + (s1 >> 29), glo = s0 << 6;
+        add128(ghi, glo, s1 << 35);
         add128(ghi, glo, 1ULL << 63);
         const u64 p0 = (u64)v[m] * c.rhoB_lo, p1 = (u64)v[m] * c.rhoB_hi;
         const u64 sub = p0 + (p1 << 32);
@@ -166,7 +166,7 @@ SFHE_DEV void scale_round_m(const u32* const (&x32)[M], size_t stride, const Rns
         ghi -= subhi + (glo < sub ? 1 : 0);
         glo -= sub;
         mK[m] = ghi;  // round(F) + K, unless glo sits in the uncertainty band
-        if (glo < (u64)K || glo >= 0ULL - ((u64)K << 30)) mK[m] = scale_round_fallback<K>(x32[m], stride, v[m], mK[m], c);
+        if (glo < (u64)K || glo >= 0ULL - ((u64)K << 37)) mK[m] = scale_round_fallback<K>(x32[m], stride, v[m], mK[m], c);
     }
 #pragma unroll
     for (int i = 0; i < L; i++) {

@@ -89,7 +89,7 @@ struct RnsConsts {
     //   round(t x / Q) = sum_k x~_k alpha_k - v alpha_B + round(F),
     //   F = (sum_k x~_k r_k - v r_B) / Q,
     // F estimated with rho = floor(r 2^64 / Q), decided exactly near a half.
-    u32 rho_s[SFHE_MAX_K][3];                     // rho_k split at bits 22 and 43
+    u32 rho_s[SFHE_MAX_K][2];                     // rho_k bits 6..34 and 35..63
     u32 rhoB_lo, rhoB_hi;                         // rho_B split in 32-bit halves
     u32 alpha_q_lo[SFHE_MAX_K][SFHE_MAX_L];       // [alpha_k]_{q_i} mod 2^27
     u32 alpha_q_hi[SFHE_MAX_K][SFHE_MAX_L];       // [alpha_k]_{q_i} >> 27
