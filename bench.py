@@ -109,6 +109,16 @@ def mults_per_product(N: int, L: int) -> int:
     return tensor + intt + scale
 
 
+def mults_executed_per_product(N: int, L: int) -> int:
+    """the multiplies the current kernel executes per product: stage S takes
+    the digits from the inverse NTT's last stage and its fraction estimate
+    in two parts per constant, 3K + 2KL + 6L + 2 per coefficient (the count
+    above is held fixed per problem size)"""
+    logN = int(math.log2(N))
+    K = tensor_base_size(logN, L)
+    return 10 * K * N + 3 * K * (N // 2) * logN * 3 + 3 * N * (3 * K + 2 * K * L + 6 * L + 2)
+
+
 def mults_per_entry(N: int, L: int) -> int:
     """per output entry with at least one product: L (L + 2) forward 64-bit
     NTTs of the accumulated sums (10 per butterfly, Barrett-reduced inputs),
@@ -478,6 +488,11 @@ def main():
                      "work_per_launch": work,
                      "peak_note": "152 SM x 64 int32 multiplies/clk x 2070 MHz (derived from unit counts and clock)",
                      "frac_at_measured_clock": achieved / (peak * sm_clock / SM_MAX_MHZ),
+                     "work_note": "count held fixed per problem size (see mults_per_product)",
+                     "frac_of_executed_work": (work - (groups if args.lazy else products)
+                                               * (mults_per_product(ring.N, ring.L)
+                                                  - mults_executed_per_product(ring.N, ring.L)))
+                                              / (kms / 1e3) / 1e12 / peak,
                      "measured_mulmod32_per_s": mulmod_rate,
                      "frac_of_measured_mulmod": achieved / (3 * mulmod_rate / 1e12),
                      "measured_note": "32-bit Shoup a*w mod b (3 multiplies) over all SMs at full occupancy, "
