@@ -488,6 +488,7 @@ def main():
                      "work_per_launch": work,
                      "peak_note": "152 SM x 64 int32 multiplies/clk x 2070 MHz (derived from unit counts and clock)",
                      "frac_at_measured_clock": achieved / (peak * sm_clock / SM_MAX_MHZ),
+                     "traffic_gbs": None if traffic is None else traffic / (kms / 1e3) / 1e9,
                      "work_note": "count held fixed per problem size (see mults_per_product)",
                      "frac_of_executed_work": (work - (groups if args.lazy else products)
                                                * (mults_per_product(ring.N, ring.L)
