@@ -30,6 +30,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -61,8 +62,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--plain-rows", type=int, default=2, help="rows of A timed through the plain path")
-    ap.add_argument("--cpu-products", type=int, default=0, help="oracle products in the CPU baseline sample "
-                    "(default: 48 / 12 / 2 at N = 4096 / 8192 / 16384)")
+    ap.add_argument("--cpu-products", type=int, default=0, help="products per entry in the CPU baseline sample "
+                    "(default: 8 / 4 / 1 at N = 4096 / 8192 / 16384; one entry per host thread)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shape", default=None, help="M,K,Nc override of the sweep shape (small profiling cases)")
     ap.add_argument("--workload", default="sweep", choices=["sweep", "tiny", "layer", "mixed", "serve", "chunked"])
@@ -96,27 +97,25 @@ def tensor_base_size(logN: int, L: int) -> int:
 
 
 def mults_per_product(N: int, L: int) -> int:
-    """32-bit multiplies of one product: tensor over the K tensor-base primes
-    (10 per coefficient and prime), 3K inverse NTTs (3 per butterfly), exact
-    scale-and-round of the 3 polynomials (6K + 2KL + 9L per coefficient: the
-    CRT digits, the overflow count, the fixed-point fraction, and the
-    reconstruction mod every q_i)."""
-    logN = int(math.log2(N))
-    K = tensor_base_size(logN, L)
-    tensor = 10 * K * N
-    intt = 3 * K * (N // 2) * logN * 3
-    scale = 3 * N * (6 * K + 2 * K * L + 9 * L)
-    return tensor + intt + scale
-
-
-def mults_executed_per_product(N: int, L: int) -> int:
-    """the multiplies the current kernel executes per product: stage S takes
-    the digits from the inverse NTT's last stage and its fraction estimate
-    in two parts per constant, 3K + 2KL + 6L + 2 per coefficient (the count
-    above is held fixed per problem size)"""
+    """32-bit multiplies one product needs in the formulation the kernel
+    runs: the tensor over the K tensor-base primes (10 per coefficient and
+    prime: four products and three Montgomery reductions at 2 each), 3K
+    inverse NTTs (3 per butterfly), and the exact scale-and-round of the 3
+    polynomials, 3K + 2KL + 6L + 2 per coefficient (the rounding estimate K,
+    the fraction estimate 2K, the reconstruction mod every q_i 2KL, the
+    v alpha_B term and the Barrett reduction 6L, the v rho_B term 2)."""
     logN = int(math.log2(N))
     K = tensor_base_size(logN, L)
     return 10 * K * N + 3 * K * (N // 2) * logN * 3 + 3 * N * (3 * K + 2 * K * L + 6 * L + 2)
+
+
+def mults_per_product_retired(N: int, L: int) -> int:
+    """the count of an earlier formulation (explicit CRT digits and a
+    three-part fraction estimate, 6K + 2KL + 9L per rounded coefficient),
+    kept only as a note beside the current count"""
+    logN = int(math.log2(N))
+    K = tensor_base_size(logN, L)
+    return 10 * K * N + 3 * K * (N // 2) * logN * 3 + 3 * N * (6 * K + 2 * K * L + 9 * L)
 
 
 def mults_per_entry(N: int, L: int) -> int:
@@ -141,6 +140,15 @@ def mults(products: int, entries: int, N: int, L: int, groups: int | None = None
     return products * tensor + groups * (mults_per_product(N, L) - tensor) + entries * mults_per_entry(N, L)
 
 
+def alu_roofline(products: int, entries: int, N: int, L: int, kernel_ms: float, groups: int | None = None) -> dict:
+    """the launch's multiply count, its rate over the kernel's time and the
+    fraction of the derived integer-multiply peak"""
+    work = mults(products, entries, N, L, groups)
+    achieved = work / (kernel_ms / 1e3) / 1e12
+    peak = SM_COUNT * IMAD_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    return {"work": work, "achieved": achieved, "peak": peak, "frac": achieved / peak}
+
+
 # ------------------------------------------------------------------- clocks ---
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -150,12 +158,12 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = None
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
+            fd, self.path = tempfile.mkstemp(prefix="sfhe_clocks_", suffix=".csv")
+            self.f = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
@@ -172,10 +180,12 @@ class ClockSampler:
             self.proc.kill()
         self.f.close()
         rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
@@ -188,22 +198,44 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- CPU oracle ---
-def cpu_oracle_rate(ring, A, B, n_products: int, seed: int = 0, skip_b_zeros: bool = False) -> dict:
-    """The oracle as it stands (OpenMP over the host cores) on a bounded
-    sample: the first n_products nonzero products of row-major order."""
+def paper_scheme_sample(octx, A, B, n_entries: int, per_entry: int, row: int = 1, skip_b_zeros: bool = False):
+    """A bounded sample of the workload for the oracle run in the paper's CPU
+    scheme (Sec. 3.4: one result entry per thread, entry (row, col) on thread
+    (row * col) mod n): the entries (row, j), j < n_entries, of the product
+    restricted to the first `per_entry` nonzeros of A's row (the same
+    ciphertexts, whole entries of that restricted product).  With row = 1
+    the entries land on distinct threads.  Returns (entries, a_list, b_list,
+    products)."""
+    row = min(row, A.shape[0] - 1)
+    ks = [k for k in range(A.shape[1]) if A[row, k] != 0][:per_entry]
+    mm_a = {k: octx.encrypt(int(A[row, k]), 1, row, k) for k in ks}
+    entries, a_list, b_list = [], [], []
+    for j in range(min(n_entries, B.shape[1])):
+        first = len(a_list)
+        for k in ks:
+            if skip_b_zeros and B[k, j] == 0:
+                continue
+            a_list.append(mm_a[k])
+            b_list.append(octx.encrypt(int(B[k, j]), 2, k, j))
+        entries.append((row, j, first, len(a_list) - first))
+    return entries, a_list, b_list, len(a_list)
+
+
+def cpu_oracle_rate(ring, A, B, per_entry: int, seed: int = 0, skip_b_zeros: bool = False) -> dict:
+    """The oracle as it stands, in the paper's CPU scheme (or_matmul_entries:
+    one result entry per thread over every host core), on a bounded sample."""
     from oracle import oracle as O
     octx = O.OracleCtx(ring.N, ring.L, seed=seed)
-    pairs = [(i, k, j) for i in range(A.shape[0]) for k in range(A.shape[1]) if A[i, k] != 0
-             for j in range(B.shape[1]) if not (skip_b_zeros and B[k, j] == 0)][:n_products]
-    ops = [(octx.encrypt(int(A[i, k]), 1, i, k), octx.encrypt(int(B[k, j]), 2, k, j)) for i, k, j in pairs]
+    nt = O.num_threads()
+    entries, a_list, b_list, n = paper_scheme_sample(octx, A, B, nt, per_entry, skip_b_zeros=skip_b_zeros)
     t0 = time.perf_counter()
-    acc = np.zeros(octx.ct_shape, dtype=np.uint64)
-    for a, b in ops:
-        octx.add_(acc, octx.mul_relin(a, b))
+    octx.matmul_entries(entries, a_list, b_list, nthreads=nt)
     dt = time.perf_counter() - t0
-    return {"value": len(ops) / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"{len(ops)} ct x ct products (multiply + relinearise + add) of the same workload, "
-                      f"schoolbook negacyclic products, {dt:.1f} s"}
+    return {"value": n / dt, "unit": UNIT, "cores": nt, "kind": "oracle",
+            "sample": f"{len(entries)} whole entries C[1][j], j < {len(entries)}, of the product over the first "
+                      f"{per_entry} nonzeros of A's row 1 ({n} ct x ct products: multiply + relinearise + add, "
+                      f"schoolbook negacyclic products), one entry per thread by (row * col) mod {nt} as the "
+                      f"paper's Sec. 3.4 scheme, {dt:.1f} s"}
 
 
 def run_reference(args):
@@ -212,20 +244,15 @@ def run_reference(args):
         return
     ring, vals, workload, sparsity = job_of(args)
     A, B = vals[0]
-    skip_b_zeros = args.b_sparse
     from oracle import oracle as O
     octx = O.OracleCtx(ring.N, ring.L, seed=0)
-    pairs = [(i, k, j) for i in range(A.shape[0]) for k in range(A.shape[1]) if A[i, k] != 0
-             for j in range(B.shape[1]) if not (skip_b_zeros and B[k, j] == 0)]
-    per_step = 2
-    need = (args.warmup + args.steps) * per_step
-    ops = [(octx.encrypt(int(A[i, k]), 1, i, k), octx.encrypt(int(B[k, j]), 2, k, j)) for i, k, j in pairs[:need]]
-    acc = np.zeros(octx.ct_shape, dtype=np.uint64)
+    nt = O.num_threads()
+    # one product per entry and thread per step (about 4 s at N = 8192 on 16 cores)
+    entries, a_list, b_list, per_step = paper_scheme_sample(octx, A, B, nt, 1, skip_b_zeros=args.b_sparse)
     times = []
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        for a, b in ops[s * per_step:(s + 1) * per_step]:
-            octx.add_(acc, octx.mul_relin(a, b))
+        octx.matmul_entries(entries, a_list, b_list, nthreads=nt)
         if s >= args.warmup:
             times.append(time.perf_counter() - t0)
     total = sum(times)
@@ -235,8 +262,10 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": workload, "N": ring.N, "L": ring.L, "t": W.T_PLAIN,
                        "sparsity": sparsity, "encoding": ENCODING},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-                             "sample": f"{per_step} products per step of the same workload"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle",
+                             "sample": f"per step {len(entries)} entries C[1][j] of the product over the first "
+                                       f"nonzero of A's row 1 ({per_step} products), one entry per thread "
+                                       f"(the paper's Sec. 3.4 scheme)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -308,7 +337,7 @@ def operand_memory(S, ring, vals) -> dict:
         tot = {"ct": 0, "ext": 0, "meta": 0}
         for a, _ in vals:
             nct, width = S.sfhe_encode_count(a, e)
-            m = S.sfhe_matrix_bytes(ring.N, ring.L, S.sfhe_matrix(a.shape[0], a.shape[1], e, nct, width, None, None,
+            m = S.sfhe_matrix_bytes(ring.N, ring.L, S.sfhe_matrix_view(a.shape[0], a.shape[1], e, nct, width, None, None,
                                                                   None, None, None, None))
             for k in tot:
                 tot[k] += m[k]
@@ -422,7 +451,7 @@ def main():
         ref = ((a @ b + W.T_PLAIN // 2) % W.T_PLAIN) - W.T_PLAIN // 2
         correct = correct and bool((dec == ref).all())
 
-    e2e = e2e_pipelined(args, api, S, torch, ctx, vals, slot, products, world)
+    e2e = e2e_host(args, api, S, torch, ctx, slot, products, world)
 
     # plain per-product path on a bounded sample: the first rows of the first A
     a0, b0 = vals[0]
@@ -457,10 +486,11 @@ def main():
     if args.lazy:
         G = ctx.lazy_group
         groups = sum(int(np.ceil((a != 0).sum(axis=1) / G).sum()) * b.shape[1] for a, b in vals)
-    work = mults(products, nonempty_entries, ring.N, ring.L, groups)
-    achieved = work / (kms / 1e3) / 1e12
+    rl = alu_roofline(products, nonempty_entries, ring.N, ring.L, kms, groups)
+    work, achieved, peak = rl["work"], rl["achieved"], rl["peak"]
+    work_retired = work + (groups if args.lazy else products) * (mults_per_product_retired(ring.N, ring.L)
+                                                                 - mults_per_product(ring.N, ring.L))
     sm_clock = clk.get("sm_mhz") or SM_MAX_MHZ
-    peak = SM_COUNT * IMAD_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
     kname = f"k_matmul_persistent<{int(math.log2(ring.N))},{ring.L}>"
     traffic = measured_traffic(workload)
     lifted = sum((M.ext.numel()) * M.ext.element_size() for M in slot.As + slot.Bs)
@@ -483,17 +513,15 @@ def main():
         "speedup_batched_vs_plain": value / world / plain_rate,
         "e2e": e2e,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T int32-mul/s",
-                     "frac": achieved / peak, "traffic": traffic,
+                     "frac": rl["frac"], "traffic": traffic,
                      "kernel": kname,
                      "work_per_launch": work,
                      "peak_note": "152 SM x 64 int32 multiplies/clk x 2070 MHz (derived from unit counts and clock)",
                      "frac_at_measured_clock": achieved / (peak * sm_clock / SM_MAX_MHZ),
                      "traffic_gbs": None if traffic is None else traffic / (kms / 1e3) / 1e9,
-                     "work_note": "count held fixed per problem size (see mults_per_product)",
-                     "frac_of_executed_work": (work - (groups if args.lazy else products)
-                                               * (mults_per_product(ring.N, ring.L)
-                                                  - mults_executed_per_product(ring.N, ring.L)))
-                                              / (kms / 1e3) / 1e12 / peak,
+                     "work_note": "32-bit multiplies the kernel's formulation needs (mults_per_product, "
+                                  "mults_per_entry); an earlier formulation's count would give frac %.3f"
+                                  % (work_retired / (kms / 1e3) / 1e12 / peak),
                      "measured_mulmod32_per_s": mulmod_rate,
                      "frac_of_measured_mulmod": achieved / (3 * mulmod_rate / 1e12),
                      "measured_note": "32-bit Shoup a*w mod b (3 multiplies) over all SMs at full occupancy, "
@@ -506,8 +534,8 @@ def main():
         "operand_memory": operand_memory(S, ring, vals),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n_cpu = args.cpu_products or {4096: 48, 8192: 12, 16384: 2}[ring.N]
-        line["cpu_baseline"] = cpu_oracle_rate(ring, a0, b0, n_cpu, skip_b_zeros=args.b_sparse)
+        per_entry = args.cpu_products or {4096: 8, 8192: 4, 16384: 1}[ring.N]
+        line["cpu_baseline"] = cpu_oracle_rate(ring, a0, b0, per_entry, skip_b_zeros=args.b_sparse)
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
@@ -655,47 +683,27 @@ def run_serve(args):
     ctx.close()
 
 
-def e2e_pipelined(args, api, S, torch, ctx, vals, slot0, products, world) -> dict:
-    """End to end through the public API: every step copies its operand
-    ciphertexts from pinned host memory, runs the matmul and copies C back to
-    pinned host memory.  Two slots of device buffers let step i+1's upload
-    and step i-1's download run on their own streams while step i computes;
-    every copy of every timed step lies inside the timed region."""
-    slots = [slot0, Slot(api, S, torch, ctx, vals, None, lazy=(slot0.flags & api.LAZY) != 0,
-                         b_encoding=slot0.b_encoding)]
-    h_in = [[torch.empty(M.ct.shape, dtype=torch.int64, pin_memory=True) for M in slots[0].As + slots[0].Bs]
-            for _ in slots]
-    for hs in h_in:
-        for h, M in zip(hs, slots[0].As + slots[0].Bs):
-            h.copy_(M.ct)
-    h_out = [[torch.empty(C.ct.shape, dtype=torch.int64, pin_memory=True) for C in slots[0].Cs] for _ in slots]
-    s_up, s_comp, s_down = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
-    up_done = [torch.cuda.Event() for _ in slots]
-    comp_done = [torch.cuda.Event() for _ in slots]
-    down_done = [torch.cuda.Event() for _ in slots]
+def e2e_host(args, api, S, torch, ctx, slot0, products, world) -> dict:
+    """End to end through the library's host-buffer entry point
+    (sfhe_matmul_host): every step hands the operands' ciphertexts in pinned
+    host memory to the library, which copies them to the device, lifts them,
+    runs the matmul and copies C back to pinned host memory.  The host plan
+    keeps two sets of device buffers, so step i+1's upload and step i-1's
+    download run on its copy streams while step i computes; every copy of
+    every timed step lies inside the timed region."""
+    hp = S.sfhe_host_plan_create(ctx.h, [a.desc() for a in slot0.As], [b.desc() for b in slot0.Bs], slot0.flags, 2)
+    st = S.sfhe_host_plan_stats(hp)
+    h_a = [torch.empty(M.ct.shape, dtype=torch.int64, pin_memory=True) for M in slot0.As]
+    h_b = [torch.empty(M.ct.shape, dtype=torch.int64, pin_memory=True) for M in slot0.Bs]
+    h_c = [torch.empty(C.ct.shape, dtype=torch.int64, pin_memory=True) for C in slot0.Cs]
+    for h, M in zip(h_a + h_b, slot0.As + slot0.Bs):
+        h.copy_(M.ct)
+    stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
 
     def run(nsteps):
-        for i in range(nsteps):
-            k = i % 2
-            sl = slots[k]
-            ins = sl.As + sl.Bs
-            with torch.cuda.stream(s_up):
-                if i >= 2:
-                    s_up.wait_event(comp_done[k])      # the slot's inputs are free
-                for h, M in zip(h_in[k], ins):
-                    M.ct.copy_(h, non_blocking=True)
-                up_done[k].record(s_up)
-            s_comp.wait_event(up_done[k])
-            if i >= 2:
-                s_comp.wait_event(down_done[k])        # the slot's C has been read
-            sl.step(s_comp)
-            comp_done[k].record(s_comp)
-            with torch.cuda.stream(s_down):
-                s_down.wait_event(comp_done[k])
-                for h, C in zip(h_out[k], sl.Cs):
-                    h.copy_(C.ct, non_blocking=True)
-                down_done[k].record(s_down)
+        for _ in range(nsteps):
+            S.sfhe_matmul_host(hp, h_a, h_b, h_c, stream)
         torch.cuda.synchronize()
 
     run(2)  # warm-up
@@ -705,12 +713,13 @@ def e2e_pipelined(args, api, S, torch, ctx, vals, slot0, products, world) -> dic
     t0 = time.perf_counter()
     run(n)
     e2e_ms = 1e3 * (time.perf_counter() - t0) / n
-    h2d = sum(M.ct.numel() * 8 for M in slot0.As + slot0.Bs)
-    d2h = sum(C.ct.numel() * 8 for C in slot0.Cs)
-    return {"value": products * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-            "note": "pinned host buffers; uploads, compute and downloads of consecutive steps overlap on three "
-                    "streams (two device buffer sets)"}
+    same = all(bool((h == C.ct.cpu()).all()) for h, C in zip(h_c, slot0.Cs))
+    S.sfhe_host_plan_destroy(hp)
+    return {"value": products * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": st["h2d_bytes"],
+            "d2h_bytes_per_step": st["d2h_bytes"], "ms_per_step": e2e_ms, "gpu_launches_per_step": st["launches"],
+            "c_equals_device_path": same,
+            "note": "sfhe_matmul_host with pinned host buffers: uploads, lift + matmul and downloads of consecutive "
+                    "steps overlap on the host plan's streams (two device buffer sets)"}
 
 
 # DRAM traffic of the persistent kernel, per launch, measured with ncu

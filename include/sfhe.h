@@ -22,7 +22,15 @@
  *  - "device" pointers are CUDA device memory owned by the caller (for
  *    example torch tensors); "host" pointers are ordinary host memory owned
  *    by the caller and only read during the call.  The library owns only
- *    what an sfhe_ctx or sfhe_plan handle holds.
+ *    what a handle holds (sfhe_ctx, sfhe_matrix, sfhe_plan,
+ *    sfhe_host_plan, sfhe_rotkeys); the caller releases each with its
+ *    *_destroy call.
+ *  - Two ways to hold operands: sfhe_matrix, an opaque handle whose device
+ *    memory the library allocates and frees (the calls of the paper's
+ *    problem statement: encrypted inputs A and B with their matrix
+ *    structure in, the encrypted product out), and sfhe_matrix_view, a
+ *    plain descriptor over device buffers the caller allocated (for callers
+ *    that manage device memory themselves: plans, CUDA graphs, serving).
  *  - Ciphertext layouts (uint64 words, canonical residues):
  *      ciphertext  [2 (c0, c1)][L][N], NTT form (slot i = evaluation at
  *                  psi^(2 bitrev(i) + 1), psi the smallest primitive 2N-th
@@ -97,6 +105,10 @@ typedef struct {
 
 typedef struct sfhe_ctx sfhe_ctx;
 typedef struct sfhe_plan sfhe_plan;
+/* an encoded, encrypted matrix in device memory the library owns */
+typedef struct sfhe_matrix sfhe_matrix;
+/* a matmul with host-resident operands (sfhe_matmul_host) */
+typedef struct sfhe_host_plan sfhe_host_plan;
 
 /*
  * Encoded left or right operand (Sec. 3.3.2).  Plaintext structure arrays
@@ -125,7 +137,7 @@ typedef struct {
     const int32_t* ell_col;
     uint64_t* ct;
     uint32_t* ext;
-} sfhe_matrix;
+} sfhe_matrix_view;
 
 /* ------------------------------------------------------------ context --- */
 /* Parameters and keys.  Selects the primes, builds the NTT and base
@@ -170,8 +182,8 @@ sfhe_status sfhe_encode_fill(const int64_t* values, int32_t rows, int32_t cols, 
  * one byte per element), (rows + 1 + nct) * 4 (CSR), rows * ell_width * 4
  * (ELL).  Reads only the descriptor's sizes and encoding.  Errors: EINVAL
  * (null, bad encoding), EUNSUPPORTED (N, L), ESHAPE (negative sizes). */
-sfhe_status sfhe_matrix_bytes(uint32_t N, uint32_t L, const sfhe_matrix* M, uint64_t* ct_bytes, uint64_t* ext_bytes,
-                              uint64_t* meta_bytes);
+sfhe_status sfhe_matrix_bytes(uint32_t N, uint32_t L, const sfhe_matrix_view* M, uint64_t* ct_bytes,
+                              uint64_t* ext_bytes, uint64_t* meta_bytes);
 
 /* Secret-key BFV encryption (the scheme of Sec. 3.1, one element per
  * ciphertext as in the c = 1 setting of Sec. 3.2): ct[n] (device, [n][2][L][N], NTT form) encrypts
@@ -289,33 +301,149 @@ sfhe_status sfhe_matmul_chunked_fused(sfhe_ctx* ctx, const sfhe_rotkeys* rk, int
  * Errors: EINVAL (null), ECUDA. */
 sfhe_status sfhe_measure_mulmod32(sfhe_ctx* ctx, double* per_s, void* stream);
 
-/* ------------------------------------------------------------ matmul --- */
-/* Workspace (device bytes) for n matmuls A[m] x B[m] under `flags`. */
-sfhe_status sfhe_matmul_workspace_size(const sfhe_ctx* ctx, int32_t n, const sfhe_matrix* A, const sfhe_matrix* B,
-                                       uint32_t flags, size_t* bytes);
+/* --------------------------------------- library-owned matrices (handles) --- */
+/* The paper states the problem as: encrypted inputs A and B with the matrix
+ * information of the left and right operands in, the encrypted product R out
+ * (Alg. 1's input and output lines; the three sparse encodings of
+ * Sec. 3.3.2).  These calls take and return that: sfhe_matrix handles own
+ * their ciphertexts (NTT form, [nct][2][L][N]) and their lift to the tensor
+ * base in device memory allocated here (cudaMalloc) and released by
+ * sfhe_matrix_destroy; the plaintext structure (mask, CSR or ELLPACK arrays)
+ * is copied into the handle.  Every call validates its arguments before it
+ * launches; errors leave *out NULL.  A handle belongs to the context that
+ * made it and must be destroyed before the context. */
+
+/* Primes of the context: q[L] the ciphertext primes (descending), p[K] the
+ * primes of the extended base the multiply runs in (the tensor base B of
+ * 30-bit primes, K = sfhe_info.K <= 32; the paper's scheme leaves the
+ * auxiliary base to the library).  Host memory.  Errors: EINVAL (null). */
+sfhe_status sfhe_ctx_get_primes(const sfhe_ctx* ctx, uint64_t* q, uint64_t* p);
+
+/* Encodes the plaintext matrix vals[rows*cols] (host, row-major) under
+ * `encoding` (Sec. 3.3.2), encrypts every stored element in its own
+ * ciphertext (secret-key BFV, the value in the constant coefficient;
+ * randomness from the stream (matrix_id, row, col) as sfhe_encrypt) and lifts
+ * the ciphertexts to the tensor base, on `stream`.  ELLPACK padding slots
+ * hold encryptions of zero.  Errors: EINVAL (null, bad encoding), ESHAPE
+ * (negative shape), ENOMEM (device), ECUDA. */
+sfhe_status sfhe_matrix_encrypt(sfhe_ctx* ctx, const int64_t* vals, int32_t rows, int32_t cols, sfhe_encoding encoding,
+                                uint64_t matrix_id, void* stream, sfhe_matrix** out);
+/* A matrix from ciphertexts already encrypted elsewhere: coeff_limbs (host,
+ * [nct][2][L][N], coefficient form, canonical residues: limb i below q_i)
+ * and the structure `idx` (host int32):
+ *   DENSE: unused (may be NULL), nct = rows*cols;
+ *   MASK:  idx[rows*cols], nonzero where the element is zero, nct = rows*cols;
+ *   CSR:   row_ptr[rows+1] followed by col_idx[nct], nct = row_ptr[rows];
+ *   ELL:   idx[0] = ell_width, then ell_col[rows*ell_width] (-1 = padding),
+ *          nct = rows*ell_width.
+ * The ciphertexts are copied to the device, taken to NTT form and lifted on
+ * `stream`; the host arrays may be reused once the call returns.  Errors:
+ * EINVAL (null, bad structure, a residue >= its prime), ESHAPE, ENOMEM,
+ * ECUDA. */
+sfhe_status sfhe_matrix_import(sfhe_ctx* ctx, const uint64_t* coeff_limbs, const int32_t* idx, int32_t rows,
+                               int32_t cols, sfhe_encoding encoding, void* stream, sfhe_matrix** out);
+/* The ciphertexts in coefficient form, canonical residues, into host
+ * coeff_limbs[nct][2][L][N] (nct from sfhe_matrix_info).  Synchronises
+ * `stream`.  Errors: EINVAL (null), ECUDA. */
+sfhe_status sfhe_matrix_export(const sfhe_matrix* M, uint64_t* coeff_limbs, void* stream);
+/* Decryption into host out[rows*cols] (row-major), centred in (-t/2, t/2]:
+ * every stored element decrypted, elements the encoding does not store
+ * (CSR / ELLPACK zeros) are 0.  Synchronises `stream`.  Errors: EINVAL (null,
+ * a handle of another context), ECUDA. */
+sfhe_status sfhe_matrix_decrypt(sfhe_ctx* ctx, const sfhe_matrix* M, int64_t* out, void* stream);
+/* Releases the handle's device memory (synchronises the device).  NULL is a no-op. */
+void sfhe_matrix_destroy(sfhe_matrix* M);
+/* Shape, encoding and stored ciphertext count of a handle (any may be NULL). */
+sfhe_status sfhe_matrix_info(const sfhe_matrix* M, int32_t* rows, int32_t* cols, int32_t* encoding, int32_t* nct);
+/* A descriptor of the handle's storage for the calls that take views
+ * (plans, graphs).  The view points into the handle (ct, ext and the
+ * structure arrays) and is valid until sfhe_matrix_destroy; a result
+ * handle not yet used as an operand is lifted here first (on `stream`). */
+sfhe_status sfhe_matrix_view_of(sfhe_matrix* M, sfhe_matrix_view* out, void* stream);
+
+/* *C = A x B over every k (the naive dense loop of Alg. 1; A must store
+ * every element: DENSE or MASK), all products in one persistent launch.  C
+ * is a new DENSE handle of A.rows x B.cols ciphertexts, written on `stream`;
+ * the transient workspace is allocated and freed on the stream
+ * (cudaMallocAsync).  An operand that is itself a result is lifted first.
+ * Errors: EINVAL (null, handles of another context, encodings), ESHAPE
+ * (A.cols != B.rows), EUNSUPPORTED (more than 1024 products in one entry),
+ * ENOMEM, ECUDA. */
+sfhe_status sfhe_matmul_dense(sfhe_ctx* ctx, const sfhe_matrix* A, const sfhe_matrix* B, sfhe_matrix** C, void* stream);
+/* *C = A x B with the k-loop over the nonzeros of A as `encoding` lists
+ * them (Sec. 3.3.2; A must carry that encoding: EINVAL otherwise); a
+ * MASK-encoded B also skips the k where B[k][j] is zero.  Otherwise as
+ * sfhe_matmul_dense. */
+sfhe_status sfhe_matmul_sparse(sfhe_ctx* ctx, const sfhe_matrix* A, const sfhe_matrix* B, sfhe_encoding encoding,
+                               sfhe_matrix** C, void* stream);
+/* n independent products C[m] = A[m] x B[m] (each A over the k its own
+ * encoding lists) in one execution under `flags` (SFHE_EXEC_PLAIN, or
+ * SFHE_EXEC_PERSISTENT optionally with SFHE_EXEC_LAZY; SFHE_EXEC_GRAPH is
+ * for plans).  C[0..n-1] receive new handles (all NULL on error).  No
+ * counterpart in the paper, whose Sec. 3.4 spreads one matmul's output
+ * entries over CPU threads. */
+sfhe_status sfhe_matmul_batch(sfhe_ctx* ctx, int32_t n, const sfhe_matrix* const* A, const sfhe_matrix* const* B,
+                              sfhe_matrix** C, uint32_t flags, void* stream);
+
+/* -------------------------------------------- host-resident operands --- */
+/* A matmul whose ciphertexts live in host memory: every call copies A's and
+ * B's ciphertexts to the device, lifts them, runs the matmul and copies C
+ * back (Alg. 1's input and output at the host).  The plan is built once from
+ * descriptors of the n matmuls' structure (their ct / ext fields are
+ * ignored) and owns `depth` (1 or 2) sets of device buffers.  With depth 2
+ * consecutive calls overlap: call i+1's upload and call i-1's download run
+ * on the plan's own copy streams while call i computes.  flags as
+ * sfhe_matmul_batch.  Errors: EINVAL, ESHAPE, EUNSUPPORTED, ENOMEM, ECUDA. */
+sfhe_status sfhe_host_plan_create(sfhe_ctx* ctx, int32_t n, const sfhe_matrix_view* A, const sfhe_matrix_view* B,
+                                  uint32_t flags, int32_t depth, sfhe_host_plan** out);
+/* One matmul: A_ct[m] (host, [nct_A][2][L][N] NTT form), B_ct[m] likewise,
+ * into C_ct[m] (host, [rows_A * cols_B][2][L][N] NTT form).  Asynchronous:
+ * the copies and kernels are ordered after the work already on `stream`,
+ * and work enqueued on `stream` after the call waits for C_ct to be written;
+ * the host buffers must stay valid and unchanged until then.  Page-locked
+ * (pinned) host buffers let the copies overlap with computation.  Errors:
+ * EINVAL (null), ECUDA. */
+sfhe_status sfhe_matmul_host(sfhe_host_plan* hp, const uint64_t* const* A_ct, const uint64_t* const* B_ct,
+                             uint64_t* const* C_ct, void* stream);
+/* products per call, bytes copied host->device and device->host per call,
+ * and the library's kernel launches per call. */
+sfhe_status sfhe_host_plan_stats(const sfhe_host_plan* hp, int64_t* products, uint64_t* h2d_bytes,
+                                 uint64_t* d2h_bytes, int64_t* launches);
+/* Waits for the plan's work and releases it.  NULL is a no-op. */
+void sfhe_host_plan_destroy(sfhe_host_plan* hp);
+
+/* ------------------------------------------- matmul over views --- */
+/* The same products over caller-owned device memory (sfhe_matrix_view):
+ * the caller allocates C's ciphertexts and the workspace, and picks the
+ * execution mode.  Workspace (device bytes) for n matmuls A[m] x B[m] under
+ * `flags`: */
+sfhe_status sfhe_matmul_workspace_size(const sfhe_ctx* ctx, int32_t n, const sfhe_matrix_view* A,
+                                       const sfhe_matrix_view* B, uint32_t flags, size_t* bytes);
 /* C = A x B with the k-loop over every k: the naive dense loop of Alg. 1
  * (Sec. 3.3.1), each product multiplied, relinearised and added (A must
  * store every element: DENSE or MASK; masks are ignored). */
-sfhe_status sfhe_matmul_dense(sfhe_ctx* ctx, const sfhe_matrix* A, const sfhe_matrix* B, sfhe_matrix* C, uint32_t flags,
-                              void* work, size_t work_bytes, void* stream);
+sfhe_status sfhe_matmul_dense_view(sfhe_ctx* ctx, const sfhe_matrix_view* A, const sfhe_matrix_view* B,
+                                   sfhe_matrix_view* C, uint32_t flags, void* work, size_t work_bytes, void* stream);
 /* C = A x B with the k-loop over the nonzeros of A as `encoding` lists them
  * (Sec. 3.3.2; A must carry that encoding; EINVAL otherwise); a MASK-encoded
  * B also skips the k where B[k][j] is zero. */
-sfhe_status sfhe_matmul_sparse(sfhe_ctx* ctx, const sfhe_matrix* A, const sfhe_matrix* B, int32_t encoding,
-                               sfhe_matrix* C, uint32_t flags, void* work, size_t work_bytes, void* stream);
+sfhe_status sfhe_matmul_sparse_view(sfhe_ctx* ctx, const sfhe_matrix_view* A, const sfhe_matrix_view* B,
+                                    int32_t encoding, sfhe_matrix_view* C, uint32_t flags, void* work,
+                                    size_t work_bytes, void* stream);
 /* n independent matmuls C[m] = A[m] x B[m] (each A in its own encoding) in
  * one execution.  No counterpart in the paper, whose Sec. 3.4 spreads one
  * matmul's output entries over CPU threads; here the entries of all n
  * matmuls share one persistent launch. */
-sfhe_status sfhe_matmul_batch(sfhe_ctx* ctx, int32_t n, const sfhe_matrix* A, const sfhe_matrix* B, sfhe_matrix* C,
-                              uint32_t flags, void* work, size_t work_bytes, void* stream);
+sfhe_status sfhe_matmul_batch_view(sfhe_ctx* ctx, int32_t n, const sfhe_matrix_view* A, const sfhe_matrix_view* B,
+                                   sfhe_matrix_view* C, uint32_t flags, void* work, size_t work_bytes, void* stream);
 
 /* Plans: the work list is built and uploaded once (into `work`), then
  * sfhe_plan_execute only launches (with SFHE_EXEC_GRAPH, one graph launch),
  * so it can be replayed and captured.  The plan keeps the pointers of A, B,
  * C and `work`; they must stay valid until sfhe_plan_destroy. */
-sfhe_status sfhe_plan_create(sfhe_ctx* ctx, int32_t n, const sfhe_matrix* A, const sfhe_matrix* B, sfhe_matrix* C,
-                             uint32_t flags, void* work, size_t work_bytes, void* stream, sfhe_plan** out);
+sfhe_status sfhe_plan_create(sfhe_ctx* ctx, int32_t n, const sfhe_matrix_view* A, const sfhe_matrix_view* B,
+                             sfhe_matrix_view* C, uint32_t flags, void* work, size_t work_bytes, void* stream,
+                             sfhe_plan** out);
 sfhe_status sfhe_plan_execute(sfhe_plan* plan, void* stream);
 /* Synchronises `stream` and reads the status word of a matmul workspace
  * after a PERSISTENT execution: SFHE_ETIMEOUT if one of the kernel's bounded
@@ -324,11 +452,13 @@ sfhe_status sfhe_plan_execute(sfhe_plan* plan, void* stream);
 sfhe_status sfhe_matmul_check(void* work, void* stream);
 /* Self-test of the bounded device waits (no fault is involved): one thread
  * waits on an mbarrier that nothing arrives at, gives up after `tries`
- * attempts (1 .. 2^20) and sets the status word of `work` (device, at
- * least 256 bytes, its first 8 bytes zeroed by the caller) as the
- * persistent kernel does; sfhe_matmul_check(work) then reports
- * SFHE_ETIMEOUT. */
-sfhe_status sfhe_selftest_wait_bound(void* work, uint32_t tries, void* stream);
+ * attempts (1 .. 2^30) or `limit_us` microseconds of the GPU's clock
+ * (1 .. 10^6), whichever comes first, and sets the status word of `work`
+ * (device, at least 256 bytes, its first 8 bytes zeroed by the caller) as
+ * the persistent kernel does; sfhe_matmul_check(work) then reports
+ * SFHE_ETIMEOUT.  The persistent kernel's own bound is one second or 2^26
+ * attempts.  Errors: EINVAL (null, bounds out of range), ECUDA. */
+sfhe_status sfhe_selftest_wait_bound(void* work, uint32_t tries, uint32_t limit_us, void* stream);
 /* products performed, output entries, own kernel launches per execute, CTAs */
 sfhe_status sfhe_plan_stats(const sfhe_plan* plan, int64_t* products, int64_t* entries, int64_t* launches,
                             int64_t* ctas);
@@ -356,7 +486,9 @@ sfhe_status sfhe_ct_mul_relin(sfhe_ctx* ctx, const uint32_t* a_ext, const uint32
  * code running during stream capture, a serving loop that must not enter an
  * allocator).  The first call on a device looks the array's address up
  * (cudaGetSymbolAddress) and should precede any stream capture; later
- * calls only launch.  The context's device must be the current device.
+ * calls only launch.  Destroying a context of the device forgets the
+ * address, so the first call after it looks the address up again (after a
+ * device reset the array lives at a new address).  The context's device must be the current device.
  * Rings whose scratch, 3 K N uint32 words (rounded up to 256 bytes) +
  * (3 L + (L+2) L) N uint64 words, exceeds the array are rejected with
  * SFHE_ENOMEM (N = 8192, L = 4 needs 3.8 MB and fits; N = 16384, L = 8

@@ -67,10 +67,10 @@ class EncMatrix:
         self.mask, self.row_ptr, self.col_idx, self.ell_col = mask, row_ptr, col_idx, ell_col
         self.ct, self.ext = ct, ext
 
-    def desc(self) -> S.sfhe_matrix:
+    def desc(self) -> S.sfhe_matrix_view:
         def p(a):
             return None if a is None else S._ptr(a)
-        return S.sfhe_matrix(self.rows, self.cols, self.encoding, self.nct, self.ell_width, p(self.mask),
+        return S.sfhe_matrix_view(self.rows, self.cols, self.encoding, self.nct, self.ell_width, p(self.mask),
                               p(self.row_ptr), p(self.col_idx), p(self.ell_col), p(self.ct), p(self.ext))
 
     def memory(self, ctx: "Context") -> dict:
@@ -181,9 +181,9 @@ def matmul(ctx: Context, A: EncMatrix, B: EncMatrix, *, dense: bool = False, mod
         work = workspace(ctx, [A], [B], flags)
     Ad, Bd, Cd = A.desc(), B.desc(), C.desc()
     if dense:
-        S.sfhe_matmul_dense(ctx.h, Ad, Bd, Cd, flags, work, stream)
+        S.sfhe_matmul_dense_view(ctx.h, Ad, Bd, Cd, flags, work, stream)
     else:
-        S.sfhe_matmul_sparse(ctx.h, Ad, Bd, A.encoding, Cd, flags, work, stream)
+        S.sfhe_matmul_sparse_view(ctx.h, Ad, Bd, A.encoding, Cd, flags, work, stream)
     C._work = work
     return C
 
@@ -192,7 +192,7 @@ def matmul_batch(ctx: Context, As, Bs, *, mode: str = "persistent", stream=None)
     Cs = [result_matrix(ctx, a.rows, b.cols) for a, b in zip(As, Bs)]
     flags = _flags(mode)
     work = workspace(ctx, As, Bs, flags)
-    S.sfhe_matmul_batch(ctx.h, [a.desc() for a in As], [b.desc() for b in Bs], [c.desc() for c in Cs], flags, work,
+    S.sfhe_matmul_batch_view(ctx.h, [a.desc() for a in As], [b.desc() for b in Bs], [c.desc() for c in Cs], flags, work,
                         stream)
     for c in Cs:
         c._work = work

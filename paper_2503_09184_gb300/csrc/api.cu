@@ -11,6 +11,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "../../include/sfhe.h"
+#include "api_internal.h"
 #include "host_math.h"
 #include "launch.h"
 
@@ -46,6 +47,30 @@ sfhe_status fail(sfhe_status st, const char* fmt, ...)
 inline cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+}  // namespace
+
+// Scratch of sfhe_ct_mul_relin_static: a file-scope device array, so that the
+// call needs no workspace from its caller and allocates nothing.  Its callers
+// are those that cannot hand over device memory: a plain C caller with no
+// device allocator of its own, code that runs while a stream is being
+// captured (where cudaMalloc is not allowed), and a serving loop that must
+// not enter an allocator between requests.  One copy exists per device; its
+// address is looked up once per device, on the first call made there, and
+// forgotten when a context of that device is destroyed (a device reset
+// between contexts would move the array), so the next first call looks it up
+// again.
+namespace {
+__device__ __align__(256) unsigned char g_static_scratch[SFHE_STATIC_SCRATCH_BYTES];
+
+std::mutex g_static_mu;
+void* g_static_addr[64];  // per device ordinal; null until the first call there
+
+void forget_static_scratch(int dev)
+{
+    if (dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    g_static_addr[dev] = nullptr;
+}
 }  // namespace
 
 struct sfhe_ctx {
@@ -87,6 +112,19 @@ struct sfhe_plan {
 
 extern "C" const char* sfhe_last_error(void) { return g_last_error.c_str(); }
 
+sfhe_status sfhe::set_error(sfhe_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+int sfhe::ctx_device(const sfhe_ctx* c) { return c->device; }
+
 // ---------------------------------------------------------------- helpers ---
 extern "C" sfhe_status sfhe_select_primes(uint32_t N, uint32_t L, uint64_t* q, uint32_t* b, int32_t* K)
 {
@@ -116,6 +154,7 @@ extern "C" sfhe_status sfhe_cdt_table(double sigma, uint64_t* T20)
 extern "C" void sfhe_ctx_destroy(sfhe_ctx* c)
 {
     if (!c) return;
+    forget_static_scratch(c->device);
     cudaFree(c->d_tw);
     cudaFree(c->d_twb);
     cudaFree(c->d_s);
@@ -253,7 +292,7 @@ extern "C" sfhe_status sfhe_encode_count(const int64_t* values, int32_t rows, in
     return SFHE_OK;
 }
 
-extern "C" sfhe_status sfhe_matrix_bytes(uint32_t N, uint32_t L, const sfhe_matrix* M, uint64_t* ct_bytes,
+extern "C" sfhe_status sfhe_matrix_bytes(uint32_t N, uint32_t L, const sfhe_matrix_view* M, uint64_t* ct_bytes,
                                          uint64_t* ext_bytes, uint64_t* meta_bytes)
 {
     if (!M || !ct_bytes || !ext_bytes || !meta_bytes) return fail(SFHE_EINVAL, "null argument");
@@ -455,7 +494,7 @@ struct Layout {
     size_t queue, mms, entries, rowlist, scratch, T, D, U, total;
 };
 
-sfhe_status validate_matrix(const sfhe_matrix& m, const char* name)
+sfhe_status validate_matrix(const sfhe_matrix_view& m, const char* name)
 {
     if (m.rows < 0 || m.cols < 0) return fail(SFHE_ESHAPE, "%s: negative shape", name);
     if (m.encoding < SFHE_ENC_DENSE || m.encoding > SFHE_ENC_ELL) return fail(SFHE_EINVAL, "%s: bad encoding", name);
@@ -491,7 +530,7 @@ sfhe_status validate_matrix(const sfhe_matrix& m, const char* name)
 }
 
 // rows of (A ciphertext index, k) pairs listed by A's encoding
-void row_pairs(const sfhe_matrix& A, int32_t i, bool dense_loop, std::vector<int2>& out)
+void row_pairs(const sfhe_matrix_view& A, int32_t i, bool dense_loop, std::vector<int2>& out)
 {
     const int32_t K = A.cols;
     if (dense_loop) {
@@ -518,7 +557,7 @@ void row_pairs(const sfhe_matrix& A, int32_t i, bool dense_loop, std::vector<int
     }
 }
 
-sfhe_status build(const sfhe_ctx* c, int32_t n, const sfhe_matrix* A, const sfhe_matrix* B, const sfhe_matrix* C,
+sfhe_status build(const sfhe_ctx* c, int32_t n, const sfhe_matrix_view* A, const sfhe_matrix_view* B, const sfhe_matrix_view* C,
                   const bool* dense_loop, sfhe_plan& P)
 {
     if (n < 0) return fail(SFHE_ESHAPE, "negative matmul count");
@@ -677,6 +716,8 @@ sfhe_status launch_plan(sfhe_plan* P, cudaStream_t s)
 
 }  // namespace
 
+sfhe_status sfhe::validate_view(const sfhe_matrix_view& m, const char* name) { return validate_matrix(m, name); }
+
 extern "C" void sfhe_plan_destroy(sfhe_plan* P)
 {
     if (!P) return;
@@ -685,8 +726,8 @@ extern "C" void sfhe_plan_destroy(sfhe_plan* P)
     delete P;
 }
 
-static sfhe_status plan_create_impl(sfhe_ctx* c, int32_t n, const sfhe_matrix* A, const sfhe_matrix* B,
-                                    sfhe_matrix* C, const bool* dense_loop, uint32_t flags, void* work,
+static sfhe_status plan_create_impl(sfhe_ctx* c, int32_t n, const sfhe_matrix_view* A, const sfhe_matrix_view* B,
+                                    sfhe_matrix_view* C, const bool* dense_loop, uint32_t flags, void* work,
                                     size_t work_bytes, void* stream, sfhe_plan** out)
 {
     if (!c || !out) return fail(SFHE_EINVAL, "null argument");
@@ -759,8 +800,8 @@ static sfhe_status plan_create_impl(sfhe_ctx* c, int32_t n, const sfhe_matrix* A
     return SFHE_OK;
 }
 
-extern "C" sfhe_status sfhe_plan_create(sfhe_ctx* c, int32_t n, const sfhe_matrix* A, const sfhe_matrix* B,
-                                        sfhe_matrix* C, uint32_t flags, void* work, size_t work_bytes, void* stream,
+extern "C" sfhe_status sfhe_plan_create(sfhe_ctx* c, int32_t n, const sfhe_matrix_view* A, const sfhe_matrix_view* B,
+                                        sfhe_matrix_view* C, uint32_t flags, void* work, size_t work_bytes, void* stream,
                                         sfhe_plan** out)
 {
     std::vector<char> dl(std::max(n, 0), 0);
@@ -774,11 +815,12 @@ extern "C" sfhe_status sfhe_plan_execute(sfhe_plan* P, void* stream)
     return launch_plan(P, as_stream(stream));
 }
 
-extern "C" sfhe_status sfhe_selftest_wait_bound(void* work, uint32_t tries, void* stream)
+extern "C" sfhe_status sfhe_selftest_wait_bound(void* work, uint32_t tries, uint32_t limit_us, void* stream)
 {
     if (!work) return fail(SFHE_EINVAL, "null workspace");
-    if (tries == 0 || tries > (1u << 20)) return fail(SFHE_EINVAL, "tries must be in 1 .. 2^20");
-    CUDA_TRY(launch_wait_selftest((unsigned*)work, tries, as_stream(stream)));
+    if (tries == 0 || tries > (1u << 30)) return fail(SFHE_EINVAL, "tries must be in 1 .. 2^30");
+    if (limit_us == 0 || limit_us > 1000000u) return fail(SFHE_EINVAL, "limit_us must be in 1 .. 10^6");
+    CUDA_TRY(launch_wait_selftest((unsigned*)work, tries, (u64)limit_us * 1000u, as_stream(stream)));
     return SFHE_OK;
 }
 
@@ -812,7 +854,7 @@ extern "C" sfhe_status sfhe_plan_stats(const sfhe_plan* P, int64_t* products, in
     return SFHE_OK;
 }
 
-static sfhe_status size_impl(const sfhe_ctx* c, int32_t n, const sfhe_matrix* A, const sfhe_matrix* B,
+static sfhe_status size_impl(const sfhe_ctx* c, int32_t n, const sfhe_matrix_view* A, const sfhe_matrix_view* B,
                              const bool* dense_loop, uint32_t flags, size_t* bytes)
 {
     if (!c || !bytes) return fail(SFHE_EINVAL, "null argument");
@@ -829,14 +871,14 @@ static sfhe_status size_impl(const sfhe_ctx* c, int32_t n, const sfhe_matrix* A,
     return SFHE_OK;
 }
 
-extern "C" sfhe_status sfhe_matmul_workspace_size(const sfhe_ctx* c, int32_t n, const sfhe_matrix* A,
-                                                  const sfhe_matrix* B, uint32_t flags, size_t* bytes)
+extern "C" sfhe_status sfhe_matmul_workspace_size(const sfhe_ctx* c, int32_t n, const sfhe_matrix_view* A,
+                                                  const sfhe_matrix_view* B, uint32_t flags, size_t* bytes)
 {
     std::vector<char> dl(std::max(n, 0), 0);
     return size_impl(c, n, A, B, (const bool*)dl.data(), flags, bytes);
 }
 
-static sfhe_status one_shot(sfhe_ctx* c, int32_t n, const sfhe_matrix* A, const sfhe_matrix* B, sfhe_matrix* C,
+static sfhe_status one_shot(sfhe_ctx* c, int32_t n, const sfhe_matrix_view* A, const sfhe_matrix_view* B, sfhe_matrix_view* C,
                             const bool* dense_loop, uint32_t flags, void* work, size_t work_bytes, void* stream)
 {
     Range range("sfhe_matmul");
@@ -850,7 +892,7 @@ static sfhe_status one_shot(sfhe_ctx* c, int32_t n, const sfhe_matrix* A, const 
     return st;
 }
 
-extern "C" sfhe_status sfhe_matmul_dense(sfhe_ctx* c, const sfhe_matrix* A, const sfhe_matrix* B, sfhe_matrix* C,
+extern "C" sfhe_status sfhe_matmul_dense_view(sfhe_ctx* c, const sfhe_matrix_view* A, const sfhe_matrix_view* B, sfhe_matrix_view* C,
                                          uint32_t flags, void* work, size_t work_bytes, void* stream)
 {
     if (!A) return fail(SFHE_EINVAL, "null A");
@@ -860,8 +902,8 @@ extern "C" sfhe_status sfhe_matmul_dense(sfhe_ctx* c, const sfhe_matrix* A, cons
     return one_shot(c, 1, A, B, C, &dl, flags, work, work_bytes, stream);
 }
 
-extern "C" sfhe_status sfhe_matmul_sparse(sfhe_ctx* c, const sfhe_matrix* A, const sfhe_matrix* B, int32_t encoding,
-                                          sfhe_matrix* C, uint32_t flags, void* work, size_t work_bytes, void* stream)
+extern "C" sfhe_status sfhe_matmul_sparse_view(sfhe_ctx* c, const sfhe_matrix_view* A, const sfhe_matrix_view* B, int32_t encoding,
+                                          sfhe_matrix_view* C, uint32_t flags, void* work, size_t work_bytes, void* stream)
 {
     if (!A) return fail(SFHE_EINVAL, "null A");
     if (encoding != SFHE_ENC_MASK && encoding != SFHE_ENC_CSR && encoding != SFHE_ENC_ELL)
@@ -871,8 +913,8 @@ extern "C" sfhe_status sfhe_matmul_sparse(sfhe_ctx* c, const sfhe_matrix* A, con
     return one_shot(c, 1, A, B, C, &dl, flags, work, work_bytes, stream);
 }
 
-extern "C" sfhe_status sfhe_matmul_batch(sfhe_ctx* c, int32_t n, const sfhe_matrix* A, const sfhe_matrix* B,
-                                         sfhe_matrix* C, uint32_t flags, void* work, size_t work_bytes, void* stream)
+extern "C" sfhe_status sfhe_matmul_batch_view(sfhe_ctx* c, int32_t n, const sfhe_matrix_view* A, const sfhe_matrix_view* B,
+                                         sfhe_matrix_view* C, uint32_t flags, void* work, size_t work_bytes, void* stream)
 {
     std::vector<char> dl(std::max(n, 0), 0);
     return one_shot(c, n, A, B, C, (const bool*)dl.data(), flags, work, work_bytes, stream);
@@ -911,19 +953,6 @@ extern "C" sfhe_status sfhe_ct_mul_relin(sfhe_ctx* c, const uint32_t* a_ext, con
     return SFHE_OK;
 }
 
-// Scratch of sfhe_ct_mul_relin_static: a file-scope device array, so that the
-// call needs no workspace from its caller and allocates nothing.  Its callers
-// are those that cannot hand over device memory: a plain C caller with no
-// device allocator of its own, code that runs while a stream is being
-// captured (where cudaMalloc is not allowed), and a serving loop that must
-// not enter an allocator between requests.  One copy exists per device; its
-// address is looked up once per device, on the first call made there.
-namespace {
-__device__ __align__(256) unsigned char g_static_scratch[SFHE_STATIC_SCRATCH_BYTES];
-
-std::mutex g_static_mu;
-void* g_static_addr[64];  // per device ordinal; null until the first call there
-}  // namespace
 
 extern "C" sfhe_status sfhe_ct_mul_relin_static(sfhe_ctx* c, const uint32_t* a_ext, const uint32_t* b_ext,
                                                 uint64_t* out, void* stream)
@@ -1299,8 +1328,8 @@ struct FusedLayout {
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-sfhe_status fused_layout(const sfhe_ctx* c, int32_t M, int32_t K, int32_t Nc, int32_t c_chunk, const sfhe_matrix& Ad,
-                         const sfhe_matrix& Bd, FusedLayout& Lo)
+sfhe_status fused_layout(const sfhe_ctx* c, int32_t M, int32_t K, int32_t Nc, int32_t c_chunk, const sfhe_matrix_view& Ad,
+                         const sfhe_matrix_view& Bd, FusedLayout& Lo)
 {
     const RnsConsts& rc = c->rc;
     const size_t ctb = (size_t)2 * rc.L * rc.N * 8, extb = (size_t)2 * rc.K * rc.N * 4;
@@ -1327,9 +1356,9 @@ sfhe_status fused_layout(const sfhe_ctx* c, int32_t M, int32_t K, int32_t Nc, in
 
 // descriptors of the rotated operands: MASK-encoded where a zero mask is
 // given (the sparse matmul skips those products), DENSE otherwise
-sfhe_matrix element_desc(int32_t rows, int32_t cols, const uint8_t* zero, uint64_t* ct, uint32_t* ext)
+sfhe_matrix_view element_desc(int32_t rows, int32_t cols, const uint8_t* zero, uint64_t* ct, uint32_t* ext)
 {
-    sfhe_matrix d;
+    sfhe_matrix_view d;
     memset(&d, 0, sizeof(d));
     d.rows = rows;
     d.cols = cols;
@@ -1348,8 +1377,8 @@ extern "C" sfhe_status sfhe_matmul_chunked_fused_workspace_size(const sfhe_ctx* 
 {
     if (!c || !bytes) return fail(SFHE_EINVAL, "null argument");
     if (M < 0 || K < 0 || Nc < 0 || chunk < 1) return fail(SFHE_ESHAPE, "negative shape or chunk size");
-    sfhe_matrix Ad = element_desc(M, K, a_zero, (uint64_t*)16, (uint32_t*)16);
-    sfhe_matrix Bd = element_desc(K, Nc, b_zero, (uint64_t*)16, (uint32_t*)16);
+    sfhe_matrix_view Ad = element_desc(M, K, a_zero, (uint64_t*)16, (uint32_t*)16);
+    sfhe_matrix_view Bd = element_desc(K, Nc, b_zero, (uint64_t*)16, (uint32_t*)16);
     FusedLayout Lo;
     sfhe_status st = fused_layout(c, M, K, Nc, chunk, Ad, Bd, Lo);
     if (st != SFHE_OK) return st;
@@ -1372,7 +1401,7 @@ extern "C" sfhe_status sfhe_matmul_chunked_fused(sfhe_ctx* c, const sfhe_rotkeys
     const int64_t nC = ((int64_t)M * Nc + ch - 1) / ch;
     if (nC > 0 && (!A || !B || !C)) return fail(SFHE_EINVAL, "null operand");
     char* w = (char*)work;
-    sfhe_matrix Ad = element_desc(M, K, a_zero, nullptr, nullptr), Bd = element_desc(K, Nc, b_zero, nullptr, nullptr);
+    sfhe_matrix_view Ad = element_desc(M, K, a_zero, nullptr, nullptr), Bd = element_desc(K, Nc, b_zero, nullptr, nullptr);
     Ad.ct = (uint64_t*)16, Ad.ext = (uint32_t*)16, Bd.ct = (uint64_t*)16, Bd.ext = (uint32_t*)16;
     FusedLayout Lo;
     sfhe_status st = fused_layout(c, M, K, Nc, ch, Ad, Bd, Lo);
@@ -1420,7 +1449,7 @@ extern "C" sfhe_status sfhe_matmul_chunked_fused(sfhe_ctx* c, const sfhe_rotkeys
     if (st != SFHE_OK) return st;
     Ad = element_desc(M, K, a_zero, arot, ea);
     Bd = element_desc(K, Nc, b_zero, brot, eb);
-    sfhe_matrix Cd = element_desc(M, Nc, nullptr, cel, nullptr);
+    sfhe_matrix_view Cd = element_desc(M, Nc, nullptr, cel, nullptr);
     const bool dl = false;
     sfhe_plan* P = nullptr;
     st = plan_create_impl(c, 1, &Ad, &Bd, &Cd, &dl, SFHE_EXEC_PERSISTENT, w + Lo.plan, Lo.plan_bytes, stream, &P);

@@ -291,9 +291,20 @@ SFHE_DEV void tma_load_1d(void* dst, const void* src, u32 bytes, u64* bar)
 // order this thread's earlier generic-proxy shared-memory accesses before
 // later async-proxy (TMA) accesses
 SFHE_DEV void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-// bounded wait for the phase with the given parity; false when the bound ran out
-SFHE_DEV bool mbar_wait(u64* bar, u32 parity, u32 max_tries)
+// the GPU's nanosecond clock (PTX %globaltimer)
+SFHE_DEV u64 global_ns()
 {
+    u64 t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// bounded wait for the phase with the given parity: false once max_tries
+// attempts have failed or max_ns nanoseconds have passed, whichever comes
+// first (an attempt may itself suspend the thread for a hardware-defined
+// time, so the time bound is the one that holds in real time)
+SFHE_DEV bool mbar_wait(u64* bar, u32 parity, u32 max_tries, u64 max_ns)
+{
+    const u64 t0 = global_ns();
     for (u32 i = 0; i < max_tries; i++) {
         u32 done;
         asm volatile(
@@ -302,6 +313,7 @@ SFHE_DEV bool mbar_wait(u64* bar, u32 parity, u32 max_tries)
             : "r"(smem_addr(bar)), "r"(parity)
             : "memory");
         if (done) return true;
+        if (global_ns() - t0 > max_ns) return false;
     }
     return false;
 }

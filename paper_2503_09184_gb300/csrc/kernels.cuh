@@ -601,9 +601,10 @@ struct PersistentPlan {
     static_assert(SMEM <= 227 * 1024 - 256, "shared-memory plan too large");
 };
 
-// bound of every mbarrier wait (each try_wait may also suspend in hardware):
-// far beyond any copy's latency, short of a hung GPU
-#define SFHE_WAIT_TRIES (1u << 24)
+// bounds of every mbarrier wait: one second of real time (a 64 KB bulk copy
+// lands within microseconds), and at most 2^26 attempts
+#define SFHE_WAIT_TRIES (1u << 26)
+#define SFHE_WAIT_NS 1000000000ull
 
 // One CTA per output entry at a time, taken from a queue in descending
 // product count.  Per product (per rounding group of mm.group products in the
@@ -660,7 +661,7 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
     // bounded wait on mbarrier bi by every thread; false (in every thread) if
     // any thread's wait ran out
     auto wait_bar = [&](int bi) -> bool {
-        const bool ok = mbar_wait(&mbar[bi], (phbits >> bi) & 1u, SFHE_WAIT_TRIES);
+        const bool ok = mbar_wait(&mbar[bi], (phbits >> bi) & 1u, SFHE_WAIT_TRIES, SFHE_WAIT_NS);
         if (ok) {
             phbits ^= 1u << bi;
             pend &= ~(1u << bi);
@@ -672,7 +673,7 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
         if (tid == 0) {
             atomicExch(queue + 1, 1u);
             for (int bi = 0; bi < 2; bi++)
-                if (pend & (1u << bi)) mbar_wait(&mbar[bi], (phbits >> bi) & 1u, SFHE_WAIT_TRIES);
+                if (pend & (1u << bi)) mbar_wait(&mbar[bi], (phbits >> bi) & 1u, SFHE_WAIT_TRIES, SFHE_WAIT_NS);
         }
     };
 

@@ -69,7 +69,7 @@ cudaError_t launch_rotate_batch(const RnsConsts& rc, const u64* in, size_t in_st
 cudaError_t launch_rotate(const RnsConsts& rc, const u64* in, u32 g, const u64* key, const u64* key_sh, u64* out,
                           u64* work, cudaStream_t s);
 // a bounded wait that runs out: sets queue[1] = 1 (selftest.cu)
-cudaError_t launch_wait_selftest(unsigned* queue, u32 tries, cudaStream_t s);
+cudaError_t launch_wait_selftest(unsigned* queue, u32 tries, u64 limit_ns, cudaStream_t s);
 // multiplies per second of shoup32_lazy over all SMs (8 independent chains
 // per thread, full occupancy), timed with events on s; synchronises s
 cudaError_t measure_mulmod32(u32 b, u32 w, u32 ws, double* per_s, cudaStream_t s);

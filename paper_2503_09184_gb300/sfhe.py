@@ -40,7 +40,7 @@ class sfhe_info(ctypes.Structure):
                 ("ext_interleave", ctypes.c_uint32), ("lazy_group", ctypes.c_int32)]
 
 
-class sfhe_matrix(ctypes.Structure):
+class sfhe_matrix_view(ctypes.Structure):
     _fields_ = [("rows", ctypes.c_int32), ("cols", ctypes.c_int32), ("encoding", ctypes.c_int32),
                 ("nct", ctypes.c_int32), ("ell_width", ctypes.c_int32),
                 ("mask", ctypes.c_void_p), ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p),
@@ -62,7 +62,7 @@ _SIGS = {
     "sfhe_cdt_table": ([ctypes.c_double, _vp], ctypes.c_int),
     "sfhe_encode_count": ([_vp, _i32, _i32, _i32, _P(_i32), _P(_i32)], ctypes.c_int),
     "sfhe_encode_fill": ([_vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
-    "sfhe_matrix_bytes": ([_u32, _u32, _P(sfhe_matrix), _P(_u64), _P(_u64), _P(_u64)], ctypes.c_int),
+    "sfhe_matrix_bytes": ([_u32, _u32, _P(sfhe_matrix_view), _P(_u64), _P(_u64), _P(_u64)], ctypes.c_int),
     "sfhe_encrypt": ([_vp, _vp, _vp, _i64, _u64, _vp, _vp], ctypes.c_int),
     "sfhe_lift_workspace_size": ([_vp, _i64, _P(_sz)], ctypes.c_int),
     "sfhe_lift": ([_vp, _vp, _i64, _vp, _vp, _sz, _vp], ctypes.c_int),
@@ -71,13 +71,13 @@ _SIGS = {
     "sfhe_from_coeff": ([_vp, _vp, _i64, _vp, _vp], ctypes.c_int),
     "sfhe_export_secret": ([_vp, _vp], ctypes.c_int),
     "sfhe_export_relin_key": ([_vp, _vp, _vp], ctypes.c_int),
-    "sfhe_matmul_workspace_size": ([_vp, _i32, _P(sfhe_matrix), _P(sfhe_matrix), _u32, _P(_sz)], ctypes.c_int),
-    "sfhe_matmul_dense": ([_vp, _P(sfhe_matrix), _P(sfhe_matrix), _P(sfhe_matrix), _u32, _vp, _sz, _vp], ctypes.c_int),
-    "sfhe_matmul_sparse": ([_vp, _P(sfhe_matrix), _P(sfhe_matrix), _i32, _P(sfhe_matrix), _u32, _vp, _sz, _vp],
+    "sfhe_matmul_workspace_size": ([_vp, _i32, _P(sfhe_matrix_view), _P(sfhe_matrix_view), _u32, _P(_sz)], ctypes.c_int),
+    "sfhe_matmul_dense_view": ([_vp, _P(sfhe_matrix_view), _P(sfhe_matrix_view), _P(sfhe_matrix_view), _u32, _vp, _sz, _vp], ctypes.c_int),
+    "sfhe_matmul_sparse_view": ([_vp, _P(sfhe_matrix_view), _P(sfhe_matrix_view), _i32, _P(sfhe_matrix_view), _u32, _vp, _sz, _vp],
                            ctypes.c_int),
-    "sfhe_matmul_batch": ([_vp, _i32, _P(sfhe_matrix), _P(sfhe_matrix), _P(sfhe_matrix), _u32, _vp, _sz, _vp],
+    "sfhe_matmul_batch_view": ([_vp, _i32, _P(sfhe_matrix_view), _P(sfhe_matrix_view), _P(sfhe_matrix_view), _u32, _vp, _sz, _vp],
                           ctypes.c_int),
-    "sfhe_plan_create": ([_vp, _i32, _P(sfhe_matrix), _P(sfhe_matrix), _P(sfhe_matrix), _u32, _vp, _sz, _vp, _P(_vp)],
+    "sfhe_plan_create": ([_vp, _i32, _P(sfhe_matrix_view), _P(sfhe_matrix_view), _P(sfhe_matrix_view), _u32, _vp, _sz, _vp, _P(_vp)],
                          ctypes.c_int),
     "sfhe_plan_execute": ([_vp, _vp], ctypes.c_int),
     "sfhe_slots_encode": ([_u32, _u64, _vp, _vp], ctypes.c_int),
@@ -102,13 +102,31 @@ _SIGS = {
     "sfhe_measure_mulmod32": ([_vp, _P(ctypes.c_double), _vp], ctypes.c_int),
     "sfhe_plan_stats": ([_vp, _P(_i64), _P(_i64), _P(_i64), _P(_i64)], ctypes.c_int),
     "sfhe_matmul_check": ([_vp, _vp], ctypes.c_int),
-    "sfhe_selftest_wait_bound": ([_vp, _u32, _vp], ctypes.c_int),
+    "sfhe_selftest_wait_bound": ([_vp, _u32, _u32, _vp], ctypes.c_int),
     "sfhe_plan_destroy": ([_vp], None),
     "sfhe_ct_tensor_scale": ([_vp, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
     "sfhe_ct_mul_relin": ([_vp, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
     "sfhe_ct_mul_relin_static": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "sfhe_ntt": ([_vp, _i32, _i32, _vp, _i64, _vp, _vp], ctypes.c_int),
     "sfhe_prng_words": ([_u64, _u32, _u64, _u64, _u64, _u64, _i64, _vp, _vp], ctypes.c_int),
+    # library-owned matrices and matmuls over them
+    "sfhe_ctx_get_primes": ([_vp, _vp, _vp], ctypes.c_int),
+    "sfhe_matrix_encrypt": ([_vp, _vp, _i32, _i32, ctypes.c_int, _u64, _vp, _P(_vp)], ctypes.c_int),
+    "sfhe_matrix_import": ([_vp, _vp, _vp, _i32, _i32, ctypes.c_int, _vp, _P(_vp)], ctypes.c_int),
+    "sfhe_matrix_export": ([_vp, _vp, _vp], ctypes.c_int),
+    "sfhe_matrix_decrypt": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+    "sfhe_matrix_destroy": ([_vp], None),
+    "sfhe_matrix_info": ([_vp, _P(_i32), _P(_i32), _P(_i32), _P(_i32)], ctypes.c_int),
+    "sfhe_matrix_view_of": ([_vp, _P(sfhe_matrix_view), _vp], ctypes.c_int),
+    "sfhe_matmul_dense": ([_vp, _vp, _vp, _P(_vp), _vp], ctypes.c_int),
+    "sfhe_matmul_sparse": ([_vp, _vp, _vp, ctypes.c_int, _P(_vp), _vp], ctypes.c_int),
+    "sfhe_matmul_batch": ([_vp, _i32, _P(_vp), _P(_vp), _P(_vp), _u32, _vp], ctypes.c_int),
+    # host-resident operands
+    "sfhe_host_plan_create": ([_vp, _i32, _P(sfhe_matrix_view), _P(sfhe_matrix_view), _u32, _i32, _P(_vp)],
+                              ctypes.c_int),
+    "sfhe_matmul_host": ([_vp, _P(_vp), _P(_vp), _P(_vp), _vp], ctypes.c_int),
+    "sfhe_host_plan_stats": ([_vp, _P(_i64), _P(_u64), _P(_u64), _P(_i64)], ctypes.c_int),
+    "sfhe_host_plan_destroy": ([_vp], None),
 }
 
 _lib = None
@@ -271,7 +289,7 @@ def sfhe_export_relin_key(ctx: int, out, stream=None) -> None:
 
 # ----------------------------------------------------------------- matmul ---
 def _mats(ms) -> ctypes.Array:
-    arr = (sfhe_matrix * len(ms))()
+    arr = (sfhe_matrix_view * len(ms))()
     for k, m in enumerate(ms):
         arr[k] = m
     return arr
@@ -283,18 +301,18 @@ def sfhe_matmul_workspace_size(ctx: int, A: list, B: list, flags: int) -> int:
     return b.value
 
 
-def sfhe_matmul_dense(ctx: int, A, B, C, flags: int, work, stream=None) -> None:
-    _check(lib().sfhe_matmul_dense(ctx, ctypes.byref(A), ctypes.byref(B), ctypes.byref(C), flags, _ptr(work),
+def sfhe_matmul_dense_view(ctx: int, A, B, C, flags: int, work, stream=None) -> None:
+    _check(lib().sfhe_matmul_dense_view(ctx, ctypes.byref(A), ctypes.byref(B), ctypes.byref(C), flags, _ptr(work),
                                    work.numel() * work.element_size(), _stream(stream)))
 
 
-def sfhe_matmul_sparse(ctx: int, A, B, encoding: int, C, flags: int, work, stream=None) -> None:
-    _check(lib().sfhe_matmul_sparse(ctx, ctypes.byref(A), ctypes.byref(B), encoding, ctypes.byref(C), flags,
+def sfhe_matmul_sparse_view(ctx: int, A, B, encoding: int, C, flags: int, work, stream=None) -> None:
+    _check(lib().sfhe_matmul_sparse_view(ctx, ctypes.byref(A), ctypes.byref(B), encoding, ctypes.byref(C), flags,
                                     _ptr(work), work.numel() * work.element_size(), _stream(stream)))
 
 
-def sfhe_matmul_batch(ctx: int, A: list, B: list, C: list, flags: int, work, stream=None) -> None:
-    _check(lib().sfhe_matmul_batch(ctx, len(A), _mats(A), _mats(B), _mats(C), flags, _ptr(work),
+def sfhe_matmul_batch_view(ctx: int, A: list, B: list, C: list, flags: int, work, stream=None) -> None:
+    _check(lib().sfhe_matmul_batch_view(ctx, len(A), _mats(A), _mats(B), _mats(C), flags, _ptr(work),
                                    work.numel() * work.element_size(), _stream(stream)))
 
 
@@ -425,8 +443,8 @@ def sfhe_matmul_check(work, stream=None) -> None:
     _check(lib().sfhe_matmul_check(_ptr(work), _stream(stream)))
 
 
-def sfhe_selftest_wait_bound(work, tries: int, stream=None) -> None:
-    _check(lib().sfhe_selftest_wait_bound(_ptr(work), tries, _stream(stream)))
+def sfhe_selftest_wait_bound(work, tries: int, limit_us: int = 1_000_000, stream=None) -> None:
+    _check(lib().sfhe_selftest_wait_bound(_ptr(work), tries, limit_us, _stream(stream)))
 
 
 def sfhe_plan_destroy(plan: int) -> None:
@@ -454,3 +472,107 @@ def sfhe_ntt(ctx: int, prime_index: int, inverse: bool, inp, npoly: int, out, st
 
 def sfhe_prng_words(seed: int, domain: int, o0: int, o1: int, o2: int, idx0: int, n: int, out, stream=None) -> None:
     _check(lib().sfhe_prng_words(seed, domain, o0, o1, o2, idx0, n, _ptr(out), _stream(stream)))
+
+
+# --------------------------------------- library-owned matrices (handles) ---
+def sfhe_ctx_get_primes(ctx: int) -> tuple[list[int], list[int]]:
+    """(ciphertext primes q, extended-base primes p)."""
+    info = sfhe_ctx_info(ctx)
+    q = np.zeros(max(info.L, 1), dtype=np.uint64)
+    p = np.zeros(max(info.K, 1), dtype=np.uint64)
+    _check(lib().sfhe_ctx_get_primes(ctx, _ptr(q), _ptr(p)))
+    return [int(x) for x in q[:info.L]], [int(x) for x in p[:info.K]]
+
+
+def sfhe_matrix_encrypt(ctx: int, vals: np.ndarray, encoding: int, matrix_id: int, stream=None) -> int:
+    v = np.ascontiguousarray(vals, dtype=np.int64)
+    h = ctypes.c_void_p()
+    _check(lib().sfhe_matrix_encrypt(ctx, _ptr(v), v.shape[0], v.shape[1], encoding, matrix_id, _stream(stream),
+                                     ctypes.byref(h)))
+    return h.value
+
+
+def sfhe_matrix_import(ctx: int, coeff_limbs: np.ndarray, idx, rows: int, cols: int, encoding: int,
+                       stream=None) -> int:
+    c = np.ascontiguousarray(coeff_limbs, dtype=np.uint64)
+    ix = None if idx is None else np.ascontiguousarray(idx, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(lib().sfhe_matrix_import(ctx, _ptr(c), _ptr(ix), rows, cols, encoding, _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def sfhe_matrix_info(M: int) -> dict:
+    v = [ctypes.c_int32() for _ in range(4)]
+    _check(lib().sfhe_matrix_info(M, *[ctypes.byref(x) for x in v]))
+    return dict(zip(("rows", "cols", "encoding", "nct"), (x.value for x in v)))
+
+
+def sfhe_matrix_export(M: int, out: np.ndarray, stream=None) -> np.ndarray:
+    """out: host uint64 [nct][2][L][N], filled in coefficient form."""
+    assert out.dtype == np.uint64 and out.flags["C_CONTIGUOUS"]
+    _check(lib().sfhe_matrix_export(M, _ptr(out), _stream(stream)))
+    return out
+
+
+def sfhe_matrix_decrypt(ctx: int, M: int, stream=None) -> np.ndarray:
+    info = sfhe_matrix_info(M)
+    out = np.zeros((max(info["rows"], 1), max(info["cols"], 1)), dtype=np.int64)
+    _check(lib().sfhe_matrix_decrypt(ctx, M, _ptr(out), _stream(stream)))
+    return out[:info["rows"], :info["cols"]]
+
+
+def sfhe_matrix_destroy(M: int) -> None:
+    lib().sfhe_matrix_destroy(M)
+
+
+def sfhe_matrix_view_of(M: int, stream=None) -> sfhe_matrix_view:
+    v = sfhe_matrix_view()
+    _check(lib().sfhe_matrix_view_of(M, ctypes.byref(v), _stream(stream)))
+    return v
+
+
+def sfhe_matmul_dense(ctx: int, A: int, B: int, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().sfhe_matmul_dense(ctx, A, B, ctypes.byref(h), _stream(stream)))
+    return h.value
+
+
+def sfhe_matmul_sparse(ctx: int, A: int, B: int, encoding: int, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().sfhe_matmul_sparse(ctx, A, B, encoding, ctypes.byref(h), _stream(stream)))
+    return h.value
+
+
+def sfhe_matmul_batch(ctx: int, A: list, B: list, flags: int, stream=None) -> list[int]:
+    n = len(A)
+    Aa = (ctypes.c_void_p * max(n, 1))(*A)
+    Ba = (ctypes.c_void_p * max(n, 1))(*B)
+    Ca = (ctypes.c_void_p * max(n, 1))()
+    _check(lib().sfhe_matmul_batch(ctx, n, Aa, Ba, Ca, flags, _stream(stream)))
+    return [Ca[m] for m in range(n)]
+
+
+# ------------------------------------------------ host-resident operands ---
+def sfhe_host_plan_create(ctx: int, A: list, B: list, flags: int, depth: int = 2) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().sfhe_host_plan_create(ctx, len(A), _mats(A), _mats(B), flags, depth, ctypes.byref(h)))
+    return h.value
+
+
+def sfhe_matmul_host(hp: int, A_ct: list, B_ct: list, C_ct: list, stream=None) -> None:
+    """A_ct, B_ct, C_ct: host buffers (numpy arrays or CPU torch tensors,
+    preferably pinned) of each matmul's ciphertexts in NTT form."""
+    def arr(xs):
+        return (ctypes.c_void_p * max(len(xs), 1))(*[_ptr(x) for x in xs])
+    _check(lib().sfhe_matmul_host(hp, arr(A_ct), arr(B_ct), arr(C_ct), _stream(stream)))
+
+
+def sfhe_host_plan_stats(hp: int) -> dict:
+    p, l = ctypes.c_int64(), ctypes.c_int64()
+    u, d = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().sfhe_host_plan_stats(hp, ctypes.byref(p), ctypes.byref(u), ctypes.byref(d), ctypes.byref(l)))
+    return {"products": p.value, "h2d_bytes": u.value, "d2h_bytes": d.value, "launches": l.value}
+
+
+def sfhe_host_plan_destroy(hp: int) -> None:
+    lib().sfhe_host_plan_destroy(hp)

@@ -28,7 +28,7 @@ def test_small_workspaces_are_refused():
     B = api.encrypt_matrix(ctx, np.array([[1], [2], [3]]), "dense", 2)
     C = api.result_matrix(ctx, 1, 1)
     tiny = torch.empty(256, dtype=torch.uint8, device="cuda")
-    assert _status(S, S.sfhe_matmul_sparse, ctx.h, A.desc(), B.desc(), S.SFHE_ENC_CSR, C.desc(), api.PERSISTENT,
+    assert _status(S, S.sfhe_matmul_sparse_view, ctx.h, A.desc(), B.desc(), S.SFHE_ENC_CSR, C.desc(), api.PERSISTENT,
                    tiny) == S.SFHE_ENOMEM
     ext = torch.empty((1, 2, ctx.K, ctx.N), dtype=torch.int32, device="cuda")
     assert _status(S, S.sfhe_lift, ctx.h, A.ct, 1, ext, tiny) == S.SFHE_ENOMEM

@@ -82,5 +82,5 @@ def test_lazy_needs_persistent():
     C = api.result_matrix(ctx, 1, 1)
     work = api.workspace(ctx, [A], [B], api.PERSISTENT)
     with pytest.raises(S.SfheError) as e:
-        S.sfhe_matmul_sparse(ctx.h, A.desc(), B.desc(), S.SFHE_ENC_CSR, C.desc(), api.PLAIN | api.LAZY, work)
+        S.sfhe_matmul_sparse_view(ctx.h, A.desc(), B.desc(), S.SFHE_ENC_CSR, C.desc(), api.PLAIN | api.LAZY, work)
     assert e.value.status == S.SFHE_EINVAL

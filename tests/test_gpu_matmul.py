@@ -174,5 +174,5 @@ def test_edge_cases(mods):
     C = api.result_matrix(ctx, 1, 1)
     work = api.workspace(ctx, [A], [B2], api.PERSISTENT)
     with pytest.raises(S.SfheError) as e:
-        S.sfhe_matmul_sparse(ctx.h, A.desc(), B2.desc(), S.SFHE_ENC_ELL, C.desc(), api.PERSISTENT, work)
+        S.sfhe_matmul_sparse_view(ctx.h, A.desc(), B2.desc(), S.SFHE_ENC_ELL, C.desc(), api.PERSISTENT, work)
     assert e.value.status == S.SFHE_EINVAL

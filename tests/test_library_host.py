@@ -110,14 +110,14 @@ def test_matrix_bytes_per_encoding(S):
     got = {}
     for enc, e in S.ENCODINGS.items():
         f = S.sfhe_encode_fill(A, e)
-        M = S.sfhe_matrix(6, 10, e, f["nct"], f["ell_width"], None, None, None, None, None, None)
+        M = S.sfhe_matrix_view(6, 10, e, f["nct"], f["ell_width"], None, None, None, None, None, None)
         got[enc] = S.sfhe_matrix_bytes(N, L, M)
         assert f["nct"] == want_nct[enc]
         assert got[enc] == {"ct": want_nct[enc] * 2 * L * N * 8, "ext": want_nct[enc] * 2 * K * N * 4,
                             "meta": want_meta[enc]}, enc
     assert got["csr"]["ct"] < got["ell"]["ct"] < got["dense"]["ct"] == got["mask"]["ct"]
     with pytest.raises(S.SfheError) as e:
-        S.sfhe_matrix_bytes(1000, 4, S.sfhe_matrix(1, 1, 0, 1, 0, None, None, None, None, None, None))
+        S.sfhe_matrix_bytes(1000, 4, S.sfhe_matrix_view(1, 1, 0, 1, 0, None, None, None, None, None, None))
     assert e.value.status == S.SFHE_EUNSUPPORTED
 
 
