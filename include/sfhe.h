@@ -398,9 +398,10 @@ sfhe_status sfhe_host_plan_create(sfhe_ctx* ctx, int32_t n, const sfhe_matrix_vi
                                   uint32_t flags, int32_t depth, sfhe_host_plan** out);
 /* One matmul: A_ct[m] (host, [nct_A][2][L][N] NTT form), B_ct[m] likewise,
  * into C_ct[m] (host, [rows_A * cols_B][2][L][N] NTT form).  Asynchronous:
- * the copies and kernels are ordered after the work already on `stream`,
- * and work enqueued on `stream` after the call waits for C_ct to be written;
- * the host buffers must stay valid and unchanged until then.  Page-locked
+ * the inputs are read from host memory at some time after the call (write
+ * them before calling; the uploads do not wait for work on `stream`), and
+ * work enqueued on `stream` after the call waits for C_ct to be written; the
+ * host buffers must stay valid and unchanged until then.  Page-locked
  * (pinned) host buffers let the copies overlap with computation.  Errors:
  * EINVAL (null), ECUDA. */
 sfhe_status sfhe_matmul_host(sfhe_host_plan* hp, const uint64_t* const* A_ct, const uint64_t* const* B_ct,
@@ -459,6 +460,22 @@ sfhe_status sfhe_matmul_check(void* work, void* stream);
  * SFHE_ETIMEOUT.  The persistent kernel's own bound is one second or 2^26
  * attempts.  Errors: EINVAL (null, bounds out of range), ECUDA. */
 sfhe_status sfhe_selftest_wait_bound(void* work, uint32_t tries, uint32_t limit_us, void* stream);
+/* Tile tuning of the per-product persistent kernel.  Where a ring has
+ * several stage-S tiles (the tiles of the exact scale-and-round: how many
+ * coefficients a thread rounds at a time and how many output primes it
+ * reconstructs per pass; N = 4096 with L = 2, N = 8192 with L = 4 and
+ * N = 16384 with L = 8 have three each), the first per-product persistent
+ * plan of a context times every tile on the plan's first entries (one per
+ * CTA, at most four products each; this writes their C, which every
+ * execution writes again, and synchronises the stream) and the context
+ * keeps the fastest for all its later plans.  sfhe_ctx_tuning: the tile in
+ * use (-1 before the first plan), how many there are, and the calibration
+ * time of each (ms[n_variants], may be NULL; zeros while untuned).
+ * sfhe_ctx_set_variant: use tile `variant` from now on (-1: tune as above).
+ * sfhe_ctx_variant_name: a description of a tile ("" if out of range). */
+sfhe_status sfhe_ctx_tuning(const sfhe_ctx* ctx, int32_t* variant, int32_t* n_variants, float* ms);
+sfhe_status sfhe_ctx_set_variant(sfhe_ctx* ctx, int32_t variant);
+const char* sfhe_ctx_variant_name(const sfhe_ctx* ctx, int32_t variant);
 /* products performed, output entries, own kernel launches per execute, CTAs */
 sfhe_status sfhe_plan_stats(const sfhe_plan* plan, int64_t* products, int64_t* entries, int64_t* launches,
                             int64_t* ctas);

@@ -1,5 +1,6 @@
 // api.cu -- the C ABI (include/sfhe.h): contexts, operands, matmul plans.
 #include <stdarg.h>
+#include <stdlib.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -83,9 +84,18 @@ struct sfhe_ctx {
     u32* d_twb;
     u64* d_s;
     signed char* d_s_coeff;
-    u64* d_rlk;
-    u64* d_rlk_sh;
+    u64* d_rlk;     // the key, followed in the same allocation by
+    u64* d_rlk_sh;  // its Shoup companions
     int* d_err;
+    // persisting-L2 window over the key and companions (bytes 0: none)
+    size_t l2_bytes;
+    float l2_hit;
+    // tile tuning of the per-product persistent kernel
+    std::mutex tune_mu;
+    int n_variants;
+    int forced_variant;  // -1: tuned on the first persistent plan
+    int tuned_variant;   // -1 until tuned
+    float variant_ms[4];
 };
 
 struct sfhe_plan {
@@ -108,6 +118,7 @@ struct sfhe_plan {
     u64 *d_D, *d_U;
     cudaGraph_t graph;
     cudaGraphExec_t gexec;
+    int variant;  // tile variant of the persistent kernel
 };
 
 extern "C" const char* sfhe_last_error(void) { return g_last_error.c_str(); }
@@ -151,6 +162,38 @@ extern "C" sfhe_status sfhe_cdt_table(double sigma, uint64_t* T20)
 }
 
 // ---------------------------------------------------------------- context ---
+// Stage R reads the whole key once per output entry.  A persisting
+// access-policy window over the key and its companions keeps them in L2
+// between entries while the per-product scratch streams through: the
+// context raises its persisting-L2 limit (a limit of this process's
+// context, released with it) to the key's size or the device's maximum,
+// and every persistent launch carries the window.  SFHE_L2_PERSIST=0 in the
+// environment leaves both alone.
+static void setup_l2_window(sfhe_ctx* c, size_t key_bytes)
+{
+    c->l2_bytes = 0;
+    c->l2_hit = 0.f;
+    const char* env = getenv("SFHE_L2_PERSIST");
+    if (env && env[0] == '0') return;
+    int max_persist = 0, max_window = 0;
+    if (cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, c->device) != cudaSuccess ||
+        max_persist <= 0 || max_window <= 0) {
+        cudaGetLastError();
+        return;
+    }
+    size_t cur = 0;
+    cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+    const size_t want = std::min(key_bytes, (size_t)max_persist);
+    if (cur < want && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+    c->l2_bytes = std::min(key_bytes, (size_t)max_window);
+    c->l2_hit = (float)std::min(1.0, (double)cur / (double)c->l2_bytes);
+}
+
 extern "C" void sfhe_ctx_destroy(sfhe_ctx* c)
 {
     if (!c) return;
@@ -159,8 +202,7 @@ extern "C" void sfhe_ctx_destroy(sfhe_ctx* c)
     cudaFree(c->d_twb);
     cudaFree(c->d_s);
     cudaFree(c->d_s_coeff);
-    cudaFree(c->d_rlk);
-    cudaFree(c->d_rlk_sh);
+    cudaFree(c->d_rlk);  // the companions share the allocation
     cudaFree(c->d_err);
     delete c;
 }
@@ -213,9 +255,10 @@ extern "C" sfhe_status sfhe_ctx_create(const sfhe_params* params, uint64_t seed,
     const size_t rlk_words = (size_t)L * 2 * L * N;
     if (cudaMalloc(&c->d_tw, tw.size() * 8) != cudaSuccess || cudaMalloc(&c->d_twb, twb.size() * 4) != cudaSuccess ||
         cudaMalloc(&c->d_s, (size_t)L * N * 8) != cudaSuccess ||
-        cudaMalloc(&c->d_s_coeff, N) != cudaSuccess || cudaMalloc(&c->d_rlk, rlk_words * 8) != cudaSuccess ||
-        cudaMalloc(&c->d_rlk_sh, rlk_words * 8) != cudaSuccess || cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess)
+        cudaMalloc(&c->d_s_coeff, N) != cudaSuccess || cudaMalloc(&c->d_rlk, 2 * rlk_words * 8) != cudaSuccess ||
+        cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess)
         return bail(fail(SFHE_ENOMEM, "device allocation of the context failed"));
+    c->d_rlk_sh = c->d_rlk + rlk_words;
     rc.tw = c->d_tw;
     rc.twb = c->d_twb;
     if (cudaMemcpy(c->d_tw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -228,6 +271,10 @@ extern "C" sfhe_status sfhe_ctx_create(const sfhe_params* params, uint64_t seed,
     int err = 0;
     cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost);
     if (err) return bail(fail(SFHE_EDEVICE, "key generation sampler failed"));
+    setup_l2_window(c, 2 * rlk_words * 8);
+    c->n_variants = persistent_variants(c->rc);
+    c->forced_variant = -1;
+    c->tuned_variant = -1;
     *out = c;
     return SFHE_OK;
 }
@@ -677,6 +724,78 @@ sfhe_status check_flags(uint32_t flags)
     return SFHE_OK;
 }
 
+PersistentArgs persistent_args(const sfhe_plan* P, int n_entries, int variant)
+{
+    const sfhe_ctx* c = P->ctx;
+    PersistentArgs a;
+    a.mms = P->d_mms;
+    a.entries = P->d_entries;
+    a.n_entries = n_entries;
+    a.rowlist = P->d_rowlist;
+    a.rlk = c->d_rlk;
+    a.rlk_sh = c->d_rlk_sh;
+    a.scratch = P->d_scratch;
+    a.scratch_stride = P->scratch_stride;
+    a.queue = P->d_queue;
+    a.grid = P->grid;
+    a.grouped = (P->flags & SFHE_EXEC_LAZY) != 0;
+    a.variant = a.grouped ? 0 : variant;
+    a.l2_base = c->d_rlk;
+    a.l2_bytes = c->l2_bytes;
+    a.l2_hit_ratio = c->l2_hit;
+    return a;
+}
+
+// The tile tuner.  On the first per-product persistent plan of a context at
+// a ring with several stage-S tiles, every tile runs on a calibration list
+// built from the plan's own work: its first `grid` entries (the longest,
+// one per CTA) cut to at most 4 products each, uploaded over the plan's
+// entry list and replaced by the real list afterwards.  Each tile runs once
+// to warm up and twice timed (CUDA events on the plan's stream); the fastest
+// is kept for the context.  The calibration writes C of those entries, which
+// every execution of the plan writes again.  Synchronises the stream.
+sfhe_status tune_variants(sfhe_plan* P, cudaStream_t s)
+{
+    sfhe_ctx* c = P->ctx;
+    const int nv = c->n_variants;
+    std::vector<Entry> cal(P->entries.begin(), P->entries.begin() + std::min<size_t>(P->entries.size(), P->grid));
+    for (Entry& e : cal) e.count = std::min(e.count, 4);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    cudaError_t e = cudaMemcpyAsync(P->d_entries, cal.data(), cal.size() * sizeof(Entry), cudaMemcpyHostToDevice, s);
+    float best = 0.f;
+    int best_v = 0;
+    for (int v = 0; v < nv && e == cudaSuccess; v++) {
+        float t = 0.f;
+        for (int rep = 0; rep < 3 && e == cudaSuccess; rep++) {
+            e = cudaMemsetAsync(P->d_queue, 0, 2 * sizeof(unsigned), s);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+            if (e == cudaSuccess) e = launch_persistent(c->rc, persistent_args(P, (int)cal.size(), v), s);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (rep == 1 || (rep == 2 && ms < t)) t = ms;
+        }
+        if (v < 4) c->variant_ms[v] = t;
+        if (v == 0 || t < best) best = t, best_v = v;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(P->d_entries, P->entries.data(), cal.size() * sizeof(Entry), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return fail(SFHE_ECUDA, "tile tuning: %s", cudaGetErrorString(e));
+    // a bounded wait that ran out during calibration is reported like one
+    // during an execution
+    unsigned err = 0;
+    CUDA_TRY(cudaMemcpy(&err, P->d_queue + 1, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (err) return fail(SFHE_ETIMEOUT, "an operand copy did not complete within its wait bound (tile tuning)");
+    c->tuned_variant = best_v;
+    return SFHE_OK;
+}
+
 sfhe_status launch_plan(sfhe_plan* P, cudaStream_t s)
 {
     const sfhe_ctx* c = P->ctx;
@@ -688,9 +807,7 @@ sfhe_status launch_plan(sfhe_plan* P, cudaStream_t s)
         }
         CUDA_TRY(cudaMemsetAsync(P->d_queue, 0, 2 * sizeof(unsigned), s));
         if (P->entries.empty()) return SFHE_OK;
-        CUDA_TRY(launch_persistent(rc, P->d_mms, P->d_entries, (int)P->entries.size(), P->d_rowlist, c->d_rlk, c->d_rlk_sh,
-                                   P->d_scratch, P->scratch_stride, P->d_queue, P->grid,
-                                   (P->flags & SFHE_EXEC_LAZY) != 0, s));
+        CUDA_TRY(launch_persistent(rc, persistent_args(P, (int)P->entries.size(), P->variant), s));
         return SFHE_OK;
     }
     // plain: C = 0, then one launch sequence per product
@@ -774,6 +891,23 @@ static sfhe_status plan_create_impl(sfhe_ctx* c, int32_t n, const sfhe_matrix_vi
         delete P;
         return fail(SFHE_ECUDA, "work list upload: %s", cudaGetErrorString(e));
     }
+    // tile variant: forced, tuned earlier, or tuned now on this plan
+    P->variant = 0;
+    if ((flags & SFHE_EXEC_PERSISTENT) && !(flags & SFHE_EXEC_LAZY) && c->n_variants > 1) {
+        std::lock_guard<std::mutex> lock(c->tune_mu);
+        if (c->forced_variant >= 0) {
+            P->variant = c->forced_variant;
+        } else {
+            if (c->tuned_variant < 0 && !P->entries.empty()) {
+                sfhe_status ts = tune_variants(P, s);
+                if (ts != SFHE_OK) {
+                    delete P;
+                    return ts;
+                }
+            }
+            P->variant = std::max(c->tuned_variant, 0);
+        }
+    }
     if (flags & SFHE_EXEC_GRAPH) {
         cudaStream_t cap;
         e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
@@ -782,9 +916,8 @@ static sfhe_status plan_create_impl(sfhe_ctx* c, int32_t n, const sfhe_matrix_vi
             sfhe_status ls = SFHE_OK;
             if (cudaMemsetAsync(P->d_queue, 0, 2 * sizeof(unsigned), cap) != cudaSuccess) ls = SFHE_ECUDA;
             if (ls == SFHE_OK && !P->entries.empty())
-                if (launch_persistent(c->rc, P->d_mms, P->d_entries, (int)P->entries.size(), P->d_rowlist, c->d_rlk,
-                                      c->d_rlk_sh, P->d_scratch, P->scratch_stride, P->d_queue, P->grid,
-                                      (P->flags & SFHE_EXEC_LAZY) != 0, cap) != cudaSuccess)
+                if (launch_persistent(c->rc, persistent_args(P, (int)P->entries.size(), P->variant), cap) !=
+                    cudaSuccess)
                     ls = SFHE_ECUDA;
             cudaError_t e2 = cudaStreamEndCapture(cap, &P->graph);
             if (ls != SFHE_OK || e2 != cudaSuccess) e = cudaErrorUnknown;
@@ -852,6 +985,33 @@ extern "C" sfhe_status sfhe_plan_stats(const sfhe_plan* P, int64_t* products, in
     if (launches) *launches = (P->flags & SFHE_EXEC_PERSISTENT) ? (P->entries.empty() ? 0 : 1) : 4 * P->products;
     if (ctas) *ctas = P->grid;
     return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_ctx_tuning(const sfhe_ctx* c, int32_t* variant, int32_t* n_variants, float* ms)
+{
+    if (!c) return fail(SFHE_EINVAL, "null context");
+    sfhe_ctx* m = const_cast<sfhe_ctx*>(c);
+    std::lock_guard<std::mutex> lock(m->tune_mu);
+    if (variant) *variant = c->forced_variant >= 0 ? c->forced_variant : c->tuned_variant;
+    if (n_variants) *n_variants = c->n_variants;
+    if (ms)
+        for (int v = 0; v < c->n_variants && v < 4; v++) ms[v] = c->tuned_variant >= 0 ? c->variant_ms[v] : 0.f;
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_ctx_set_variant(sfhe_ctx* c, int32_t variant)
+{
+    if (!c) return fail(SFHE_EINVAL, "null context");
+    if (variant < -1 || variant >= c->n_variants)
+        return fail(SFHE_EINVAL, "variant %d outside -1 .. %d", variant, c->n_variants - 1);
+    std::lock_guard<std::mutex> lock(c->tune_mu);
+    c->forced_variant = variant;
+    return SFHE_OK;
+}
+
+extern "C" const char* sfhe_ctx_variant_name(const sfhe_ctx* c, int32_t variant)
+{
+    return c ? persistent_variant_name(c->rc, variant) : "";
 }
 
 static sfhe_status size_impl(const sfhe_ctx* c, int32_t n, const sfhe_matrix_view* A, const sfhe_matrix_view* B,

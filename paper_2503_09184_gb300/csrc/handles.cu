@@ -473,7 +473,6 @@ struct sfhe_host_plan {
     };
     std::vector<Set> sets;
     cudaStream_t s_up = nullptr, s_comp = nullptr, s_down = nullptr;
-    cudaEvent_t ev_caller = nullptr;
     int64_t calls = 0, products = 0, launches = 0;
     uint64_t h2d = 0, d2h = 0;
 };
@@ -491,7 +490,6 @@ extern "C" void sfhe_host_plan_destroy(sfhe_host_plan* hp)
     }
     for (cudaStream_t s : {hp->s_up, hp->s_comp, hp->s_down})
         if (s) cudaStreamDestroy(s);
-    if (hp->ev_caller) cudaEventDestroy(hp->ev_caller);
     delete hp;
 }
 
@@ -560,8 +558,7 @@ extern "C" sfhe_status sfhe_host_plan_create(sfhe_ctx* c, int32_t n, const sfhe_
     }
     if (cudaStreamCreateWithFlags(&hp->s_up, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&hp->s_comp, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&hp->s_down, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&hp->ev_caller, cudaEventDisableTiming) != cudaSuccess)
+        cudaStreamCreateWithFlags(&hp->s_down, cudaStreamNonBlocking) != cudaSuccess)
         return bail(set_error(SFHE_ECUDA, "stream or event creation failed"));
     hp->sets.resize(depth);
     for (auto& S : hp->sets) {
@@ -632,10 +629,10 @@ extern "C" sfhe_status sfhe_matmul_host(sfhe_host_plan* hp, const uint64_t* cons
     cudaStream_t s = as_stream(stream);
     auto& S = hp->sets[hp->calls % hp->depth];
     const bool reuse = hp->calls >= hp->depth;
-    // uploads: after the caller's earlier work, and once the set's previous
-    // inputs have been consumed (its lift ran before its matmul finished)
-    CUDA_OR_FAIL(cudaEventRecord(hp->ev_caller, s));
-    CUDA_OR_FAIL(cudaStreamWaitEvent(hp->s_up, hp->ev_caller, 0));
+    // uploads: once the set's previous inputs have been consumed (its lift
+    // ran before its matmul finished).  They do not wait for `stream`: that
+    // stream waits for the previous call's download, and waiting on it
+    // would serialise every upload behind the previous call's whole matmul.
     if (reuse) CUDA_OR_FAIL(cudaStreamWaitEvent(hp->s_up, S.comp_done, 0));
     for (int32_t m = 0; m < hp->n; m++) {
         if (hp->a_bytes[m])

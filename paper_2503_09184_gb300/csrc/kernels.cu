@@ -1,5 +1,6 @@
 // kernels.cu -- template instantiations and launchers of the device code.
 #define SFHE_KERNELS_TU
+#include <stdio.h>
 #include "launch.h"
 #include "launch_util.cuh"
 
@@ -249,16 +250,46 @@ int persistent_ctas_per_sm(const RnsConsts& rc)
     }
 }
 
-cudaError_t launch_persistent(const RnsConsts& rc, const MmDesc* mms, const Entry* entries, int n_entries,
-                              const int2* rowlist, const u64* rlk, const u64* rlk_sh, u64* scratch,
-                              size_t scratch_stride, unsigned* queue, int grid, bool grouped, cudaStream_t s)
+cudaError_t launch_persistent(const RnsConsts& rc, const PersistentArgs& a, cudaStream_t s)
 {
     switch (rc.logN) {
-    case 12: return persistent_launch<12>(rc, mms, entries, n_entries, rowlist, rlk, rlk_sh, scratch, scratch_stride, queue, grid, grouped, s);
-    case 13: return persistent_launch<13>(rc, mms, entries, n_entries, rowlist, rlk, rlk_sh, scratch, scratch_stride, queue, grid, grouped, s);
-    case 14: return persistent_launch<14>(rc, mms, entries, n_entries, rowlist, rlk, rlk_sh, scratch, scratch_stride, queue, grid, grouped, s);
+    case 12: return persistent_launch<12>(rc, a, s);
+    case 13: return persistent_launch<13>(rc, a, s);
+    case 14: return persistent_launch<14>(rc, a, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+int persistent_variants(const RnsConsts& rc)
+{
+    const bool v = (rc.logN == 12 && rc.L == 2) || (rc.logN == 13 && rc.L == 4) || (rc.logN == 14 && rc.L == 8);
+    return v ? 3 : 1;
+}
+
+// the tiles of PersistentTile, as the host names them
+static_assert(PersistentTile<13, 4, 0>::SM == 2 && PersistentTile<13, 4, 0>::LS == 4, "tile table");
+static_assert(PersistentTile<13, 4, 1>::SM == 2 && PersistentTile<13, 4, 1>::LS == 2, "tile table");
+static_assert(PersistentTile<13, 4, 2>::SM == 1 && PersistentTile<13, 4, 2>::LS == 4, "tile table");
+static_assert(PersistentTile<14, 8, 0>::SM == 1 && PersistentTile<14, 8, 0>::LS == 8, "tile table");
+static_assert(PersistentTile<14, 8, 1>::SM == 1 && PersistentTile<14, 8, 1>::LS == 4, "tile table");
+static_assert(PersistentTile<14, 8, 2>::SM == 1 && PersistentTile<14, 8, 2>::LS == 2, "tile table");
+static_assert(PersistentTile<12, 2, 0>::SM == 2 && PersistentTile<12, 2, 0>::LS == 2, "tile table");
+static_assert(PersistentTile<12, 2, 1>::SM == 2 && PersistentTile<12, 2, 1>::LS == 1, "tile table");
+static_assert(PersistentTile<12, 2, 2>::SM == 1 && PersistentTile<12, 2, 2>::LS == 2, "tile table");
+
+const char* persistent_variant_name(const RnsConsts& rc, int v)
+{
+    static const char* names[][3] = {
+        {"2 coefficients per thread, 4 primes per pass", "2 coefficients per thread, 2 primes per pass",
+         "1 coefficient per thread, 4 primes per pass"},
+        {"1 coefficient per thread, 8 primes per pass", "1 coefficient per thread, 4 primes per pass",
+         "1 coefficient per thread, 2 primes per pass"},
+        {"2 coefficients per thread, 2 primes per pass", "2 coefficients per thread, 1 prime per pass",
+         "1 coefficient per thread, 2 primes per pass"},
+    };
+    if (v < 0 || v >= persistent_variants(rc)) return "";
+    if (persistent_variants(rc) == 1) return "default stage-S tile";
+    return names[rc.logN == 13 ? 0 : (rc.logN == 14 ? 1 : 2)][v];
 }
 
 cudaError_t launch_prng(u64 seed, u64 dom, u64 o0, u64 o1, u64 o2, u64 idx0, long long n, u64* out, cudaStream_t s)

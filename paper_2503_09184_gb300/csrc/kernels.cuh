@@ -136,17 +136,17 @@ __device__ __noinline__ u64 scale_round_fallback(const u32* xt32, size_t stride,
 // independent; they are interleaved for instruction-level parallelism.
 // LAZY: d[m][i] in [0, 3 q_i) (congruent, one Barrett step without the final
 // subtractions) instead of canonical.
-template <int L, int K, int M, bool LAZY = false>
-SFHE_DEV void scale_round_m(const u32* const (&x32)[M], size_t stride, const RnsConsts& c, u64 (&d)[M][L])
+// The first half of the rounding: the x~_k of M coefficients into registers,
+// v and round(F) + K of each.
+template <int K, int M>
+SFHE_DEV void scale_round_est(const u32* const (&x32)[M], size_t stride, const RnsConsts& c, u32 (&xt)[M][K],
+                              u32 (&v)[M], u64 (&mK)[M])
 {
-    u32 xt[M][K];
 #pragma unroll
     for (int k = 0; k < K; k++) {
 #pragma unroll
         for (int m = 0; m < M; m++) xt[m][k] = x32[m][(size_t)k * stride];
     }
-    u32 v[M];
-    u64 mK[M];
 #pragma unroll
     for (int m = 0; m < M; m++) {
         v[m] = round_b<K>(xt[m], c);
@@ -168,8 +168,16 @@ SFHE_DEV void scale_round_m(const u32* const (&x32)[M], size_t stride, const Rns
         mK[m] = ghi;  // round(F) + K, unless glo sits in the uncertainty band
         if (glo < (u64)K || glo >= 0ULL - ((u64)K << 37)) mK[m] = scale_round_fallback<K>(x32[m], stride, v[m], mK[m], c);
     }
+}
+
+// The second half: round(t x / Q) mod q_i for the primes i = I0 .. I0+NI-1.
+template <int K, int M, int NI, bool LAZY>
+SFHE_DEV void scale_round_out(const u32 (&xt)[M][K], const u32 (&v)[M], const u64 (&mK)[M], const RnsConsts& c,
+                              int I0, u64 (&d)[M][NI])
+{
 #pragma unroll
-    for (int i = 0; i < L; i++) {
+    for (int ii = 0; ii < NI; ii++) {
+        const int i = I0 + ii;
 #pragma unroll
         for (int m = 0; m < M; m++) {
             // sum_k x~_k alpha_k - v alpha_B + round(F) = shi 2^27 + slo (mod q_i)
@@ -181,9 +189,39 @@ SFHE_DEV void scale_round_m(const u32* const (&x32)[M], size_t stride, const Rns
             }
             u64 hi = shi >> 37, lo = shi << 27;
             add128(hi, lo, slo);
-            d[m][i] = LAZY ? barrett_lazy(hi, lo, c.m[i]) : barrett(hi, lo, c.m[i]);
+            d[m][ii] = LAZY ? barrett_lazy(hi, lo, c.m[i]) : barrett(hi, lo, c.m[i]);
         }
     }
+}
+
+// Exact round(t x / Q) mod q_i for M tensor coefficients x, each given by
+// x~_k = [x_k (B/b_k)^-1]_{b_k} at xt32[m][k * stride] (canonical, k < K; the
+// tensor stage's inverse NTT produces them):
+//   x = sum_k x~_k (B/b_k) - v B,
+//   v = round(sum_k x~_k / b_k)  (sum_k x~_k / b_k = v + x / B, |x| / B < 1/4);
+//   with t (B/b_k) = alpha_k Q + r_k and t B = alpha_B Q + r_B,
+//   t x / Q = sum_k x~_k alpha_k - v alpha_B + F,  F = (sum_k x~_k r_k - v r_B) / Q,
+// so round(t x / Q) = sum_k x~_k alpha_k - v alpha_B + round(F).  F + K > 0
+// is estimated as G / 2^64 with G = sum_k x~_k rho_k - v rho_B + K 2^64,
+// rho = floor(r 2^64 / Q); with the exact rho_k the true value lies in
+// (G - K, G + K 2^30) / 2^64,
+// so round(F) + K = floor((G + 2^63) / 2^64) unless that interval crosses
+// the rounding point, where the decision is taken exactly (Q is odd: no ties).
+// Every product is one 32x32-bit multiply into a 64-bit sum without carries:
+// G takes rho_k without its low 6 bits, in two 29-bit parts (products below
+// 2^59), which widens the band to (G - K, G + K 2^37); the 54-bit
+// [alpha_k]_{q_i} is split at bit 27 (below 2^62).  The M coefficients are
+// independent; they are interleaved for instruction-level parallelism.
+// LAZY: d[m][i] in [0, 3 q_i) (congruent, one Barrett step without the final
+// subtractions) instead of canonical.
+template <int L, int K, int M, bool LAZY = false>
+SFHE_DEV void scale_round_m(const u32* const (&x32)[M], size_t stride, const RnsConsts& c, u64 (&d)[M][L])
+{
+    u32 xt[M][K];
+    u32 v[M];
+    u64 mK[M];
+    scale_round_est<K, M>(x32, stride, c, xt, v, mK);
+    scale_round_out<K, M, L, LAZY>(xt, v, mK, c, 0, d);
 }
 
 template <int L, int K>
@@ -601,6 +639,22 @@ struct PersistentPlan {
     static_assert(SMEM <= 227 * 1024 - 256, "shared-memory plan too large");
 };
 
+// Tile of stage S (the exact scale-and-round inside the persistent kernel),
+// one per variant V that the run-time tuner can pick: SM coefficients per
+// thread at a time (interleaved for instruction-level parallelism) and the
+// output primes in chunks of LS (fewer live registers per chunk).  V = 0 is
+// the default; variants 1 and 2 exist for the rings persistent_variants()
+// lists.
+template <int LOGN, int L, int V>
+struct PersistentTile {
+    static constexpr int K = tensor_base_size(LOGN, L);
+    static constexpr int R = NttGeom<LOGN>::T32::R;
+    static constexpr int SMD = (K <= 16 && R <= 16) ? 2 : 1;
+    static constexpr int SM = (V == 2 && SMD == 2) ? 1 : SMD;
+    static constexpr int LS = V == 1 ? (L >= 2 ? L / 2 : L) : ((V == 2 && SMD == 1) ? (L >= 4 ? L / 4 : L) : L);
+    static_assert(L % LS == 0, "output primes in whole chunks");
+};
+
 // bounds of every mbarrier wait: one second of real time (a 64 KB bulk copy
 // lands within microseconds), and at most 2^26 attempts
 #define SFHE_WAIT_TRIES (1u << 26)
@@ -622,7 +676,7 @@ struct PersistentPlan {
 // uint32 (x~_k, the inverse NTT's output).  queue[0] is the entry counter, queue[1] the error word (1: a
 // bulk copy did not complete within the wait bound).  mbarriers 0 and 1
 // track the operand pairs of stage T.
-template <int LOGN, int L, bool GROUPED>
+template <int LOGN, int L, bool GROUPED, int V>
 __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
     const __grid_constant__ RnsConsts c, const MmDesc* __restrict__ mms, const Entry* __restrict__ entries, int n_entries,
     const int2* __restrict__ rowlist, const u64* __restrict__ rlk, const u64* __restrict__ rlk_sh, u64* scratch,
@@ -700,30 +754,44 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
         // d1 only need to be congruent (stage R reduces their sums), so they
         // stay in [0, 3 q_i); the digits of d2 must be canonical.
         auto stage_s = [&](int pr) {
-            constexpr int SM = (K <= 16 && R <= 16) ? 2 : 1;
+            using TL = PersistentTile<LOGN, L, V>;
+            constexpr int SM = TL::SM, LS = TL::LS;
             const bool fold = pr != 0 && (pr & 255) == 0;  // sums below 2^64: fold every 256 products
             auto poly = [&](int p, int k, auto lazy) {
                 constexpr bool LZ = decltype(lazy)::value;
                 const u32* src[SM];
 #pragma unroll
                 for (int m = 0; m < SM; m++) src[m] = T + (size_t)p * K * N + k + m * NTH;
-                // the sums so far, loaded ahead of the arithmetic so that their
+                // the sums so far of one chunk of output primes; the first
+                // chunk's are loaded ahead of the arithmetic so that their
                 // latency overlaps it
-                u64 prev[SM][L];
+                u64 prev[SM][LS];
+                auto load_prev = [&](int i0) {
 #pragma unroll
-                for (int m = 0; m < SM; m++) {
+                    for (int m = 0; m < SM; m++) {
 #pragma unroll
-                    for (int i = 0; i < L; i++)
-                        prev[m][i] = pr == 0 ? 0 : acc[((size_t)p * L + i) * N + k + m * NTH];
-                }
-                u64 d[SM][L];
-                scale_round_m<L, K, SM, LZ>(src, N, c, d);
+                        for (int ii = 0; ii < LS; ii++)
+                            prev[m][ii] = pr == 0 ? 0 : acc[((size_t)p * L + i0 + ii) * N + k + m * NTH];
+                    }
+                };
+                load_prev(0);
+                u32 xt[SM][K];
+                u32 v[SM];
+                u64 mK[SM];
+                scale_round_est<K, SM>(src, N, c, xt, v, mK);
 #pragma unroll
-                for (int m = 0; m < SM; m++) {
+                for (int i0 = 0; i0 < L; i0 += LS) {
+                    if (i0 > 0) load_prev(i0);
+                    u64 d[SM][LS];
+                    scale_round_out<K, SM, LS, LZ>(xt, v, mK, c, i0, d);
 #pragma unroll
-                    for (int i = 0; i < L; i++) {
-                        const u64 base = LZ && fold ? barrett64(prev[m][i], c.m[i]) : prev[m][i];
-                        acc[((size_t)p * L + i) * N + k + m * NTH] = base + d[m][i];
+                    for (int m = 0; m < SM; m++) {
+#pragma unroll
+                        for (int ii = 0; ii < LS; ii++) {
+                            const int i = i0 + ii;
+                            const u64 base = LZ && fold ? barrett64(prev[m][ii], c.m[i]) : prev[m][ii];
+                            acc[((size_t)p * L + i) * N + k + m * NTH] = base + d[m][ii];
+                        }
                     }
                 }
             };

@@ -37,19 +37,43 @@ cudaError_t launch_scale_round(const RnsConsts& rc, const u32* T, u64* D, cudaSt
 cudaError_t launch_relin_ntt(const RnsConsts& rc, const u64* D, u64* U, cudaStream_t s);
 cudaError_t launch_relin_accum(const RnsConsts& rc, const u64* U, const u64* rlk, const u64* rlk_sh, u64* C,
                                cudaStream_t s);
-// fused persistent path (persistent_<logN>.cu)
+// fused persistent path (persistent_<logN>.cu).  One launch: the work list,
+// the key, the per-CTA scratch, the grid, the mode, the tile variant and a
+// persisting-L2 access-policy window (over the relinearisation key and its
+// companions; l2_bytes = 0: none).
+struct PersistentArgs {
+    const MmDesc* mms;
+    const Entry* entries;
+    int n_entries;
+    const int2* rowlist;
+    const u64* rlk;
+    const u64* rlk_sh;
+    u64* scratch;
+    size_t scratch_stride;
+    unsigned* queue;
+    int grid;
+    bool grouped;
+    int variant;
+    const void* l2_base;
+    size_t l2_bytes;
+    float l2_hit_ratio;
+};
 template <int LOGN>
 int persistent_occupancy(int L);
 template <int LOGN>
-cudaError_t persistent_launch(const RnsConsts& rc, const MmDesc* mms, const Entry* entries, int n_entries,
-                              const int2* rowlist, const u64* rlk, const u64* rlk_sh, u64* scratch,
-                              size_t scratch_stride, unsigned* queue, int grid, bool grouped, cudaStream_t s);
+cudaError_t persistent_launch(const RnsConsts& rc, const PersistentArgs& a, cudaStream_t s);
+// the tuned stage-S variants 1 and 2 of the rings that have them
+// (persistent_tuned_<logN>.cu)
+template <int LOGN, int L, int V>
+cudaError_t persistent_launch_variant(const RnsConsts& rc, const PersistentArgs& a, cudaStream_t s);
 // words of the per-CTA scratch of the persistent kernel (uint64 units)
 size_t persistent_scratch_words(const RnsConsts& rc);
 int persistent_ctas_per_sm(const RnsConsts& rc);
-cudaError_t launch_persistent(const RnsConsts& rc, const MmDesc* mms, const Entry* entries, int n_entries,
-                              const int2* rowlist, const u64* rlk, const u64* rlk_sh, u64* scratch,
-                              size_t scratch_stride, unsigned* queue, int grid, bool grouped, cudaStream_t s);
+// tile variants of the per-product persistent kernel at this ring (1: the
+// default only; 3 where the tuner has candidates) and a name for each
+int persistent_variants(const RnsConsts& rc);
+const char* persistent_variant_name(const RnsConsts& rc, int v);
+cudaError_t launch_persistent(const RnsConsts& rc, const PersistentArgs& a, cudaStream_t s);
 // slot-packed ciphertexts (slots.cu)
 cudaError_t launch_galois_keygen(const RnsConsts& rc, const u64* s_ntt, u32 g, u64* key, u64* key_sh, int* err,
                                  cudaStream_t s);

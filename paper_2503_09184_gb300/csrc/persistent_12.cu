@@ -3,6 +3,5 @@
 
 namespace sfhe {
 template int persistent_occupancy<12>(int);
-template cudaError_t persistent_launch<12>(const RnsConsts&, const MmDesc*, const Entry*, int, const int2*, const u64*,
-                                           const u64*, u64*, size_t, unsigned*, int, bool, cudaStream_t);
+template cudaError_t persistent_launch<12>(const RnsConsts&, const PersistentArgs&, cudaStream_t);
 }  // namespace sfhe

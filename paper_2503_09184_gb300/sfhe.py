@@ -101,6 +101,9 @@ _SIGS = {
                                   ctypes.c_int),
     "sfhe_measure_mulmod32": ([_vp, _P(ctypes.c_double), _vp], ctypes.c_int),
     "sfhe_plan_stats": ([_vp, _P(_i64), _P(_i64), _P(_i64), _P(_i64)], ctypes.c_int),
+    "sfhe_ctx_tuning": ([_vp, _P(_i32), _P(_i32), _vp], ctypes.c_int),
+    "sfhe_ctx_set_variant": ([_vp, _i32], ctypes.c_int),
+    "sfhe_ctx_variant_name": ([_vp, _i32], ctypes.c_char_p),
     "sfhe_matmul_check": ([_vp, _vp], ctypes.c_int),
     "sfhe_selftest_wait_bound": ([_vp, _u32, _u32, _vp], ctypes.c_int),
     "sfhe_plan_destroy": ([_vp], None),
@@ -437,6 +440,25 @@ def sfhe_plan_stats(plan: int) -> dict:
     v = [ctypes.c_int64() for _ in range(4)]
     _check(lib().sfhe_plan_stats(plan, *[ctypes.byref(x) for x in v]))
     return dict(zip(("products", "entries", "launches", "ctas"), (x.value for x in v)))
+
+
+def sfhe_ctx_tuning(ctx: int) -> dict:
+    """{"variant", "variants", "ms", "names"}: the stage-S tile in use (-1
+    before the first persistent plan), how many exist, their calibration
+    times and descriptions."""
+    v, n = ctypes.c_int32(), ctypes.c_int32()
+    ms = np.zeros(4, dtype=np.float32)
+    _check(lib().sfhe_ctx_tuning(ctx, ctypes.byref(v), ctypes.byref(n), _ptr(ms)))
+    names = [lib().sfhe_ctx_variant_name(ctx, i).decode() for i in range(n.value)]
+    return {"variant": v.value, "variants": n.value, "ms": [float(x) for x in ms[:n.value]], "names": names}
+
+
+def sfhe_ctx_set_variant(ctx: int, variant: int) -> None:
+    _check(lib().sfhe_ctx_set_variant(ctx, variant))
+
+
+def sfhe_ctx_variant_name(ctx: int, variant: int) -> str:
+    return lib().sfhe_ctx_variant_name(ctx, variant).decode()
 
 
 def sfhe_matmul_check(work, stream=None) -> None:
