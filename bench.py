@@ -531,6 +531,8 @@ def main():
                   % ctx.lazy_group) if args.lazy else "per product (Alg. 1)",
         "clocks": clk,
         "persistent_ctas": ctas,
+        "tile_tuning": S.sfhe_ctx_tuning(ctx.h),
+        "l2_key_window": {"bytes": ctx.l2_window, "hit_ratio": ctx.l2_hit_ratio},
         "operand_memory": operand_memory(S, ring, vals),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

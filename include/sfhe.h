@@ -101,6 +101,8 @@ typedef struct {
     int32_t num_sms;
     uint32_t ext_interleave; /* R of the lifted layout (16, or 32 at N = 16384) */
     int32_t lazy_group;      /* G of SFHE_EXEC_LAZY: floor(B / (2 N Q^2)), at most 1024 */
+    uint64_t l2_window;      /* bytes of the persisting-L2 window over the relinearisation key (0: none) */
+    float l2_hit_ratio;      /* its hit ratio (the persisting limit over the window) */
 } sfhe_info;
 
 typedef struct sfhe_ctx sfhe_ctx;

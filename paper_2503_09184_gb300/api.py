@@ -41,6 +41,7 @@ class Context:
         self.ct_words, self.ext_words, self.num_sms = int(info.ct_words), int(info.ext_words), info.num_sms
         self.ext_interleave = int(info.ext_interleave)
         self.lazy_group = int(info.lazy_group)
+        self.l2_window, self.l2_hit_ratio = int(info.l2_window), float(info.l2_hit_ratio)
         self.seed = seed
 
     def close(self):

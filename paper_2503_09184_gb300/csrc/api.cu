@@ -294,6 +294,8 @@ extern "C" sfhe_status sfhe_ctx_info(const sfhe_ctx* c, sfhe_info* out)
     out->num_sms = c->num_sms;
     out->ext_interleave = (uint32_t)ext_interleave(c->rc.logN);
     out->lazy_group = c->rc.lazy_group;
+    out->l2_window = c->l2_bytes;
+    out->l2_hit_ratio = c->l2_hit;
     return SFHE_OK;
 }
 

@@ -756,15 +756,17 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
         auto stage_s = [&](int pr) {
             using TL = PersistentTile<LOGN, L, V>;
             constexpr int SM = TL::SM, LS = TL::LS;
+            constexpr bool HOIST = K <= 16;
             const bool fold = pr != 0 && (pr & 255) == 0;  // sums below 2^64: fold every 256 products
             auto poly = [&](int p, int k, auto lazy) {
                 constexpr bool LZ = decltype(lazy)::value;
                 const u32* src[SM];
 #pragma unroll
                 for (int m = 0; m < SM; m++) src[m] = T + (size_t)p * K * N + k + m * NTH;
-                // the sums so far of one chunk of output primes; the first
-                // chunk's are loaded ahead of the arithmetic so that their
-                // latency overlaps it
+                // the sums so far of one chunk of output primes; with K <= 16
+                // the first chunk's are loaded ahead of the arithmetic so that
+                // their latency overlaps it (with more primes the registers
+                // they would hold across the estimate are needed for x~)
                 u64 prev[SM][LS];
                 auto load_prev = [&](int i0) {
 #pragma unroll
@@ -774,14 +776,14 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                             prev[m][ii] = pr == 0 ? 0 : acc[((size_t)p * L + i0 + ii) * N + k + m * NTH];
                     }
                 };
-                load_prev(0);
+                if constexpr (HOIST) load_prev(0);
                 u32 xt[SM][K];
                 u32 v[SM];
                 u64 mK[SM];
                 scale_round_est<K, SM>(src, N, c, xt, v, mK);
 #pragma unroll
                 for (int i0 = 0; i0 < L; i0 += LS) {
-                    if (i0 > 0) load_prev(i0);
+                    if (i0 > 0 || !HOIST) load_prev(i0);
                     u64 d[SM][LS];
                     scale_round_out<K, SM, LS, LZ>(xt, v, mK, c, i0, d);
 #pragma unroll
@@ -1190,26 +1192,36 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                 }
             }
         } else {
-            u64* U = reinterpret_cast<u64*>(T);  // [L + 2][N], slot tid * R + v at its place
+            // the L + 2 forward transforms of a limb run with 16 words per
+            // thread (two virtual threads of the 16-word geometry per thread,
+            // the data in shared memory between passes), which keeps stage R
+            // within the registers the CTA is launched with
+            using NH = NttT<LOGN, 4, Arith64>;
+            constexpr int VT = NH::NT / NTH;
+            static_assert(NH::SMEM_WORDS * 8 <= PP::SMEM, "shared memory of the looped transform");
+            u64* U = reinterpret_cast<u64*>(T);  // [L + 2][N], slot e at its place
             for (int i = 0; i < L; i++) {
                 const Mod m = c.m[i];
                 const u64* tw = c.tw + (size_t)i * 4 * N;
                 for (int s = 0; s < L + 2; s++) {
                     const u64* src = s < 2 ? acc + ((size_t)s * L + i) * N : acc + ((size_t)2 * L + (s - 2)) * N;
-                    u64 x[NQ::R];
+                    u64* dst = U + (size_t)s * N;
+                    NH::template forward_looped<VT>(
+                        sm, tid, tw, m.q, [&](int e) { return barrett64(src[e], m); },
+                        [&](int vt, const u64(&x)[NH::R]) {
 #pragma unroll
-                    for (int v = 0; v < NQ::R; v++) x[v] = barrett64(src[NQ::fwd_in_idx(v, tid)], m);
-                    NQ::forward(x, sm, tid, tw, m.q);
-                    u64* dst = U + (size_t)s * N + (size_t)tid * NQ::R;
-#pragma unroll
-                    for (int v = 0; v < NQ::R; v += 2)
-                        *reinterpret_cast<ulonglong2*>(dst + v) = make_ulonglong2(x[v], x[v + 1]);
+                            for (int v = 0; v < NH::R; v += 2)
+                                *reinterpret_cast<ulonglong2*>(dst + (size_t)vt * NH::R + v) = make_ulonglong2(x[v], x[v + 1]);
+                        });
                 }
-                const size_t e0 = (size_t)tid * NQ::R;
+                // every thread reads back the slots its virtual threads wrote
+#pragma unroll 1
+                for (int jv = 0; jv < VT; jv++) {
+                const size_t e0 = (size_t)(tid + jv * NTH) * NH::R;
                 u64* c0 = Cout + (size_t)i * N + e0;
                 u64* c1 = Cout + ((size_t)L + i) * N + e0;
-#pragma unroll 2
-                for (int v = 0; v < NQ::R; v += 2) {
+#pragma unroll 1
+                for (int v = 0; v < NH::R; v += 2) {
                     const ulonglong2 u0 = *reinterpret_cast<const ulonglong2*>(U + e0 + v);
                     const ulonglong2 u1 = *reinterpret_cast<const ulonglong2*>(U + N + e0 + v);
                     u64 b0 = u0.x, b1 = u0.y, a0 = u1.x, a1 = u1.y;
@@ -1229,6 +1241,7 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                     }
                     *reinterpret_cast<ulonglong2*>(c0 + v) = make_ulonglong2(barrett64(b0, m), barrett64(b1, m));
                     *reinterpret_cast<ulonglong2*>(c1 + v) = make_ulonglong2(barrett64(a0, m), barrett64(a1, m));
+                }
                 }
             }
         }

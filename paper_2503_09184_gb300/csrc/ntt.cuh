@@ -243,6 +243,59 @@ struct NttT {
         fwd_full<NFULL - 1>(x, sm, tid, w, ws, q);
     }
 
+    // Forward transform kept in shared memory, VT virtual threads of this
+    // geometry per physical thread (the CTA has NT / VT threads): each pass
+    // loads one virtual thread's R elements, runs its stages in registers and
+    // stores them back in place, so only R elements are live per thread at a
+    // time (the register-resident forward above keeps all of a thread's
+    // elements across the passes).  in(e) returns input element e (natural
+    // order, below 2^63); out(vt, x) receives the R outputs of virtual
+    // thread vt, slots vt R .. vt R + R - 1 (the run layout).  sm holds
+    // SMEM_WORDS words.
+    template <int VT, typename In, typename Out>
+    SFHE_DEV static void forward_looped(W* sm, int tid, const W* tw, W q, In in, Out out)
+    {
+        constexpr int NTP = NT / VT;
+        static_assert(NTP * VT == NT, "whole virtual threads");
+        const W* w = tw;
+        const W* ws = tw + N;
+        __syncthreads();  // earlier users of sm are done
+#pragma unroll 1
+        for (int j = 0; j < VT; j++) {
+            const int vt = tid + j * NTP;
+            W x[R];
+#pragma unroll
+            for (int v = 0; v < R; v++) x[v] = in(fwd_in_idx(v, vt));
+            if constexpr (REM > 0) {
+                fwd_pass<LOGN - REM, REM>(x, vt, w, ws, q);
+                store<LOGN - REM, REM>(x, sm, vt);
+            } else {
+                fwd_pass<(NFULL - 1) * LOGR, LOGR>(x, vt, w, ws, q);
+                if constexpr (NFULL == 1) out(vt, x);
+                else store<(NFULL - 1) * LOGR, LOGR>(x, sm, vt);
+            }
+        }
+        looped_rest<VT, (REM > 0 ? NFULL - 1 : NFULL - 2)>(sm, tid, w, ws, q, out);
+    }
+    template <int VT, int P, typename Out>
+    SFHE_DEV static void looped_rest(W* sm, int tid, const W* w, const W* ws, W q, Out out)
+    {
+        if constexpr (P >= 0) {
+            constexpr int NTP = NT / VT;
+            __syncthreads();  // the previous pass has stored every element
+#pragma unroll 1
+            for (int j = 0; j < VT; j++) {
+                const int vt = tid + j * NTP;
+                W x[R];
+                load<P * LOGR, LOGR>(x, sm, vt);
+                fwd_pass<P * LOGR, LOGR>(x, vt, w, ws, q);
+                if constexpr (P > 0) store<P * LOGR, LOGR>(x, sm, vt);
+                else out(vt, x);
+            }
+            looped_rest<VT, P - 1>(sm, tid, w, ws, q, out);
+        }
+    }
+
     // ------------------------------------------------------------ inverse ---
     // The inverse transforms NP polynomials modulo the same prime at once:
     // x[j] holds polynomial j, every twiddle is fetched once for all of them,

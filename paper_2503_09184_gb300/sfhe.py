@@ -37,7 +37,8 @@ class sfhe_info(ctypes.Structure):
     _fields_ = [("N", ctypes.c_uint32), ("L", ctypes.c_uint32), ("K", ctypes.c_uint32),
                 ("t", ctypes.c_uint64), ("q", ctypes.c_uint64 * 8), ("b", ctypes.c_uint32 * 32),
                 ("ct_words", ctypes.c_uint64), ("ext_words", ctypes.c_uint64), ("num_sms", ctypes.c_int32),
-                ("ext_interleave", ctypes.c_uint32), ("lazy_group", ctypes.c_int32)]
+                ("ext_interleave", ctypes.c_uint32), ("lazy_group", ctypes.c_int32),
+                ("l2_window", ctypes.c_uint64), ("l2_hit_ratio", ctypes.c_float)]
 
 
 class sfhe_matrix_view(ctypes.Structure):
