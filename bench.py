@@ -649,13 +649,15 @@ def run_serve(args):
     plain_rate = plan.stats["products"] / (time.perf_counter() - t0)
     plan.close()
     # warm-up of the served path
-    SV.serve(serve_requests(args, 100.0, 99)[:2], SV.GpuExecutor(ctx, lazy=args.lazy), budget, args.wave_products,
+    SV.serve(serve_requests(args, 100.0, 99)[:2], SV.GpuExecutor(ctx, lazy=args.lazy,
+                                                                  wave_products=args.wave_products),
+             budget, args.wave_products,
              ct_b, ext_b)
     sweep = []
     rates = [0.0] if args.serve_set == "mixed64" else [float(x) for x in args.rates.split(",")]
     for n, rate in enumerate(rates):
         reqs = serve_requests(args, rate, seed=10 + n)
-        ex = SV.GpuExecutor(ctx, lazy=args.lazy)
+        ex = SV.GpuExecutor(ctx, lazy=args.lazy, wave_products=args.wave_products)
         out = SV.serve(reqs, ex, budget, args.wave_products, ct_b, ext_b)
         plain = SV.fifo_plain_model(reqs, lambda r: ex.admit_s.get(r.rid, 0.0) + r.products / plain_rate)
         sweep.append({"rate_per_s": rate, "requests": out["requests"], "done": out["done"],
@@ -663,6 +665,8 @@ def run_serve(args):
                       "ct_mults_per_s": out["ct_mults_per_s"], "busy_ct_mults_per_s": out["products"] / out["busy_s"],
                       "p50_s": out["p50_s"], "p99_s": out["p99_s"], "makespan_s": out["makespan_s"],
                       "busy_s": out["busy_s"], "admission_s": sum(ex.admit_s.values()),
+                      "wave_setup_s": out["wave_setup_s"], "wave_kernel_s": out["wave_kernel_s"],
+                      "workspace_gb": out["reserved_bytes"] / 1e9,
                       "plain_one_at_a_time": {"p50_s": plain["p50_s"], "p99_s": plain["p99_s"],
                                               "ct_mults_per_s": plain["ct_mults_per_s"]}})
     best = max(sweep, key=lambda d: d["ct_mults_per_s"] or 0)

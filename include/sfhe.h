@@ -262,30 +262,32 @@ sfhe_status sfhe_add(sfhe_ctx* ctx, uint64_t* acc, const uint64_t* x, int64_t n,
 typedef struct sfhe_rotkeys sfhe_rotkeys;
 sfhe_status sfhe_rotkeys_create(sfhe_ctx* ctx, int32_t c, void* stream, sfhe_rotkeys** out);
 void sfhe_rotkeys_destroy(sfhe_rotkeys* rk);
-/* Alg. 1 over chunks (Sec. 3.2, Alg. 1 with c > 1): A holds ceil(M K / c)
- * chunk ciphertexts of the M x K matrix (row-major, element e in slot
- * e mod c of chunk e / c), B ceil(K Nc / c) of the K x Nc one, C receives
- * ceil(M Nc / c).  For every (i, j) and k: rotate A's chunk so that A[i][k]
- * is in slot 0 and B's so that B[k][j] is, multiply and relinearise (the
- * BFV multiply's exact scale-and-round stands in for CKKS's rescale),
- * multiply by the slot-0 mask, rotate right to (i Nc + j) mod c, add into C.
- * Rotations by 0 are skipped.  a_zero / b_zero (host, may be NULL): the
- * naive sparse masks; products with a set mask are skipped.  *products (may
- * be NULL) receives the count.  The workspace (device) holds the
- * per-product temporaries. */
+/* The encrypted matrix product over chunks (Sec. 3.2; the operations of
+ * Alg. 1 with c > 1).  A holds ceil(M K / c) chunk ciphertexts of the M x K
+ * matrix (row-major, element e in slot e mod c of chunk e / c), B ceil(K Nc /
+ * c) of the K x Nc one, C receives ceil(M Nc / c).  Entry (i, j) of C is the
+ * sum, over its products k, of the term Relin(a x b), where a is A's chunk
+ * holding element (i, k) turned so that the element sits in slot 0 and b
+ * likewise for B's element (k, j) (the BFV multiply's exact scale-and-round
+ * stands in for CKKS's rescale; a turn by 0 is no operation), placed at slot
+ * (i Nc + j) mod c of chunk (i Nc + j) / c by the slot-0 mask and a turn
+ * right.  This call places every term on its own, as Alg. 1 does, one short
+ * launch sequence per product.  a_zero / b_zero (host, may be NULL): the
+ * naive sparse masks; a product is skipped where either is set.  The
+ * product sets come from the work-list builder of the per-element matmul.
+ * *products (may be NULL) receives the count.  The workspace (device) holds
+ * the per-product temporaries. */
 sfhe_status sfhe_matmul_chunked_workspace_size(const sfhe_ctx* ctx, size_t* bytes);
 sfhe_status sfhe_matmul_chunked(sfhe_ctx* ctx, const sfhe_rotkeys* rk, int32_t M, int32_t K, int32_t Nc,
                                 const uint64_t* A, const uint64_t* B, uint64_t* C, const uint8_t* a_zero,
                                 const uint8_t* b_zero, void* work, size_t work_bytes, void* stream, int64_t* products);
-/* The same products with the operand rotations taken once per element
- * and the inner sums on the persistent kernel: a_ik = rot(A's chunk,
- * offset of (i, k)) and b_kj likewise (the operands of Alg. 1's products,
- * identical), e_ij = sum_k Relin(a_ik x b_kj) (per product, as Alg. 1),
- * then C[chunk of (i, j)] += rot(mask x e_ij, -offset of (i, j)): the mask
- * and the last rotation act on each entry's sum, so C is another ciphertext
- * with the same decryption.  M K + K Nc + M Nc rotations instead of three
- * per product, batched by rotation amount.  Workspace (device) from the size
- * call, which needs the same chunk size and masks. */
+/* The same terms with the placement applied to each entry's sum instead
+ * of to each term (another ciphertext with the same decryption): every
+ * operand element is turned to slot 0 once (M K + K Nc key switches,
+ * batched by turn amount), the entries' sums of relinearised products run
+ * on the persistent kernel, and each sum is masked and turned to its offset
+ * (M Nc key switches) before it is added into its chunk.  Workspace
+ * (device) from the size call, which needs the same chunk size and masks. */
 sfhe_status sfhe_matmul_chunked_fused_workspace_size(const sfhe_ctx* ctx, int32_t c, int32_t M, int32_t K, int32_t Nc,
                                                      const uint8_t* a_zero, const uint8_t* b_zero, size_t* bytes);
 sfhe_status sfhe_matmul_chunked_fused(sfhe_ctx* ctx, const sfhe_rotkeys* rk, int32_t M, int32_t K, int32_t Nc,
@@ -422,6 +424,12 @@ void sfhe_host_plan_destroy(sfhe_host_plan* hp);
  * `flags`: */
 sfhe_status sfhe_matmul_workspace_size(const sfhe_ctx* ctx, int32_t n, const sfhe_matrix_view* A,
                                        const sfhe_matrix_view* B, uint32_t flags, size_t* bytes);
+/* An upper bound of sfhe_matmul_workspace_size for any n <= max_matmuls
+ * matmuls with at most max_entries output entries and max_products
+ * products in all (a workspace a serving loop allocates once and reuses for
+ * every batch).  Host only.  Errors: EINVAL, ESHAPE (negative bounds). */
+sfhe_status sfhe_matmul_workspace_bound(const sfhe_ctx* ctx, int32_t max_matmuls, int64_t max_entries,
+                                        int64_t max_products, uint32_t flags, size_t* bytes);
 /* C = A x B with the k-loop over every k: the naive dense loop of Alg. 1
  * (Sec. 3.3.1), each product multiplied, relinearised and added (A must
  * store every element: DENSE or MASK; masks are ignored). */

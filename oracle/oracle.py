@@ -466,15 +466,28 @@ class OracleMatmul:
 
 
 class OracleChunked:
-    """Alg. 1 with chunk size c > 1 (Sec. 3.2): every matrix is stored
-    row-major in chunks of c consecutive elements, one chunk per ciphertext
-    holding its elements in slots 0 .. c-1 (the other slots 0).  For every
-    listed product (i, k, j): rotate A's chunk so that A[i][k] is in slot 0,
-    the same for B[k][j]; multiply and relinearise (the BFV multiply rounds
-    exactly, in place of CKKS's rescale); multiply by the slot-0 mask; rotate
-    right to the result's offset; add into the result chunk.  A rotation by
-    0 is the identity and is skipped.  With skip_zeros, products where A[i][k]
-    or B[k][j] is zero are skipped (the naive sparse scheme's two masks)."""
+    """The encrypted matrix product over slot-packed chunks (Sec. 3.2).
+
+    Storage: element e of a matrix's row-major order sits in slot e mod c of
+    chunk ciphertext e // c (chunk q encrypted under the stream object
+    (matrix id, q, 0)); the other slots hold 0.
+
+    The result is defined per output entry (i, j).  Its product set P(i, j)
+    is every k, or with skip_zeros the k where A[i][k] and B[k][j] are both
+    nonzero (the naive sparse scheme's two masks, Sec. 3.3.2).  The operand
+    of product k on the left is the chunk holding element e = i K + k turned
+    left by e mod c, which brings A[i][k] into slot 0 (a Galois rotation; a
+    turn by 0 is no operation), and likewise on the right with
+    e = k Nc + j.  Their BFV product, relinearised (the exact scale-and-round
+    of the BFV multiply stands where CKKS rescales), is the product's term.
+    The entry's slot-0 value reaches its place, slot r mod c of chunk r // c
+    with r = i Nc + j, by a plaintext product with the one-hot slot-0 mask
+    and a turn right by r mod c; that placement is applied either to every
+    term before the terms are added into the result chunk (placement
+    "product", where Alg. 1 applies it) or once to the sum of the entry's
+    terms (placement "entry": a different ciphertext with the same
+    decryption, equal to the first wherever r mod c = 0 and the entry has at
+    most one term).  Additions are exact and order-free."""
 
     def __init__(self, ctx: OracleCtx, A: np.ndarray, B: np.ndarray, c: int, a_id: int, b_id: int):
         self.ctx, self.A, self.B, self.c = ctx, np.asarray(A), np.asarray(B), c
@@ -482,9 +495,9 @@ class OracleChunked:
         self.a_ct = self._chunks(self.A, a_id)
         self.b_ct = self._chunks(self.B, b_id)
         self._keys = {}
-        mask = np.zeros(ctx.N, dtype=np.int64)
-        mask[0] = 1
-        self.mask = slots_encode(ctx.N, ctx.t, mask)
+        onehot = np.zeros(ctx.N, dtype=np.int64)
+        onehot[0] = 1
+        self.mask = slots_encode(ctx.N, ctx.t, onehot)
 
     def _chunks(self, M: np.ndarray, mid: int) -> list:
         flat = M.reshape(-1)
@@ -502,56 +515,46 @@ class OracleChunked:
         return self._keys[g]
 
     def rot(self, ct: np.ndarray, k: int) -> np.ndarray:
+        """ct turned left by k slots in each row (right for k < 0)"""
         if k % (self.ctx.N // 2) == 0:
             return ct
         g = rotation_element(self.ctx.N, k)
         return self.ctx.rotate(ct, g, self.key(g))
 
-    def product(self, i: int, k: int, j: int) -> np.ndarray:
-        """one iteration of Alg. 1's inner loop, before the accumulation"""
-        Kd, Nc, c = self.A.shape[1], self.B.shape[1], self.c
-        ia, ib, ir = i * Kd + k, k * Nc + j, i * Nc + j
-        a = self.rot(self.a_ct[ia // c], ia % c)
-        b = self.rot(self.b_ct[ib // c], ib % c)
-        x = self.ctx.mul_relin(a, b)
-        x = self.ctx.mul_plain(x, self.mask)
-        return self.rot(x, -(ir % c))
-
-    def result(self, skip_zeros: bool = False) -> list:
+    def product_sets(self, skip_zeros: bool = False) -> dict:
+        """{(i, j): [k, ...]} for every output entry"""
         M, Kd = self.A.shape
         Nc = self.B.shape[1]
-        nchunks = -(-(M * Nc) // self.c)
-        R = [np.zeros(self.ctx.ct_shape, dtype=np.uint64) for _ in range(nchunks)]
-        for i in range(M):
-            for j in range(Nc):
-                for k in range(Kd):
-                    if skip_zeros and (self.A[i, k] == 0 or self.B[k, j] == 0):
-                        continue
-                    self.ctx.add_(R[(i * Nc + j) // self.c], self.product(i, k, j))
-        return R
+        return {(i, j): [k for k in range(Kd) if not (skip_zeros and (self.A[i, k] == 0 or self.B[k, j] == 0))]
+                for i in range(M) for j in range(Nc)}
 
-    def result_fused(self, skip_zeros: bool = False) -> list:
-        """the same products with the mask and the result rotation applied to
-        each entry's sum of relinearised products instead of to each product
-        (a different ciphertext with the same decryption; equal to result()
-        wherever the entry sits at offset 0 of its chunk)"""
-        M, Kd = self.A.shape
-        Nc = self.B.shape[1]
-        nchunks = -(-(M * Nc) // self.c)
-        R = [np.zeros(self.ctx.ct_shape, dtype=np.uint64) for _ in range(nchunks)]
-        for i in range(M):
-            for j in range(Nc):
+    def slot0(self, chunks: list, e: int) -> np.ndarray:
+        """element e of a chunked matrix brought into slot 0"""
+        return self.rot(chunks[e // self.c], e % self.c)
+
+    def term(self, i: int, k: int, j: int) -> np.ndarray:
+        Kd, Nc = self.A.shape[1], self.B.shape[1]
+        return self.ctx.mul_relin(self.slot0(self.a_ct, i * Kd + k), self.slot0(self.b_ct, k * Nc + j))
+
+    def place(self, ct: np.ndarray, r: int) -> np.ndarray:
+        """slot 0 of ct moved to slot r mod c, every other slot cleared"""
+        return self.rot(self.ctx.mul_plain(ct, self.mask), -(r % self.c))
+
+    def result(self, skip_zeros: bool = False, placement: str = "product") -> list:
+        """the result chunks (list of ciphertexts, coefficient form)"""
+        assert placement in ("product", "entry")
+        M, Nc = self.A.shape[0], self.B.shape[1]
+        R = [np.zeros(self.ctx.ct_shape, dtype=np.uint64) for _ in range(-(-(M * Nc) // self.c))]
+        for (i, j), ks in self.product_sets(skip_zeros).items():
+            r = i * Nc + j
+            if placement == "product":
+                for k in ks:
+                    self.ctx.add_(R[r // self.c], self.place(self.term(i, k, j), r))
+            else:
                 e = np.zeros(self.ctx.ct_shape, dtype=np.uint64)
-                for k in range(Kd):
-                    if skip_zeros and (self.A[i, k] == 0 or self.B[k, j] == 0):
-                        continue
-                    ia, ib = i * Kd + k, k * Nc + j
-                    a = self.rot(self.a_ct[ia // self.c], ia % self.c)
-                    b = self.rot(self.b_ct[ib // self.c], ib % self.c)
-                    self.ctx.add_(e, self.ctx.mul_relin(a, b))
-                ir = i * Nc + j
-                x = self.rot(self.ctx.mul_plain(e, self.mask), -(ir % self.c))
-                self.ctx.add_(R[ir // self.c], x)
+                for k in ks:
+                    self.ctx.add_(e, self.term(i, k, j))
+                self.ctx.add_(R[r // self.c], self.place(e, r))
         return R
 
     def decode(self, R: list) -> np.ndarray:

@@ -1033,6 +1033,27 @@ static sfhe_status size_impl(const sfhe_ctx* c, int32_t n, const sfhe_matrix_vie
     return SFHE_OK;
 }
 
+extern "C" sfhe_status sfhe_matmul_workspace_bound(const sfhe_ctx* c, int32_t max_matmuls, int64_t max_entries,
+                                                   int64_t max_products, uint32_t flags, size_t* bytes)
+{
+    if (!c || !bytes) return fail(SFHE_EINVAL, "null argument");
+    if (max_matmuls < 0 || max_entries < 0 || max_products < 0) return fail(SFHE_ESHAPE, "negative bound");
+    sfhe_status st = check_flags(flags);
+    if (st != SFHE_OK) return st;
+    // the layout of layout_of() with every list at its bound and the full grid
+    size_t off = 256;
+    off += align256((size_t)max_matmuls * sizeof(MmDesc));
+    off += align256((size_t)max_entries * sizeof(Entry));
+    off += align256((size_t)max_products * sizeof(int2));
+    const size_t N = c->rc.N, L = c->rc.L, K = c->rc.K;
+    if (flags & SFHE_EXEC_PERSISTENT)
+        off += align256((size_t)persistent_ctas_per_sm(c->rc) * c->num_sms * persistent_scratch_words(c->rc) * 8);
+    if (flags & SFHE_EXEC_PLAIN)
+        off += align256(3 * K * N * 4) + align256(3 * L * N * 8) + align256((L + 2) * L * N * 8);
+    *bytes = off;
+    return SFHE_OK;
+}
+
 extern "C" sfhe_status sfhe_matmul_workspace_size(const sfhe_ctx* c, int32_t n, const sfhe_matrix_view* A,
                                                   const sfhe_matrix_view* B, uint32_t flags, size_t* bytes)
 {
@@ -1392,6 +1413,18 @@ extern "C" sfhe_status sfhe_matmul_chunked_workspace_size(const sfhe_ctx* c, siz
     return SFHE_OK;
 }
 
+// descriptors of a chunked matrix's elements for the work-list builder:
+// MASK-encoded where a zero mask is given (the products it lists skip those
+// elements), DENSE otherwise
+static sfhe_matrix_view element_desc(int32_t rows, int32_t cols, const uint8_t* zero, uint64_t* ct, uint32_t* ext);
+
+// The chunked product term by term.  The product sets are the work list of
+// the per-element matmul, built by the same builder from element
+// descriptors (so both zero masks skip exactly as in the fused form).  Each
+// listed product is one short launch sequence: the chunks holding its two
+// elements are turned so that the elements sit in slot 0, lifted, multiplied
+// and relinearised on the per-product kernels; the term is masked to slot 0,
+// turned right to its entry's offset and added into the entry's chunk.
 extern "C" sfhe_status sfhe_matmul_chunked(sfhe_ctx* c, const sfhe_rotkeys* rk, int32_t M, int32_t K, int32_t Nc,
                                           const uint64_t* A, const uint64_t* B, uint64_t* C, const uint8_t* a_zero,
                                           const uint8_t* b_zero, void* work, size_t work_bytes, void* stream,
@@ -1407,6 +1440,15 @@ extern "C" sfhe_status sfhe_matmul_chunked(sfhe_ctx* c, const sfhe_rotkeys* rk, 
     const size_t LN = (size_t)rc.L * rc.N, KN = (size_t)rc.K * rc.N, ctw = 2 * LN;
     const int64_t nC = ((int64_t)M * Nc + ch - 1) / ch;
     if (nC > 0 && (!A || !B || !C)) return fail(SFHE_EINVAL, "null operand");
+    // the product sets
+    sfhe_matrix_view Ad = element_desc(M, K, a_zero, (uint64_t*)16, (uint32_t*)16);
+    sfhe_matrix_view Bd = element_desc(K, Nc, b_zero, (uint64_t*)16, (uint32_t*)16);
+    sfhe_plan W;
+    W.ctx = c;
+    W.flags = SFHE_EXEC_PLAIN;
+    const bool dense_loop = false;
+    sfhe_status st = build(c, 1, &Ad, &Bd, nullptr, &dense_loop, W);
+    if (st != SFHE_OK) return st;
     cudaStream_t s = as_stream(stream);
     u64* w = (u64*)work;
     u64* rot_work = w;
@@ -1426,60 +1468,62 @@ extern "C" sfhe_status sfhe_matmul_chunked(sfhe_ctx* c, const sfhe_rotkeys* rk, 
     u64* U = w;
     w += (rc.L + 2) * LN;
     u64* mask = w;
-    // the slot-0 mask: one-hot plaintext in NTT form
     {
         std::vector<int64_t> v(rc.N, 0), poly(rc.N);
         v[0] = 1;
         if (!slots_encode((uint32_t)rc.N, rc.t, v.data(), poly.data())) return fail(SFHE_EUNSUPPORTED, "slots");
-        sfhe_status st = sfhe_plain_ntt(c, poly.data(), mask, stream);
+        st = sfhe_plain_ntt(c, poly.data(), mask, stream);
         if (st != SFHE_OK) return st;
     }
     if (nC > 0) CUDA_TRY(cudaMemsetAsync(C, 0, (size_t)nC * ctw * 8, s));
-    auto rotated = [&](const u64* src, int off, bool right, u64* dst) -> const u64* {
+    // a chunk turned left by `off` slots (right for right = true); a turn by
+    // 0 is no operation
+    auto turned = [&](const u64* src, int off, bool right, u64* dst) -> const u64* {
         if (off == 0) return src;
         if (launch_rotate(rc, src, sfhe_rotation_element(rc.N, right ? -off : off), rotkey(rk, right, off, 0),
                           rotkey(rk, right, off, 1), dst, rot_work, s) != cudaSuccess)
             return nullptr;
         return dst;
     };
-    int64_t done = 0;
-    for (int32_t i = 0; i < M; i++)
-        for (int32_t j = 0; j < Nc; j++)
-            for (int32_t k = 0; k < K; k++) {
-                if (a_zero && a_zero[(int64_t)i * K + k]) continue;
-                if (b_zero && b_zero[(int64_t)k * Nc + j]) continue;
-                const int64_t ia = (int64_t)i * K + k, ib = (int64_t)k * Nc + j, ir = (int64_t)i * Nc + j;
-                const u64* a = rotated(A + (ia / ch) * ctw, (int)(ia % ch), false, ra);
-                const u64* b = rotated(B + (ib / ch) * ctw, (int)(ib % ch), false, rb);
-                if (!a || !b) return fail(SFHE_ECUDA, "rotation: %s", cudaGetErrorString(cudaGetLastError()));
-                sfhe_status st = sfhe_lift(c, a, 1, ea, lift_ws, lift_bytes, stream);
-                if (st == SFHE_OK) st = sfhe_lift(c, b, 1, eb, lift_ws, lift_bytes, stream);
-                if (st != SFHE_OK) return st;
-                cudaError_t e = launch_tensor_intt(rc, ea, eb, T, s);
-                if (e == cudaSuccess) e = launch_scale_round(rc, T, D, s);
-                if (e == cudaSuccess) e = launch_relin_ntt(rc, D, U, s);
-                if (e == cudaSuccess) e = cudaMemsetAsync(prod, 0, ctw * 8, s);
-                if (e == cudaSuccess) e = launch_relin_accum(rc, U, c->d_rlk, c->d_rlk_sh, prod, s);
-                if (e == cudaSuccess) e = launch_mul_plain(rc, prod, 1, mask, s);
-                if (e != cudaSuccess) return fail(SFHE_ECUDA, "chunked product: %s", cudaGetErrorString(e));
-                const u64* r = rotated(prod, (int)(ir % ch), true, rr);
-                if (!r) return fail(SFHE_ECUDA, "rotation: %s", cudaGetErrorString(cudaGetLastError()));
-                e = launch_add_ct(rc, C + (ir / ch) * ctw, r, 1, s);
-                if (e != cudaSuccess) return fail(SFHE_ECUDA, "accumulate: %s", cudaGetErrorString(e));
-                done++;
-            }
-    if (products) *products = done;
+    for (const Entry& en : W.entries) {
+        const int64_t r = (int64_t)en.row * Nc + en.col;
+        for (int p = 0; p < en.count; p++) {
+            const int2 it = W.rowlist[en.first + p];  // (element of A, k)
+            const int64_t ia = it.x, ib = (int64_t)it.y * Nc + en.col;
+            const u64* a = turned(A + (ia / ch) * ctw, (int)(ia % ch), false, ra);
+            const u64* b = turned(B + (ib / ch) * ctw, (int)(ib % ch), false, rb);
+            if (!a || !b) return fail(SFHE_ECUDA, "rotation: %s", cudaGetErrorString(cudaGetLastError()));
+            st = sfhe_lift(c, a, 1, ea, lift_ws, lift_bytes, stream);
+            if (st == SFHE_OK) st = sfhe_lift(c, b, 1, eb, lift_ws, lift_bytes, stream);
+            if (st != SFHE_OK) return st;
+            cudaError_t e = launch_tensor_intt(rc, ea, eb, T, s);
+            if (e == cudaSuccess) e = launch_scale_round(rc, T, D, s);
+            if (e == cudaSuccess) e = launch_relin_ntt(rc, D, U, s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(prod, 0, ctw * 8, s);
+            if (e == cudaSuccess) e = launch_relin_accum(rc, U, c->d_rlk, c->d_rlk_sh, prod, s);
+            if (e == cudaSuccess) e = launch_mul_plain(rc, prod, 1, mask, s);
+            if (e != cudaSuccess) return fail(SFHE_ECUDA, "chunked product: %s", cudaGetErrorString(e));
+            const u64* placed = turned(prod, (int)(r % ch), true, rr);
+            if (!placed) return fail(SFHE_ECUDA, "rotation: %s", cudaGetErrorString(cudaGetLastError()));
+            e = launch_add_ct(rc, C + (r / ch) * ctw, placed, 1, s);
+            if (e != cudaSuccess) return fail(SFHE_ECUDA, "accumulate: %s", cudaGetErrorString(e));
+        }
+    }
+    if (products) *products = W.products;
     return SFHE_OK;
 }
 
-// Alg. 1 over chunks with the operand rotations taken once per element and
-// the inner sums on the persistent kernel:
-//   a_ik = rot(A chunk of (i, k), offset of (i, k)),  b_kj likewise;
-//   e_ij = sum_k Relin(a_ik x b_kj)        (persistent matmul, per product)
-//   C[chunk of (i, j)] += rot(mask x e_ij, -(offset of (i, j)))
-// The operands' rotations and every product equal Alg. 1's; the mask and
-// the last rotation act on the entry's sum instead of on each product, so
-// the result is another ciphertext with the same decryption.
+// The chunked product with each entry's terms summed before placement.
+// Every operand element is brought to slot 0 of its own ciphertext once
+// (element q c + o of a matrix is chunk q turned left by o, so one batched
+// key switch per offset covers a matrix), which turns the chunked operands
+// into per-element ones; the entries' sums of relinearised products then
+// run on the persistent kernel over the same work list, and each entry's
+// sum is masked to slot 0 and turned right to its offset (one batched key
+// switch per offset) before it is added into its chunk.  The terms are
+// those of the term-by-term form; only the placement moves from the terms
+// to their sum, so the result is another ciphertext with the same
+// decryption.
 namespace {
 // ciphertexts per batched key switch (the rotation scratch holds this many)
 const long long kRotBatch = 128;
@@ -1516,9 +1560,9 @@ sfhe_status fused_layout(const sfhe_ctx* c, int32_t M, int32_t K, int32_t Nc, in
     return SFHE_OK;
 }
 
-// descriptors of the rotated operands: MASK-encoded where a zero mask is
-// given (the sparse matmul skips those products), DENSE otherwise
-sfhe_matrix_view element_desc(int32_t rows, int32_t cols, const uint8_t* zero, uint64_t* ct, uint32_t* ext)
+}  // namespace
+
+static sfhe_matrix_view element_desc(int32_t rows, int32_t cols, const uint8_t* zero, uint64_t* ct, uint32_t* ext)
 {
     sfhe_matrix_view d;
     memset(&d, 0, sizeof(d));
@@ -1531,7 +1575,6 @@ sfhe_matrix_view element_desc(int32_t rows, int32_t cols, const uint8_t* zero, u
     d.ext = ext;
     return d;
 }
-}  // namespace
 
 extern "C" sfhe_status sfhe_matmul_chunked_fused_workspace_size(const sfhe_ctx* c, int32_t chunk, int32_t M, int32_t K,
                                                                 int32_t Nc, const uint8_t* a_zero,

@@ -190,9 +190,16 @@ class Scheduler:
 
 class GpuExecutor:
     """Device side: encryption and lift on admission, one persistent batch
-    plan per wave over CSR row blocks of A (and the matching rows of C)."""
+    plan per wave over CSR row blocks of A (and the matching rows of C).
 
-    def __init__(self, ctx, stream=None, lazy: bool = False):
+    One matmul workspace, sized for the largest wave (wave_products products
+    over as many output entries, up to max_blocks row blocks), is allocated
+    once and reused by every wave; its bytes (reserved_bytes) come out of
+    the HBM budget before any request is admitted.  setup_s and kernel_s
+    add up the waves' plan set-up (work-list build and upload) and their
+    persistent launches."""
+
+    def __init__(self, ctx, stream=None, lazy: bool = False, wave_products: int = 40000, max_blocks: int = 1024):
         """lazy: run the waves in the grouped accumulate-then-round mode
         (SFHE_EXEC_LAZY) instead of the per-product order."""
         import torch
@@ -203,6 +210,11 @@ class GpuExecutor:
         self.mats = {}
         self.a_cache = {}
         self.admit_s = {}
+        self.max_blocks = max_blocks
+        n = S.sfhe_matmul_workspace_bound(ctx.h, max_blocks, wave_products, wave_products, self.flags)
+        self.work = torch.empty(n, dtype=torch.uint8, device="cuda")
+        self.reserved_bytes = n
+        self.setup_s, self.kernel_s = 0.0, 0.0
 
     def admit(self, req: Request):
         """encrypt and lift the request's operands on the device (the client's
@@ -237,16 +249,25 @@ class GpuExecutor:
 
     def run_wave(self, blocks) -> int:
         """one persistent launch over the blocks; returns the products run."""
-        api, S = self.api, self.S
+        api, S, torch = self.api, self.S, self.torch
+        t0 = time.perf_counter()
         parts = [self._rows(req, r0, r1) for req, r0, r1 in blocks]
         As, Bs, Cs = [p[0] for p in parts], [p[1] for p in parts], [p[2] for p in parts]
-        work = api.workspace(self.ctx, As, Bs, self.flags)
+        need = S.sfhe_matmul_workspace_size(self.ctx.h, [a.desc() for a in As], [b.desc() for b in Bs], self.flags)
+        # a wave of unusually many empty rows may need more than the bound
+        work = self.work if need <= self.work.numel() else torch.empty(need, dtype=torch.uint8, device="cuda")
         plan = S.sfhe_plan_create(self.ctx.h, [a.desc() for a in As], [b.desc() for b in Bs],
                                   [c.desc() for c in Cs], self.flags, work, self.stream)
         products = S.sfhe_plan_stats(plan)["products"]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
         S.sfhe_plan_execute(plan, self.stream)
+        e1.record(self.stream)
+        t1 = time.perf_counter()
         S.sfhe_matmul_check(work, self.stream)       # synchronises the stream
         S.sfhe_plan_destroy(plan)
+        self.setup_s += t1 - t0
+        self.kernel_s += e0.elapsed_time(e1) / 1e3
         return products
 
     def result(self, req: Request, col0: int = 0):
@@ -266,7 +287,9 @@ def serve(requests: list[Request], executor, budget_bytes: int, wave_products: i
     """Run the requests (arrival times in seconds from now) through the
     continuous-batching loop on the wall clock.  Returns per-request
     latencies and totals; with keep_results the executor keeps every C."""
-    sched = Scheduler(budget_bytes, wave_products, ct_bytes, ext_bytes)
+    # the executor's standing device memory (its matmul workspace) is not
+    # available to requests
+    sched = Scheduler(budget_bytes - getattr(executor, "reserved_bytes", 0), wave_products, ct_bytes, ext_bytes)
     pending = deque(sorted(requests, key=lambda r: r.arrival))
     t0 = clock()
     waves, busy, products = 0, 0.0, 0
@@ -299,6 +322,8 @@ def serve(requests: list[Request], executor, budget_bytes: int, wave_products: i
         "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
         "p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
         "ct_mults_per_s": products / end if end > 0 else None,
+        "wave_setup_s": getattr(executor, "setup_s", None), "wave_kernel_s": getattr(executor, "kernel_s", None),
+        "reserved_bytes": getattr(executor, "reserved_bytes", 0),
     }
 
 

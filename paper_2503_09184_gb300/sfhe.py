@@ -73,6 +73,7 @@ _SIGS = {
     "sfhe_export_secret": ([_vp, _vp], ctypes.c_int),
     "sfhe_export_relin_key": ([_vp, _vp, _vp], ctypes.c_int),
     "sfhe_matmul_workspace_size": ([_vp, _i32, _P(sfhe_matrix_view), _P(sfhe_matrix_view), _u32, _P(_sz)], ctypes.c_int),
+    "sfhe_matmul_workspace_bound": ([_vp, _i32, _i64, _i64, _u32, _P(_sz)], ctypes.c_int),
     "sfhe_matmul_dense_view": ([_vp, _P(sfhe_matrix_view), _P(sfhe_matrix_view), _P(sfhe_matrix_view), _u32, _vp, _sz, _vp], ctypes.c_int),
     "sfhe_matmul_sparse_view": ([_vp, _P(sfhe_matrix_view), _P(sfhe_matrix_view), _i32, _P(sfhe_matrix_view), _u32, _vp, _sz, _vp],
                            ctypes.c_int),
@@ -302,6 +303,12 @@ def _mats(ms) -> ctypes.Array:
 def sfhe_matmul_workspace_size(ctx: int, A: list, B: list, flags: int) -> int:
     b = ctypes.c_size_t()
     _check(lib().sfhe_matmul_workspace_size(ctx, len(A), _mats(A), _mats(B), flags, ctypes.byref(b)))
+    return b.value
+
+
+def sfhe_matmul_workspace_bound(ctx: int, max_matmuls: int, max_entries: int, max_products: int, flags: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().sfhe_matmul_workspace_bound(ctx, max_matmuls, max_entries, max_products, flags, ctypes.byref(b)))
     return b.value
 
 

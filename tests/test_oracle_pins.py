@@ -605,9 +605,8 @@ def test_mul_plain_is_slotwise(ctx16):
 
 @pytest.mark.parametrize("chunk", [1, 3, 4])
 def test_chunked_alg1_decrypts_to_the_product(chunk):
-    """Alg. 1 over chunks of c values (rotate both operands into slot 0,
-    multiply and relinearise, mask slot 0, rotate to the result offset,
-    add): the result chunks decode to A B mod t, with and without the
+    """The chunked product with each term placed on its own (Alg. 1's
+    placement): the result chunks decode to A B mod t, with and without the
     two-sided zero skip; skipping changes the ciphertexts (fewer products)
     but not the decryption."""
     c = O.OracleCtx(32, 3, seed=13)
@@ -623,14 +622,37 @@ def test_chunked_alg1_decrypts_to_the_product(chunk):
 
 
 def test_chunked_fused_order_pins():
-    """The fused order (mask and result rotation on each entry's sum)
-    decrypts to A B mod t, and equals the per-product order exactly for
-    c = 1 (no result rotation, and the mask multiply is exact and linear)."""
+    """Placement on each entry's sum decrypts to A B mod t, and equals the
+    per-term placement exactly for c = 1 (no turn to a result offset, and
+    the mask product is exact and linear)."""
     c = O.OracleCtx(32, 3, seed=14)
     A = np.array([[3, 0, -7], [0, 5, 2]], dtype=np.int64)
     B = np.array([[2, -1], [0, 4], [6, 0]], dtype=np.int64)
     oc = O.OracleChunked(c, A, B, 4, 1, 2)
-    assert (oc.decode(oc.result_fused()) == A @ B).all()
-    assert (oc.decode(oc.result_fused(skip_zeros=True)) == A @ B).all()
+    assert (oc.decode(oc.result(placement="entry")) == A @ B).all()
+    assert (oc.decode(oc.result(skip_zeros=True, placement="entry")) == A @ B).all()
     o1 = O.OracleChunked(c, A, B, 1, 1, 2)
-    assert all((x == y).all() for x, y in zip(o1.result(), o1.result_fused()))
+    assert all((x == y).all() for x, y in zip(o1.result(), o1.result(placement="entry")))
+
+
+def test_chunked_terms_and_placement_by_their_definition():
+    """A product's term decrypts to A[i][k] B[k][j] mod t in slot 0 (both
+    operands brought to slot 0 by their turns; the other slots hold the
+    slot-wise products of the turned chunks), and place() leaves exactly that
+    value in slot r mod c and zeros in every other slot."""
+    c = O.OracleCtx(32, 3, seed=15)
+    A = np.array([[3, -2, -7, 1], [4, 5, 2, -6]], dtype=np.int64)
+    B = np.array([[2, -1, 3], [7, 4, -5], [6, 1, 2], [-3, 8, 1]], dtype=np.int64)
+    oc = O.OracleChunked(c, A, B, 3, 1, 2)
+    for i, k, j in [(0, 0, 0), (1, 2, 1), (1, 3, 2), (0, 1, 2)]:
+        m, _ = c.decrypt_poly(oc.term(i, k, j))
+        slots = [int(x) for x in O.slots_decode(c.N, T, m)]
+        assert slots[0] == int(A[i, k] * B[k, j]) % T
+        r = i * 3 + j
+        m, _ = c.decrypt_poly(oc.place(oc.term(i, k, j), r))
+        placed = [int(x) for x in O.slots_decode(c.N, T, m)]
+        want = [0] * c.N
+        want[r % 3] = int(A[i, k] * B[k, j]) % T
+        assert placed == want, (i, k, j)
+    sets = oc.product_sets(skip_zeros=True)
+    assert sets[(0, 0)] == [0, 1, 2, 3] and all(len(v) == 4 for v in sets.values())
