@@ -66,6 +66,9 @@ def parse():
                     "(default: 8 / 4 / 1 at N = 4096 / 8192 / 16384; one entry per host thread)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shape", default=None, help="M,K,Nc override of the sweep shape (small profiling cases)")
+    ap.add_argument("--ring", default=None, help="N,L override of the sweep ring (small profiling cases, ints in "
+                                                 "[-8, 8] at N = 16384)")
+    ap.add_argument("--tile", type=int, default=-1, help="stage-S tile of the persistent kernel (default: tuned)")
     ap.add_argument("--workload", default="sweep", choices=["sweep", "tiny", "layer", "mixed", "serve", "chunked"])
     ap.add_argument("--chunk", type=int, default=8, help="chunked: values per ciphertext (Alg. 1 with c > 1)")
     ap.add_argument("--chunked-shape", default="16,16,16", help="chunked: M,K,Nc")
@@ -292,13 +295,20 @@ def job_of(args):
         s = SPARSITY if args.sparsity is None else args.sparsity
         shape = W.sweep(s)
         name = f"sweep-64x64x64-s{s:g}"
+        ring = W.SWEEP_RING
+        if args.ring:
+            ring = W.Ring(*(int(x) for x in args.ring.split(",")))
+            if ring.N == 16384:
+                shape = W.MatmulShape(shape.M, shape.K, shape.Nc, s, -8, 8, shape.seed)
         if args.shape:
             M, K, Nc = (int(x) for x in args.shape.split(","))
             shape = W.MatmulShape(M, K, Nc, s, shape.lo, shape.hi, shape.seed)
             name = f"sweep-{M}x{K}x{Nc}-s{s:g}"
+        if args.ring:
+            name += f"-N{ring.N}-L{ring.L}"
         if args.b_sparse:
             name += "-bmask"
-        return W.SWEEP_RING, [W.operands(shape, b_sparse=args.b_sparse)], name, s
+        return ring, [W.operands(shape, b_sparse=args.b_sparse)], name, s
     if wl == "tiny":
         return W.TINY_RING, [W.operands(W.TINY)], "tiny-8x8x8-s0.5", W.TINY.sparsity
     if wl == "layer":
@@ -409,6 +419,8 @@ def main():
     if args.lazy:
         workload += "-lazy"
     ctx = api.Context(ring.N, ring.L, seed=0)
+    if args.tile >= 0:
+        S.sfhe_ctx_set_variant(ctx.h, args.tile)
     stream = torch.cuda.current_stream()
 
     # setup (untimed): encryption of the operands

@@ -145,7 +145,12 @@ typedef struct {
 /* Parameters and keys.  Selects the primes, builds the NTT and base
  * conversion tables, and runs key generation on the current device from
  * `seed` (secret and relinearisation key never leave the device unless
- * exported).  Synchronous.  Errors: EINVAL (null), EUNSUPPORTED (N, L or t
+ * exported).  Synchronous.  The key and its Shoup companions share one
+ * allocation, over which every persistent launch carries a persisting-L2
+ * access-policy window: the context raises its persisting-L2 limit (a limit
+ * of this process's CUDA context, gone with it) up to the key's size.  The
+ * environment variable SFHE_L2_PERSIST=0 leaves the limit alone and launches
+ * without the window.  Errors: EINVAL (null), EUNSUPPORTED (N, L or t
  * outside the list above), ECUDA / ENOMEM (device), EDEVICE (sampling). */
 sfhe_status sfhe_ctx_create(const sfhe_params* params, uint64_t seed, sfhe_ctx** out);
 void sfhe_ctx_destroy(sfhe_ctx* ctx);

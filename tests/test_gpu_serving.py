@@ -23,9 +23,12 @@ def test_requests_alone_and_in_the_mix_are_identical():
         reqs.append(SV.Request(rid, A, B, arrival=0.01 * rid))
     ct_b = 2 * ctx.L * ctx.N * 8
     ext_b = 2 * ctx.K * ctx.N * 4
-    budget = 2 * max(SV.request_bytes(r, ct_b, ext_b) for r in reqs)   # at most two or three in flight
-    ex = SV.GpuExecutor(ctx)
+    ex = SV.GpuExecutor(ctx, wave_products=96)
+    # at most two or three requests in flight beside the executor's workspace
+    budget = 2 * max(SV.request_bytes(r, ct_b, ext_b) for r in reqs) + ex.reserved_bytes
     out = SV.serve(reqs, ex, budget, wave_products=96, ct_bytes=ct_b, ext_bytes=ext_b, keep_results=True)
+    assert out["reserved_bytes"] == ex.reserved_bytes > 0
+    assert out["wave_kernel_s"] > 0 and out["wave_setup_s"] > 0
     assert out["done"] == len(reqs) and out["waves"] > len(reqs)
     for r in reqs:
         C_mix = ex.result(r)
@@ -48,8 +51,9 @@ def test_column_tiles_equal_the_untiled_request():
     req = SV.Request(7, A, B, arrival=0.0)
     ct_b, ext_b = 2 * ctx.L * ctx.N * 8, 2 * ctx.K * ctx.N * 4
     nnz = int((A != 0).sum())
-    budget = nnz * (ct_b + ext_b) + 4 * (8 * (ct_b + ext_b) + 6 * ct_b)      # four columns per tile
-    ex = SV.GpuExecutor(ctx)
+    ex = SV.GpuExecutor(ctx, wave_products=64)
+    # four columns per tile beside A and the executor's workspace
+    budget = nnz * (ct_b + ext_b) + 4 * (8 * (ct_b + ext_b) + 6 * ct_b) + ex.reserved_bytes
     out = SV.serve([req], ex, budget, wave_products=64, ct_bytes=ct_b, ext_bytes=ext_b, keep_results=True)
     assert out["done"] == 1 and req.state == "done"
     Ae = api.encrypt_matrix(ctx, A, "csr", 2 * req.rid + 1)
