@@ -1129,3 +1129,58 @@ int or_mul_plain(void *vc, const u64 *ct, const u64 *pt, u64 *out)
     free(pm);
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* helpers of the CKKS oracle (oracle/ckks.py, the parameter set of      */
+/* Sec. 3.1): prime lists of other sizes, the generator's samplers as     */
+/* whole polynomials, scalar products                                    */
+/* ------------------------------------------------------------------ */
+/* The primes p = 1 mod 2N below 2^bits in descending order, the first
+ * `skip` of them left out, `count` of them into out. */
+int or_ntt_primes_bits(int N, int bits, int skip, int count, u64 *out)
+{
+    u64 twoN = 2 * (u64)N;
+    u64 k = ((1ULL << bits) - 2) / twoN;
+    int seen = 0, got = 0;
+    while (got < count && k > 0) {
+        u64 p = k * twoN + 1;
+        if (or_is_prime(p)) {
+            if (seen >= skip) out[got++] = p;
+            seen++;
+        }
+        k--;
+    }
+    return got == count ? 0 : -1;
+}
+
+/* One polynomial of the stream (seed, dom, o0, o1, o2), as residues mod q:
+ * kind 0: uniform residues mod q, coefficient k from slot limb N + k;
+ * kind 1: ternary, coefficient k from slot k;
+ * kind 2: the rounded Gaussian of the table T20 (or_cdt), slot k.
+ * Returns -1 if a rejection sampler ran out of words. */
+int or_sample_poly(u64 seed, u64 dom, u64 o0, u64 o1, u64 o2, int kind, u64 q, int limb, int N, const u64 *T20,
+                   u64 *out)
+{
+    u64 key = sm_key(seed, dom, o0, o1, o2);
+    int rc = 0;
+    for (int k = 0; k < N; k++) {
+        if (kind == 0) {
+            if (sample_uniform(key, (u64)limb * N + k, q, &out[k])) rc = -1;
+        } else if (kind == 1) {
+            int v = 0;
+            if (sample_ternary(key, (u64)k, &v)) rc = -1;
+            out[k] = v >= 0 ? (u64)v : q - 1;
+        } else {
+            int64_t e = sample_gauss(key, (u64)k, T20);
+            out[k] = e >= 0 ? (u64)e : q - (u64)(-e);
+        }
+    }
+    return rc;
+}
+
+/* out = a * s mod q, coefficient by coefficient (a < q, any s) */
+void or_mul_scalar(u64 q, int N, const u64 *a, u64 s, u64 *out)
+{
+    s %= q;
+    for (int k = 0; k < N; k++) out[k] = mulmod(a[k], s, q);
+}
