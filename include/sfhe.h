@@ -300,6 +300,99 @@ sfhe_status sfhe_matmul_chunked_fused(sfhe_ctx* ctx, const sfhe_rotkeys* rk, int
                                       const uint8_t* b_zero, void* work, size_t work_bytes, void* stream,
                                       int64_t* products);
 
+/* ------------------------------------------------------------- CKKS --- */
+/* The scheme and parameter set the paper runs (Sec. 3.1): ring degree
+ * p = 8192, a coefficient modulus of 50, 40, 40 and 40 bits plus a 40-bit
+ * prime for key switching, initial scale 2^40; the chunked product of Alg. 1
+ * over it with its rescales.  (N = 64 is accepted for small tests.)
+ * Primes: per bit size, the largest primes below 2^bits that are 1 mod 2N,
+ * in the order of the list, the key-switching prime P last.  Slots: slot
+ * j < N/2 of a real-coefficient polynomial m is m(zeta^(3^j)), zeta =
+ * exp(i pi / N); X -> X^(3^k) turns the slots left by k (sfhe_rotation_element).
+ * Ciphertexts: [2][L][N] uint64, NTT form; at level l only limbs 0 .. l
+ * (primes q_0 .. q_l) are used.  Key switching (relinearisation, rotations)
+ * takes one digit per prime: digits D_j = [d]_{q_j}, the sum of D_j times
+ * key digit j over q_0 .. q_l and P, then the rounded division by P.  A key
+ * digit for w = s^2 or s(X^g) is (-a_j s + e_j + P g_j w, a_j), g_j = 1 mod
+ * q_j and 0 mod the other q_i.  Rescaling from level l: round(c / q_l) in
+ * every limb below l; the scale is divided by q_l.  Randomness: the secret
+ * from the same stream as the BFV context's (ternary, domain 1); encryption
+ * domains 11 / 12 with the stream object (matrix id, row, col); key
+ * domains 9 / 10 with objects (g, j, 0), g = 0 for relinearisation. */
+typedef struct {
+    uint32_t N;             /* 8192 (64 for tests) */
+    uint32_t L;             /* data primes, 3 .. 8 for the chunked product */
+    uint32_t bits[8];       /* their sizes, e.g. 50, 40, 40, 40 */
+    uint32_t special_bits;  /* the key-switching prime, e.g. 40 */
+    uint32_t log_scale;     /* initial scale 2^log_scale, e.g. 40 */
+    double sigma;           /* error width (3.2) */
+} sfhe_ckks_params;
+typedef struct sfhe_ckks_ctx sfhe_ckks_ctx;
+typedef struct sfhe_ckks_rotkeys sfhe_ckks_rotkeys;
+/* Primes, tables, the secret and the relinearisation key on the current
+ * device.  Synchronous.  Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA, EDEVICE. */
+sfhe_status sfhe_ckks_ctx_create(const sfhe_ckks_params* params, uint64_t seed, sfhe_ckks_ctx** out);
+void sfhe_ckks_ctx_destroy(sfhe_ckks_ctx* ctx);
+/* q[L] the data primes, *p the key-switching prime, *scale the initial scale (any may be NULL) */
+sfhe_status sfhe_ckks_ctx_primes(const sfhe_ckks_ctx* ctx, uint64_t* q, uint64_t* p, double* scale);
+/* Host only.  Encoding of n <= N/2 real values (the other slots 0) at
+ * `scale`: poly[k] = round((2 scale / N) sum_j values[j] cos(pi 3^j k / N))
+ * in double precision.  Decoding of a plaintext given as coefficient-form
+ * residues coeff[level + 1][N] (limbs of the primes q_0 .. q_level; the
+ * centred integer is rebuilt by CRT): values[j] = (1 / scale)
+ * sum_k m_k cos(pi 3^j k / N), j < n. */
+sfhe_status sfhe_ckks_encode(const sfhe_ckks_ctx* ctx, const double* values, int32_t n, double scale, int64_t* poly);
+sfhe_status sfhe_ckks_decode(const sfhe_ckks_ctx* ctx, const uint64_t* coeff, int32_t level, double scale, int32_t n,
+                             double* values);
+/* Secret-key encryption of n integer plaintext polynomials polys[n][N]
+ * (host) at the top level: c = (-a s + e + m, a); ct device [n][2][L][N]. */
+sfhe_status sfhe_ckks_encrypt(sfhe_ckks_ctx* ctx, const int64_t* polys, const int32_t* coords, int64_t n,
+                              uint64_t matrix_id, uint64_t* ct, void* stream);
+/* Decryption and decoding of n ciphertexts at `level`: values[n][slots]
+ * (host).  Synchronises `stream`. */
+sfhe_status sfhe_ckks_decrypt(sfhe_ckks_ctx* ctx, const uint64_t* ct, int32_t level, int64_t n, double scale,
+                              int32_t slots, double* values, void* stream);
+/* limbs 0 .. level of n ciphertexts to coefficient form (device [n][2][L][N], other limbs 0) */
+sfhe_status sfhe_ckks_to_coeff(sfhe_ckks_ctx* ctx, const uint64_t* ct, int32_t level, int64_t n, uint64_t* out,
+                               void* stream);
+/* Device workspace of one key switch (sfhe_ckks_rotate); sfhe_ckks_mul_relin
+ * needs L N words more, sfhe_ckks_rescale (2 n + 2 n level) N words. */
+sfhe_status sfhe_ckks_workspace_size(const sfhe_ckks_ctx* ctx, size_t* bytes);
+/* out = a x b relinearised, at `level` (out distinct from a and b) */
+sfhe_status sfhe_ckks_mul_relin(sfhe_ckks_ctx* ctx, const uint64_t* a, const uint64_t* b, int32_t level, uint64_t* out,
+                                void* work, size_t work_bytes, void* stream);
+/* n ciphertexts from `level` to level - 1 (in may equal out) */
+sfhe_status sfhe_ckks_rescale(sfhe_ckks_ctx* ctx, const uint64_t* in, int32_t level, int64_t n, uint64_t* out,
+                              void* work, size_t work_bytes, void* stream);
+/* Galois keys of the left and right turns by 1 .. c-1 (domains 9 / 10, object (g, j, 0)) */
+sfhe_status sfhe_ckks_rotkeys_create(sfhe_ckks_ctx* ctx, int32_t c, void* stream, sfhe_ckks_rotkeys** out);
+void sfhe_ckks_rotkeys_destroy(sfhe_ckks_rotkeys* rk);
+/* out = the slots of in turned left by k (right for k < 0), 0 < |k| < c; in, out distinct */
+sfhe_status sfhe_ckks_rotate(sfhe_ckks_ctx* ctx, const sfhe_ckks_rotkeys* rk, const uint64_t* in, int32_t level,
+                             int32_t k, uint64_t* out, void* work, size_t work_bytes, void* stream);
+/* A plaintext polynomial (host, signed coefficients) in NTT form over limbs
+ * 0 .. level: pt device [L][N].  Synchronous.  sfhe_ckks_mul_plain: ct[n]
+ * *= pt; sfhe_ckks_add: acc[n] += x[n]; both over limbs 0 .. level. */
+sfhe_status sfhe_ckks_plain_ntt(sfhe_ckks_ctx* ctx, const int64_t* poly, int32_t level, uint64_t* pt, void* stream);
+sfhe_status sfhe_ckks_mul_plain(sfhe_ckks_ctx* ctx, uint64_t* ct, int32_t level, int64_t n, const uint64_t* pt,
+                                void* stream);
+sfhe_status sfhe_ckks_add(sfhe_ckks_ctx* ctx, uint64_t* acc, const uint64_t* x, int32_t level, int64_t n, void* stream);
+/* The chunked product of Alg. 1 with chunk size rk->c: A holds ceil(M K / c)
+ * chunks at the top level (element e in slot e mod c of chunk e / c, scale
+ * D), B ceil(K Nc / c); C receives ceil(M Nc / c) chunks two levels lower at
+ * the scale *result_scale = D^2 / q_top.  Entry (i, j) is the sum over its
+ * products k of: the chunks holding A[i][k] and B[k][j] turned to slot 0,
+ * multiplied, relinearised, rescaled; times the slot-0 mask encoded at the
+ * scale q_{top-1}; rescaled; turned right to (i Nc + j) mod c.  (Alg. 1's
+ * relinearisation after the mask product has nothing to do with a
+ * plaintext.)  a_zero / b_zero (host, may be NULL): the naive sparse masks.
+ * Workspace from the size call. */
+sfhe_status sfhe_ckks_matmul_chunked_workspace_size(const sfhe_ckks_ctx* ctx, size_t* bytes);
+sfhe_status sfhe_ckks_matmul_chunked(sfhe_ckks_ctx* ctx, const sfhe_ckks_rotkeys* rk, int32_t M, int32_t K, int32_t Nc,
+                                     const uint64_t* A, const uint64_t* B, uint64_t* C, const uint8_t* a_zero,
+                                     const uint8_t* b_zero, void* work, size_t work_bytes, void* stream,
+                                     int64_t* products, double* result_scale);
+
 /* Measured rate of the 32-bit Shoup modular multiply a w mod b (three
  * 32-bit multiplies: the high product with the precomputed companion and two
  * low products; the butterfly multiply of the tensor stage's inverse NTTs)

@@ -48,6 +48,11 @@ class sfhe_matrix_view(ctypes.Structure):
                 ("ell_col", ctypes.c_void_p), ("ct", ctypes.c_void_p), ("ext", ctypes.c_void_p)]
 
 
+class sfhe_ckks_params(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_uint32), ("L", ctypes.c_uint32), ("bits", ctypes.c_uint32 * 8),
+                ("special_bits", ctypes.c_uint32), ("log_scale", ctypes.c_uint32), ("sigma", ctypes.c_double)]
+
+
 _vp, _u32, _u64, _i32, _i64, _sz = (ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32,
                                      ctypes.c_int64, ctypes.c_size_t)
 _P = ctypes.POINTER
@@ -132,6 +137,27 @@ _SIGS = {
     "sfhe_matmul_host": ([_vp, _P(_vp), _P(_vp), _P(_vp), _vp], ctypes.c_int),
     "sfhe_host_plan_stats": ([_vp, _P(_i64), _P(_u64), _P(_u64), _P(_i64)], ctypes.c_int),
     "sfhe_host_plan_destroy": ([_vp], None),
+    # CKKS
+    "sfhe_ckks_ctx_create": ([_P(sfhe_ckks_params), _u64, _P(_vp)], ctypes.c_int),
+    "sfhe_ckks_ctx_destroy": ([_vp], None),
+    "sfhe_ckks_ctx_primes": ([_vp, _vp, _P(_u64), _P(ctypes.c_double)], ctypes.c_int),
+    "sfhe_ckks_encode": ([_vp, _vp, _i32, ctypes.c_double, _vp], ctypes.c_int),
+    "sfhe_ckks_decode": ([_vp, _vp, _i32, ctypes.c_double, _i32, _vp], ctypes.c_int),
+    "sfhe_ckks_encrypt": ([_vp, _vp, _vp, _i64, _u64, _vp, _vp], ctypes.c_int),
+    "sfhe_ckks_decrypt": ([_vp, _vp, _i32, _i64, ctypes.c_double, _i32, _vp, _vp], ctypes.c_int),
+    "sfhe_ckks_to_coeff": ([_vp, _vp, _i32, _i64, _vp, _vp], ctypes.c_int),
+    "sfhe_ckks_workspace_size": ([_vp, _P(_sz)], ctypes.c_int),
+    "sfhe_ckks_mul_relin": ([_vp, _vp, _vp, _i32, _vp, _vp, _sz, _vp], ctypes.c_int),
+    "sfhe_ckks_rescale": ([_vp, _vp, _i32, _i64, _vp, _vp, _sz, _vp], ctypes.c_int),
+    "sfhe_ckks_rotkeys_create": ([_vp, _i32, _vp, _P(_vp)], ctypes.c_int),
+    "sfhe_ckks_rotkeys_destroy": ([_vp], None),
+    "sfhe_ckks_rotate": ([_vp, _vp, _vp, _i32, _i32, _vp, _vp, _sz, _vp], ctypes.c_int),
+    "sfhe_ckks_plain_ntt": ([_vp, _vp, _i32, _vp, _vp], ctypes.c_int),
+    "sfhe_ckks_mul_plain": ([_vp, _vp, _i32, _i64, _vp, _vp], ctypes.c_int),
+    "sfhe_ckks_add": ([_vp, _vp, _vp, _i32, _i64, _vp], ctypes.c_int),
+    "sfhe_ckks_matmul_chunked_workspace_size": ([_vp, _P(_sz)], ctypes.c_int),
+    "sfhe_ckks_matmul_chunked": ([_vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp, _P(_i64),
+                                  _P(ctypes.c_double)], ctypes.c_int),
 }
 
 _lib = None
@@ -606,3 +632,116 @@ def sfhe_host_plan_stats(hp: int) -> dict:
 
 def sfhe_host_plan_destroy(hp: int) -> None:
     lib().sfhe_host_plan_destroy(hp)
+
+
+# ------------------------------------------------------------------- CKKS ---
+def _nbytes(t) -> int:
+    return t.numel() * t.element_size()
+
+
+def sfhe_ckks_ctx_create(N: int = 8192, bits=(50, 40, 40, 40), special_bits: int = 40, log_scale: int = 40,
+                         sigma: float = 3.2, seed: int = 0) -> int:
+    b = (ctypes.c_uint32 * 8)(*list(bits))
+    h = ctypes.c_void_p()
+    _check(lib().sfhe_ckks_ctx_create(ctypes.byref(sfhe_ckks_params(N, len(bits), b, special_bits, log_scale, sigma)),
+                                      seed, ctypes.byref(h)))
+    return h.value
+
+
+def sfhe_ckks_ctx_destroy(ctx: int) -> None:
+    lib().sfhe_ckks_ctx_destroy(ctx)
+
+
+def sfhe_ckks_ctx_primes(ctx: int, L: int) -> tuple[list[int], int, float]:
+    q = np.zeros(8, dtype=np.uint64)
+    p, sc = ctypes.c_uint64(), ctypes.c_double()
+    _check(lib().sfhe_ckks_ctx_primes(ctx, _ptr(q), ctypes.byref(p), ctypes.byref(sc)))
+    return [int(x) for x in q[:L]], p.value, sc.value
+
+
+def sfhe_ckks_encode(ctx: int, N: int, values, scale: float) -> np.ndarray:
+    v = np.ascontiguousarray(np.asarray(values, dtype=np.float64))
+    out = np.zeros(N, dtype=np.int64)
+    _check(lib().sfhe_ckks_encode(ctx, _ptr(v) if v.size else None, v.size, scale, _ptr(out)))
+    return out
+
+
+def sfhe_ckks_decode(ctx: int, coeff: np.ndarray, level: int, scale: float, n: int) -> np.ndarray:
+    c = np.ascontiguousarray(coeff, dtype=np.uint64)
+    out = np.zeros(max(n, 1), dtype=np.float64)
+    _check(lib().sfhe_ckks_decode(ctx, _ptr(c), level, scale, n, _ptr(out)))
+    return out[:n]
+
+
+def sfhe_ckks_encrypt(ctx: int, polys: np.ndarray, coords: np.ndarray, matrix_id: int, ct, stream=None) -> None:
+    p = np.ascontiguousarray(polys, dtype=np.int64)
+    c = np.ascontiguousarray(coords, dtype=np.int32)
+    _check(lib().sfhe_ckks_encrypt(ctx, _ptr(p), _ptr(c), p.shape[0], matrix_id, _ptr(ct), _stream(stream)))
+
+
+def sfhe_ckks_decrypt(ctx: int, ct, level: int, n: int, scale: float, slots: int, stream=None) -> np.ndarray:
+    out = np.zeros((max(n, 1), max(slots, 1)), dtype=np.float64)
+    _check(lib().sfhe_ckks_decrypt(ctx, _ptr(ct), level, n, scale, slots, _ptr(out), _stream(stream)))
+    return out[:n, :slots]
+
+
+def sfhe_ckks_to_coeff(ctx: int, ct, level: int, n: int, out, stream=None) -> None:
+    _check(lib().sfhe_ckks_to_coeff(ctx, _ptr(ct), level, n, _ptr(out), _stream(stream)))
+
+
+def sfhe_ckks_workspace_size(ctx: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().sfhe_ckks_workspace_size(ctx, ctypes.byref(b)))
+    return b.value
+
+
+def sfhe_ckks_mul_relin(ctx: int, a, b, level: int, out, work, stream=None) -> None:
+    _check(lib().sfhe_ckks_mul_relin(ctx, _ptr(a), _ptr(b), level, _ptr(out), _ptr(work), _nbytes(work),
+                                     _stream(stream)))
+
+
+def sfhe_ckks_rescale(ctx: int, inp, level: int, n: int, out, work, stream=None) -> None:
+    _check(lib().sfhe_ckks_rescale(ctx, _ptr(inp), level, n, _ptr(out), _ptr(work), _nbytes(work), _stream(stream)))
+
+
+def sfhe_ckks_rotkeys_create(ctx: int, c: int, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().sfhe_ckks_rotkeys_create(ctx, c, _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def sfhe_ckks_rotkeys_destroy(rk: int) -> None:
+    lib().sfhe_ckks_rotkeys_destroy(rk)
+
+
+def sfhe_ckks_rotate(ctx: int, rk: int, inp, level: int, k: int, out, work, stream=None) -> None:
+    _check(lib().sfhe_ckks_rotate(ctx, rk, _ptr(inp), level, k, _ptr(out), _ptr(work), _nbytes(work),
+                                  _stream(stream)))
+
+
+def sfhe_ckks_plain_ntt(ctx: int, poly, level: int, pt, stream=None) -> None:
+    p = np.ascontiguousarray(np.asarray(poly, dtype=np.int64))
+    _check(lib().sfhe_ckks_plain_ntt(ctx, _ptr(p), level, _ptr(pt), _stream(stream)))
+
+
+def sfhe_ckks_mul_plain(ctx: int, ct, level: int, n: int, pt, stream=None) -> None:
+    _check(lib().sfhe_ckks_mul_plain(ctx, _ptr(ct), level, n, _ptr(pt), _stream(stream)))
+
+
+def sfhe_ckks_add(ctx: int, acc, x, level: int, n: int, stream=None) -> None:
+    _check(lib().sfhe_ckks_add(ctx, _ptr(acc), _ptr(x), level, n, _stream(stream)))
+
+
+def sfhe_ckks_matmul_chunked_workspace_size(ctx: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().sfhe_ckks_matmul_chunked_workspace_size(ctx, ctypes.byref(b)))
+    return b.value
+
+
+def sfhe_ckks_matmul_chunked(ctx: int, rk: int, M: int, K: int, Nc: int, A, B, C, a_zero, b_zero, work,
+                             stream=None) -> tuple[int, float]:
+    n, sc = ctypes.c_int64(), ctypes.c_double()
+    _check(lib().sfhe_ckks_matmul_chunked(ctx, rk, M, K, Nc, _ptr(A), _ptr(B), _ptr(C), _ptr(a_zero), _ptr(b_zero),
+                                          _ptr(work), _nbytes(work), _stream(stream), ctypes.byref(n),
+                                          ctypes.byref(sc)))
+    return n.value, sc.value
