@@ -69,7 +69,8 @@ def parse():
     ap.add_argument("--ring", default=None, help="N,L override of the sweep ring (small profiling cases, ints in "
                                                  "[-8, 8] at N = 16384)")
     ap.add_argument("--tile", type=int, default=-1, help="stage-S tile of the persistent kernel (default: tuned)")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "tiny", "layer", "mixed", "serve", "chunked"])
+    ap.add_argument("--workload", default="sweep",
+                    choices=["sweep", "tiny", "layer", "mixed", "serve", "chunked", "ckks"])
     ap.add_argument("--chunk", type=int, default=8, help="chunked: values per ciphertext (Alg. 1 with c > 1)")
     ap.add_argument("--chunked-shape", default="16,16,16", help="chunked: M,K,Nc")
     ap.add_argument("--alg1-order", action="store_true",
@@ -401,6 +402,9 @@ def main():
     if args.workload == "chunked":
         run_chunked(args)
         return
+    if args.workload == "ckks":
+        run_ckks(args)
+        return
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -632,6 +636,66 @@ def run_chunked(args):
     print(json.dumps(line))
     rk.close()
     ctx.close()
+
+
+def run_ckks(args):
+    """The chunked product of Alg. 1 under the paper's CKKS parameter set
+    (N = 8192, primes of 50, 40, 40, 40 bits and a 40-bit key-switching
+    prime, scale 2^40): per product two turns into slot 0, multiply +
+    relinearise, rescale, the slot-0 mask, rescale, the turn to the result
+    offset, add; A 50% zeros, products where A or B is zero skipped."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2503_09184_gb300 import sfhe as S
+    M, K, Nc = (int(x) for x in args.chunked_shape.split(","))
+    c = args.chunk
+    A, B = W.operands(W.MatmulShape(M, K, Nc, 0.5, -16, 16, 7))
+    h = S.sfhe_ckks_ctx_create(N=8192, seed=0)
+    q, P, scale = S.sfhe_ckks_ctx_primes(h, 4)
+    stream = torch.cuda.current_stream()
+
+    def chunks(Mv, mid):
+        flat = Mv.reshape(-1).astype(np.float64)
+        n = -(-flat.size // c)
+        polys = np.stack([S.sfhe_ckks_encode(h, 8192, flat[k * c:(k + 1) * c], scale) for k in range(n)])
+        ct = torch.empty((n, 2, 4, 8192), dtype=torch.int64, device="cuda")
+        S.sfhe_ckks_encrypt(h, polys, np.array([[k, 0] for k in range(n)], dtype=np.int32), mid, ct)
+        return ct
+    Ag, Bg = chunks(A, 1), chunks(B, 2)
+    nC = -(-(M * Nc) // c)
+    C = torch.empty((nC, 2, 4, 8192), dtype=torch.int64, device="cuda")
+    rk = S.sfhe_ckks_rotkeys_create(h, c)
+    work = torch.empty(S.sfhe_ckks_matmul_chunked_workspace_size(h), dtype=torch.uint8, device="cuda")
+    az, bz = (A == 0).astype(np.uint8).reshape(-1), (B == 0).astype(np.uint8).reshape(-1)
+    for _ in range(args.warmup):
+        products, rscale = S.sfhe_ckks_matmul_chunked(h, rk, M, K, Nc, Ag, Bg, C, az, bz, work)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        products, rscale = S.sfhe_ckks_matmul_chunked(h, rk, M, K, Nc, Ag, Bg, C, az, bz, work)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    vals = S.sfhe_ckks_decrypt(h, C, 1, nC, rscale, c).reshape(-1)[:M * Nc].reshape(M, Nc)
+    err = float(np.max(np.abs(vals - A @ B)))
+    line = {"metric": METRIC, "value": products / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"ckks-chunked-{M}x{K}x{Nc}-c{c}-s0.5", "N": 8192, "primes_bits": [50, 40, 40, 40],
+                       "special_bits": 40, "scale": scale, "chunk": c, "products_per_step": products,
+                       "step": "Alg. 1 under CKKS, term by term: 2 turns, multiply + relinearise, rescale, "
+                               "slot-0 mask, rescale, turn to the offset, add"},
+            "max_abs_error": err, "correct": err < 1e-2, "e2e": None, "roofline": None, "clocks": clk,
+            "note": "the paper's scheme and parameter set; approximate arithmetic, error against A B reported"}
+    print(json.dumps(line))
+    S.sfhe_ckks_rotkeys_destroy(rk)
+    S.sfhe_ckks_ctx_destroy(h)
 
 
 def run_serve(args):
