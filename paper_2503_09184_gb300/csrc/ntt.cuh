@@ -32,12 +32,14 @@
 
 struct Arith64 {
     using W = u64;
+    template <bool LEAN>
     SFHE_DEV static void fwd(W& X, W& Y, W w, W ws, W q)
     {
         const W T = shoup_lazy(Y, w, ws, q);
         Y = X - T + 2 * q;
         X = X + T;
     }
+    template <bool LEAN>
     SFHE_DEV static void inv(W& X, W& Y, W w, W ws, W q)
     {
         const W s = X + Y;
@@ -55,18 +57,24 @@ struct Arith64 {
 
 struct Arith32 {
     using W = u32;
+    // LEAN: min(s, s - 2b) reduces s < 4b to [0, 2b) (below 2b the
+    // difference wraps above 2^31 > s); otherwise a compare and select
+    SFHE_DEV static W red2(W s, W b) { return s >= 2 * b ? s - 2 * b : s; }
+    SFHE_DEV static W red2_lean(W s, W b) { return min(s, s - 2 * b); }
+    template <bool LEAN>
     SFHE_DEV static void fwd(W& X, W& Y, W w, W ws, W b)
     {
-        const W X1 = X >= 2 * b ? X - 2 * b : X;
+        const W X1 = LEAN ? red2_lean(X, b) : red2(X, b);
         const W T = shoup32_lazy(Y, w, ws, b);
         Y = X1 - T + 2 * b;
         X = X1 + T;
     }
+    template <bool LEAN>
     SFHE_DEV static void inv(W& X, W& Y, W w, W ws, W b)
     {
         const W s = X + Y;
         const W d = X - Y + 2 * b;
-        X = s >= 2 * b ? s - 2 * b : s;
+        X = LEAN ? red2_lean(s, b) : red2(s, b);
         Y = shoup32_lazy(d, w, ws, b);
     }
     SFHE_DEV static void inv_last(W& X, W& Y, W ni, W nis, W wl, W wls, W b)
@@ -88,6 +96,11 @@ struct NttT {
     static constexpr int NFULL = LOGN / LOGR;
     static constexpr int REM = LOGN % LOGR;
     static constexpr bool SWIZZLE = sizeof(W) == 4;
+    // Lean forms (exchange addresses as a base and per-slot constants, the
+    // 32-bit reductions by an unsigned minimum): measured faster inside the
+    // persistent kernel at N = 16384 and slower at N = 8192, where the
+    // kernel sits at the register limit; so they are taken from N = 16384.
+    static constexpr bool LEAN = LOGN >= 14;
     static constexpr int SMEM_WORDS = SWIZZLE ? N : N + (N >> LOGR);
     static_assert(!SWIZZLE || LOGR == 4 || LOGR == 5, "swizzle defined for R = 16 and 32");
 
@@ -127,17 +140,30 @@ struct NttT {
         else return idx<(NFULL - 1) * LOGR, LOGR>(v, tid);
     }
 
+    // Exchange addresses.  idx(v, tid) places the bits of v and of tid in
+    // disjoint fields, so idx(v, tid) = idx(0, tid) | idx(v, 0); the swizzle
+    // is XOR-linear and the padding additive on disjoint fields, so the word
+    // of slot v is the thread's base word combined with a per-slot constant:
+    // one XOR per slot (swizzled) or an immediate offset (padded).
+    template <int S, int RR>
+    SFHE_DEV static int slot_addr(int base, int v)
+    {
+        if constexpr (SWIZZLE) return base ^ pad(idx<S, RR>(v, 0));
+        else return base + pad(idx<S, RR>(v, 0));
+    }
     template <int S, int RR>
     SFHE_DEV static void store(const W (&x)[R], W* sm, int tid)
     {
+        const int base = pad(idx<S, RR>(0, tid));
 #pragma unroll
-        for (int v = 0; v < R; v++) sm[pad(idx<S, RR>(v, tid))] = x[v];
+        for (int v = 0; v < R; v++) sm[LEAN ? slot_addr<S, RR>(base, v) : pad(idx<S, RR>(v, tid))] = x[v];
     }
     template <int S, int RR>
     SFHE_DEV static void load(W (&x)[R], const W* sm, int tid)
     {
+        const int base = pad(idx<S, RR>(0, tid));
 #pragma unroll
-        for (int v = 0; v < R; v++) x[v] = sm[pad(idx<S, RR>(v, tid))];
+        for (int v = 0; v < R; v++) x[v] = sm[LEAN ? slot_addr<S, RR>(base, v) : pad(idx<S, RR>(v, tid))];
     }
 
     // The C twiddles (and Shoup companions) at w[ti0 .. ti0+C-1]; ti0 is a
@@ -199,7 +225,7 @@ struct NttT {
 #pragma unroll
                         for (int r = 0; r < h; r++) {
                             const int v = (g << RR) + ((t0 + t) << (RR - D)) + r;
-                            A::fwd(x[v], x[v + h], wv[t], wsv[t], q);
+                            A::template fwd<LEAN>(x[v], x[v + h], wv[t], wsv[t], q);
                         }
                     }
                 }
@@ -332,7 +358,7 @@ struct NttT {
                                 if constexpr (LAST && D == RR - 1)
                                     A::inv_last(x[j][v], x[j][v + (1 << D)], ni, nis, wl, wls, q);
                                 else
-                                    A::inv(x[j][v], x[j][v + (1 << D)], wv[t], wsv[t], q);
+                                    A::template inv<LEAN>(x[j][v], x[j][v + (1 << D)], wv[t], wsv[t], q);
                             }
                         }
                     }
