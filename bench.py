@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--serve-dims", default="16,32,64", help="serve: M, K, Nc drawn from these")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: HBM ciphertext budget")
     ap.add_argument("--wave-products", type=int, default=40000, help="serve: products per wave")
+    ap.add_argument("--preempt", action="store_true",
+                    help="serve: a new arrival stops the running wave, whose rows resume after the newcomer's")
     ap.add_argument("--serve-set", default="poisson", choices=["poisson", "mixed64"],
                     help="serve: Poisson requests, or the 64 matmuls of the mixed workload arriving at once")
     ap.add_argument("--sparsity", type=float, default=None, help="sweep / layer sparsity (default 0.5)")
@@ -727,19 +729,21 @@ def run_serve(args):
     plain_rate = plan.stats["products"] / (time.perf_counter() - t0)
     plan.close()
     # warm-up of the served path
-    SV.serve(serve_requests(args, 100.0, 99)[:2], SV.GpuExecutor(ctx, lazy=args.lazy,
-                                                                  wave_products=args.wave_products),
+    preempt = args.preempt
+    SV.serve(serve_requests(args, 100.0, 99)[:2], SV.GpuExecutor(ctx, lazy=args.lazy, wave_products=args.wave_products,
+                                                                  preempt=preempt),
              budget, args.wave_products,
              ct_b, ext_b)
     sweep = []
     rates = [0.0] if args.serve_set == "mixed64" else [float(x) for x in args.rates.split(",")]
     for n, rate in enumerate(rates):
         reqs = serve_requests(args, rate, seed=10 + n)
-        ex = SV.GpuExecutor(ctx, lazy=args.lazy, wave_products=args.wave_products)
+        ex = SV.GpuExecutor(ctx, lazy=args.lazy, wave_products=args.wave_products, preempt=preempt)
         out = SV.serve(reqs, ex, budget, args.wave_products, ct_b, ext_b)
         plain = SV.fifo_plain_model(reqs, lambda r: ex.admit_s.get(r.rid, 0.0) + r.products / plain_rate)
         sweep.append({"rate_per_s": rate, "requests": out["requests"], "done": out["done"],
                       "rejected": out["rejected"], "products": out["products"], "waves": out["waves"],
+                      "waves_stopped": out["waves_stopped"],
                       "ct_mults_per_s": out["ct_mults_per_s"], "busy_ct_mults_per_s": out["products"] / out["busy_s"],
                       "p50_s": out["p50_s"], "p99_s": out["p99_s"], "makespan_s": out["makespan_s"],
                       "busy_s": out["busy_s"], "admission_s": sum(ex.admit_s.values()),
@@ -755,7 +759,7 @@ def run_serve(args):
                                     if args.serve_set == "poisson" else f"mixed64-waves-N{ring.N}-L{ring.L}")
                                    + ("-lazy" if args.lazy else ""),
                        "N": ring.N, "L": ring.L, "t": W.T_PLAIN, "budget_gb": args.budget_gb,
-                       "wave_products": args.wave_products, "requests_per_rate": args.requests,
+                       "wave_products": args.wave_products, "preempt": preempt, "requests_per_rate": args.requests,
                        "dims": args.serve_dims, "sparsity": "U[0.30, 0.95]"},
             "plain_rate_ct_mults_per_s": plain_rate,
             "serving": sweep,

@@ -559,6 +559,27 @@ sfhe_status sfhe_plan_execute(sfhe_plan* plan, void* stream);
  * waits for an operand copy ran out (the kernel then stopped early and C is
  * incomplete). */
 sfhe_status sfhe_matmul_check(void* work, void* stream);
+/* Preemption of a persistent plan: the serving loop's continuous admission
+ * (a request that arrives while a plan runs need not wait for the whole
+ * launch; the paper's Sec. 3.4 runs one matmul at a time and has no
+ * counterpart).
+ * sfhe_plan_set_stop: `word` is the device address of one uint32 (NULL
+ * clears it), which the caller owns and writes, e.g. with a copy on another
+ * stream while the launch runs.  Every CTA of the plan's persistent launches
+ * reads it before it takes its next output entry and takes none once it is
+ * nonzero; no CTA waits on it, so a launch ends within one entry's time of
+ * the word being set, the entries it took complete, C of the others is
+ * untouched.  Errors: EINVAL (null plan, a PLAIN or GRAPH plan, misaligned).
+ * sfhe_plan_progress: synchronises `stream` and reports how many output
+ * entries, in the plan's execution order, the launches so far completed
+ * (all of them after an execution that was not stopped).
+ * sfhe_plan_resume: launches the plan again from its first entry not taken
+ * (clear the word first); a stopped execution plus its resumptions write
+ * the same C, limb for limb, as one execution.  sfhe_plan_execute restarts
+ * from the first entry.  Errors: EINVAL (null plan, a PLAIN plan), ECUDA. */
+sfhe_status sfhe_plan_set_stop(sfhe_plan* plan, const uint32_t* word);
+sfhe_status sfhe_plan_progress(const sfhe_plan* plan, int64_t* done, void* stream);
+sfhe_status sfhe_plan_resume(sfhe_plan* plan, void* stream);
 /* Self-test of the bounded device waits (no fault is involved): one thread
  * waits on an mbarrier that nothing arrives at, gives up after `tries`
  * attempts (1 .. 2^30) or `limit_us` microseconds of the GPU's clock

@@ -119,6 +119,7 @@ struct sfhe_plan {
     cudaGraph_t graph;
     cudaGraphExec_t gexec;
     int variant;  // tile variant of the persistent kernel
+    const unsigned* d_stop;  // preemption word of the persistent launches (nullable)
 };
 
 extern "C" const char* sfhe_last_error(void) { return g_last_error.c_str(); }
@@ -739,6 +740,7 @@ PersistentArgs persistent_args(const sfhe_plan* P, int n_entries, int variant)
     a.scratch = P->d_scratch;
     a.scratch_stride = P->scratch_stride;
     a.queue = P->d_queue;
+    a.stop = P->d_stop;
     a.grid = P->grid;
     a.grouped = (P->flags & SFHE_EXEC_LAZY) != 0;
     a.variant = a.grouped ? 0 : variant;
@@ -859,6 +861,7 @@ static sfhe_status plan_create_impl(sfhe_ctx* c, int32_t n, const sfhe_matrix_vi
     P->flags = flags;
     P->graph = nullptr;
     P->gexec = nullptr;
+    P->d_stop = nullptr;
     st = build(c, n, A, B, C, dense_loop, *P);
     if (st != SFHE_OK) {
         delete P;
@@ -948,6 +951,39 @@ extern "C" sfhe_status sfhe_plan_execute(sfhe_plan* P, void* stream)
     Range range("sfhe_plan_execute");
     if (!P) return fail(SFHE_EINVAL, "null plan");
     return launch_plan(P, as_stream(stream));
+}
+
+extern "C" sfhe_status sfhe_plan_set_stop(sfhe_plan* P, const uint32_t* word)
+{
+    if (!P) return fail(SFHE_EINVAL, "null plan");
+    if (!(P->flags & SFHE_EXEC_PERSISTENT)) return fail(SFHE_EINVAL, "a stop word needs a PERSISTENT plan");
+    if (P->gexec) return fail(SFHE_EINVAL, "a stop word cannot be set on a GRAPH plan (its launch is captured)");
+    if (reinterpret_cast<uintptr_t>(word) % alignof(uint32_t)) return fail(SFHE_EINVAL, "misaligned stop word");
+    P->d_stop = reinterpret_cast<const unsigned*>(word);
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_plan_progress(const sfhe_plan* P, int64_t* done, void* stream)
+{
+    if (!P || !done) return fail(SFHE_EINVAL, "null argument");
+    if (!(P->flags & SFHE_EXEC_PERSISTENT)) return fail(SFHE_EINVAL, "progress is kept by PERSISTENT plans");
+    CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
+    unsigned taken = 0;
+    CUDA_TRY(cudaMemcpy(&taken, P->d_queue, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    *done = std::min<int64_t>((int64_t)taken, (int64_t)P->entries.size());
+    return SFHE_OK;
+}
+
+extern "C" sfhe_status sfhe_plan_resume(sfhe_plan* P, void* stream)
+{
+    Range range("sfhe_plan_resume");
+    if (!P) return fail(SFHE_EINVAL, "null plan");
+    if (!(P->flags & SFHE_EXEC_PERSISTENT)) return fail(SFHE_EINVAL, "only PERSISTENT plans resume");
+    // the entry counter is left as the stopped launch left it: the entries
+    // below it are complete, the rest are taken from it on
+    if (P->entries.empty()) return SFHE_OK;
+    CUDA_TRY(launch_persistent(P->ctx->rc, persistent_args(P, (int)P->entries.size(), P->variant), as_stream(stream)));
+    return SFHE_OK;
 }
 
 extern "C" sfhe_status sfhe_selftest_wait_bound(void* work, uint32_t tries, uint32_t limit_us, void* stream)

@@ -680,7 +680,7 @@ template <int LOGN, int L, bool GROUPED, int V>
 __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
     const __grid_constant__ RnsConsts c, const MmDesc* __restrict__ mms, const Entry* __restrict__ entries, int n_entries,
     const int2* __restrict__ rowlist, const u64* __restrict__ rlk, const u64* __restrict__ rlk_sh, u64* scratch,
-    size_t scratch_stride, unsigned* queue)
+    size_t scratch_stride, unsigned* queue, const unsigned* stop)
 {
     using CF = Cfg<LOGN, L>;
     using NQ = typename CF::NQ;
@@ -733,7 +733,12 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
 
     for (;;) {
         __syncthreads();
-        if (tid == 0) s_entry = (int)atomicAdd(queue, 1u);
+        // a set stop word ends the launch at this entry boundary: the CTA
+        // takes no entry (it is never waited on), so queue[0] stays the
+        // number of entries taken and a later launch resumes from there
+        if (tid == 0)
+            s_entry = (stop && *reinterpret_cast<const volatile unsigned*>(stop)) ? n_entries
+                                                                                   : (int)atomicAdd(queue, 1u);
         __syncthreads();
         const int e = s_entry;
         if (e >= n_entries) break;

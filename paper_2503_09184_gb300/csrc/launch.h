@@ -51,6 +51,7 @@ struct PersistentArgs {
     u64* scratch;
     size_t scratch_stride;
     unsigned* queue;
+    const unsigned* stop;  // nullable: once *stop != 0, no CTA takes another entry
     int grid;
     bool grouped;
     int variant;

@@ -64,7 +64,7 @@ static cudaError_t launch_instance(const RnsConsts& rc, const PersistentArgs& a,
         cfg.numAttrs = 1;
     }
     return cudaLaunchKernelEx(&cfg, kern, rc, a.mms, a.entries, a.n_entries, a.rowlist, a.rlk, a.rlk_sh, a.scratch,
-                              a.scratch_stride, a.queue);
+                              a.scratch_stride, a.queue, a.stop);
 }
 
 template <int LOGN, int L>

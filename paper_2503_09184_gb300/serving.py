@@ -12,9 +12,13 @@ rejected.  Work runs in waves: a
 wave is one persistent launch (a batch plan) over row blocks taken in turn
 from every admitted request, up to a product budget, so requests that
 arrive while others are on the GPU join the next wave and their products
-overlap with those already running.  Every output entry is computed by
-exactly one wave from its own products, so a request's result is the same
-limb for limb alone and in any mix.
+overlap with those already running.  With preemption (GpuExecutor's
+preempt) a request that arrives while a wave runs stops that wave at its
+next output-entry boundary (the plan's stop word): the newcomer is admitted,
+a wave over its rows runs, and the stopped wave resumes from its first entry
+not taken.  Every output entry is computed by exactly one wave from its own
+products, so a request's result is the same limb for limb alone and in any
+mix, stopped or not.
 
 `Scheduler` is the host-side policy (admission, row blocks, completion);
 `GpuExecutor` carries it out through the C ABI.
@@ -138,12 +142,13 @@ class Scheduler:
             out.append(req)
         return out
 
-    def next_wave(self) -> list[tuple[Request, int, int]]:
+    def next_wave(self, only=None) -> list[tuple[Request, int, int]]:
         """row blocks (request, r0, r1) of the next wave: whole rows, taken in
         turn from every running request (starting one further each wave) until
         the wave's product budget is reached; every request with rows left
-        gets at least one row."""
-        live = [r for r in self.running if r.next_row < r.rows]
+        gets at least one row.  only: take rows of these requests alone."""
+        keep = None if only is None else {id(r) for r in only}
+        live = [r for r in self.running if r.next_row < r.rows and (keep is None or id(r) in keep)]
         if not live:
             return []
         k = self._turn % len(live)
@@ -188,20 +193,36 @@ class Scheduler:
         return not self.queue and not self.running
 
 
+@dataclasses.dataclass
+class Wave:
+    """one persistent launch over row blocks, possibly stopped and resumed"""
+    blocks: list
+    products: int
+    entries: int = 0
+    plan: int = 0
+    work: object = None
+    slot: int = 0
+    events: list = dataclasses.field(default_factory=list)
+
+
 class GpuExecutor:
     """Device side: encryption and lift on admission, one persistent batch
     plan per wave over CSR row blocks of A (and the matching rows of C).
 
-    One matmul workspace, sized for the largest wave (wave_products products
-    over as many output entries, up to max_blocks row blocks), is allocated
-    once and reused by every wave; its bytes (reserved_bytes) come out of
-    the HBM budget before any request is admitted.  setup_s and kernel_s
-    add up the waves' plan set-up (work-list build and upload) and their
-    persistent launches."""
+    Matmul workspaces, each sized for the largest wave (wave_products
+    products over as many output entries, up to max_blocks row blocks), are
+    allocated once and reused: one, or two with preempt (a stopped wave keeps
+    its plan and workspace while the wave that stopped it runs).  Their bytes
+    (reserved_bytes) come out of the HBM budget before any request is
+    admitted.  setup_s and kernel_s add up the waves' plan set-up (work-list
+    build and upload) and their persistent launches."""
 
-    def __init__(self, ctx, stream=None, lazy: bool = False, wave_products: int = 40000, max_blocks: int = 1024):
+    def __init__(self, ctx, stream=None, lazy: bool = False, wave_products: int = 40000, max_blocks: int = 1024,
+                 preempt: bool = False):
         """lazy: run the waves in the grouped accumulate-then-round mode
-        (SFHE_EXEC_LAZY) instead of the per-product order."""
+        (SFHE_EXEC_LAZY) instead of the per-product order.  preempt: waves
+        can be stopped by a new arrival (the serving loop then runs a wave
+        for the newcomer and resumes the stopped one)."""
         import torch
         from . import api, sfhe as S
         self.ctx, self.api, self.S, self.torch = ctx, api, S, torch
@@ -211,10 +232,19 @@ class GpuExecutor:
         self.a_cache = {}
         self.admit_s = {}
         self.max_blocks = max_blocks
+        self.preempt = preempt
         n = S.sfhe_matmul_workspace_bound(ctx.h, max_blocks, wave_products, wave_products, self.flags)
-        self.work = torch.empty(n, dtype=torch.uint8, device="cuda")
-        self.reserved_bytes = n
+        self.works = [torch.empty(n, dtype=torch.uint8, device="cuda") for _ in range(2 if preempt else 1)]
+        self.free = list(range(len(self.works)))
+        self.reserved_bytes = n * len(self.works)
+        if preempt:
+            # the stop word (device) and its set value (pinned host), written
+            # on a side stream while a wave runs
+            self.stop = torch.zeros(1, dtype=torch.int32, device="cuda")
+            self.one = torch.ones(1, dtype=torch.int32, pin_memory=True)
+            self.side = torch.cuda.Stream()
         self.setup_s, self.kernel_s = 0.0, 0.0
+        self.stops = 0
 
     def admit(self, req: Request):
         """encrypt and lift the request's operands on the device (the client's
@@ -247,28 +277,75 @@ class GpuExecutor:
                            ct=C.ct[r0 * C.cols:r1 * C.cols])
         return Ab, B, Cb
 
-    def run_wave(self, blocks) -> int:
-        """one persistent launch over the blocks; returns the products run."""
+    def _launch(self, w: Wave, resume: bool):
+        torch, S = self.torch, self.S
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
+        (S.sfhe_plan_resume if resume else S.sfhe_plan_execute)(w.plan, self.stream)
+        e1.record(self.stream)
+        w.events.append((e0, e1))
+
+    def start_wave(self, blocks) -> Wave:
+        """build the wave's plan and launch it (returns at once)."""
         api, S, torch = self.api, self.S, self.torch
         t0 = time.perf_counter()
         parts = [self._rows(req, r0, r1) for req, r0, r1 in blocks]
         As, Bs, Cs = [p[0] for p in parts], [p[1] for p in parts], [p[2] for p in parts]
+        slot = self.free.pop(0)
         need = S.sfhe_matmul_workspace_size(self.ctx.h, [a.desc() for a in As], [b.desc() for b in Bs], self.flags)
         # a wave of unusually many empty rows may need more than the bound
-        work = self.work if need <= self.work.numel() else torch.empty(need, dtype=torch.uint8, device="cuda")
+        work = self.works[slot] if need <= self.works[slot].numel() else torch.empty(need, dtype=torch.uint8,
+                                                                                     device="cuda")
         plan = S.sfhe_plan_create(self.ctx.h, [a.desc() for a in As], [b.desc() for b in Bs],
                                   [c.desc() for c in Cs], self.flags, work, self.stream)
-        products = S.sfhe_plan_stats(plan)["products"]
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(self.stream)
-        S.sfhe_plan_execute(plan, self.stream)
-        e1.record(self.stream)
-        t1 = time.perf_counter()
-        S.sfhe_matmul_check(work, self.stream)       # synchronises the stream
-        S.sfhe_plan_destroy(plan)
-        self.setup_s += t1 - t0
+        st = S.sfhe_plan_stats(plan)
+        if self.preempt:
+            S.sfhe_plan_set_stop(plan, self.stop)
+        w = Wave(blocks, st["products"], st["entries"], plan, work, slot)
+        self._launch(w, resume=False)
+        self.setup_s += time.perf_counter() - t0
+        return w
+
+    def finish_wave(self, w: Wave, within_s: float | None = None) -> bool:
+        """wait for the wave; if within_s (seconds) passes first, stop it at
+        its next entry boundary.  True once every entry is done (the plan is
+        released), False if it stopped short (resume_wave continues it)."""
+        torch, S = self.torch, self.S
+        deadline = None if within_s is None or not self.preempt else time.perf_counter() + within_s
+        stopped = False
+        while not w.events[-1][1].query():
+            if deadline is not None and time.perf_counter() >= deadline:
+                with torch.cuda.stream(self.side):
+                    self.stop.copy_(self.one, non_blocking=True)
+                stopped = True
+                break
+            time.sleep(0.0005)
+        S.sfhe_matmul_check(w.work, self.stream)  # synchronises the stream
+        e0, e1 = w.events[-1]
         self.kernel_s += e0.elapsed_time(e1) / 1e3
-        return products
+        if stopped:
+            # the set value has landed before the word is cleared, and the
+            # clearing precedes every later launch on the stream
+            self.side.synchronize()
+            with torch.cuda.stream(self.stream):
+                self.stop.zero_()
+            if S.sfhe_plan_progress(w.plan, self.stream) < w.entries:
+                self.stops += 1
+                return False
+        S.sfhe_plan_destroy(w.plan)
+        self.free.append(w.slot)
+        return True
+
+    def resume_wave(self, w: Wave):
+        """launch a stopped wave's remaining entries (returns at once)."""
+        self._launch(w, resume=True)
+
+    def run_wave(self, blocks) -> int:
+        """one persistent launch over the blocks, to completion; returns the
+        products run."""
+        w = self.start_wave(blocks)
+        self.finish_wave(w)
+        return w.products
 
     def result(self, req: Request, col0: int = 0):
         """C of a request, or of its column tile starting at col0."""
@@ -286,31 +363,78 @@ def serve(requests: list[Request], executor, budget_bytes: int, wave_products: i
           ext_bytes: int, keep_results: bool = False, clock=time.perf_counter) -> dict:
     """Run the requests (arrival times in seconds from now) through the
     continuous-batching loop on the wall clock.  Returns per-request
-    latencies and totals; with keep_results the executor keeps every C."""
-    # the executor's standing device memory (its matmul workspace) is not
+    latencies and totals; with keep_results the executor keeps every C.
+
+    An executor with start_wave / finish_wave / resume_wave (and preempt
+    set) has a running wave stopped when the next request arrives: the
+    arrival is admitted, a wave over the newcomers' rows runs to completion,
+    and the stopped wave resumes (at most one wave is stopped at a time), so
+    a short request that arrives behind long ones completes within about
+    one entry's time plus its own work.  Without them every wave runs to
+    completion (run_wave)."""
+    # the executor's standing device memory (its matmul workspaces) is not
     # available to requests
     sched = Scheduler(budget_bytes - getattr(executor, "reserved_bytes", 0), wave_products, ct_bytes, ext_bytes)
     pending = deque(sorted(requests, key=lambda r: r.arrival))
+    can_stop = hasattr(executor, "start_wave") and getattr(executor, "preempt", False)
     t0 = clock()
     waves, busy, products = 0, 0.0, 0
-    while pending or not sched.idle():
+    suspended, resume_next = None, False
+    newcomers = []   # requests (or tiles) admitted while a wave is stopped
+
+    def completed(blocks):
+        for req in sched.complete(blocks, clock() - t0):
+            if not keep_results:
+                executor.release(req)
+
+    while pending or not sched.idle() or suspended is not None:
         now = clock() - t0
         while pending and pending[0].arrival <= now:
             sched.arrive(pending.popleft())
         for req in sched.admit(clock() - t0):
             executor.admit(req)
-        blocks = sched.next_wave()
-        if not blocks:
-            if pending:   # nothing to run: wait for the next arrival
-                time.sleep(max(0.0, pending[0].arrival - (clock() - t0)))
+            if suspended is not None:
+                newcomers.append(req)
+        if not can_stop:
+            blocks = sched.next_wave()
+            if not blocks:
+                if pending:   # nothing to run: wait for the next arrival
+                    time.sleep(max(0.0, pending[0].arrival - (clock() - t0)))
+                continue
+            w0 = clock()
+            products += executor.run_wave(blocks)
+            busy += clock() - w0
+            waves += 1
+            completed(blocks)
             continue
+        # the next wave: the stopped one once the wave that stopped it is
+        # done, else new rows (stoppable unless another wave is stopped)
+        if suspended is not None and resume_next:
+            wave, suspended, resume_next, stoppable = suspended, None, False, True
+            executor.resume_wave(wave)
+        else:
+            blocks = sched.next_wave(only=newcomers if suspended is not None else None)
+            newcomers = []
+            if blocks:
+                wave = executor.start_wave(blocks)
+                stoppable, resume_next = suspended is None, suspended is not None
+            elif suspended is not None:
+                wave, suspended, stoppable = suspended, None, True
+                executor.resume_wave(wave)
+            else:
+                if pending:
+                    time.sleep(max(0.0, pending[0].arrival - (clock() - t0)))
+                continue
+        within = max(0.0, pending[0].arrival - (clock() - t0)) if stoppable and pending else None
         w0 = clock()
-        products += executor.run_wave(blocks)
+        done = executor.finish_wave(wave, within)
         busy += clock() - w0
-        waves += 1
-        for req in sched.complete(blocks, clock() - t0):
-            if not keep_results:
-                executor.release(req)
+        if done:
+            waves += 1
+            products += wave.products
+            completed(wave.blocks)
+        else:
+            suspended = wave
     end = clock() - t0
     done = [r for r in requests if r.state == "done"]
     lat = np.array([r.finished - r.arrival for r in done]) if done else np.zeros(0)
@@ -323,6 +447,7 @@ def serve(requests: list[Request], executor, budget_bytes: int, wave_products: i
         "p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
         "ct_mults_per_s": products / end if end > 0 else None,
         "wave_setup_s": getattr(executor, "setup_s", None), "wave_kernel_s": getattr(executor, "kernel_s", None),
+        "waves_stopped": getattr(executor, "stops", 0),
         "reserved_bytes": getattr(executor, "reserved_bytes", 0),
     }
 

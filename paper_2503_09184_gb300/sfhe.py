@@ -87,6 +87,9 @@ _SIGS = {
     "sfhe_plan_create": ([_vp, _i32, _P(sfhe_matrix_view), _P(sfhe_matrix_view), _P(sfhe_matrix_view), _u32, _vp, _sz, _vp, _P(_vp)],
                          ctypes.c_int),
     "sfhe_plan_execute": ([_vp, _vp], ctypes.c_int),
+    "sfhe_plan_set_stop": ([_vp, _vp], ctypes.c_int),
+    "sfhe_plan_progress": ([_vp, _P(_i64), _vp], ctypes.c_int),
+    "sfhe_plan_resume": ([_vp, _vp], ctypes.c_int),
     "sfhe_slots_encode": ([_u32, _u64, _vp, _vp], ctypes.c_int),
     "sfhe_slots_decode": ([_u32, _u64, _vp, _vp], ctypes.c_int),
     "sfhe_rotation_element": ([_u32, _i32], _u32),
@@ -362,6 +365,21 @@ def sfhe_plan_create(ctx: int, A: list, B: list, C: list, flags: int, work, stre
 
 def sfhe_plan_execute(plan: int, stream=None) -> None:
     _check(lib().sfhe_plan_execute(plan, _stream(stream)))
+
+
+def sfhe_plan_set_stop(plan: int, word) -> None:
+    """word: a device tensor whose first 4 bytes are the stop word, or None"""
+    _check(lib().sfhe_plan_set_stop(plan, None if word is None else _ptr(word)))
+
+
+def sfhe_plan_progress(plan: int, stream=None) -> int:
+    done = _i64()
+    _check(lib().sfhe_plan_progress(plan, ctypes.byref(done), _stream(stream)))
+    return done.value
+
+
+def sfhe_plan_resume(plan: int, stream=None) -> None:
+    _check(lib().sfhe_plan_resume(plan, _stream(stream)))
 
 
 # ------------------------------------------------ slot-packed chunks ---

@@ -4,6 +4,8 @@ every row exactly once and visit every running request each wave, budget
 release on completion, and the one-at-a-time baseline model."""
 from __future__ import annotations
 
+import time
+
 import numpy as np
 
 from paper_2503_09184_gb300.serving import Request, Scheduler, fifo_plain_model, request_bytes, serve
@@ -110,6 +112,67 @@ def test_serve_loop_with_fake_executor():
         assert ex.rows[r.key] == list(range(r.rows))
         assert r.finished >= r.arrival
     assert out["p99_s"] >= out["p50_s"] >= 0.0
+
+
+class FakeStoppableExecutor(FakeExecutor):
+    """stands in for a GPU whose waves can be stopped: the first `stops`
+    waits with an arrival ahead stop the wave when the arrival is due
+    (having run none of its rows); each later wait completes the wave."""
+
+    preempt = True
+
+    def __init__(self, stops):
+        super().__init__()
+        self.stops_left = stops
+        self.log = []
+        self.rids = {}
+
+    def start_wave(self, blocks):
+        from paper_2503_09184_gb300.serving import Wave
+        w = Wave(blocks, int(sum(int(req.row_products()[r0:r1].sum()) for req, r0, r1 in blocks)))
+        w.tag = len(self.log)
+        self.log.append(("start", w.tag))
+        self.rids[w.tag] = {req.rid for req, _, _ in blocks}
+        return w
+
+    def finish_wave(self, w, within_s=None):
+        if within_s is not None and self.stops_left > 0:
+            time.sleep(within_s)  # the wave is stopped when the arrival is due
+            self.stops_left -= 1
+            self.log.append(("stop", w.tag))
+            return False
+        self.run_wave(w.blocks)
+        self.log.append(("done", w.tag))
+        return True
+
+    def resume_wave(self, w):
+        self.log.append(("resume", w.tag))
+
+
+def test_serve_loop_stops_a_wave_for_an_arrival_and_resumes_it():
+    reqs = [_req(i, 6, 8, 3, arrival=0.05 * i) for i in range(4)]
+    one = max(request_bytes(r, CT, EXT) for r in reqs)
+    ex = FakeStoppableExecutor(stops=2)
+    out = serve(reqs, ex, budget_bytes=4 * one, wave_products=8, ct_bytes=CT, ext_bytes=EXT)
+    assert out["done"] == 4 and out["products"] == sum(r.products for r in reqs)
+    # every row of every request ran exactly once (a stopped wave's rows
+    # complete after those of the wave that stopped it)
+    for r in reqs:
+        assert sorted(ex.rows[r.key]) == list(range(r.rows))
+    # a stop is followed by a fresh wave run to completion, then the resume
+    # of the stopped wave; no second wave is stopped while one is
+    kinds = [k for k, _ in ex.log]
+    assert kinds.count("stop") == 2
+    for i, (k, w) in enumerate(ex.log):
+        if k == "stop":
+            assert ex.log[i + 1][0] == "start" and ex.log[i + 2][0] == "done"
+            assert ex.log[i + 3] == ("resume", w)
+            # the wave in between serves the newcomers alone
+            assert not (ex.rids[ex.log[i + 1][1]] & ex.rids[w])
+    # each stopped wave is completed exactly once
+    done = [w for k, w in ex.log if k == "done"]
+    assert len(done) == len(set(done))
+    assert {w for k, w in ex.log if k == "stop"} <= set(done)
 
 
 def test_over_budget_request_runs_as_column_tiles():
