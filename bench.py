@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--serve-dims", default="16,32,64", help="serve: M, K, Nc drawn from these")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: HBM ciphertext budget")
     ap.add_argument("--wave-products", type=int, default=40000, help="serve: products per wave")
+    ap.add_argument("--order", default="rr", choices=["rr", "srpt"],
+                    help="serve: wave shares round-robin, or shortest remaining work first")
     ap.add_argument("--preempt", action="store_true",
                     help="serve: a new arrival stops the running wave, whose rows resume after the newcomer's")
     ap.add_argument("--serve-set", default="poisson", choices=["poisson", "mixed64"],
@@ -739,7 +741,7 @@ def run_serve(args):
     for n, rate in enumerate(rates):
         reqs = serve_requests(args, rate, seed=10 + n)
         ex = SV.GpuExecutor(ctx, lazy=args.lazy, wave_products=args.wave_products, preempt=preempt)
-        out = SV.serve(reqs, ex, budget, args.wave_products, ct_b, ext_b)
+        out = SV.serve(reqs, ex, budget, args.wave_products, ct_b, ext_b, order=args.order)
         plain = SV.fifo_plain_model(reqs, lambda r: ex.admit_s.get(r.rid, 0.0) + r.products / plain_rate)
         sweep.append({"rate_per_s": rate, "requests": out["requests"], "done": out["done"],
                       "rejected": out["rejected"], "products": out["products"], "waves": out["waves"],
@@ -759,7 +761,8 @@ def run_serve(args):
                                     if args.serve_set == "poisson" else f"mixed64-waves-N{ring.N}-L{ring.L}")
                                    + ("-lazy" if args.lazy else ""),
                        "N": ring.N, "L": ring.L, "t": W.T_PLAIN, "budget_gb": args.budget_gb,
-                       "wave_products": args.wave_products, "preempt": preempt, "requests_per_rate": args.requests,
+                       "wave_products": args.wave_products, "preempt": preempt, "order": args.order,
+                       "requests_per_rate": args.requests,
                        "dims": args.serve_dims, "sparsity": "U[0.30, 0.95]"},
             "plain_rate_ct_mults_per_s": plain_rate,
             "serving": sweep,

@@ -84,9 +84,15 @@ def request_bytes(req: Request, ct_bytes: int, ext_bytes: int) -> int:
 
 
 class Scheduler:
-    """Admission by budget (FIFO, no overtaking) and round-robin row blocks."""
+    """Admission by budget (FIFO, no overtaking) and row blocks per wave:
+    order "rr" gives every running request an equal share of a wave in turn;
+    "srpt" fills a wave shortest remaining work first (every running request
+    still gets a row)."""
 
-    def __init__(self, budget_bytes: int, wave_products: int, ct_bytes: int, ext_bytes: int):
+    def __init__(self, budget_bytes: int, wave_products: int, ct_bytes: int, ext_bytes: int, order: str = "rr"):
+        if order not in ("rr", "srpt"):
+            raise ValueError(f"unknown wave order {order!r}")
+        self.order = order
         self.budget = budget_bytes
         self.wave_products = max(1, wave_products)
         self.ct_bytes, self.ext_bytes = ct_bytes, ext_bytes
@@ -151,11 +157,27 @@ class Scheduler:
         live = [r for r in self.running if r.next_row < r.rows and (keep is None or id(r) in keep)]
         if not live:
             return []
+        if self.order == "srpt":
+            # shortest remaining work first, each taking what the wave has
+            # left after one row for every request behind it
+            live.sort(key=lambda r: (int(r.row_products()[r.next_row:].sum()), r.arrival, r.rid))
+            left = self.wave_products
+            blocks = []
+            for n, req in enumerate(live):
+                rp = req.row_products()
+                r0 = r1 = req.next_row
+                reserve = sum(int(q.row_products()[q.next_row]) for q in live[n + 1:])
+                while r1 < req.rows and (r1 == r0 or rp[r1] <= left - reserve):
+                    left -= int(rp[r1])
+                    r1 += 1
+                req.next_row = r1
+                blocks.append((req, r0, r1))
+            return blocks
         k = self._turn % len(live)
         live = live[k:] + live[:k]
         self._turn += 1
         share = max(1, self.wave_products // len(live))
-        blocks, total = [], 0
+        blocks = []
         for req in live:
             rp = req.row_products()
             r0 = r1 = req.next_row
@@ -165,7 +187,6 @@ class Scheduler:
                 r1 += 1
             req.next_row = r1
             blocks.append((req, r0, r1))
-            total += taken
         return blocks
 
     def complete(self, blocks, now: float) -> list[Request]:
@@ -360,10 +381,12 @@ class GpuExecutor:
 
 
 def serve(requests: list[Request], executor, budget_bytes: int, wave_products: int, ct_bytes: int,
-          ext_bytes: int, keep_results: bool = False, clock=time.perf_counter) -> dict:
+          ext_bytes: int, keep_results: bool = False, clock=time.perf_counter, order: str = "rr") -> dict:
     """Run the requests (arrival times in seconds from now) through the
     continuous-batching loop on the wall clock.  Returns per-request
     latencies and totals; with keep_results the executor keeps every C.
+    order: how waves share their products among running requests
+    (Scheduler).
 
     An executor with start_wave / finish_wave / resume_wave (and preempt
     set) has a running wave stopped when the next request arrives: the
@@ -374,7 +397,8 @@ def serve(requests: list[Request], executor, budget_bytes: int, wave_products: i
     completion (run_wave)."""
     # the executor's standing device memory (its matmul workspaces) is not
     # available to requests
-    sched = Scheduler(budget_bytes - getattr(executor, "reserved_bytes", 0), wave_products, ct_bytes, ext_bytes)
+    sched = Scheduler(budget_bytes - getattr(executor, "reserved_bytes", 0), wave_products, ct_bytes, ext_bytes,
+                      order)
     pending = deque(sorted(requests, key=lambda r: r.arrival))
     can_stop = hasattr(executor, "start_wave") and getattr(executor, "preempt", False)
     t0 = clock()

@@ -7,6 +7,7 @@ from __future__ import annotations
 import time
 
 import numpy as np
+import pytest
 
 from paper_2503_09184_gb300.serving import Request, Scheduler, fifo_plain_model, request_bytes, serve
 
@@ -70,6 +71,33 @@ def test_waves_cover_rows_once_and_round_robin():
     assert s.used == 0
 
 
+def test_srpt_order_fills_waves_shortest_remaining_first():
+    def dense(rid, M, K, Nc):
+        return Request(rid, np.ones((M, K), dtype=np.int64), np.ones((K, Nc), dtype=np.int64))
+    big, small, mid = dense(0, 8, 2, 4), dense(1, 2, 2, 4), dense(2, 4, 2, 4)  # 8 products a row
+    s = Scheduler(budget_bytes=10**9, wave_products=40, ct_bytes=CT, ext_bytes=EXT, order="srpt")
+    for r in (big, small, mid):
+        s.arrive(r)
+    s.admit(0.0)
+    # small (16 left) whole, then mid (32 left) up to what leaves big one row
+    w = {req.rid: (r0, r1) for req, r0, r1 in s.next_wave()}
+    assert w == {1: (0, 2), 2: (0, 2), 0: (0, 1)}
+    w = {req.rid: (r0, r1) for req, r0, r1 in s.next_wave()}
+    assert w == {2: (2, 4), 0: (1, 4)}
+    # every request keeps a row per wave, even when the shortest fill the wave
+    s2 = Scheduler(budget_bytes=10**9, wave_products=8, ct_bytes=CT, ext_bytes=EXT, order="srpt")
+    a, b = dense(3, 4, 2, 4), dense(4, 4, 2, 4)
+    for r in (a, b):
+        s2.arrive(r)
+    s2.admit(0.0)
+    assert sorted((req.rid, r1 - r0) for req, r0, r1 in s2.next_wave()) == [(3, 1), (4, 1)]
+    try:
+        Scheduler(1, 1, 1, 1, order="fifo")
+        raise AssertionError("unknown order accepted")
+    except ValueError:
+        pass
+
+
 def test_fifo_plain_model_closed_form():
     reqs = [_req(i, 3, 4, 2, arrival=a) for i, a in enumerate([0.0, 0.5, 10.0])]
     m = fifo_plain_model(reqs, lambda r: 1.0)
@@ -100,11 +128,12 @@ class FakeExecutor:
         pass
 
 
-def test_serve_loop_with_fake_executor():
+@pytest.mark.parametrize("order", ["rr", "srpt"])
+def test_serve_loop_with_fake_executor(order):
     reqs = [_req(i, 6, 8, 3, arrival=0.002 * i) for i in range(5)]
     one = max(request_bytes(r, CT, EXT) for r in reqs)
     ex = FakeExecutor()
-    out = serve(reqs, ex, budget_bytes=2 * one, wave_products=8, ct_bytes=CT, ext_bytes=EXT)
+    out = serve(reqs, ex, budget_bytes=2 * one, wave_products=8, ct_bytes=CT, ext_bytes=EXT, order=order)
     assert out["done"] == 5 and out["rejected"] == 0
     assert out["products"] == sum(r.products for r in reqs)
     assert ex.admitted == [(i, 0) for i in range(5)]
