@@ -285,42 +285,53 @@ __global__ void __launch_bounds__(256) k_ck_tensor(const __grid_constant__ CkksC
     d2[(size_t)i * N + k] = mulmod_g(a1, b1, m);
 }
 
-// Key products of a switch: for target t of the list (limbs 0 .. l, then P)
-// u_c[t] = sum_{j <= l} U[t][j] key_j[c][prime(t)], U the transforms of the
-// digits mod the target's prime; grid (N / 256, l + 2).
-__global__ void __launch_bounds__(256) k_ck_ks_accum(const __grid_constant__ CkksConsts c, int level, PrimeList pl,
-                                                     const u64* U, const u64* key, const u64* key_sh, u64* u)
+// Key products of a switch of n polynomials: for target t of the list
+// (limbs 0 .. l, then P) and polynomial b,
+// u_c[b][t] = sum_{j <= l} U[t][b][j] key_j[c][prime(t)], U the transforms
+// of the digits mod the target's prime, key the polynomial's own key; grid
+// (N / 256, l + 2, n).
+__global__ void __launch_bounds__(256) k_ck_ks_accum(const __grid_constant__ CkksConsts c, int level, int n,
+                                                     PrimeList pl, const u64* U, const u64* key0, const u64* key_sh0,
+                                                     size_t key_stride, const int* key_of, u64* u)
 {
-    const int N = c.N, L = c.L, k = blockIdx.x * 256 + threadIdx.x, t = blockIdx.y;
+    const int N = c.N, L = c.L, k = blockIdx.x * 256 + threadIdx.x, t = blockIdx.y, b = blockIdx.z;
     if (k >= N) return;
+    // polynomial b's key: key0 + key_of[b] key_stride (key_of NULL: key0)
+    const size_t ko = key_of ? (size_t)key_of[b] * key_stride : 0;
+    const u64* key = key0 + ko;
+    const u64* key_sh = key_sh0 + ko;
     const int pi = pl.idx[t];
     const ModG m = c.m[pi];
     const int nt = level + 2;
     u64 s0 = 0, s1 = 0;
     for (int j = 0; j <= level; j++) {
-        const u64 x = U[((size_t)t * (level + 1) + j) * N + k];
+        const u64 x = U[(((size_t)t * n + b) * (level + 1) + j) * N + k];
         const size_t ob = (((size_t)j * 2 + 0) * (L + 1) + pi) * N + k, oa = (((size_t)j * 2 + 1) * (L + 1) + pi) * N + k;
         s0 += shoup_lazy(x, key[ob], key_sh[ob], m.q);  // < 2q each, at most 9 terms: below 2^64
         s1 += shoup_lazy(x, key[oa], key_sh[oa], m.q);
     }
-    u[((size_t)0 * nt + t) * N + k] = reduce_g(s0, m);
-    u[((size_t)1 * nt + t) * N + k] = reduce_g(s1, m);
+    u[(((size_t)0 * n + b) * nt + t) * N + k] = reduce_g(s0, m);
+    u[(((size_t)1 * n + b) * nt + t) * N + k] = reduce_g(s1, m);
 }
 
-// The division of a switch's sums by P: out_c[i] (+)= (u_c[i] - X_c[i]) P^-1
-// mod q_i, X the centred P-limb transformed mod q_i; grid (N / 256, l + 1, 2).
-// accumulate: add the result into out (c0 and c1 of a ciphertext), else store.
-__global__ void __launch_bounds__(256) k_ck_moddown(const __grid_constant__ CkksConsts c, int level, const u64* u,
-                                                    const u64* X, u64* out, int accumulate)
+// The division of a switch's sums by P: out_c[b][i] (+)= (u_c[b][i] -
+// X_c[b][i]) P^-1 mod q_i, X the centred P-limb transformed mod q_i; out_c[b]
+// is polynomial c of the ciphertext at out + b out_stride; bit c of
+// add_mask: add into it, else store; grid (N / 256, l + 1, 2 n).
+__global__ void __launch_bounds__(256) k_ck_moddown(const __grid_constant__ CkksConsts c, int level, int n,
+                                                    const u64* u, const u64* X, u64* out, size_t out_stride,
+                                                    int add_mask)
 {
-    const int N = c.N, L = c.L, k = blockIdx.x * 256 + threadIdx.x, i = blockIdx.y, cc = blockIdx.z;
+    const int N = c.N, L = c.L, k = blockIdx.x * 256 + threadIdx.x, i = blockIdx.y;
     if (k >= N) return;
+    const int cc = blockIdx.z / n, b = blockIdx.z - cc * n;
     const ModG m = c.m[i];
     const int nt = level + 2;
-    const u64 d = sub_mod(u[((size_t)cc * nt + i) * N + k], X[((size_t)cc * (level + 1) + i) * N + k], m.q);
+    const size_t g = (size_t)cc * n + b;
+    const u64 d = sub_mod(u[(g * nt + i) * N + k], X[(g * (level + 1) + i) * N + k], m.q);
     const u64 v = csub(shoup_lazy(d, c.pinv[i].w, c.pinv[i].ws, m.q), m.q);
-    u64* o = out + ((size_t)cc * L + i) * N + k;
-    *o = accumulate ? add_mod(*o, v, m.q) : v;
+    u64* o = out + b * out_stride + ((size_t)cc * L + i) * N + k;
+    *o = ((add_mask >> cc) & 1) ? add_mod(*o, v, m.q) : v;
 }
 
 // Rescale from level l: out_c[i] = (in_c[i] - X_c[i]) q_l^-1 mod q_i, i < l,
@@ -374,6 +385,57 @@ __global__ void __launch_bounds__(256) k_ck_phase(const __grid_constant__ CkksCo
     const size_t n = blockIdx.z;
     const u64 c0 = ct[(n * 2 * L + i) * N + k], c1 = ct[((n * 2 + 1) * L + i) * N + k];
     v[(n * L + i) * N + k] = add_mod(c0, mulmod_g(c1, s_ntt[(size_t)i * N + k], c.m[i]), c.m[i].q);
+}
+
+// Gathers of the batched chunked product (ciphertexts [2][L][N], limbs
+// 0 .. l).  Slot q of out receives ciphertext src[q] of in with its slots
+// permuted by X -> X^g[q] (g = 1: a copy); grid (N / 256, l + 1, 2 n).
+template <int LOGN>
+__global__ void __launch_bounds__(256) k_ck_galois_gather(const __grid_constant__ CkksConsts c, const u64* in,
+                                                          const int* src, const int* gs, u64* out)
+{
+    const int N = c.N, L = c.L, k = blockIdx.x * 256 + threadIdx.x, i = blockIdx.y;
+    if (k >= N) return;
+    const int q = blockIdx.z >> 1, cc = blockIdx.z & 1;
+    const u32 g = (u32)gs[q];
+    const size_t ctw = (size_t)2 * L * N;
+    out[(size_t)q * ctw + ((size_t)cc * L + i) * N + k] =
+        in[(size_t)src[q] * ctw + ((size_t)cc * L + i) * N + galois_src_ck<LOGN>(k, g)];
+}
+
+// tensor of product p from ra slot pa[p] and rb slot pb[p]: d0, d1 into
+// prod[p], d2 into d2[p] ([L][N] each); grid (N / 256, l + 1, n)
+__global__ void __launch_bounds__(256) k_ck_tensor_gather(const __grid_constant__ CkksConsts c, const u64* ra,
+                                                          const u64* rb, const int* pa, const int* pb, u64* prod,
+                                                          u64* d2)
+{
+    const int N = c.N, L = c.L, k = blockIdx.x * 256 + threadIdx.x, i = blockIdx.y, p = blockIdx.z;
+    if (k >= N) return;
+    const size_t ctw = (size_t)2 * L * N;
+    const u64* a = ra + (size_t)pa[p] * ctw;
+    const u64* b = rb + (size_t)pb[p] * ctw;
+    const ModG m = c.m[i];
+    const size_t o0 = (size_t)i * N + k, o1 = ((size_t)L + i) * N + k;
+    const u64 a0 = a[o0], a1 = a[o1], b0 = b[o0], b1 = b[o1];
+    u64* o = prod + (size_t)p * ctw;
+    o[o0] = mulmod_g(a0, b0, m);
+    o[o1] = add_mod(mulmod_g(a0, b1, m), mulmod_g(a1, b0, m), m.q);
+    d2[(size_t)p * L * N + o0] = mulmod_g(a1, b1, m);
+}
+
+// C[chunk[j]] += the placed terms list[ptr[j] .. ptr[j+1]) (slots of
+// placed); grid (N / 256, l + 1, 2 m)
+__global__ void __launch_bounds__(256) k_ck_add_lists(const __grid_constant__ CkksConsts c, u64* C, const u64* placed,
+                                                      const int* chunk, const int* ptr, const int* list)
+{
+    const int N = c.N, L = c.L, k = blockIdx.x * 256 + threadIdx.x, i = blockIdx.y;
+    if (k >= N) return;
+    const int j = blockIdx.z >> 1, cc = blockIdx.z & 1;
+    const size_t ctw = (size_t)2 * L * N, o = ((size_t)cc * L + i) * N + k;
+    const u64 q = c.m[i].q;
+    u64 acc = C[(size_t)chunk[j] * ctw + o];
+    for (int t = ptr[j]; t < ptr[j + 1]; t++) acc = add_mod(acc, placed[(size_t)list[t] * ctw + o], q);
+    C[(size_t)chunk[j] * ctw + o] = acc;
 }
 
 // =================================================================== host ===
@@ -478,39 +540,38 @@ cudaError_t ntt_centred(const CkksConsts& c, int from, const u64* in, size_t in_
 
 dim3 ew_grid(const CkksConsts& c, int y, int z) { return dim3((unsigned)((c.N + 255) / 256), (unsigned)y, (unsigned)z); }
 
-// Key switch of one polynomial d (NTT form, limbs 0 .. l of a [L][N]
-// layout) with a key: mode bit c set: add the result into out's polynomial
-// c, else store it there (out a [2][L][N] ciphertext).
-cudaError_t keyswitch(const CkksConsts& c, const u64* d, int l, const u64* key, const u64* key_sh, u64* out, int add_mask,
-                      u64* w, cudaStream_t s)
+// Key switch of n polynomials d_b = d + b d_stride (NTT form, limbs 0 .. l
+// of a [L][N] layout): bit c of add_mask set: add the result into
+// polynomial c of the ciphertext at out + b out_stride, else store it
+// there.  Polynomial b switches with key + key_of[b] key_stride (its Shoup
+// companions at the same offset from key_sh); key_of NULL: every one with
+// key.  Scratch w: n ks_words.  One launch per step covers all n.
+cudaError_t keyswitch(const CkksConsts& c, const u64* d, size_t d_stride, int n, int l, const u64* key,
+                      const u64* key_sh, u64* out, size_t out_stride, int add_mask, u64* w, cudaStream_t s,
+                      const int* key_of = nullptr, size_t key_stride = 0)
 {
-    const size_t N = c.N, L = c.L;
-    u64* D = w;
-    u64* U = D + L * N;
-    u64* u = U + (L + 1) * L * N;
-    u64* Pc = u + 2 * (L + 1) * N;
-    u64* X = Pc + 2 * N;
-    cudaError_t e = ntt(c, true, d, 0, N, D, 0, N, primes_upto(l), l + 1, 1, s);
+    if (n <= 0) return cudaSuccess;
+    const size_t N = c.N, L = c.L, nl = (size_t)l + 1, nt = (size_t)l + 2;
+    u64* D = w;                       // [n][l + 1][N]: digits, coefficient form
+    u64* U = D + n * L * N;           // [l + 2][n][l + 1][N]: digits mod every target
+    u64* u = U + n * (L + 1) * L * N; // [2][n][l + 2][N]: key products
+    u64* Pc = u + 2 * n * (L + 1) * N; // [2][n][N]: their P-limbs, coefficient form
+    u64* X = Pc + 2 * n * N;          // [2][n][l + 1][N]: the P-limbs centred into every q_i
+    cudaError_t e = ntt(c, true, d, d_stride, N, D, nl * N, N, primes_upto(l), l + 1, n, s);
     for (int t = 0; t <= l + 1 && e == cudaSuccess; t++) {
         const int p = t <= l ? t : (int)L;
-        e = ntt(c, false, D, N, 0, U + (size_t)t * (l + 1) * N, N, 0, one_prime(p), 1, l + 1, s);
+        e = ntt(c, false, D, N, 0, U + (size_t)t * n * nl * N, N, 0, one_prime(p), 1, (int)(n * nl), s);
     }
     if (e != cudaSuccess) return e;
-    k_ck_ks_accum<<<ew_grid(c, l + 2, 1), 256, 0, s>>>(c, l, primes_upto(l, (int)L), U, key, key_sh, u);
+    k_ck_ks_accum<<<ew_grid(c, l + 2, n), 256, 0, s>>>(c, l, n, primes_upto(l, (int)L), U, key, key_sh, key_stride,
+                                                        key_of, u);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // the P-limb of both sums to coefficient form, centred into every q_i
-    e = ntt(c, true, u + (size_t)(l + 1) * N, (size_t)(l + 2) * N, 0, Pc, N, 0, one_prime((int)L), 1, 2, s);
-    if (e == cudaSuccess)
-        e = ntt_centred(c, (int)L, Pc, N, X, (size_t)(l + 1) * N, N, primes_upto(l), l + 1, 2, s);
+    // the P-limb of every sum to coefficient form, centred into every q_i
+    e = ntt(c, true, u + (size_t)(l + 1) * N, nt * N, 0, Pc, N, 0, one_prime((int)L), 1, 2 * n, s);
+    if (e == cudaSuccess) e = ntt_centred(c, (int)L, Pc, N, X, nl * N, N, primes_upto(l), l + 1, 2 * n, s);
     if (e != cudaSuccess) return e;
-    for (int cc = 0; cc < 2; cc++) {
-        // one launch per polynomial: the two may differ in add / store
-        k_ck_moddown<<<ew_grid(c, l + 1, 1), 256, 0, s>>>(c, l, u + (size_t)cc * (l + 2) * N,
-                                                          X + (size_t)cc * (l + 1) * N, out + (size_t)cc * L * N,
-                                                          (add_mask >> cc) & 1);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    k_ck_moddown<<<ew_grid(c, l + 1, 2 * n), 256, 0, s>>>(c, l, n, u, X, out, out_stride, add_mask);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -860,7 +921,7 @@ extern "C" sfhe_status sfhe_ckks_mul_relin(sfhe_ckks_ctx* c, const uint64_t* a, 
     u64* w = d2 + (size_t)c->cc.L * c->cc.N;
     k_ck_tensor<<<ew_grid(c->cc, level + 1, 1), 256, 0, s>>>(c->cc, a, b, out, d2);
     CK_TRY(cudaGetLastError());
-    CK_TRY(keyswitch(c->cc, d2, level, c->d_rlk, c->d_rlk_sh, out, 3, w, s));
+    CK_TRY(keyswitch(c->cc, d2, 0, 1, level, c->d_rlk, c->d_rlk_sh, out, 0, 3, w, s));
     return SFHE_OK;
 }
 
@@ -939,7 +1000,7 @@ sfhe_status rotate_one(sfhe_ckks_ctx* c, const sfhe_ckks_rotkeys* rk, const uint
         });
     };
     e = gal();
-    if (e == cudaSuccess) e = keyswitch(c->cc, out + L * N, level, key, key + kw, out, 1, w, s);
+    if (e == cudaSuccess) e = keyswitch(c->cc, out + L * N, 0, 1, level, key, key + kw, out, 0, 1, w, s);
     if (e != cudaSuccess) return set_error(SFHE_ECUDA, "rotate: %s", cudaGetErrorString(e));
     return SFHE_OK;
 }
@@ -1008,18 +1069,42 @@ extern "C" sfhe_status sfhe_ckks_add(sfhe_ckks_ctx* c, uint64_t* acc, const uint
 
 // ----------------------------------------------- the chunked matrix product ---
 namespace {
-size_t chunked_words(const CkksConsts& c)
+// products per batch of the chunked product (the workspace holds one batch)
+const int kCkBatch = 128;
+// ints of the batch's index arrays per product
+const int kCkIdx = 8;
+
+struct CkChunkedLayout {
+    u64 *ks, *ra, *rb, *prod, *d2, *rs, *mask;
+    int* idx;
+    size_t words;
+};
+
+// ks: kCkBatch key switches; ra, rb: the turned operands (ra later holds the
+// placed terms); prod; d2; rs: a batch's rescale; mask; idx: the batch's
+// index arrays (kCkIdx ints a product, plus one)
+CkChunkedLayout chunked_layout(const CkksConsts& c, u64* base)
 {
-    const size_t N = c.N, L = c.L, ctw = 2 * L * N;
-    return ks_words(c) + L * N /* d2 */ + 4 * ctw /* two turned operands, the term, the placed term */ +
-           L * N /* mask */ + 2 * N + 2 * L * N /* rescale */;
+    const size_t N = c.N, L = c.L, ctw = 2 * L * N, n = kCkBatch;
+    CkChunkedLayout Lo;
+    u64* w = base;
+    Lo.ks = w, w += n * ks_words(c);
+    Lo.ra = w, w += n * ctw;
+    Lo.rb = w, w += n * ctw;
+    Lo.prod = w, w += n * ctw;
+    Lo.d2 = w, w += n * L * N;
+    Lo.rs = w, w += 2 * n * N + 2 * n * L * N;
+    Lo.mask = w, w += L * N;
+    Lo.idx = reinterpret_cast<int*>(w), w += (kCkIdx * n + 2) / 2;
+    Lo.words = (size_t)(w - base);
+    return Lo;
 }
 }  // namespace
 
 extern "C" sfhe_status sfhe_ckks_matmul_chunked_workspace_size(const sfhe_ckks_ctx* c, size_t* bytes)
 {
     if (!c || !bytes) return set_error(SFHE_EINVAL, "null argument");
-    *bytes = chunked_words(c->cc) * 8;
+    *bytes = chunked_layout(c->cc, nullptr).words * 8;
     return SFHE_OK;
 }
 
@@ -1031,6 +1116,13 @@ extern "C" sfhe_status sfhe_ckks_matmul_chunked_workspace_size(const sfhe_ckks_c
 // prime, so that the rescale after it keeps the scale at D^2 / q_top),
 // rescaled, turned right to the entry's offset and added into the entry's
 // chunk, two levels below the operands.
+// The terms are independent until that addition, which is exact modular
+// addition, so they run in batches of kCkBatch products, each step of the
+// term one batched launch sequence (a turn is one gather and one key switch
+// over the batch, each ciphertext with the key of its own offset; a turn by
+// 0 is a copy), and each batch's terms are added into their chunks by one
+// gather: the result is the same, limb for limb, as taking the terms one
+// after another.
 extern "C" sfhe_status sfhe_ckks_matmul_chunked(sfhe_ckks_ctx* c, const sfhe_ckks_rotkeys* rk, int32_t M, int32_t K,
                                                 int32_t Nc, const uint64_t* A, const uint64_t* B, uint64_t* C,
                                                 const uint8_t* a_zero, const uint8_t* b_zero, void* work,
@@ -1046,57 +1138,139 @@ extern "C" sfhe_status sfhe_ckks_matmul_chunked(sfhe_ckks_ctx* c, const sfhe_ckk
     if (M < 0 || K < 0 || Nc < 0) return set_error(SFHE_ESHAPE, "negative shape");
     const CkksConsts& cc = c->cc;
     if (cc.L < 3) return set_error(SFHE_EUNSUPPORTED, "the term's two rescales need at least 3 data primes");
-    if (work_bytes < chunked_words(cc) * 8) return set_error(SFHE_ENOMEM, "workspace too small");
+    const CkChunkedLayout Lo = chunked_layout(cc, (u64*)work);
+    if (work_bytes < Lo.words * 8) return set_error(SFHE_ENOMEM, "workspace too small");
     const int ch = rk->c, top = cc.L - 1;
-    const size_t N = cc.N, L = cc.L, ctw = 2 * L * N;
+    const size_t N = cc.N, L = cc.L, ctw = 2 * L * N, kw = key_words(cc);
     const int64_t nC = ((int64_t)M * Nc + ch - 1) / ch;
     if (nC > 0 && (!A || !B || !C)) return set_error(SFHE_EINVAL, "null operand");
     cudaStream_t s = as_stream(stream);
-    // d2 and the key-switch scratch back to back: sfhe_ckks_mul_relin takes both
-    u64* d2 = (u64*)work;
-    u64* ks = d2 + L * N;
-    u64 *ra = ks + ks_words(cc), *rb = ra + ctw, *prod = rb + ctw, *placed = prod + ctw;
-    u64* mask = placed + ctw;
-    u64* rs = mask + L * N;
-    const size_t rs_bytes = (2 * N + 2 * L * N) * 8;
     // the one-hot slot-0 mask at the scale of q_{top-1}
     {
         std::vector<int64_t> poly(N);
         const double one = 1.0;
         sfhe_status st = sfhe_ckks_encode(c, &one, 1, (double)cc.m[top - 1].q, poly.data());
-        if (st == SFHE_OK) st = sfhe_ckks_plain_ntt(c, poly.data(), top - 1, mask, stream);
+        if (st == SFHE_OK) st = sfhe_ckks_plain_ntt(c, poly.data(), top - 1, Lo.mask, stream);
         if (st != SFHE_OK) return st;
     }
     if (nC > 0) CK_TRY(cudaMemsetAsync(C, 0, (size_t)nC * ctw * 8, s));
-    // product sets: entry (i, j) takes the k where neither mask is set
-    int64_t done = 0;
-    std::vector<int32_t> ks_of;
+    // the terms: entry (i, j) takes the k where neither mask is set
+    struct Term {
+        int64_t ea, eb, r;
+    };
+    std::vector<Term> terms;
     for (int32_t i = 0; i < M; i++)
-        for (int32_t j = 0; j < Nc; j++) {
-            ks_of.clear();
+        for (int32_t j = 0; j < Nc; j++)
             for (int32_t k = 0; k < K; k++)
-                if (!(a_zero && a_zero[(int64_t)i * K + k]) && !(b_zero && b_zero[(int64_t)k * Nc + j])) ks_of.push_back(k);
-            const int64_t r = (int64_t)i * Nc + j;
-            for (int32_t k : ks_of) {
-                const int64_t ea = (int64_t)i * K + k, eb = (int64_t)k * Nc + j;
-                const u64* a = A + (ea / ch) * ctw;
-                const u64* b = B + (eb / ch) * ctw;
-                sfhe_status st = SFHE_OK;
-                if (ea % ch) st = rotate_one(c, rk, a, top, (int)(ea % ch), ra, ks, s), a = ra;
-                if (st == SFHE_OK && eb % ch) st = rotate_one(c, rk, b, top, (int)(eb % ch), rb, ks, s), b = rb;
-                if (st == SFHE_OK)
-                    st = sfhe_ckks_mul_relin(c, a, b, top, prod, d2, (ks_words(cc) + L * N) * 8, stream);
-                if (st == SFHE_OK) st = sfhe_ckks_rescale(c, prod, top, 1, prod, rs, rs_bytes, stream);
-                if (st == SFHE_OK) st = sfhe_ckks_mul_plain(c, prod, top - 1, 1, mask, stream);
-                if (st == SFHE_OK) st = sfhe_ckks_rescale(c, prod, top - 1, 1, prod, rs, rs_bytes, stream);
-                const u64* term = prod;
-                if (st == SFHE_OK && r % ch) st = rotate_one(c, rk, prod, top - 2, -(int)(r % ch), placed, ks, s), term = placed;
-                if (st == SFHE_OK) st = sfhe_ckks_add(c, C + (r / ch) * ctw, term, top - 2, 1, stream);
-                if (st != SFHE_OK) return st;
-                done++;
+                if (!(a_zero && a_zero[(int64_t)i * K + k]) && !(b_zero && b_zero[(int64_t)k * Nc + j]))
+                    terms.push_back({(int64_t)i * K + k, (int64_t)k * Nc + j, (int64_t)i * Nc + j});
+    // the rotation keys [2][c - 1][2][kw]: left turns by 1 .. c-1, then right
+    // turns; key (right, off) has index right (c - 1) + off - 1
+    auto key_index = [&](bool right, int off) { return (right ? 1 : 0) * (ch - 1) + (off - 1); };
+    // Turn ciphertexts src[q] of `in` into out's slots q, slot q by offs[q]
+    // (left, or right), the slots sorted by offset: one gather for all, then
+    // one key switch over the slots with a nonzero offset, each with its own
+    // key.  idx: src, then the Galois elements, then the key indices.
+    auto turn = [&](const u64* in, const int* d_idx, const std::vector<int>& offs, int level,
+                    u64* out) -> cudaError_t {
+        const int n = (int)offs.size();
+        int z = 0;
+        while (z < n && offs[z] == 0) z++;
+        cudaError_t e = cudaSuccess;
+        CK_DISPATCH(cc.logN, {
+            k_ck_galois_gather<LG><<<ew_grid(cc, level + 1, 2 * n), 256, 0, s>>>(cc, in, d_idx, d_idx + n, out);
+            e = cudaGetLastError();
+            break;
+        });
+        if (e == cudaSuccess && z < n)
+            e = keyswitch(cc, out + (size_t)z * ctw + L * N, ctw, n - z, level, rk->d_keys, rk->d_keys + kw,
+                          out + (size_t)z * ctw, ctw, 1, Lo.ks, s, d_idx + 2 * n + z, 2 * kw);
+        return e;
+    };
+    // the index arrays of one turn: src, Galois element, key index per slot
+    auto turn_arrays = [&](int* dst, const std::vector<int>& src, const std::vector<int>& offs, bool right) {
+        const int n = (int)offs.size();
+        for (int q = 0; q < n; q++) {
+            dst[q] = src[q];
+            dst[n + q] = offs[q] ? (int)sfhe_rotation_element((uint32_t)N, right ? -offs[q] : offs[q]) : 1;
+            dst[2 * n + q] = offs[q] ? key_index(right, offs[q]) : 0;
+        }
+    };
+    std::vector<int> host_idx;
+    for (size_t t0 = 0; t0 < terms.size(); t0 += kCkBatch) {
+        const int n = (int)std::min<size_t>(kCkBatch, terms.size() - t0);
+        auto sorted_by = [&](auto off_of) {
+            std::vector<int> perm(n);
+            for (int p = 0; p < n; p++) perm[p] = p;
+            std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return off_of(x) < off_of(y); });
+            return perm;
+        };
+        const auto perm_a = sorted_by([&](int p) { return (int)(terms[t0 + p].ea % ch); });
+        const auto perm_b = sorted_by([&](int p) { return (int)(terms[t0 + p].eb % ch); });
+        const auto perm_c = sorted_by([&](int p) { return (int)(terms[t0 + p].r % ch); });
+        std::vector<int> src_a(n), src_b(n), oa(n), ob(n), pos_a(n), pos_b(n);
+        for (int q = 0; q < n; q++) {
+            const Term& ta = terms[t0 + perm_a[q]];
+            const Term& tb = terms[t0 + perm_b[q]];
+            src_a[q] = (int)(ta.ea / ch), oa[q] = (int)(ta.ea % ch), pos_a[perm_a[q]] = q;
+            src_b[q] = (int)(tb.eb / ch), ob[q] = (int)(tb.eb % ch), pos_b[perm_b[q]] = q;
+        }
+        // index region: [0, 3n) the turn of A, [3n, 6n) of B, [6n, 7n) and
+        // [7n, 8n) the slots of each product's turned operands
+        host_idx.assign((size_t)kCkIdx * kCkBatch + 1, 0);
+        turn_arrays(host_idx.data(), src_a, oa, false);
+        turn_arrays(host_idx.data() + 3 * n, src_b, ob, false);
+        for (int p = 0; p < n; p++) host_idx[6 * n + p] = pos_a[p], host_idx[7 * n + p] = pos_b[p];
+        CK_TRY(cudaMemcpyAsync(Lo.idx, host_idx.data(), 8 * (size_t)n * sizeof(int), cudaMemcpyHostToDevice, s));
+        // both operands to slot 0, multiply, relinearise
+        CK_TRY(turn(A, Lo.idx, oa, top, Lo.ra));
+        CK_TRY(turn(B, Lo.idx + 3 * n, ob, top, Lo.rb));
+        k_ck_tensor_gather<<<ew_grid(cc, top + 1, n), 256, 0, s>>>(cc, Lo.ra, Lo.rb, Lo.idx + 6 * n, Lo.idx + 7 * n,
+                                                                    Lo.prod, Lo.d2);
+        CK_TRY(cudaGetLastError());
+        CK_TRY(keyswitch(cc, Lo.d2, L * N, n, top, c->d_rlk, c->d_rlk_sh, Lo.prod, ctw, 3, Lo.ks, s));
+        // rescale, the slot-0 mask, rescale
+        const size_t rs_bytes = (2 * (size_t)n * N + 2 * (size_t)n * L * N) * 8;
+        sfhe_status st = sfhe_ckks_rescale(c, Lo.prod, top, n, Lo.prod, Lo.rs, rs_bytes, stream);
+        if (st == SFHE_OK) st = sfhe_ckks_mul_plain(c, Lo.prod, top - 1, n, Lo.mask, stream);
+        if (st == SFHE_OK) st = sfhe_ckks_rescale(c, Lo.prod, top - 1, n, Lo.prod, Lo.rs, rs_bytes, stream);
+        if (st != SFHE_OK) return st;
+        // turn right to the entries' offsets (placed terms in ra's slots),
+        // then add each chunk's terms into it
+        std::vector<int> src_c(n), oc(n), chunk_of, ptr(1, 0), list;
+        {
+            std::vector<std::vector<int>> by_chunk;
+            std::vector<int64_t> chunk_ids;
+            for (int q = 0; q < n; q++) {
+                src_c[q] = perm_c[q];
+                oc[q] = (int)(terms[t0 + perm_c[q]].r % ch);
+                const int64_t chk = terms[t0 + perm_c[q]].r / ch;
+                size_t m = 0;
+                while (m < chunk_ids.size() && chunk_ids[m] != chk) m++;
+                if (m == chunk_ids.size()) chunk_ids.push_back(chk), by_chunk.emplace_back();
+                by_chunk[m].push_back(q);
+            }
+            for (size_t m = 0; m < chunk_ids.size(); m++) {
+                chunk_of.push_back((int)chunk_ids[m]);
+                for (int q : by_chunk[m]) list.push_back(q);
+                ptr.push_back((int)list.size());
             }
         }
-    if (products) *products = done;
+        const int mch = (int)chunk_of.size();
+        // index region again: [0, 3n) the placement turn, [3n, 3n + mch) the
+        // chunks, [4n, 4n + mch + 1) list offsets, [5n + 1, 6n + 1) the lists
+        host_idx.assign((size_t)kCkIdx * kCkBatch + 1, 0);
+        turn_arrays(host_idx.data(), src_c, oc, true);
+        for (int m = 0; m < mch; m++) host_idx[3 * n + m] = chunk_of[m];
+        for (int m = 0; m <= mch; m++) host_idx[4 * n + m] = ptr[m];
+        for (int q = 0; q < n; q++) host_idx[5 * n + 1 + q] = list[q];
+        CK_TRY(cudaMemcpyAsync(Lo.idx, host_idx.data(), (6 * (size_t)n + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+        CK_TRY(turn(Lo.prod, Lo.idx, oc, top - 2, Lo.ra));
+        k_ck_add_lists<<<ew_grid(cc, top - 1, 2 * mch), 256, 0, s>>>(cc, C, Lo.ra, Lo.idx + 3 * n, Lo.idx + 4 * n,
+                                                                     Lo.idx + 5 * n + 1);
+        CK_TRY(cudaGetLastError());
+    }
+    if (products) *products = (int64_t)terms.size();
     if (result_scale) *result_scale = c->scale * c->scale / (double)cc.m[top].q;
     return SFHE_OK;
 }

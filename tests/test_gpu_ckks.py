@@ -147,6 +147,46 @@ def test_chunked_product_limb_for_limb(small, chunk, skip):
     assert np.max(np.abs(vals - A @ B)) < 1e-3
 
 
+@pytest.mark.parametrize("chunk,skip,shape", [(4, True, (8, 9, 7)), (5, False, (6, 7, 5))])
+def test_chunked_product_many_batches_limb_for_limb(small, chunk, skip, shape):
+    """products in several batches of the batched term-by-term product
+    (64 products a batch), chunks touched by terms of several batches, every
+    turn offset: each chunk limb for limb against the oracle's sequence"""
+    g, ck = small
+    S = g.S
+    M, K, Nc = shape
+    rng = np.random.default_rng(7 + chunk)
+    A = rng.integers(-8, 9, (M, K))
+    B = rng.integers(-8, 9, (K, Nc))
+    if skip:
+        A[rng.random((M, K)) < 0.4] = 0
+        B[rng.random((K, Nc)) < 0.3] = 0
+    oc = CK.OracleCkksChunked(ck, A, B, chunk, 1, 2)
+    want = oc.result(skip_zeros=skip)
+    assert sum(len(v) for v in oc.product_sets(skip).values()) > 2 * 64
+
+    def chunks(Mv, mid):
+        flat = Mv.reshape(-1).astype(np.float64)
+        polys = [CK.encode(64, flat[q * chunk:(q + 1) * chunk], ck.scale) for q in range(-(-flat.size // chunk))]
+        return _encrypt(g, polys, mid, [[q, 0] for q in range(len(polys))])
+    Ag, Bg = chunks(A, 1), chunks(B, 2)
+    nC = -(-(M * Nc) // chunk)
+    C = g.ct(nC)
+    rk = S.sfhe_ckks_rotkeys_create(g.h, chunk)
+    try:
+        az = (A == 0).astype(np.uint8).reshape(-1) if skip else None
+        bz = (B == 0).astype(np.uint8).reshape(-1) if skip else None
+        n, scale = S.sfhe_ckks_matmul_chunked(g.h, rk, M, K, Nc, Ag, Bg, C, az, bz, g.work)
+    finally:
+        S.sfhe_ckks_rotkeys_destroy(rk)
+    assert n == sum(len(v) for v in oc.product_sets(skip).values())
+    got = g.coeff(C, 1, nC)
+    for q in range(nC):
+        _same(got[q], want[q], 1, f"chunk {q}")
+    vals = S.sfhe_ckks_decrypt(g.h, C, 1, nC, scale, chunk).reshape(-1)[:M * Nc].reshape(M, Nc)
+    assert np.max(np.abs(vals - A @ B)) < 1e-2
+
+
 def test_paper_ring_8192():
     """The paper's ring: encryption, the product with relinearisation and a
     rescale limb for limb against the oracle; the chunked product of a
