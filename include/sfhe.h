@@ -576,7 +576,8 @@ sfhe_status sfhe_matmul_check(void* work, void* stream);
  * sfhe_plan_resume: launches the plan again from its first entry not taken
  * (clear the word first); a stopped execution plus its resumptions write
  * the same C, limb for limb, as one execution.  sfhe_plan_execute restarts
- * from the first entry.  Errors: EINVAL (null plan, a PLAIN plan), ECUDA. */
+ * from the first entry.  Errors: EINVAL (null plan, a PLAIN plan, resume
+ * before the first execution), ECUDA. */
 sfhe_status sfhe_plan_set_stop(sfhe_plan* plan, const uint32_t* word);
 sfhe_status sfhe_plan_progress(const sfhe_plan* plan, int64_t* done, void* stream);
 sfhe_status sfhe_plan_resume(sfhe_plan* plan, void* stream);

@@ -120,6 +120,7 @@ struct sfhe_plan {
     cudaGraphExec_t gexec;
     int variant;  // tile variant of the persistent kernel
     const unsigned* d_stop;  // preemption word of the persistent launches (nullable)
+    bool launched;           // an execution has set the entry counter
 };
 
 extern "C" const char* sfhe_last_error(void) { return g_last_error.c_str(); }
@@ -862,6 +863,7 @@ static sfhe_status plan_create_impl(sfhe_ctx* c, int32_t n, const sfhe_matrix_vi
     P->graph = nullptr;
     P->gexec = nullptr;
     P->d_stop = nullptr;
+    P->launched = false;
     st = build(c, n, A, B, C, dense_loop, *P);
     if (st != SFHE_OK) {
         delete P;
@@ -950,6 +952,7 @@ extern "C" sfhe_status sfhe_plan_execute(sfhe_plan* P, void* stream)
 {
     Range range("sfhe_plan_execute");
     if (!P) return fail(SFHE_EINVAL, "null plan");
+    P->launched = true;
     return launch_plan(P, as_stream(stream));
 }
 
@@ -967,6 +970,10 @@ extern "C" sfhe_status sfhe_plan_progress(const sfhe_plan* P, int64_t* done, voi
 {
     if (!P || !done) return fail(SFHE_EINVAL, "null argument");
     if (!(P->flags & SFHE_EXEC_PERSISTENT)) return fail(SFHE_EINVAL, "progress is kept by PERSISTENT plans");
+    if (!P->launched) {
+        *done = 0;
+        return SFHE_OK;
+    }
     CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
     unsigned taken = 0;
     CUDA_TRY(cudaMemcpy(&taken, P->d_queue, sizeof(unsigned), cudaMemcpyDeviceToHost));
@@ -979,6 +986,7 @@ extern "C" sfhe_status sfhe_plan_resume(sfhe_plan* P, void* stream)
     Range range("sfhe_plan_resume");
     if (!P) return fail(SFHE_EINVAL, "null plan");
     if (!(P->flags & SFHE_EXEC_PERSISTENT)) return fail(SFHE_EINVAL, "only PERSISTENT plans resume");
+    if (!P->launched) return fail(SFHE_EINVAL, "resume before the plan's first execution");
     // the entry counter is left as the stopped launch left it: the entries
     // below it are complete, the rest are taken from it on
     if (P->entries.empty()) return SFHE_OK;

@@ -184,15 +184,20 @@ SFHE_DEV u32 reduce64b(u64 x, Mod32 m)
 }
 
 // round(sum_{k<n} y_k / b_k) for y_k in [0, b_k) when the sum is known to lie
-// within 1/4 of an integer: with bfrac_k = floor(2^58 / b_k) the estimate
-// is at most n 2^-28 below the sum, which cannot cross a half-integer.
+// within 1/4 of an integer, in 32-bit products: with bfrac_k =
+// floor(2^43 / b_k) < 2^14, the term floor(y_k / 2^16) bfrac_k is below
+// y_k 2^27 / b_k < 2^27 by less than y_k / 2^16 + 2^43 / b_k < 2^15, so
+// E = sum of the terms is below 2^27 sum_k y_k / b_k (and below 2^32 for
+// n <= 31) by less than n 2^-12 units of 2^27: far from moving the sum
+// across a half-integer.
 template <int n>
 SFHE_DEV u32 round_b(const u32* y, const RnsConsts& c)
 {
-    u64 E = 0;
+    static_assert(n <= 31, "the 32-bit estimate holds up to 31 primes");
+    u32 E = 0;
 #pragma unroll
-    for (int k = 0; k < n; k++) E += (u64)y[k] * c.bfrac[k];
-    return (u32)((E + (1ULL << 57)) >> 58);
+    for (int k = 0; k < n; k++) E += (y[k] >> 16) * c.bfrac[k];
+    return (E + (1u << 26)) >> 27;
 }
 
 // ---------------------------------------------------------- generator ------

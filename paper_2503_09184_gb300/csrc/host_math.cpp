@@ -425,7 +425,7 @@ bool fill_constants(RnsConsts& rc)
     for (int k = 0; k < K; ++k) {
         const uint64_t b = rc.mb[k].b;
         rc.bhat_inv[k] = shoup32_of(invm(prod_b(rc, K, k, b), b), b);
-        rc.bfrac[k] = (uint32_t)((1ULL << 58) / b);
+        rc.bfrac[k] = (uint32_t)((1ULL << 43) / b);
     }
 
     // ---- scale and round directly from B: t (B/b_k) = alpha_k Q + r_k, t B = alpha_B Q + r_B

@@ -82,7 +82,7 @@ struct RnsConsts {
 
     // tensor x from B:  x = sum_k x~_k (B/b_k) - v B, |x| < B / 4
     Shoup32 bhat_inv[SFHE_MAX_K];           // [(B/b_k)^-1]_{b_k}
-    u32 bfrac[SFHE_MAX_K];                  // floor(2^58 / b_k)
+    u32 bfrac[SFHE_MAX_K];                  // floor(2^43 / b_k)
 
     // scale and round by t/Q, directly from B: with t (B/b_k) = alpha_k Q + r_k
     // and t B = alpha_B Q + r_B,

@@ -85,12 +85,18 @@ def test_stop_while_running_then_resume_equals_one_execution(delay_ms):
     plan.close()
 
 
-def test_stop_word_needs_a_plain_persistent_plan():
+def test_stop_word_needs_a_plain_persistent_plan_and_resume_an_execution():
     api, S = gpu_modules()
     import torch
     ctx = gpu_ctx(4096, 2, 13)
     _, _, A, B = _operands(api, ctx, 4, 4, 4, 0.5, 9)
     stop = torch.zeros(1, dtype=torch.int32, device="cuda")
+    plan = api.Plan(ctx, [A], [B])
+    assert S.sfhe_plan_progress(plan.h) == 0
+    with pytest.raises(S.SfheError) as ex:
+        S.sfhe_plan_resume(plan.h)  # nothing to resume yet
+    assert ex.value.status == S.SFHE_EINVAL
+    plan.close()
     for kw in ({"mode": "plain"}, {"graph": True}):
         plan = api.Plan(ctx, [A], [B], **kw)
         with pytest.raises(S.SfheError) as ex:
