@@ -848,6 +848,21 @@ extern "C" void sfhe_plan_destroy(sfhe_plan* P)
     delete P;
 }
 
+static sfhe_status plan_finish(sfhe_ctx* c, sfhe_plan* P, uint32_t flags, void* work, size_t work_bytes, void* stream,
+                               sfhe_plan** out);
+
+static sfhe_plan* new_plan(sfhe_ctx* c, uint32_t flags)
+{
+    sfhe_plan* P = new sfhe_plan();
+    P->ctx = c;
+    P->flags = flags;
+    P->graph = nullptr;
+    P->gexec = nullptr;
+    P->d_stop = nullptr;
+    P->launched = false;
+    return P;
+}
+
 static sfhe_status plan_create_impl(sfhe_ctx* c, int32_t n, const sfhe_matrix_view* A, const sfhe_matrix_view* B,
                                     sfhe_matrix_view* C, const bool* dense_loop, uint32_t flags, void* work,
                                     size_t work_bytes, void* stream, sfhe_plan** out)
@@ -857,18 +872,20 @@ static sfhe_status plan_create_impl(sfhe_ctx* c, int32_t n, const sfhe_matrix_vi
     sfhe_status st = check_flags(flags);
     if (st != SFHE_OK) return st;
     if (n > 0 && !C) return fail(SFHE_EINVAL, "null C");
-    sfhe_plan* P = new sfhe_plan();
-    P->ctx = c;
-    P->flags = flags;
-    P->graph = nullptr;
-    P->gexec = nullptr;
-    P->d_stop = nullptr;
-    P->launched = false;
+    sfhe_plan* P = new_plan(c, flags);
     st = build(c, n, A, B, C, dense_loop, *P);
     if (st != SFHE_OK) {
         delete P;
         return st;
     }
+    return plan_finish(c, P, flags, work, work_bytes, stream, out);
+}
+
+// A plan whose work list is filled: lay it out in `work`, upload the list,
+// pick the tile, capture the graph.  Takes P (deleted on error).
+static sfhe_status plan_finish(sfhe_ctx* c, sfhe_plan* P, uint32_t flags, void* work, size_t work_bytes, void* stream,
+                               sfhe_plan** out)
+{
     Layout Lo = layout_of(c, *P, flags, &P->grid, &P->scratch_stride);
     if ((flags & SFHE_EXEC_PERSISTENT) && P->grid <= 0) {
         delete P;
@@ -1439,21 +1456,65 @@ extern "C" void sfhe_rotkeys_destroy(sfhe_rotkeys* rk)
     delete rk;
 }
 
-// workspace of sfhe_matmul_chunked (bytes): rotation scratch; four
-// ciphertexts (the two rotated operands, the product, the rotated product);
-// the lift of two ciphertexts and its scratch; the tensor T [3][K][N] u32;
-// D [3][L][N], U [(L+2)][L][N]; the mask [L][N]
-static size_t chunked_words(const RnsConsts& rc)
+// ciphertexts per batched key switch of the term-by-term product
+static const long long kTermRotBatch = 128;
+
+// The term-by-term chunked product runs its terms in batches of
+// term_batch(c): three rounds of the persistent kernel's grid.
+static int64_t term_batch(const sfhe_ctx* c)
 {
-    const size_t LN = (size_t)rc.L * rc.N, KN = (size_t)rc.K * rc.N;
-    return rotate_work_words(rc) + 4 * 2 * LN + 2 * KN /* ext a, b: 2 x [2][K][N] u32 */ +
-           (2 * LN + KN) /* lift scratch of one ciphertext */ + (3 * KN + 1) / 2 + 3 * LN + (rc.L + 2) * LN + LN;
+    return 3 * (int64_t)std::max(1, persistent_ctas_per_sm(c->rc) * c->num_sms);
+}
+
+// workspace of sfhe_matmul_chunked: the batched rotation scratch; five
+// ciphertexts a term (gathered chunks, the two turned operands, the
+// product, the placed product); both operands lifted and the lift's
+// scratch; the mask; the work list of one batch; the batch's index arrays
+struct TermLayout {
+    size_t rot, tmp, ra, rb, prod, rr, ea, eb, lift, mask, plan, idx, total, lift_bytes, plan_bytes;
+    int64_t n;
+};
+
+static sfhe_status term_layout(const sfhe_ctx* c, TermLayout& Lo)
+{
+    const RnsConsts& rc = c->rc;
+    const int64_t n = term_batch(c);
+    const size_t ctb = (size_t)2 * rc.L * rc.N * 8, extb = (size_t)2 * rc.K * rc.N * 4;
+    Lo.n = n;
+    size_t off = 0;
+    Lo.rot = off, off += align256(rotate_batch_words(rc, kTermRotBatch) * 8);
+    Lo.tmp = off, off += align256((size_t)n * ctb);
+    Lo.ra = off, off += align256((size_t)n * ctb);
+    Lo.rb = off, off += align256((size_t)n * ctb);
+    Lo.prod = off, off += align256((size_t)n * ctb);
+    Lo.rr = off, off += align256((size_t)n * ctb);
+    Lo.ea = off, off += align256((size_t)n * extb);
+    Lo.eb = off, off += align256((size_t)n * extb);
+    sfhe_status st = sfhe_lift_workspace_size(c, n, &Lo.lift_bytes);
+    if (st != SFHE_OK) return st;
+    Lo.lift = off, off += align256(Lo.lift_bytes);
+    Lo.mask = off, off += align256((size_t)rc.L * rc.N * 8);
+    // the batch's work list: one matmul, n entries of one product each
+    sfhe_plan W;
+    W.mms.resize(1);
+    W.entries.resize((size_t)n);
+    W.rowlist.resize((size_t)n);
+    int grid = 0;
+    size_t stride = 0;
+    Lo.plan_bytes = layout_of(c, W, SFHE_EXEC_PERSISTENT, &grid, &stride).total;
+    Lo.plan = off, off += align256(Lo.plan_bytes);
+    Lo.idx = off, off += align256((size_t)(6 * n + 1) * sizeof(int));
+    Lo.total = off;
+    return SFHE_OK;
 }
 
 extern "C" sfhe_status sfhe_matmul_chunked_workspace_size(const sfhe_ctx* c, size_t* bytes)
 {
     if (!c || !bytes) return fail(SFHE_EINVAL, "null argument");
-    *bytes = chunked_words(c->rc) * 8;
+    TermLayout Lo;
+    sfhe_status st = term_layout(c, Lo);
+    if (st != SFHE_OK) return st;
+    *bytes = Lo.total;
     return SFHE_OK;
 }
 
@@ -1469,6 +1530,18 @@ static sfhe_matrix_view element_desc(int32_t rows, int32_t cols, const uint8_t* 
 // elements are turned so that the elements sit in slot 0, lifted, multiplied
 // and relinearised on the per-product kernels; the term is masked to slot 0,
 // turned right to its entry's offset and added into the entry's chunk.
+// The chunked product term by term (Alg. 1's placement): for every output
+// entry and every product of its product set, the chunks holding the two
+// elements are turned so that the elements sit in slot 0, multiplied and
+// relinearised, masked to slot 0, turned right to the entry's offset and
+// added into the entry's chunk.  The terms are independent until those
+// additions, so they run in batches of term_batch(c): the chunks of the
+// batch's operands gathered and turned (one batched key switch per offset),
+// lifted, multiplied and relinearised by the persistent kernel over a work
+// list of one-product entries (each product into its own ciphertext),
+// masked, turned right (one batched key switch per offset), and added into
+// their chunks in the terms' order.  Every ciphertext is the one the terms
+// taken one after another give, limb for limb.
 extern "C" sfhe_status sfhe_matmul_chunked(sfhe_ctx* c, const sfhe_rotkeys* rk, int32_t M, int32_t K, int32_t Nc,
                                           const uint64_t* A, const uint64_t* B, uint64_t* C, const uint8_t* a_zero,
                                           const uint8_t* b_zero, void* work, size_t work_bytes, void* stream,
@@ -1478,40 +1551,23 @@ extern "C" sfhe_status sfhe_matmul_chunked(sfhe_ctx* c, const sfhe_rotkeys* rk, 
     if (!c || !rk || !work) return fail(SFHE_EINVAL, "null argument");
     if (rk->ctx != c) return fail(SFHE_EINVAL, "rotation keys of another context");
     if (M < 0 || K < 0 || Nc < 0) return fail(SFHE_ESHAPE, "negative shape");
-    if (work_bytes < chunked_words(c->rc) * 8) return fail(SFHE_ENOMEM, "chunked workspace too small");
+    TermLayout Lo;
+    sfhe_status st = term_layout(c, Lo);
+    if (st != SFHE_OK) return st;
+    if (work_bytes < Lo.total) return fail(SFHE_ENOMEM, "chunked workspace of %zu bytes needed, %zu given", Lo.total,
+                                           work_bytes);
     const RnsConsts& rc = c->rc;
     const int32_t ch = rk->c;
-    const size_t LN = (size_t)rc.L * rc.N, KN = (size_t)rc.K * rc.N, ctw = 2 * LN;
+    const size_t ctw = (size_t)2 * rc.L * rc.N;
     const int64_t nC = ((int64_t)M * Nc + ch - 1) / ch;
     if (nC > 0 && (!A || !B || !C)) return fail(SFHE_EINVAL, "null operand");
-    // the product sets
-    sfhe_matrix_view Ad = element_desc(M, K, a_zero, (uint64_t*)16, (uint32_t*)16);
-    sfhe_matrix_view Bd = element_desc(K, Nc, b_zero, (uint64_t*)16, (uint32_t*)16);
-    sfhe_plan W;
-    W.ctx = c;
-    W.flags = SFHE_EXEC_PLAIN;
-    const bool dense_loop = false;
-    sfhe_status st = build(c, 1, &Ad, &Bd, nullptr, &dense_loop, W);
-    if (st != SFHE_OK) return st;
     cudaStream_t s = as_stream(stream);
-    u64* w = (u64*)work;
-    u64* rot_work = w;
-    w += rotate_work_words(rc);
-    u64 *ra = w, *rb = w + ctw, *prod = w + 2 * ctw, *rr = w + 3 * ctw;
-    w += 4 * ctw;
-    u32* ea = (u32*)w;
-    u32* eb = ea + 2 * KN;
-    w += 2 * KN;
-    u64* lift_ws = w;
-    const size_t lift_bytes = (2 * LN + KN) * 8;
-    w += 2 * LN + KN;
-    u32* T = (u32*)w;
-    w += (3 * KN + 1) / 2;
-    u64* D = w;
-    w += 3 * LN;
-    u64* U = w;
-    w += (rc.L + 2) * LN;
-    u64* mask = w;
+    char* w = (char*)work;
+    u64* rot_work = (u64*)(w + Lo.rot);
+    u64 *tmp = (u64*)(w + Lo.tmp), *ra = (u64*)(w + Lo.ra), *rb = (u64*)(w + Lo.rb), *prod = (u64*)(w + Lo.prod),
+        *rr = (u64*)(w + Lo.rr), *mask = (u64*)(w + Lo.mask);
+    u32 *ea = (u32*)(w + Lo.ea), *eb = (u32*)(w + Lo.eb);
+    int* d_idx = (int*)(w + Lo.idx);
     {
         std::vector<int64_t> v(rc.N, 0), poly(rc.N);
         v[0] = 1;
@@ -1520,40 +1576,124 @@ extern "C" sfhe_status sfhe_matmul_chunked(sfhe_ctx* c, const sfhe_rotkeys* rk, 
         if (st != SFHE_OK) return st;
     }
     if (nC > 0) CUDA_TRY(cudaMemsetAsync(C, 0, (size_t)nC * ctw * 8, s));
-    // a chunk turned left by `off` slots (right for right = true); a turn by
-    // 0 is no operation
-    auto turned = [&](const u64* src, int off, bool right, u64* dst) -> const u64* {
-        if (off == 0) return src;
-        if (launch_rotate(rc, src, sfhe_rotation_element(rc.N, right ? -off : off), rotkey(rk, right, off, 0),
-                          rotkey(rk, right, off, 1), dst, rot_work, s) != cudaSuccess)
-            return nullptr;
-        return dst;
+    // the terms in Alg. 1's order: entry (i, j), then k where neither
+    // element is zero
+    struct Term {
+        int64_t ea, eb, r;
     };
-    for (const Entry& en : W.entries) {
-        const int64_t r = (int64_t)en.row * Nc + en.col;
-        for (int p = 0; p < en.count; p++) {
-            const int2 it = W.rowlist[en.first + p];  // (element of A, k)
-            const int64_t ia = it.x, ib = (int64_t)it.y * Nc + en.col;
-            const u64* a = turned(A + (ia / ch) * ctw, (int)(ia % ch), false, ra);
-            const u64* b = turned(B + (ib / ch) * ctw, (int)(ib % ch), false, rb);
-            if (!a || !b) return fail(SFHE_ECUDA, "rotation: %s", cudaGetErrorString(cudaGetLastError()));
-            st = sfhe_lift(c, a, 1, ea, lift_ws, lift_bytes, stream);
-            if (st == SFHE_OK) st = sfhe_lift(c, b, 1, eb, lift_ws, lift_bytes, stream);
-            if (st != SFHE_OK) return st;
-            cudaError_t e = launch_tensor_intt(rc, ea, eb, T, s);
-            if (e == cudaSuccess) e = launch_scale_round(rc, T, D, s);
-            if (e == cudaSuccess) e = launch_relin_ntt(rc, D, U, s);
-            if (e == cudaSuccess) e = cudaMemsetAsync(prod, 0, ctw * 8, s);
-            if (e == cudaSuccess) e = launch_relin_accum(rc, U, c->d_rlk, c->d_rlk_sh, prod, s);
-            if (e == cudaSuccess) e = launch_mul_plain(rc, prod, 1, mask, s);
-            if (e != cudaSuccess) return fail(SFHE_ECUDA, "chunked product: %s", cudaGetErrorString(e));
-            const u64* placed = turned(prod, (int)(r % ch), true, rr);
-            if (!placed) return fail(SFHE_ECUDA, "rotation: %s", cudaGetErrorString(cudaGetLastError()));
-            e = launch_add_ct(rc, C + (r / ch) * ctw, placed, 1, s);
-            if (e != cudaSuccess) return fail(SFHE_ECUDA, "accumulate: %s", cudaGetErrorString(e));
+    std::vector<Term> terms;
+    for (int32_t i = 0; i < M; i++)
+        for (int32_t j = 0; j < Nc; j++)
+            for (int32_t k = 0; k < K; k++)
+                if (!(a_zero && a_zero[(int64_t)i * K + k]) && !(b_zero && b_zero[(int64_t)k * Nc + j]))
+                    terms.push_back({(int64_t)i * K + k, (int64_t)k * Nc + j, (int64_t)i * Nc + j});
+    // turn the gathered ciphertexts src[0 .. n) (slots sorted by offset)
+    // from `tmp` into out: a turn by 0 is a copy
+    auto turn = [&](const std::vector<int>& offs, bool right, u64* out) -> cudaError_t {
+        const int64_t n = (int64_t)offs.size();
+        for (int64_t q0 = 0; q0 < n;) {
+            int64_t q1 = q0;
+            while (q1 < n && offs[q1] == offs[q0]) q1++;
+            const int off = offs[q0];
+            cudaError_t e;
+            if (off == 0)
+                e = cudaMemcpyAsync(out + q0 * ctw, tmp + q0 * ctw, (size_t)(q1 - q0) * ctw * 8, cudaMemcpyDeviceToDevice,
+                                    s);
+            else
+                e = launch_rotate_batch(rc, tmp + q0 * ctw, ctw, q1 - q0, sfhe_rotation_element(rc.N, right ? -off : off),
+                                        rotkey(rk, right, off, 0), rotkey(rk, right, off, 1), out + q0 * ctw, ctw,
+                                        rot_work, kTermRotBatch, s);
+            if (e != cudaSuccess) return e;
+            q0 = q1;
         }
+        return cudaSuccess;
+    };
+    std::vector<int> host_idx;
+    for (size_t t0 = 0; t0 < terms.size(); t0 += (size_t)Lo.n) {
+        const int n = (int)std::min<size_t>((size_t)Lo.n, terms.size() - t0);
+        auto sorted_by = [&](auto off_of) {
+            std::vector<int> perm(n);
+            for (int p = 0; p < n; p++) perm[p] = p;
+            std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return off_of(x) < off_of(y); });
+            return perm;
+        };
+        const auto perm_a = sorted_by([&](int p) { return (int)(terms[t0 + p].ea % ch); });
+        const auto perm_b = sorted_by([&](int p) { return (int)(terms[t0 + p].eb % ch); });
+        const auto perm_c = sorted_by([&](int p) { return (int)(terms[t0 + p].r % ch); });
+        std::vector<int> oa(n), ob(n), oc(n), pos_a(n), pos_b(n), pos_c(n);
+        // index region: [0, n) A chunks, [n, 2n) B chunks, [2n, 3n) the
+        // placement's sources, [3n, 4n) chunks, [4n, 5n + 1) list offsets,
+        // [5n + 1, 6n + 1) the lists
+        host_idx.assign((size_t)(6 * n + 1), 0);
+        for (int q = 0; q < n; q++) {
+            const Term& ta = terms[t0 + perm_a[q]];
+            const Term& tb = terms[t0 + perm_b[q]];
+            host_idx[q] = (int)(ta.ea / ch), oa[q] = (int)(ta.ea % ch), pos_a[perm_a[q]] = q;
+            host_idx[n + q] = (int)(tb.eb / ch), ob[q] = (int)(tb.eb % ch), pos_b[perm_b[q]] = q;
+            host_idx[2 * n + q] = perm_c[q], oc[q] = (int)(terms[t0 + perm_c[q]].r % ch), pos_c[perm_c[q]] = q;
+        }
+        // the chunks the batch adds into, each with its terms in order
+        std::vector<int64_t> chunk_ids;
+        std::vector<std::vector<int>> by_chunk;
+        for (int p = 0; p < n; p++) {
+            const int64_t chk = terms[t0 + p].r / ch;
+            if (chunk_ids.empty() || chunk_ids.back() != chk) {
+                size_t m = 0;
+                while (m < chunk_ids.size() && chunk_ids[m] != chk) m++;
+                if (m == chunk_ids.size()) chunk_ids.push_back(chk), by_chunk.emplace_back();
+                by_chunk[m].push_back(pos_c[p]);
+            } else {
+                by_chunk.back().push_back(pos_c[p]);
+            }
+        }
+        const int64_t mch = (int64_t)chunk_ids.size();
+        int listed = 0;
+        for (int64_t m = 0; m < mch; m++) {
+            host_idx[3 * n + m] = (int)chunk_ids[m];
+            host_idx[4 * n + m] = listed;
+            for (int q : by_chunk[m]) host_idx[5 * n + 1 + listed++] = q;
+        }
+        host_idx[4 * n + mch] = listed;
+        CUDA_TRY(cudaMemcpyAsync(d_idx, host_idx.data(), host_idx.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+        // both operands to slot 0 and lifted
+        cudaError_t e = launch_gather_ct(rc, A, d_idx, n, tmp, s);
+        if (e == cudaSuccess) e = turn(oa, false, ra);
+        if (e == cudaSuccess) e = launch_gather_ct(rc, B, d_idx + n, n, tmp, s);
+        if (e == cudaSuccess) e = turn(ob, false, rb);
+        if (e != cudaSuccess) return fail(SFHE_ECUDA, "operand turns: %s", cudaGetErrorString(e));
+        st = sfhe_lift(c, ra, n, ea, w + Lo.lift, Lo.lift_bytes, stream);
+        if (st == SFHE_OK) st = sfhe_lift(c, rb, n, eb, w + Lo.lift, Lo.lift_bytes, stream);
+        if (st != SFHE_OK) return st;
+        // every product into its own ciphertext: a work list of one-product
+        // entries over a matmul whose B "row" is the term (Nc = 1)
+        sfhe_plan* P = new_plan(c, SFHE_EXEC_PERSISTENT);
+        MmDesc mm;
+        memset(&mm, 0, sizeof(mm));
+        mm.A_ext = ea, mm.B_ext = eb, mm.C = prod, mm.Nc = 1, mm.group = 1;
+        P->mms.push_back(mm);
+        P->c_words.push_back((size_t)n * ctw);
+        P->products = n;
+        for (int p = 0; p < n; p++) {
+            Entry en;
+            memset(&en, 0, sizeof(en));
+            en.mm = 0, en.row = p, en.col = 0, en.count = 1, en.first = p;
+            P->entries.push_back(en);
+            P->rowlist.push_back(make_int2(pos_a[p], pos_b[p]));
+        }
+        sfhe_plan* Pf = nullptr;
+        st = plan_finish(c, P, SFHE_EXEC_PERSISTENT, w + Lo.plan, Lo.plan_bytes, stream, &Pf);
+        if (st != SFHE_OK) return st;
+        st = launch_plan(Pf, s);
+        sfhe_plan_destroy(Pf);
+        if (st != SFHE_OK) return st;
+        // mask, turn right to the entries' offsets, add into the chunks
+        e = launch_mul_plain(rc, prod, n, mask, s);
+        if (e == cudaSuccess) e = launch_gather_ct(rc, prod, d_idx + 2 * n, n, tmp, s);
+        if (e == cudaSuccess) e = turn(oc, true, rr);
+        if (e == cudaSuccess) e = launch_add_lists(rc, C, rr, d_idx + 3 * n, d_idx + 4 * n, d_idx + 5 * n + 1, mch, s);
+        if (e != cudaSuccess) return fail(SFHE_ECUDA, "chunked terms: %s", cudaGetErrorString(e));
     }
-    if (products) *products = W.products;
+    if (products) *products = (int64_t)terms.size();
     return SFHE_OK;
 }
 

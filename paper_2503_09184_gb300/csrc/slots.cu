@@ -196,6 +196,33 @@ __global__ void __launch_bounds__(256) k_add_ct(const __grid_constant__ RnsConst
     acc[o] = add_mod(csub(acc[o], q), csub(x[o], q), q);
 }
 
+// out[q] = in[src[q]] over whole ciphertexts of `words` uint64 each; grid
+// (ceil(words / 256), n)
+__global__ void __launch_bounds__(256) k_gather_ct(const u64* in, const int* src, size_t words, u64* out)
+{
+    const size_t w = (size_t)blockIdx.x * 256 + threadIdx.x;
+    if (w >= words) return;
+    const size_t q = blockIdx.y;
+    out[q * words + w] = in[(size_t)src[q] * words + w];
+}
+
+// C[chunk[j]] += x[list[t]] for t in ptr[j] .. ptr[j+1], one after another in
+// list order (the additions of k_add_ct); grid (N / 256, L, 2 m)
+__global__ void __launch_bounds__(256) k_add_lists(const __grid_constant__ RnsConsts c, u64* C, const u64* x,
+                                                   const int* chunk, const int* ptr, const int* list)
+{
+    const int N = c.N, L = c.L;
+    const int k = blockIdx.x * 256 + threadIdx.x, l = blockIdx.y;
+    if (k >= N) return;
+    const int j = blockIdx.z >> 1, p = blockIdx.z & 1;
+    const u64 q = c.m[l].q;
+    const size_t ctw = (size_t)2 * L * N, o = ((size_t)p * L + l) * N + k;
+    u64* a = C + (size_t)chunk[j] * ctw + o;
+    u64 acc = *a;
+    for (int t = ptr[j]; t < ptr[j + 1]; t++) acc = add_mod(csub(acc, q), csub(x[(size_t)list[t] * ctw + o], q), q);
+    *a = acc;
+}
+
 // batched key switching: ciphertext z of a batch at its own stride
 template <int LOGN>
 __global__ void __launch_bounds__(256) k_galois_apply_b(const __grid_constant__ RnsConsts c, const u64* in,
@@ -376,6 +403,32 @@ cudaError_t launch_add_ct(const RnsConsts& rc, u64* acc, const u64* x, long long
 }
 
 size_t rotate_batch_words(const RnsConsts& rc, long long n) { return (size_t)n * rotate_work_words(rc); }
+
+cudaError_t launch_gather_ct(const RnsConsts& rc, const u64* in, const int* src, long long n, u64* out, cudaStream_t s)
+{
+    const size_t words = (size_t)2 * rc.L * rc.N;
+    for (long long z0 = 0; z0 < n; z0 += 65535) {
+        const long long cnt = n - z0 < 65535 ? n - z0 : 65535;
+        k_gather_ct<<<dim3((unsigned)((words + 255) / 256), (unsigned)cnt), 256, 0, s>>>(in, src + z0, words,
+                                                                                          out + (size_t)z0 * words);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_add_lists(const RnsConsts& rc, u64* C, const u64* x, const int* chunk, const int* ptr,
+                             const int* list, long long m, cudaStream_t s)
+{
+    const unsigned bx = (unsigned)((rc.N + 255) / 256);
+    for (long long z0 = 0; z0 < m; z0 += 32767) {
+        const long long cnt = m - z0 < 32767 ? m - z0 : 32767;
+        k_add_lists<<<dim3(bx, rc.L, (unsigned)(2 * cnt)), 256, 0, s>>>(rc, C, x, chunk + z0, ptr + z0, list);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
 
 // n ciphertexts at in + z in_stride -> out + z out_stride (words), in
 // batches of at most `batch` (the workspace holds rotate_batch_words(batch))

@@ -112,6 +112,74 @@ def test_chunked_matmul_matches_oracle(chunk):
     rk.close()
 
 
+def test_chunked_matmul_batches_equal_the_terms_one_by_one():
+    """the term-by-term product runs its terms in batches; over several
+    batches (chunks receiving terms from two of them, every turn offset)
+    each chunk is, limb for limb, what the terms give one after another
+    through the single-ciphertext calls (turn, lift, multiply + relinearise,
+    mask, turn back, add: each checked against the oracle above)"""
+    import torch
+    api, S = gpu_modules()
+    Lc, ch = 3, 4
+    ctx = gpu_ctx(N, Lc, SEED)
+    rng = np.random.default_rng(9)
+    A = rng.integers(-16, 17, size=(12, 20)) * (rng.random((12, 20)) < 0.5)
+    B = rng.integers(-16, 17, size=(20, 10))
+    Ae = api.encrypt_chunked(ctx, A, ch, 1)
+    Be = api.encrypt_chunked(ctx, B, ch, 2)
+    rk = api.RotationKeys(ctx, ch)
+    C, n = api.matmul_chunked(ctx, Ae, Be, rk, skip_zeros=True)
+    terms = [(i * 20 + k, k * 10 + j, i * 10 + j) for i in range(12) for j in range(10) for k in range(20)
+             if A[i, k] != 0 and B[k, j] != 0]
+    assert n == len(terms) > 2 * 456
+    # the same terms one by one
+    shape = (1, 2, Lc, N)
+    keys = {}
+
+    def turn(ct, k):
+        if k == 0:
+            return ct
+        g = S.sfhe_rotation_element(N, k)
+        if g not in keys:
+            key = torch.empty((Lc, 2, Lc, N), dtype=torch.int64, device="cuda")
+            key_sh = torch.empty_like(key)
+            S.sfhe_galois_keygen(ctx.h, g, key, key_sh)
+            keys[g] = (key, key_sh)
+        out = torch.empty(shape, dtype=torch.int64, device="cuda")
+        S.sfhe_rotate(ctx.h, ct, 1, g, *keys[g], out, rot_work)
+        return out
+
+    rot_work = torch.empty(S.sfhe_rotate_workspace_size(ctx.h), dtype=torch.uint8, device="cuda")
+    lift_work = torch.empty(S.sfhe_lift_workspace_size(ctx.h, 1), dtype=torch.uint8, device="cuda")
+    K_ = ctx.K
+    mul_work = torch.empty(((3 * K_ * N * 4 + 255) // 256) * 256 + (3 * Lc + (Lc + 2) * Lc) * N * 8,
+                           dtype=torch.uint8, device="cuda")
+
+    def lifted(M, e):
+        ct = turn(M.ct[e // ch:e // ch + 1].contiguous(), e % ch)
+        ext = torch.empty((1, 2, K_, N), dtype=torch.int32, device="cuda")
+        S.sfhe_lift(ctx.h, ct, 1, ext, lift_work)
+        return ext
+
+    ea = {e: lifted(Ae, e) for e in {t[0] for t in terms}}
+    eb = {e: lifted(Be, e) for e in {t[1] for t in terms}}
+    v = np.zeros(N, dtype=np.int64)
+    v[0] = 1
+    mask = torch.empty((Lc, N), dtype=torch.int64, device="cuda")
+    S.sfhe_plain_ntt(ctx.h, S.sfhe_slots_encode(N, T, v), mask)
+    ref = torch.zeros_like(C.ct)
+    for a, b, r in terms:
+        prod = torch.empty(shape, dtype=torch.int64, device="cuda")
+        S.sfhe_ct_mul_relin(ctx.h, ea[a], eb[b], prod, mul_work)
+        S.sfhe_mul_plain(ctx.h, prod, 1, mask)
+        placed = turn(prod, -(r % ch))
+        S.sfhe_add(ctx.h, ref[r // ch:r // ch + 1], placed.contiguous(), 1)
+    assert torch.equal(C.ct, ref)
+    want = ((A @ B + T // 2) % T) - T // 2
+    assert (api.decrypt_chunked(ctx, C) == want).all()
+    rk.close()
+
+
 def test_chunked_matmul_8192_decrypts():
     api, S = gpu_modules()
     ctx = gpu_ctx(8192, 4, 0)
