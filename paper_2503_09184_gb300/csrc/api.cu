@@ -15,6 +15,7 @@
 #include "api_internal.h"
 #include "host_math.h"
 #include "launch.h"
+#include "chunk_launch.h"
 
 using namespace sfhe;
 

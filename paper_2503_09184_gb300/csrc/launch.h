@@ -86,11 +86,6 @@ cudaError_t launch_decrypt_poly(const RnsConsts& rc, const u64* s_ntt, const u64
 cudaError_t launch_galois_apply(const RnsConsts& rc, const u64* in, long long n, u32 g, u64* out, cudaStream_t s);
 cudaError_t launch_mul_plain(const RnsConsts& rc, u64* ct, long long n, const u64* pt, cudaStream_t s);
 cudaError_t launch_add_ct(const RnsConsts& rc, u64* acc, const u64* x, long long n, cudaStream_t s);
-// out[q] = in[src[q]] (whole ciphertexts); C[chunk[j]] += x[list[t]],
-// t in ptr[j] .. ptr[j+1], in list order (slots.cu)
-cudaError_t launch_gather_ct(const RnsConsts& rc, const u64* in, const int* src, long long n, u64* out, cudaStream_t s);
-cudaError_t launch_add_lists(const RnsConsts& rc, u64* C, const u64* x, const int* chunk, const int* ptr,
-                             const int* list, long long m, cudaStream_t s);
 size_t rotate_work_words(const RnsConsts& rc);
 size_t rotate_batch_words(const RnsConsts& rc, long long n);
 cudaError_t launch_rotate_batch(const RnsConsts& rc, const u64* in, size_t in_stride, long long n, u32 g,

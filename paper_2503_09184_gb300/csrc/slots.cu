@@ -7,6 +7,7 @@
 // evaluation at psi^e_i, e_i = 2 bitrev(i) + 1, and X -> X^g evaluates the
 // input at psi^(g e_i), which is the input's slot with e = g e_i mod 2N.
 #include "launch.h"
+#include "chunk_launch.h"
 #include "launch_util.cuh"
 
 namespace sfhe {
