@@ -268,8 +268,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": workload, "N": ring.N, "L": ring.L, "t": W.T_PLAIN,
-                       "sparsity": sparsity, "encoding": ENCODING},
+            "config": job_config(args, vals, ring, workload, sparsity, max(1, args.gpus),
+                                 "mask" if args.b_sparse else "dense"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle",
                              "sample": f"per step {len(entries)} entries C[1][j] of the product over the first "
                                        f"nonzero of A's row 1 ({per_step} products), one entry per thread "
@@ -293,6 +293,35 @@ def aggregate_over_ranks(ms: float, products: int, world: int, device) -> tuple[
 
 
 # ---------------------------------------------------------------- workloads ---
+L2_BYTES = 126 * 1024 * 1024  # GB300 L2
+
+
+def tensor_base_primes(logN: int, L: int) -> int:
+    """primes of the 30-bit tensor base the library sizes for a ring (its
+    host-side formula: enough 30-bit primes for B > 2 N Q^2)"""
+    return (10 * (logN + 108 * L + 1) + 298) // 299
+
+
+def job_config(args, vals, ring, workload: str, sparsity, world: int, b_encoding: str) -> dict:
+    """The workload's config block, from the operands alone (the reference
+    arm prints the same one)."""
+    K = tensor_base_primes(int(math.log2(ring.N)), ring.L)
+    ext_bytes = 2 * K * ring.N * 4
+    if b_encoding == "mask":
+        products = sum(int(((a != 0).astype(np.int64) @ (b != 0).astype(np.int64)).sum()) for a, b in vals)
+    else:
+        products = sum(int((a != 0).sum()) * b.shape[1] for a, b in vals)
+    lifted = sum((int((a != 0).sum()) + b.size) * ext_bytes for a, b in vals)
+    return {"workload": workload, "matmuls": len(vals),
+            "shapes": [f"{a.shape[0]}x{a.shape[1]}x{b.shape[1]}" for a, b in vals][:8],
+            "sparsity": sparsity, "encoding": ENCODING, "b_encoding": b_encoding, "N": ring.N,
+            "L": ring.L, "t": W.T_PLAIN, "products_per_step": products,
+            "dense_products": sum(a.shape[0] * a.shape[1] * b.shape[1] for a, b in vals),
+            "l2": (f"inputs larger than L2 (lifted operands: {lifted / 1e9:.1f} GB)" if lifted > L2_BYTES else
+                   f"inputs smaller than L2 (lifted operands: {lifted / 1e6:.1f} MB), steps not flushed"),
+            "step": "lift A and B + work list + persistent matmul", "parallelism": f"replicas x{world}"}
+
+
 def job_of(args):
     """(ring, [(A values, B values)], workload name, sparsity) of the selected workload."""
     wl = args.workload
@@ -516,17 +545,16 @@ def main():
     sm_clock = clk.get("sm_mhz") or SM_MAX_MHZ
     kname = f"k_matmul_persistent<{int(math.log2(ring.N))},{ring.L}>"
     traffic = measured_traffic(workload)
+    config = job_config(args, vals, ring, workload, sparsity, world, slot.b_encoding)
     lifted = sum((M.ext.numel()) * M.ext.element_size() for M in slot.As + slot.Bs)
+    if config["products_per_step"] != products or (f"{lifted / 1e9:.1f} GB" not in config["l2"]
+                                                   and f"{lifted / 1e6:.1f} MB" not in config["l2"]):
+        raise SystemExit(f"config block disagrees with the plan: {config} vs {products} products, {lifted} B")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": workload, "matmuls": len(vals),
-                   "shapes": [f"{a.shape[0]}x{a.shape[1]}x{b.shape[1]}" for a, b in vals][:8],
-                   "sparsity": sparsity, "encoding": ENCODING, "b_encoding": slot.b_encoding, "N": ring.N,
-                   "L": ring.L, "t": W.T_PLAIN, "products_per_step": products, "dense_products": dense_products,
-                   "l2": f"inputs larger than L2 (lifted operands: {lifted / 1e9:.1f} GB)",
-                   "step": "lift A and B + work list + persistent matmul", "parallelism": f"replicas x{world}"},
+        "config": config,
         "matmul_ms": ms,
         "kernel_ms": kms,
         "correct": correct,
