@@ -56,6 +56,15 @@ def test_primes_match_oracle(S, N, L):
     assert B > 2 * N * Q * Q                # |tensor| < N Q^2 / 2: |x| / B < 1/4
 
 
+@pytest.mark.parametrize("N,L", [(4096, 2), (8192, 4), (16384, 8), (4096, 3), (16384, 4)])
+def test_bench_sizes_the_tensor_base_like_the_library(S, N, L):
+    """bench.py's config block (the same for the GPU and the reference arm)
+    sizes lifted operands with the library's tensor-base formula"""
+    import math
+    import bench
+    assert bench.tensor_base_primes(int(math.log2(N)), L) == len(S.sfhe_select_primes(N, L)[1])
+
+
 def test_cdt_matches_oracle_and_golden(S):
     from oracle import oracle as O
     path = os.path.join(ROOT, "tests", "golden", "cdt_sigma3.2.txt")
