@@ -180,6 +180,24 @@ def test_chunked_matmul_batches_equal_the_terms_one_by_one():
     rk.close()
 
 
+def test_chunked_matmul_without_terms():
+    """every product skipped (A all zero under the mask): no terms, C zero in
+    both placements"""
+    api, S = gpu_modules()
+    ctx = gpu_ctx(N, 3, SEED)
+    A = np.zeros((3, 5), dtype=np.int64)
+    B = np.arange(10, dtype=np.int64).reshape(5, 2)
+    Ae = api.encrypt_chunked(ctx, A, 4, 1)
+    Be = api.encrypt_chunked(ctx, B, 4, 2)
+    rk = api.RotationKeys(ctx, 4)
+    for fused in (False, True):
+        C, n = api.matmul_chunked(ctx, Ae, Be, rk, skip_zeros=True, fused=fused)
+        assert n == 0
+        assert not C.ct.any()
+        assert (api.decrypt_chunked(ctx, C) == 0).all()
+    rk.close()
+
+
 def test_chunked_matmul_8192_decrypts():
     api, S = gpu_modules()
     ctx = gpu_ctx(8192, 4, 0)

@@ -187,6 +187,26 @@ def test_chunked_product_many_batches_limb_for_limb(small, chunk, skip, shape):
     assert np.max(np.abs(vals - A @ B)) < 1e-2
 
 
+def test_chunked_product_without_terms(small):
+    """every product skipped: no terms, every chunk of C zero"""
+    g, ck = small
+    S = g.S
+    A = np.zeros((2, 3), dtype=np.int64)
+    B = np.ones((3, 2), dtype=np.int64)
+    Ag = _encrypt(g, [CK.encode(64, [0.0] * 4, ck.scale)] * 2, 1, [[0, 0], [1, 0]])
+    Bg = _encrypt(g, [CK.encode(64, [1.0] * 4, ck.scale)] * 2, 2, [[0, 0], [1, 0]])
+    C = g.ct(1)
+    C.fill_(5)
+    rk = S.sfhe_ckks_rotkeys_create(g.h, 4)
+    try:
+        n, _ = S.sfhe_ckks_matmul_chunked(g.h, rk, 2, 3, 2, Ag, Bg, C, (A == 0).astype(np.uint8).reshape(-1),
+                                          None, g.work)
+    finally:
+        S.sfhe_ckks_rotkeys_destroy(rk)
+    assert n == 0
+    assert not C.any()
+
+
 def test_paper_ring_8192():
     """The paper's ring: encryption, the product with relinearisation and a
     rescale limb for limb against the oracle; the chunked product of a
