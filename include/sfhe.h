@@ -591,16 +591,18 @@ sfhe_status sfhe_plan_resume(sfhe_plan* plan, void* stream);
  * attempts.  Errors: EINVAL (null, bounds out of range), ECUDA. */
 sfhe_status sfhe_selftest_wait_bound(void* work, uint32_t tries, uint32_t limit_us, void* stream);
 /* Tile tuning of the per-product persistent kernel.  Where a ring has
- * several stage-S tiles (the tiles of the exact scale-and-round: how many
+ * several tiles (stage-S tiles of the exact scale-and-round: how many
  * coefficients a thread rounds at a time and how many output primes it
- * reconstructs per pass; N = 4096 with L = 2, N = 8192 with L = 4 and
- * N = 16384 with L = 8 have three each), the first per-product persistent
- * plan of a context times every tile on the plan's first entries (one per
+ * reconstructs per pass; and code forms of the tensor's inverse NTT: lean
+ * exchange addresses and reductions, a warp-shuffle stage; N = 4096 with
+ * L = 2 and N = 16384 with L = 8 have three tiles, N = 8192 with L = 4
+ * five), the first per-product persistent plan of a context times every
+ * tile on the plan's first entries (one per
  * CTA, at most four products each; this writes their C, which every
  * execution writes again, and synchronises the stream) and the context
  * keeps the fastest for all its later plans.  sfhe_ctx_tuning: the tile in
  * use (-1 before the first plan), how many there are, and the calibration
- * time of each (ms[n_variants], may be NULL; zeros while untuned).
+ * time of each (ms[n_variants], at most 8, may be NULL; zeros while untuned).
  * sfhe_ctx_set_variant: use tile `variant` from now on (-1: tune as above).
  * sfhe_ctx_variant_name: a description of a tile ("" if out of range). */
 sfhe_status sfhe_ctx_tuning(const sfhe_ctx* ctx, int32_t* variant, int32_t* n_variants, float* ms);

@@ -96,7 +96,7 @@ struct sfhe_ctx {
     int n_variants;
     int forced_variant;  // -1: tuned on the first persistent plan
     int tuned_variant;   // -1 until tuned
-    float variant_ms[4];
+    float variant_ms[8];
 };
 
 struct sfhe_plan {
@@ -784,7 +784,7 @@ sfhe_status tune_variants(sfhe_plan* P, cudaStream_t s)
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
             if (rep == 1 || (rep == 2 && ms < t)) t = ms;
         }
-        if (v < 4) c->variant_ms[v] = t;
+        if (v < 8) c->variant_ms[v] = t;
         if (v == 0 || t < best) best = t, best_v = v;
     }
     if (e == cudaSuccess)
@@ -1059,7 +1059,7 @@ extern "C" sfhe_status sfhe_ctx_tuning(const sfhe_ctx* c, int32_t* variant, int3
     if (variant) *variant = c->forced_variant >= 0 ? c->forced_variant : c->tuned_variant;
     if (n_variants) *n_variants = c->n_variants;
     if (ms)
-        for (int v = 0; v < c->n_variants && v < 4; v++) ms[v] = c->tuned_variant >= 0 ? c->variant_ms[v] : 0.f;
+        for (int v = 0; v < c->n_variants && v < 8; v++) ms[v] = c->tuned_variant >= 0 ? c->variant_ms[v] : 0.f;
     return SFHE_OK;
 }
 

@@ -262,7 +262,8 @@ cudaError_t launch_persistent(const RnsConsts& rc, const PersistentArgs& a, cuda
 
 int persistent_variants(const RnsConsts& rc)
 {
-    const bool v = (rc.logN == 12 && rc.L == 2) || (rc.logN == 13 && rc.L == 4) || (rc.logN == 14 && rc.L == 8);
+    if (rc.logN == 13 && rc.L == 4) return 5;  // three stage-S tiles, two NTT forms
+    const bool v = (rc.logN == 12 && rc.L == 2) || (rc.logN == 14 && rc.L == 8);
     return v ? 3 : 1;
 }
 
@@ -270,6 +271,11 @@ int persistent_variants(const RnsConsts& rc)
 static_assert(PersistentTile<13, 4, 0>::SM == 2 && PersistentTile<13, 4, 0>::LS == 4, "tile table");
 static_assert(PersistentTile<13, 4, 1>::SM == 2 && PersistentTile<13, 4, 1>::LS == 2, "tile table");
 static_assert(PersistentTile<13, 4, 2>::SM == 1 && PersistentTile<13, 4, 2>::LS == 4, "tile table");
+static_assert(PersistentTile<13, 4, 3>::SM == 2 && PersistentTile<13, 4, 3>::LS == 2 &&
+                  PersistentTile<13, 4, 3>::NB::LEAN, "tile table");
+static_assert(PersistentTile<13, 4, 4>::SM == 2 && PersistentTile<13, 4, 4>::LS == 2 &&
+                  PersistentTile<13, 4, 4>::NB::SHUF, "tile table");
+static_assert(!PersistentTile<13, 4, 1>::NB::LEAN && !PersistentTile<13, 4, 1>::NB::SHUF, "tile table");
 static_assert(PersistentTile<14, 8, 0>::SM == 1 && PersistentTile<14, 8, 0>::LS == 8, "tile table");
 static_assert(PersistentTile<14, 8, 1>::SM == 1 && PersistentTile<14, 8, 1>::LS == 4, "tile table");
 static_assert(PersistentTile<14, 8, 2>::SM == 1 && PersistentTile<14, 8, 2>::LS == 2, "tile table");
@@ -279,13 +285,15 @@ static_assert(PersistentTile<12, 2, 2>::SM == 1 && PersistentTile<12, 2, 2>::LS 
 
 const char* persistent_variant_name(const RnsConsts& rc, int v)
 {
-    static const char* names[][3] = {
+    static const char* names[][5] = {
         {"2 coefficients per thread, 4 primes per pass", "2 coefficients per thread, 2 primes per pass",
-         "1 coefficient per thread, 4 primes per pass"},
+         "1 coefficient per thread, 4 primes per pass",
+         "2 coefficients per thread, 2 primes per pass; lean NTT exchange addresses and reductions",
+         "2 coefficients per thread, 2 primes per pass; inverse NTT with a warp-shuffle stage"},
         {"1 coefficient per thread, 8 primes per pass", "1 coefficient per thread, 4 primes per pass",
-         "1 coefficient per thread, 2 primes per pass"},
+         "1 coefficient per thread, 2 primes per pass", "", ""},
         {"2 coefficients per thread, 2 primes per pass", "2 coefficients per thread, 1 prime per pass",
-         "1 coefficient per thread, 2 primes per pass"},
+         "1 coefficient per thread, 2 primes per pass", "", ""},
     };
     if (v < 0 || v >= persistent_variants(rc)) return "";
     if (persistent_variants(rc) == 1) return "default stage-S tile";

@@ -639,20 +639,25 @@ struct PersistentPlan {
     static_assert(SMEM <= 227 * 1024 - 256, "shared-memory plan too large");
 };
 
-// Tile of stage S (the exact scale-and-round inside the persistent kernel),
-// one per variant V that the run-time tuner can pick: SM coefficients per
-// thread at a time (interleaved for instruction-level parallelism) and the
-// output primes in chunks of LS (fewer live registers per chunk).  V = 0 is
-// the default; variants 1 and 2 exist for the rings persistent_variants()
-// lists.
+// Tile of the persistent kernel, one per variant V that the run-time tuner
+// can pick.  Stage S (the exact scale-and-round): SM coefficients per thread
+// at a time (interleaved for instruction-level parallelism) and the output
+// primes in chunks of LS (fewer live registers per chunk).  Stage T: the
+// code form of the inverse NTT (NttT's FORM).  V = 0 is the default;
+// variants 1 and 2 (stage-S tiles) exist for the rings
+// persistent_variants() lists, variants 3 and 4 (tile 1 with the lean and
+// with the shuffle-stage inverse NTT) at N = 8192, L = 4.
 template <int LOGN, int L, int V>
 struct PersistentTile {
     static constexpr int K = tensor_base_size(LOGN, L);
     static constexpr int R = NttGeom<LOGN>::T32::R;
+    static constexpr int VS = V >= 3 ? 1 : V;  // the stage-S tile
+    static constexpr int NTT_FORM = V == 3 ? 1 : (V == 4 ? 2 : 0);
     static constexpr int SMD = (K <= 16 && R <= 16) ? 2 : 1;
-    static constexpr int SM = (V == 2 && SMD == 2) ? 1 : SMD;
-    static constexpr int LS = V == 1 ? (L >= 2 ? L / 2 : L) : ((V == 2 && SMD == 1) ? (L >= 4 ? L / 4 : L) : L);
+    static constexpr int SM = (VS == 2 && SMD == 2) ? 1 : SMD;
+    static constexpr int LS = VS == 1 ? (L >= 2 ? L / 2 : L) : ((VS == 2 && SMD == 1) ? (L >= 4 ? L / 4 : L) : L);
     static_assert(L % LS == 0, "output primes in whole chunks");
+    using NB = NttT<LOGN, NttGeom<LOGN>::T32::LOGR, Arith32, NTT_FORM>;  // stage T's transforms
 };
 
 // bounds of every mbarrier wait: one second of real time (a 64 KB bulk copy
@@ -684,7 +689,7 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
 {
     using CF = Cfg<LOGN, L>;
     using NQ = typename CF::NQ;
-    using NB = typename CF::NB;
+    using NB = typename PersistentTile<LOGN, L, V>::NB;
     using PP = PersistentPlan<LOGN, L>;
     static_assert(NQ::NT == NB::NT, "both transforms use the same CTA");
     constexpr int N = NQ::N, NTH = NQ::NT, K = CF::K, R = NB::R;

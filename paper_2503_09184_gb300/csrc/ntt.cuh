@@ -85,7 +85,10 @@ struct Arith32 {
     }
 };
 
-template <int LOGN_, int LOGR_, typename A>
+// FORM_ picks code forms of the same transform (the run-time tuner's NTT
+// candidates; every form computes the same values): 0 the default, 1 the
+// lean forms at every size, 2 the inverse's shuffle stage where it applies.
+template <int LOGN_, int LOGR_, typename A, int FORM_ = 0>
 struct NttT {
     using W = typename A::W;
     static constexpr int LOGN = LOGN_;
@@ -99,8 +102,15 @@ struct NttT {
     // Lean forms (exchange addresses as a base and per-slot constants, the
     // 32-bit reductions by an unsigned minimum): measured faster inside the
     // persistent kernel at N = 16384 and slower at N = 8192, where the
-    // kernel sits at the register limit; so they are taken from N = 16384.
-    static constexpr bool LEAN = LOGN >= 14;
+    // kernel sits at the register limit; so by default they are taken from
+    // N = 16384 (form 1 takes them everywhere).
+    static constexpr int FORM = FORM_;
+    static constexpr bool LEAN = LOGN >= 14 || FORM == 1;
+    // Inverse with one stage more than whole passes (32-bit words, form 2):
+    // the stage after the first pass pairs each thread with its neighbour
+    // (tid ^ 1) and runs on warp shuffles, so the passes are LOGR + 1, LOGR,
+    // ... stages with one shared-memory exchange fewer.
+    static constexpr bool SHUF = FORM == 2 && SWIZZLE && REM == 1;
     static constexpr int SMEM_WORDS = SWIZZLE ? N : N + (N >> LOGR);
     static_assert(!SWIZZLE || LOGR == 4 || LOGR == 5, "swizzle defined for R = 16 and 32");
 
@@ -136,7 +146,8 @@ struct NttT {
     }
     SFHE_DEV static int inv_out_idx(int v, int tid)
     {
-        if constexpr (REM > 0) return idx<NFULL * LOGR, REM>(v, tid);
+        if constexpr (SHUF) return idx<LOGN - LOGR, LOGR>(v, tid);
+        else if constexpr (REM > 0) return idx<NFULL * LOGR, REM>(v, tid);
         else return idx<(NFULL - 1) * LOGR, LOGR>(v, tid);
     }
 
@@ -394,6 +405,63 @@ struct NttT {
         }
     }
 
+    // The shuffle stage (distance R, the stage after the first pass): element
+    // tid R + v pairs with (tid + 1) R + v for even tid; the even thread
+    // takes slots v < R/2, the odd one the others, each receiving the half it
+    // lacks from its neighbour.  Afterwards slot v of thread t holds element
+    // 2R (t >> 1) + (R/2) (t & 1) + (v mod R/2) + R (v div R/2).
+    SFHE_DEV static int shuf_elem(int v, int tid)
+    {
+        return 2 * R * (tid >> 1) + (R / 2) * (tid & 1) + (v & (R / 2 - 1)) + R * (v >> (LOGR - 1));
+    }
+    template <int NP>
+    SFHE_DEV static void shuffle_stage(W (&x)[NP][R], int tid, const W* __restrict__ w, const W* __restrict__ ws, W q)
+    {
+        // twiddle of the pair: N / 2^(LOGR+1) + (e >> (LOGR+1)) = ... + (tid >> 1)
+        const int ti = (N >> (LOGR + 1)) + (tid >> 1);
+        const W tw = __ldg(w + ti), tws = __ldg(ws + ti);
+        const bool odd = tid & 1;
+#pragma unroll
+        for (int j = 0; j < NP; j++) {
+#pragma unroll
+            for (int k = 0; k < R / 2; k++) {
+                const W send = odd ? x[j][k] : x[j][R / 2 + k];
+                const W recv = __shfl_xor_sync(0xffffffffu, send, 1);
+                W X = odd ? recv : x[j][k];
+                W Y = odd ? x[j][R / 2 + k] : recv;
+                A::template inv<LEAN>(X, Y, tw, tws, q);
+                x[j][k] = X;
+                x[j][R / 2 + k] = Y;
+            }
+        }
+    }
+    // the passes after the shuffle stage: pass PS starts at S = LOGR + 1 +
+    // (PS - 1) LOGR
+    template <int NP, int PS>
+    SFHE_DEV static void inv_rest_shuf(W (&x)[NP][R], W* sm, int tid, const W* w, const W* ws, W q, W ni, W nis,
+                                       W wl, W wls)
+    {
+        if constexpr (PS < NFULL) {
+            constexpr int S = LOGR + 1 + (PS - 1) * LOGR;
+            if constexpr (PS == 1) {
+                __syncthreads();
+#pragma unroll
+                for (int j = 0; j < NP; j++) {
+                    W* smj = sm + (size_t)j * SMEM_WORDS;
+#pragma unroll
+                    for (int v = 0; v < R; v++) smj[pad(shuf_elem(v, tid))] = x[j][v];
+                }
+                __syncthreads();
+#pragma unroll
+                for (int j = 0; j < NP; j++) load<S, LOGR>(x[j], sm + (size_t)j * SMEM_WORDS, tid);
+            } else {
+                exchange<NP, S - LOGR, LOGR, S, LOGR>(x, sm, tid);
+            }
+            inv_stages<NP, S, LOGR, PS == NFULL - 1, 0>(x, tid, w, ws, q, ni, nis, wl, wls);
+            inv_rest_shuf<NP, PS + 1>(x, sm, tid, w, ws, q, ni, nis, wl, wls);
+        }
+    }
+
     // x: run_idx layout in ([0, 2q)), inv_out_idx layout out ([0, 2q)).
     // (ni, nis) = N^-1 and its Shoup companion; (wl, wls) = ipsi_rev[1] N^-1.
     // sm holds NP * SMEM_WORDS words.
@@ -402,8 +470,15 @@ struct NttT {
     {
         const W* w = tw + 2 * N;
         const W* ws = tw + 3 * N;
-        inv_stages<NP, 0, LOGR, (NFULL == 1 && REM == 0), 0>(x, tid, w, ws, q, ni, nis, wl, wls);
-        inv_rest<NP, 1>(x, sm, tid, w, ws, q, ni, nis, wl, wls);
+        if constexpr (SHUF) {
+            static_assert(NFULL >= 2, "the shuffle form needs two whole passes");
+            inv_stages<NP, 0, LOGR, false, 0>(x, tid, w, ws, q, ni, nis, wl, wls);
+            shuffle_stage<NP>(x, tid, w, ws, q);
+            inv_rest_shuf<NP, 1>(x, sm, tid, w, ws, q, ni, nis, wl, wls);
+        } else {
+            inv_stages<NP, 0, LOGR, (NFULL == 1 && REM == 0), 0>(x, tid, w, ws, q, ni, nis, wl, wls);
+            inv_rest<NP, 1>(x, sm, tid, w, ws, q, ni, nis, wl, wls);
+        }
     }
     SFHE_DEV static void inverse(W (&x)[R], W* sm, int tid, const W* tw, W q, W ni, W nis, W wl, W wls)
     {

@@ -14,6 +14,9 @@ constexpr bool has_variants(int logN, int L)
     return (logN == 12 && L == 2) || (logN == 13 && L == 4) || (logN == 14 && L == 8);
 }
 
+// rings with the NTT-form variants 3 and 4 (persistent_tuned_13b.cu)
+constexpr bool has_ntt_variants(int logN, int L) { return logN == 13 && L == 4; }
+
 template <int LOGN, int L>
 static int occupancy_of()
 {
@@ -74,6 +77,10 @@ static cudaError_t launch_one(const RnsConsts& rc, const PersistentArgs& a, cuda
     if constexpr (has_variants(LOGN, L)) {
         if (a.variant == 1) return persistent_launch_variant<LOGN, L, 1>(rc, a, s);
         if (a.variant == 2) return persistent_launch_variant<LOGN, L, 2>(rc, a, s);
+    }
+    if constexpr (has_ntt_variants(LOGN, L)) {
+        if (a.variant == 3) return persistent_launch_variant<LOGN, L, 3>(rc, a, s);
+        if (a.variant == 4) return persistent_launch_variant<LOGN, L, 4>(rc, a, s);
     }
     if (a.variant != 0) return cudaErrorInvalidValue;
     return launch_instance<LOGN, L, false, 0>(rc, a, s);

@@ -495,11 +495,11 @@ def sfhe_plan_stats(plan: int) -> dict:
 
 
 def sfhe_ctx_tuning(ctx: int) -> dict:
-    """{"variant", "variants", "ms", "names"}: the stage-S tile in use (-1
-    before the first persistent plan), how many exist, their calibration
-    times and descriptions."""
+    """{"variant", "variants", "ms", "names"}: the tile in use (-1 before the
+    first persistent plan), how many exist, their calibration times and
+    descriptions."""
     v, n = ctypes.c_int32(), ctypes.c_int32()
-    ms = np.zeros(4, dtype=np.float32)
+    ms = np.zeros(8, dtype=np.float32)
     _check(lib().sfhe_ctx_tuning(ctx, ctypes.byref(v), ctypes.byref(n), _ptr(ms)))
     names = [lib().sfhe_ctx_variant_name(ctx, i).decode() for i in range(n.value)]
     return {"variant": v.value, "variants": n.value, "ms": [float(x) for x in ms[:n.value]], "names": names}
