@@ -87,11 +87,15 @@ class Scheduler:
     """Admission by budget (FIFO, no overtaking) and row blocks per wave:
     order "rr" gives every running request an equal share of a wave in turn;
     "srpt" fills a wave shortest remaining work first (every running request
-    still gets a row)."""
+    still gets a row); "auto" takes srpt while the running requests' remaining
+    work is at most backlog_waves waves and rr beyond (the median of
+    shortest-first below overload, the tail of round-robin under it)."""
 
-    def __init__(self, budget_bytes: int, wave_products: int, ct_bytes: int, ext_bytes: int, order: str = "rr"):
-        if order not in ("rr", "srpt"):
+    def __init__(self, budget_bytes: int, wave_products: int, ct_bytes: int, ext_bytes: int, order: str = "rr",
+                 backlog_waves: float = 4.0):
+        if order not in ("rr", "srpt", "auto"):
             raise ValueError(f"unknown wave order {order!r}")
+        self.backlog_waves = backlog_waves
         self.order = order
         self.budget = budget_bytes
         self.wave_products = max(1, wave_products)
@@ -157,7 +161,11 @@ class Scheduler:
         live = [r for r in self.running if r.next_row < r.rows and (keep is None or id(r) in keep)]
         if not live:
             return []
-        if self.order == "srpt":
+        srpt = self.order == "srpt"
+        if self.order == "auto":
+            backlog = sum(int(r.row_products()[r.next_row:].sum()) for r in live)
+            srpt = backlog <= self.backlog_waves * self.wave_products
+        if srpt:
             # shortest remaining work first, each taking what the wave has
             # left after one row for every request behind it
             live.sort(key=lambda r: (int(r.row_products()[r.next_row:].sum()), r.arrival, r.rid))

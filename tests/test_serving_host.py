@@ -98,6 +98,23 @@ def test_srpt_order_fills_waves_shortest_remaining_first():
         pass
 
 
+def test_auto_order_is_srpt_below_the_backlog_and_round_robin_above():
+    def dense(rid, M, K, Nc):
+        return Request(rid, np.ones((M, K), dtype=np.int64), np.ones((K, Nc), dtype=np.int64))
+
+    def first_wave(backlog_waves):
+        big, small = dense(0, 8, 2, 4), dense(1, 2, 2, 4)  # 64 and 16 products left
+        s = Scheduler(10**9, 40, CT, EXT, order="auto", backlog_waves=backlog_waves)
+        for r in (big, small):
+            s.arrive(r)
+        s.admit(0.0)
+        return {req.rid: (r0, r1) for req, r0, r1 in s.next_wave()}
+
+    # 80 products left: srpt when 2 waves of 40 may be queued, rr when one
+    assert first_wave(2.0) == {1: (0, 2), 0: (0, 3)}
+    assert first_wave(1.0) == {0: (0, 2), 1: (0, 2)}
+
+
 def test_fifo_plain_model_closed_form():
     reqs = [_req(i, 3, 4, 2, arrival=a) for i, a in enumerate([0.0, 0.5, 10.0])]
     m = fifo_plain_model(reqs, lambda r: 1.0)
