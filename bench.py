@@ -869,7 +869,9 @@ KERNEL_SOURCES = ("kernels.cuh", "ntt.cuh", "device_math.cuh", "rns.h", "launch.
                   "persistent_12.cu", "persistent_13.cu", "persistent_14.cu", "persistent_tuned_12.cu",
                   "persistent_tuned_13.cu", "persistent_tuned_13b.cu", "persistent_tuned_14.cu")
 TRAFFIC = {  # (source hash, workload) -> (bytes per launch, profile summary)
-    ("f4793e021a144d30", "sweep-64x64x64-s0.5"): (709.54e9, "profiles/matmul_persistent_sweep64x64x64_s0.5_dram.md"),
+    ("a6654f27039fa051", "sweep-64x64x64-s0.5"): (715.07e9, "profiles/matmul_persistent_sweep64x64x64_s0.5_dram.md"),
+    ("a6654f27039fa051", "sweep-64x64x64-s0.5-lazy"): (170.46e9,
+                                                       "profiles/matmul_persistent_grouped_sweep64x64x64_s0.5_dram.md"),
 }
 
 

@@ -727,6 +727,16 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
         }
         return !__syncthreads_or(!ok);
     };
+    // the same wait without the block-wide vote: the caller votes on the
+    // result at its next barrier
+    auto wait_own = [&](int bi) -> bool {
+        const bool ok = mbar_wait(&mbar[bi], (phbits >> bi) & 1u, SFHE_WAIT_TRIES, SFHE_WAIT_NS);
+        if (ok) {
+            phbits ^= 1u << bi;
+            pend &= ~(1u << bi);
+        }
+        return ok;
+    };
     // error exit: flag it, let the copies still in flight land, leave
     auto abort_cta = [&]() {
         if (tid == 0) {
@@ -883,19 +893,35 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                     }
                 }
             } else {
-            // position of the next bulk copy: group, prime, product in group
+            // The operand limbs stream in parts: part h of a step is the
+            // lane-interleaved words [h N/NP, (h+1) N/NP) of its four limbs
+            // (every thread's register slots h R/NP .. (h+1) R/NP - 1), copied
+            // into buffer h (four limb parts) and tracked by mbarrier h; a
+            // buffer is refilled with the next step's part as soon as it has
+            // been summed, so NP - 1 parts' copies are in flight meanwhile.
+            constexpr int NP = 2;  // one mbarrier per part
+            constexpr int RH = R / NP;
+            constexpr int HW = N / NP;  // words of a limb part
+            static_assert(RH * NB::NT == HW && RH * NP == R, "a part is a contiguous slice of each limb");
+            constexpr size_t PB = PP::SLOT / NP;  // bytes of a limb part
+            auto hslot = [&](int h, int limb) {  // limbs 0 a0, 1 a1, 2 b0, 3 b1
+                return reinterpret_cast<u32*>(smb + PP::EXB + (size_t)(h * 4 + limb) * PB);
+            };
+            // position of the next copy: group, prime, product in group
             int ig = 0, ik = 0, ip = 0, iGg = min(G, en.count);
-            auto issue = [&](int pair) {
+            auto issue_part = [&](int h) {
                 if (tid == 0) {
                     const u32 *a, *b;
                     operands(ig * G + ip, a, b);
-                    const size_t off = (size_t)pair * K * N + (size_t)ik * N;
+                    const size_t o0 = (size_t)ik * N + (size_t)h * HW, o1 = (size_t)K * N + o0;
                     fence_proxy_async();
-                    mbar_arrive_expect_tx(&mbar[pair], (u32)(2 * PP::SLOT));
-                    tma_load_1d(slot(pair), a + off, (u32)PP::SLOT, &mbar[pair]);
-                    tma_load_1d(slot(2 + pair), b + off, (u32)PP::SLOT, &mbar[pair]);
+                    mbar_arrive_expect_tx(&mbar[h], (u32)(4 * PB));
+                    tma_load_1d(hslot(h, 0), a + o0, (u32)PB, &mbar[h]);
+                    tma_load_1d(hslot(h, 1), a + o1, (u32)PB, &mbar[h]);
+                    tma_load_1d(hslot(h, 2), b + o0, (u32)PB, &mbar[h]);
+                    tma_load_1d(hslot(h, 3), b + o1, (u32)PB, &mbar[h]);
                 }
-                pend |= 1u << pair;
+                pend |= 1u << h;
             };
             auto advance = [&]() {  // false once every step has been issued
                 if (++ip < iGg) return true;
@@ -906,8 +932,8 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                 iGg = min(G, en.count - ig * G);
                 return iGg > 0;
             };
-            issue(0);
-            issue(1);
+#pragma unroll
+            for (int h = 0; h < NP; h++) issue_part(h);
             bool more = advance();
             for (int g = 0; g * G < en.count; g++) {
                 const int Gg = min(G, en.count - g * G);
@@ -919,32 +945,40 @@ __global__ void __launch_bounds__(NttGeom<LOGN>::T::NT) k_matmul_persistent(
                     u32* acc3 = sm32;
                     __syncthreads();  // every thread is past the last transform's exchanges
                     for (int p = 0; p < Gg; p++) {
-                        if (!wait_bar(0) || !wait_bar(1)) {
-                            abort_cta();
-                            return;
-                        }
-                        const u32* s0 = slot(0);
-                        const u32* s1 = slot(1);
-                        const u32* s2 = slot(2);
-                        const u32* s3 = slot(3);
 #pragma unroll
-                        for (int v = 0; v < R; v++) {
-                            const int i = NB::lane_idx(v, tid);
-                            const u64 a0 = s0[i], a1 = s1[i], b0 = s2[i], b1 = s3[i];
-                            const u32 t0 = redc32(a0 * b0, m), t1 = redc32(a0 * b1 + a1 * b0, m),
-                                      t2 = redc32(a1 * b1, m);
-                            u32* q0 = acc3 + i;
-                            u32* q1 = acc3 + NB::SMEM_WORDS + i;
-                            u32* q2 = acc3 + 2 * NB::SMEM_WORDS + i;
-                            *q0 = p == 0 ? t0 : csub32(*q0 + t0, 2 * m.b);
-                            *q1 = p == 0 ? t1 : csub32(*q1 + t1, 2 * m.b);
-                            *q2 = p == 0 ? t2 : csub32(*q2 + t2, 2 * m.b);
-                        }
-                        __syncthreads();  // every thread has read the slots
-                        if (more) {
-                            issue(0);
-                            issue(1);
-                            more = advance();
+                        for (int h = 0; h < NP; h++) {
+                            // each thread waits for buffer h by itself; whether
+                            // any wait ran out is voted at the barrier that
+                            // also releases the buffer for its next copy
+                            const bool ok = wait_own(h);
+                            if (ok) {
+                                const u32* s0 = hslot(h, 0);
+                                const u32* s1 = hslot(h, 1);
+                                const u32* s2 = hslot(h, 2);
+                                const u32* s3 = hslot(h, 3);
+#pragma unroll
+                                for (int vv = 0; vv < RH; vv++) {
+                                    const int i = NB::lane_idx(h * RH + vv, tid);
+                                    const int li = i - h * HW;
+                                    const u64 a0 = s0[li], a1 = s1[li], b0 = s2[li], b1 = s3[li];
+                                    const u32 t0 = redc32(a0 * b0, m), t1 = redc32(a0 * b1 + a1 * b0, m),
+                                              t2 = redc32(a1 * b1, m);
+                                    u32* q0 = acc3 + i;
+                                    u32* q1 = acc3 + NB::SMEM_WORDS + i;
+                                    u32* q2 = acc3 + 2 * NB::SMEM_WORDS + i;
+                                    *q0 = p == 0 ? t0 : csub32(*q0 + t0, 2 * m.b);
+                                    *q1 = p == 0 ? t1 : csub32(*q1 + t1, 2 * m.b);
+                                    *q2 = p == 0 ? t2 : csub32(*q2 + t2, 2 * m.b);
+                                }
+                            }
+                            if (__syncthreads_or(!ok)) {  // every thread has read buffer h
+                                abort_cta();
+                                return;
+                            }
+                            if (more) {
+                                issue_part(h);
+                                if (h == NP - 1) more = advance();
+                            }
                         }
                     }
                     u32 x[3][R];
