@@ -81,8 +81,9 @@ def parse():
     ap.add_argument("--serve-dims", default="16,32,64", help="serve: M, K, Nc drawn from these")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: HBM ciphertext budget")
     ap.add_argument("--wave-products", type=int, default=40000, help="serve: products per wave")
-    ap.add_argument("--order", default="rr", choices=["rr", "srpt", "auto"],
-                    help="serve: wave shares round-robin, shortest remaining work first, or srpt below a backlog")
+    ap.add_argument("--order", default="hrrn", choices=["rr", "srpt", "auto", "hrrn"],
+                    help="serve: wave shares round-robin, shortest remaining work first, srpt below a backlog, or "
+                         "highest response ratio first (default)")
     ap.add_argument("--preempt", action="store_true",
                     help="serve: a new arrival stops the running wave, whose rows resume after the newcomer's")
     ap.add_argument("--serve-set", default="poisson", choices=["poisson", "mixed64"],

@@ -9,8 +9,10 @@ request larger than the whole budget runs as column tiles (B and C split
 by columns) that each fit beside its A, which is encrypted once and stays
 resident until the last tile completes; one whose A alone does not fit is
 rejected.  Work runs in waves: a
-wave is one persistent launch (a batch plan) over row blocks taken in turn
-from every admitted request, up to a product budget, so requests that
+wave is one persistent launch (a batch plan) over row blocks of every
+admitted request, up to a product budget, filled by a priority order
+(highest response ratio first by default; shortest remaining work first and
+round-robin shares are the alternatives), so requests that
 arrive while others are on the GPU join the next wave and their products
 overlap with those already running.  With preemption (GpuExecutor's
 preempt) a request that arrives while a wave runs stops that wave at its
@@ -89,11 +91,16 @@ class Scheduler:
     "srpt" fills a wave shortest remaining work first (every running request
     still gets a row); "auto" takes srpt while the running requests' remaining
     work is at most backlog_waves waves and rr beyond (the median of
-    shortest-first below overload, the tail of round-robin under it)."""
+    shortest-first below overload, the tail of round-robin under it);
+    "hrrn" (the default) fills a wave highest response ratio first (Brinch
+    Hansen's highest-response-ratio-next): a request's ratio is 1 + its time since
+    arrival over its remaining service time (remaining products at the
+    loop's observed product rate), so with no waiting it is srpt, and a long
+    request gains on newer short ones the longer it waits."""
 
-    def __init__(self, budget_bytes: int, wave_products: int, ct_bytes: int, ext_bytes: int, order: str = "rr",
+    def __init__(self, budget_bytes: int, wave_products: int, ct_bytes: int, ext_bytes: int, order: str = "hrrn",
                  backlog_waves: float = 4.0):
-        if order not in ("rr", "srpt", "auto"):
+        if order not in ("rr", "srpt", "auto", "hrrn"):
             raise ValueError(f"unknown wave order {order!r}")
         self.backlog_waves = backlog_waves
         self.order = order
@@ -152,23 +159,36 @@ class Scheduler:
             out.append(req)
         return out
 
-    def next_wave(self, only=None) -> list[tuple[Request, int, int]]:
+    def next_wave(self, only=None, now: float | None = None,
+                  rate: float | None = None) -> list[tuple[Request, int, int]]:
         """row blocks (request, r0, r1) of the next wave: whole rows, taken in
         turn from every running request (starting one further each wave) until
         the wave's product budget is reached; every request with rows left
-        gets at least one row.  only: take rows of these requests alone."""
+        gets at least one row.  only: take rows of these requests alone.
+        now (seconds since the start) and rate (products per second of wave
+        time so far) feed the response ratios of order "hrrn"; without them
+        every ratio is 1 and the order is srpt's."""
         keep = None if only is None else {id(r) for r in only}
         live = [r for r in self.running if r.next_row < r.rows and (keep is None or id(r) in keep)]
         if not live:
             return []
-        srpt = self.order == "srpt"
+        srpt = self.order in ("srpt", "hrrn")
         if self.order == "auto":
             backlog = sum(int(r.row_products()[r.next_row:].sum()) for r in live)
             srpt = backlog <= self.backlog_waves * self.wave_products
         if srpt:
-            # shortest remaining work first, each taking what the wave has
+            # a priority order (shortest remaining work first, or highest
+            # response ratio first), each request taking what the wave has
             # left after one row for every request behind it
-            live.sort(key=lambda r: (int(r.row_products()[r.next_row:].sum()), r.arrival, r.rid))
+            def remaining(r):
+                return int(r.row_products()[r.next_row:].sum())
+
+            def ratio(r):
+                if self.order != "hrrn" or now is None or not rate:
+                    return 1.0
+                return 1.0 + max(0.0, now - r.arrival) * rate / max(1, remaining(r))
+
+            live.sort(key=lambda r: (-ratio(r), remaining(r), r.arrival, r.rid))
             left = self.wave_products
             blocks = []
             for n, req in enumerate(live):
@@ -389,12 +409,12 @@ class GpuExecutor:
 
 
 def serve(requests: list[Request], executor, budget_bytes: int, wave_products: int, ct_bytes: int,
-          ext_bytes: int, keep_results: bool = False, clock=time.perf_counter, order: str = "rr") -> dict:
+          ext_bytes: int, keep_results: bool = False, clock=time.perf_counter, order: str = "hrrn") -> dict:
     """Run the requests (arrival times in seconds from now) through the
     continuous-batching loop on the wall clock.  Returns per-request
     latencies and totals; with keep_results the executor keeps every C.
     order: how waves share their products among running requests
-    (Scheduler).
+    (Scheduler; highest response ratio first by default).
 
     An executor with start_wave / finish_wave / resume_wave (and preempt
     set) has a running wave stopped when the next request arrives: the
@@ -427,8 +447,9 @@ def serve(requests: list[Request], executor, budget_bytes: int, wave_products: i
             executor.admit(req)
             if suspended is not None:
                 newcomers.append(req)
+        rate = products / busy if busy > 0 else None
         if not can_stop:
-            blocks = sched.next_wave()
+            blocks = sched.next_wave(now=clock() - t0, rate=rate)
             if not blocks:
                 if pending:   # nothing to run: wait for the next arrival
                     time.sleep(max(0.0, pending[0].arrival - (clock() - t0)))
@@ -445,7 +466,8 @@ def serve(requests: list[Request], executor, budget_bytes: int, wave_products: i
             wave, suspended, resume_next, stoppable = suspended, None, False, True
             executor.resume_wave(wave)
         else:
-            blocks = sched.next_wave(only=newcomers if suspended is not None else None)
+            blocks = sched.next_wave(only=newcomers if suspended is not None else None, now=clock() - t0,
+                                     rate=rate)
             newcomers = []
             if blocks:
                 wave = executor.start_wave(blocks)

@@ -48,16 +48,17 @@ def test_admission_fifo_by_budget_and_rejection():
     assert [r.rid for r in s.admit(2.0)] == [2]
 
 
-def test_waves_cover_rows_once_and_round_robin():
+@pytest.mark.parametrize("order", ["rr", "srpt", "auto", "hrrn"])
+def test_waves_cover_rows_once_and_every_running_request_progresses(order):
     reqs = [_req(i, 5 + i, 6, 4, arrival=0.0) for i in range(3)]
-    s = Scheduler(budget_bytes=10**9, wave_products=20, ct_bytes=CT, ext_bytes=EXT)
+    s = Scheduler(budget_bytes=10**9, wave_products=20, ct_bytes=CT, ext_bytes=EXT, order=order)
     for r in reqs:
         s.arrive(r)
     s.admit(0.0)
     seen = {r.rid: [] for r in reqs}
     waves = 0
     while not s.idle():
-        blocks = s.next_wave()
+        blocks = s.next_wave(now=float(waves), rate=10.0)
         live = {r.rid for r in s.running if r.next_row < r.rows or any(b[0] is r for b in blocks)}
         assert {b[0].rid for b in blocks} == live          # every running request progresses
         for req, r0, r1 in blocks:
@@ -92,7 +93,7 @@ def test_srpt_order_fills_waves_shortest_remaining_first():
     s2.admit(0.0)
     assert sorted((req.rid, r1 - r0) for req, r0, r1 in s2.next_wave()) == [(3, 1), (4, 1)]
     try:
-        Scheduler(1, 1, 1, 1, order="fifo")
+        Scheduler(1, 1, 1, 1, order="fifo")  # not a wave order
         raise AssertionError("unknown order accepted")
     except ValueError:
         pass
@@ -113,6 +114,32 @@ def test_auto_order_is_srpt_below_the_backlog_and_round_robin_above():
     # 80 products left: srpt when 2 waves of 40 may be queued, rr when one
     assert first_wave(2.0) == {1: (0, 2), 0: (0, 3)}
     assert first_wave(1.0) == {0: (0, 2), 1: (0, 2)}
+
+
+def test_hrrn_order_is_srpt_without_waiting_and_ages_long_requests():
+    def dense(rid, M, arrival):
+        return Request(rid, np.ones((M, 2), dtype=np.int64), np.ones((2, 4), dtype=np.int64), arrival)
+
+    def first_wave(order, now=None, rate=None, small_arrival=0.5):
+        big, small = dense(0, 8, 0.0), dense(1, 2, small_arrival)  # 8 products a row: 64 and 16 left
+        s = Scheduler(10**9, 40, CT, EXT, order=order)
+        for r in (big, small):
+            s.arrive(r)
+        s.admit(0.0)
+        return {req.rid: (r0, r1) for req, r0, r1 in s.next_wave(now=now, rate=rate)}
+
+    # no clock or no rate yet: every ratio is 1, the order is srpt's
+    assert first_wave("hrrn") == first_wave("srpt") == {1: (0, 2), 0: (0, 3)}
+    assert first_wave("hrrn", now=5.0, rate=None) == first_wave("srpt")
+    # soon after the arrivals the short request's ratio is higher:
+    # big 1 + 1/64, small 1 + 0.5/16 (rate 1 product/s)
+    assert first_wave("hrrn", now=1.0, rate=1.0) == {1: (0, 2), 0: (0, 3)}
+    # the long request has waited 10 s, the short one 1 s:
+    # big 1 + 10/64 = 1.16 > small 1 + 1/16 = 1.06, so big fills the wave
+    # first and leaves the short request one row
+    assert first_wave("hrrn", now=10.0, rate=1.0, small_arrival=9.0) == {0: (0, 4), 1: (0, 1)}
+    # srpt ignores waiting
+    assert first_wave("srpt", now=10.0, rate=1.0, small_arrival=9.0) == {1: (0, 2), 0: (0, 3)}
 
 
 def test_fifo_plain_model_closed_form():
@@ -145,7 +172,7 @@ class FakeExecutor:
         pass
 
 
-@pytest.mark.parametrize("order", ["rr", "srpt"])
+@pytest.mark.parametrize("order", ["rr", "srpt", "auto", "hrrn"])
 def test_serve_loop_with_fake_executor(order):
     reqs = [_req(i, 6, 8, 3, arrival=0.002 * i) for i in range(5)]
     one = max(request_bytes(r, CT, EXT) for r in reqs)
@@ -195,11 +222,12 @@ class FakeStoppableExecutor(FakeExecutor):
         self.log.append(("resume", w.tag))
 
 
-def test_serve_loop_stops_a_wave_for_an_arrival_and_resumes_it():
+@pytest.mark.parametrize("order", ["rr", "hrrn"])
+def test_serve_loop_stops_a_wave_for_an_arrival_and_resumes_it(order):
     reqs = [_req(i, 6, 8, 3, arrival=0.05 * i) for i in range(4)]
     one = max(request_bytes(r, CT, EXT) for r in reqs)
     ex = FakeStoppableExecutor(stops=2)
-    out = serve(reqs, ex, budget_bytes=4 * one, wave_products=8, ct_bytes=CT, ext_bytes=EXT)
+    out = serve(reqs, ex, budget_bytes=4 * one, wave_products=8, ct_bytes=CT, ext_bytes=EXT, order=order)
     assert out["done"] == 4 and out["products"] == sum(r.products for r in reqs)
     # every row of every request ran exactly once (a stopped wave's rows
     # complete after those of the wave that stopped it)
