@@ -4,7 +4,6 @@ CSR / ELLPACK arrays, bad Galois elements, aliasing, rotation keys of
 another context and chunk sizes out of range each return their status."""
 from __future__ import annotations
 
-import ctypes
 
 import numpy as np
 import pytest

@@ -7,7 +7,6 @@ from __future__ import annotations
 
 import time
 
-import numpy as np
 import pytest
 
 import workloads as W

@@ -11,7 +11,6 @@ import pytest
 
 from gpu_common import coeff_of, gpu_ctx, gpu_modules, oracle_ctx
 from oracle import oracle as O
-import workloads as W
 
 pytestmark = pytest.mark.gpu
 T = 65537

@@ -3,7 +3,6 @@ waves, budget-limited admission) give, limb for limb, the ciphertexts each
 request gives alone, and decrypt to A B mod t."""
 from __future__ import annotations
 
-import numpy as np
 import pytest
 
 import workloads as W
